@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the
+oracle.
+
+This module only describes runs and draws their initial particles; it holds
+none of the method's arithmetic (no interpolation, push, deposition or field
+update).  A run is a plain dict:
+
+    n, d          cells and cell sizes per axis (x, y)
+    dt            time step
+    patch         patch size in cells (px, py)
+    field_bc      per axis: "periodic" | "sm" (Silver-Mueller, open)
+    part_bc       per axis (lo, hi): "periodic" | "reflect" | "remove"
+    q, m          charge and mass of the mobile species (electrons: -1, 1)
+    laser         None or {a0, waist, tau, t_peak, y_center}
+    moving_window None or {t0}
+    injection     None or {n0, x0, ramp, ppc: (ppcx, ppcy)} (plasma entering
+                  with the moving window)
+
+Particles are dicts of float64 arrays x, y (global positions in c/w),
+ux, uy, uz (u = p / mc) and w (weight = local density / particles per cell).
+"""
+import math
+
+import numpy as np
+
+
+def cfl_dt(d, frac=0.95):
+    """frac x the 2D Yee stability limit 1 / sqrt(sum 1/d^2) (c = 1)."""
+    return frac / math.sqrt(sum(1.0 / x ** 2 for x in d))
+
+
+def periodic_run(n, d, patch, dt=None):
+    return {
+        "n": tuple(int(v) for v in n), "d": tuple(float(v) for v in d),
+        "dt": cfl_dt(d) if dt is None else float(dt), "patch": tuple(patch),
+        "field_bc": ("periodic", "periodic"),
+        "part_bc": (("periodic", "periodic"), ("periodic", "periodic")),
+        "q": -1.0, "m": 1.0, "laser": None, "moving_window": None, "injection": None,
+    }
+
+
+def thermal_particles(run, ppc=4, uth=0.05, n0=1.0, seed=1):
+    """Uniform thermal plasma: ppc particles per cell at uniform random
+    positions inside each cell, Maxwellian momenta N(0, uth^2) per component,
+    weight n0 / ppc."""
+    rng = np.random.default_rng(seed)
+    nx, ny = run["n"]
+    dx, dy = run["d"]
+    cx, cy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    cx = np.repeat(cx.ravel(), ppc)
+    cy = np.repeat(cy.ravel(), ppc)
+    n = cx.size
+    x = (cx + rng.random(n)) * dx
+    y = (cy + rng.random(n)) * dy
+    # keep positions strictly inside the box after rounding
+    x = np.minimum(x, np.nextafter(nx * dx, 0.0))
+    y = np.minimum(y, np.nextafter(ny * dy, 0.0))
+    u = rng.normal(0.0, uth, size=(3, n))
+    w = np.full(n, n0 / ppc)
+    return {"x": x, "y": y, "ux": u[0], "uy": u[1], "uz": u[2], "w": w}
+
+
+def thermal_2d(n=(128, 128), d=(0.1, 0.1), patch=(16, 16), ppc=4, uth=0.05, seed=1):
+    """Uniform thermal plasma, periodic fields and particles, electrons on a
+    uniform neutralising background (the 128x128, 4 ppc, u_th = 0.05 case)."""
+    run = periodic_run(n, d, patch)
+    return run, thermal_particles(run, ppc=ppc, uth=uth, seed=seed)
+
+
+def density_profile(x, n0, x0, ramp):
+    """Plasma density at x: linear up-ramp of length `ramp` from x0, then n0."""
+    x = np.asarray(x, dtype=np.float64)
+    if ramp <= 0.0:
+        return np.where(x >= x0, n0, 0.0)
+    return n0 * np.clip((x - x0) / ramp, 0.0, 1.0)
+
+
+def regular_particles(nx, ny, dx, dy, ppc, profile, x_offset=0.0, cells_x=None):
+    """Particles placed regularly (ppcx x ppcy per cell) at rest; weight is
+    the profile at the particle's x divided by the particles per cell."""
+    ppcx, ppcy = ppc
+    i0, i1 = (0, nx) if cells_x is None else cells_x
+    ii = np.arange(i0, i1)
+    jj = np.arange(ny)
+    a = (np.arange(ppcx) + 0.5) / ppcx
+    b = (np.arange(ppcy) + 0.5) / ppcy
+    # order: cell row j, cell i, sub-row b, sub-column a
+    J, I, B, A = np.meshgrid(jj, ii, b, a, indexing="ij")
+    x = ((I + A) * dx).ravel()
+    y = ((J + B) * dy).ravel()
+    w = profile(x + x_offset) / (ppcx * ppcy)
+    z = np.zeros_like(x)
+    return {"x": x, "y": y, "ux": z.copy(), "uy": z.copy(), "uz": z.copy(), "w": w}
+
+
+def lwfa_2d(n=(2048, 512), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2), n0=0.01,
+            ramp=200.0, a0=2.0, waist=20.0, tau=30.0, t_mw=None, frac=0.95):
+    """2D3V LWFA-shaped run: Gaussian y-polarised laser entering at x_min,
+    cold electrons on immobile ions with a linear density ramp, moving
+    window at c, Silver-Mueller fields on every face, particles removed
+    through the x faces and reflected at the y faces."""
+    nx, ny = n
+    dx, dy = d
+    Lx, Ly = nx * dx, ny * dy
+    run = {
+        "n": (nx, ny), "d": (dx, dy), "dt": cfl_dt(d, frac), "patch": tuple(patch),
+        "field_bc": ("sm", "sm"),
+        "part_bc": (("remove", "remove"), ("reflect", "reflect")),
+        "q": -1.0, "m": 1.0,
+        "laser": {"a0": a0, "waist": waist, "tau": tau, "t_peak": 2.0 * tau,
+                  "y_center": Ly / 2.0},
+        "moving_window": {"t0": Lx / 2.0 if t_mw is None else t_mw},
+        "injection": {"n0": n0, "x0": 0.0, "ramp": ramp, "ppc": tuple(ppc)},
+    }
+    parts = regular_particles(nx, ny, dx, dy, ppc,
+                              lambda x: density_profile(x, n0, 0.0, ramp))
+    return run, parts
+
+
+def random_fields(shape, seed, amp=0.05, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz",
+                                                  "Bmx", "Bmy", "Bmz")):
+    """Smooth-ish random fields for identical-state single-step tests."""
+    rng = np.random.default_rng(seed)
+    return {k: amp * rng.standard_normal(shape) for k in names}
+
+
+def small_random_particles(run, n, seed, uth=0.3):
+    """n particles uniformly over the box, momenta N(0, uth^2) (test cases)."""
+    rng = np.random.default_rng(seed)
+    nx, ny = run["n"]
+    dx, dy = run["d"]
+    x = np.minimum(rng.random(n) * nx * dx, np.nextafter(nx * dx, 0))
+    y = np.minimum(rng.random(n) * ny * dy, np.nextafter(ny * dy, 0))
+    u = rng.normal(0.0, uth, size=(3, n))
+    w = 0.5 + rng.random(n)
+    return {"x": x, "y": y, "ux": u[0], "uy": u[1], "uz": u[2], "w": w}
+
+
+def field_shape(run):
+    """Shape (ny_e, nx_e) of the field arrays exchanged with either side:
+    per axis n (periodic, indices [0, n)) or n + 2 (open, indices [-1, n])."""
+    nx, ny = run["n"]
+    fx, fy = run["field_bc"]
+    return (ny if fy == "periodic" else ny + 2, nx if fx == "periodic" else nx + 2)
