@@ -1,0 +1,195 @@
+/*
+ * libpic: GB300-native (sm_103a) patch-decomposed particle-in-cell step.
+ *
+ * The method is Single Domain Multiple Decompositions (SDMD, Section 2.2 of
+ * "Single Domain Multiple Decompositions for Particle-in-Cell simulations"):
+ * macro-particles live in small patches, fields live in one large region.
+ * Here a patch is one thread block whose field tile and current tile sit in
+ * shared memory, and the region is the whole single domain in HBM.  One step
+ * is: region -> patch field staging (SDMD step (ii)), interpolation, Boris
+ * push, Esirkepov deposition into the patch current tile, patch -> region
+ * current reduction (SDMD step (i)), re-binning of particles that left their
+ * patch, Yee FDTD update of the region with open (Silver-Mueller) or periodic
+ * boundaries, and the moving-window shift when due (Section 3.2 / 3.3).
+ *
+ * Conventions (every entry point):
+ *  - returns a pic_status; never aborts, exits or prints;
+ *  - keeps no caller pointer after it returns; inputs are copied;
+ *  - pointers tagged PIC_HOST are host memory, PIC_DEVICE are device memory
+ *    of the context's device;
+ *  - device-side faults (capacity overflow, non-finite particle, move of more
+ *    than one cell, a wait that ran out) are sticky: they are reported by the
+ *    next synchronising call (pic_step, pic_sync, pic_get_*, pic_diag) as
+ *    PIC_EOVERFLOW / PIC_ENONFINITE / PIC_ETIMEOUT, and every later call then
+ *    returns PIC_ESTATE until pic_restore succeeds;
+ *  - pic_last_error(ctx) gives a human-readable reason for the last failure.
+ *
+ * Units are normalised: lengths c/w, time 1/w, momentum u = p / (m c),
+ * fields m c w / e, densities n_c; dE/dt = curl B - J, dB/dt = -curl E.
+ *
+ * Field arrays exchanged with the library (pic_set_field / pic_get_field)
+ * are float64, row-major (ny_e, nx_e), y slowest.  Per axis, a periodic axis
+ * gives n_e = n entries for grid indices [0, n); an open axis gives
+ * n_e = n + 2 entries for grid indices [-1, n] (ghost, interior, boundary).
+ * A component staggered (dual) along an axis has grid index i at (i + 1/2) d,
+ * otherwise at i d (Yee lattice: Ex (1/2,0), Ey (0,1/2), Ez (0,0),
+ * Bx (0,1/2), By (1/2,0), Bz (1/2,1/2); J like E; rho at nodes).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = 1,     /* bad argument or configuration */
+  PIC_ENOMEM = 2,     /* device or host allocation failed */
+  PIC_ECUDA = 3,      /* a CUDA runtime call failed */
+  PIC_EOVERFLOW = 4,  /* a patch or re-binning buffer ran out of capacity */
+  PIC_ETIMEOUT = 5,   /* a bounded device wait ran out */
+  PIC_ENONFINITE = 6, /* a particle became non-finite or moved > 1 cell */
+  PIC_ESTATE = 7      /* context unusable after an earlier device fault */
+} pic_status;
+
+typedef enum { PIC_FP64 = 0, PIC_FP32 = 1 } pic_precision;
+/* Field boundary per axis. */
+enum { PIC_BC_PERIODIC = 0, PIC_BC_SILVER_MULLER = 1 };
+/* Particle boundary per face. */
+enum { PIC_PBC_PERIODIC = 0, PIC_PBC_REFLECT = 1, PIC_PBC_REMOVE = 2 };
+/* Where a caller buffer lives. */
+enum { PIC_HOST = 0, PIC_DEVICE = 1 };
+/* Field identifiers for pic_set_field / pic_get_field. */
+enum {
+  PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_BMX, PIC_BMY,
+  PIC_BMZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO, PIC_RHO_BG, PIC_NFIELDS
+};
+/* Background charge modes for pic_set_background. */
+enum { PIC_BG_NONE = 0, PIC_BG_UNIFORM = 1, PIC_BG_NEUTRALISING = 2 };
+
+typedef struct pic_config {
+  int dims;              /* 2 (2D3V) */
+  int n[3];              /* cells per axis; n[i] % patch[i] == 0 */
+  double d[3];           /* cell size per axis */
+  double dt;             /* time step; must satisfy dt < min(d) (CFL) */
+  int patch[3];          /* patch size in cells, multiple of 4, 4..64 */
+  int prec;              /* pic_precision */
+  int bc_field[3];       /* PIC_BC_* per axis */
+  int bc_part[3][2];     /* PIC_PBC_* per face (lo, hi); periodic must pair
+                            with a periodic field axis */
+  double q, m;           /* charge and mass of the mobile species */
+  /* Laser entering through x_min (requires an open x axis): Ey_inc(y, t) =
+   * a0 exp(-((y-yc)/waist)^2) exp(-2 ln2 (tr/tau)^2) sin(tr),
+   * tr = t - x_shift - t_peak, x_shift the moving window's displacement. */
+  int laser_on;
+  double laser_a0, laser_waist, laser_tau, laser_t_peak, laser_y_center;
+  /* Moving window at c along +x: after a step that brings t - mw_t0 to at
+   * least (k+1) patch widths, the domain shifts one patch column. */
+  int moving_window;
+  double mw_t0;
+  /* Plasma injected in the new column: density n0 min(1, max(0,
+   * (x - x0) / ramp)) (a step at x0 if ramp <= 0), ppc[0] x ppc[1] particles
+   * per cell placed regularly, at rest. */
+  double inj_n0, inj_x0, inj_ramp;
+  int inj_ppc[3];
+  double capacity_factor; /* patch capacity = factor x the fullest patch at
+                             the first load (>= 1; 0 means 2.0) */
+  int capacity_min;       /* lower bound on the patch capacity (0 = 256) */
+  void *stream;           /* cudaStream_t to run on; NULL = library-owned */
+  int device;             /* CUDA device ordinal */
+  int use_graph;          /* 1: replay the captured step as a CUDA graph */
+  int timing;             /* 1: per-phase CUDA-event timers (no graph) */
+  int tma;                /* 1 (default if >= 0): stage field tiles with TMA;
+                             0: plain coalesced loads */
+  int block;              /* threads per patch block (0 = default 256) */
+} pic_config;
+
+typedef struct pic_diag_t {
+  long long step;         /* steps taken */
+  double t;               /* simulated time */
+  long long np;           /* particles, including those in flight between
+                             patches */
+  double U_E, U_B, U_K;   /* 1/2 sum |E|^2 dV, 1/2 sum |Bm|^2 dV over the
+                             cells [0,nx) x [0,ny); sum w (gamma - 1) m dV */
+  double gauss;           /* max |div_h E - rho - rho_bg| (open axes: 3 cells
+                             from the faces excluded) */
+  double continuity;      /* max |(rho^{n+1} - rho^n)/dt + div_h J| of the
+                             last step, NaN if unavailable */
+  double charge;          /* sum q w dV of the particles */
+  int shifts;             /* moving-window shifts done */
+  int max_patch_count;    /* fullest patch after the last step */
+  int capacity;           /* particles per patch */
+  double ms_particles, ms_fields, ms_window; /* timers (timing = 1) */
+  long long launches;     /* kernels launched by this context so far */
+  long long particle_step_launches;
+} pic_diag_t;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Create a context: validates the configuration and allocates the fields
+ * (particles are allocated by the first pic_load_particles).  The context
+ * owns all device memory it allocates. */
+pic_status pic_create(const pic_config *cfg, pic_ctx **out);
+
+/* Append n particles (global positions x, y in c/w; momenta u; weights w =
+ * local density / particles per cell), float64, PIC_HOST or PIC_DEVICE.
+ * They are binned into patches on the device; positions outside the domain
+ * give PIC_EINVAL.  The first call sizes the patch capacity. */
+pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y,
+                              const double *ux, const double *uy,
+                              const double *uz, const double *w, size_t n,
+                              int where);
+
+/* Overwrite one field component (PIC_EX..PIC_BMZ or PIC_RHO_BG) from an
+ * array in the layout above.  B is taken at t + dt/2, Bm at t. */
+pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where);
+
+/* Background charge (immobile ions): none, uniform value, or neutralising
+ * the particles currently loaded. */
+pic_status pic_set_background(pic_ctx *ctx, int mode, double value);
+
+/* Advance nsteps steps.  Synchronises with the device at the end and reports
+ * device-side faults. */
+pic_status pic_step(pic_ctx *ctx, int nsteps);
+
+/* Read one field component (PIC_EX..PIC_RHO_BG) into dst (layout above).
+ * PIC_JX..PIC_JZ give the current of the last step; PIC_RHO deposits the
+ * particles' charge in float64. */
+pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where);
+
+/* Copy the particles out as 6 x n float64 rows (x, y, ux, uy, uz, w), global
+ * positions, in patch order.  cap is the row length of out; *n receives the
+ * count (PIC_EINVAL if it exceeds cap). */
+pic_status pic_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n,
+                             int where);
+
+/* Diagnostics (float64 reductions on the device). */
+pic_status pic_diag(pic_ctx *ctx, pic_diag_t *out);
+
+/* Wait for the context's stream and report sticky device faults. */
+pic_status pic_sync(pic_ctx *ctx);
+
+/* Checkpoint: with host == NULL, *bytes receives the size needed; otherwise
+ * the whole state is written to host (size *bytes). */
+pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes);
+/* Restore a snapshot taken from a context with the same configuration; also
+ * clears a sticky device fault. */
+pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes);
+
+/* Device bytes a context with this configuration and at most np_max
+ * particles at the first load would allocate (used for admission). */
+size_t pic_footprint(const pic_config *cfg, size_t np_max);
+
+const char *pic_last_error(const pic_ctx *ctx);
+void pic_destroy(pic_ctx *ctx);
+
+/* Library version string. */
+const char *pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

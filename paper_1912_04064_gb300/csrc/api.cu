@@ -1,0 +1,991 @@
+// C-ABI of libpic (declared in include/pic.h): context, particle loading,
+// the step loop (optionally replayed as CUDA graphs), moving window, field
+// and particle I/O, float64 diagnostics and checkpoint/restore.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "common.cuh"
+
+using namespace pic;
+
+struct pic_ctx {
+  pic_config cfg;
+  Geom g;
+  bool fp32;
+  size_t rs;  // bytes per real
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *F = nullptr;
+  double *rho_bg = nullptr, *rho_a = nullptr, *rho_b = nullptr;
+  void *seg[2][6] = {};
+  int *cnt[2] = {};
+  void *bkt[2][6] = {};
+  int *bcnt[2] = {};
+  int cap = 0, bcap = 0;
+  DevState *st = nullptr;
+  double *partials = nullptr;
+  int npartials = 0;
+  long long *offsets = nullptr;
+  double *staging = nullptr;
+  size_t staging_n = 0;
+  // host mirrors of the device state
+  long long step = 0;
+  double t = 0.0;
+  int nshift = 0, col0 = 0;
+  bool prev_valid = false;  // previous particle state + last J usable
+  CUtensorMap tmap;
+  bool tmap_ok = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double ms_particles = 0, ms_fields = 0, ms_window = 0;
+  long long launches = 0, ps_launches = 0;
+  int sticky = PIC_OK;
+  std::string err;
+};
+
+namespace {
+
+const char *kVersion = "libpic 0.1 (sm_103a, 2D3V SDMD patch PIC)";
+
+pic_status fail(pic_ctx *c, pic_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(ctx, PIC_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool valid_config(const pic_config *c, std::string &why) {
+  if (!c) { why = "null config"; return false; }
+  if (c->dims != 2) { why = "only dims = 2 (2D3V) is supported"; return false; }
+  for (int a = 0; a < 2; ++a) {
+    if (c->n[a] <= 0 || c->patch[a] <= 0) { why = "cells and patch sizes must be positive"; return false; }
+    if (c->patch[a] % 4 || c->patch[a] < 4 || c->patch[a] > 64) { why = "patch sizes must be multiples of 4 in [4, 64]"; return false; }
+    if (c->n[a] % c->patch[a]) { why = "cells must be a multiple of the patch size"; return false; }
+    if (!(c->d[a] > 0)) { why = "cell sizes must be positive"; return false; }
+    if (c->bc_field[a] != PIC_BC_PERIODIC && c->bc_field[a] != PIC_BC_SILVER_MULLER) { why = "bad field boundary"; return false; }
+    for (int f = 0; f < 2; ++f) {
+      int b = c->bc_part[a][f];
+      if (b < 0 || b > 2) { why = "bad particle boundary"; return false; }
+      if ((b == PIC_PBC_PERIODIC) != (c->bc_field[a] == PIC_BC_PERIODIC)) { why = "periodic particle and field boundaries must pair"; return false; }
+    }
+  }
+  if (c->n[0] / c->patch[0] < 1) { why = "no patches"; return false; }
+  if (!(c->dt > 0) || !(c->dt < std::min(c->d[0], c->d[1]))) { why = "dt must be in (0, min(d))"; return false; }
+  if (c->prec != PIC_FP64 && c->prec != PIC_FP32) { why = "bad precision"; return false; }
+  if (!(c->m > 0) || c->q == 0) { why = "mass must be positive and charge nonzero"; return false; }
+  if (c->laser_on && c->bc_field[0] != PIC_BC_SILVER_MULLER) { why = "the laser needs an open x axis"; return false; }
+  if (c->laser_on && !(c->laser_waist > 0 && c->laser_tau > 0)) { why = "laser waist and duration must be positive"; return false; }
+  if (c->moving_window) {
+    if (c->bc_field[0] != PIC_BC_SILVER_MULLER) { why = "the moving window needs an open x axis"; return false; }
+    if (c->n[0] / c->patch[0] < 2) { why = "the moving window needs two patch columns"; return false; }
+    if (c->inj_ppc[0] < 1 || c->inj_ppc[1] < 1) { why = "injected particles per cell must be >= 1"; return false; }
+  }
+  if (c->capacity_factor < 0) { why = "capacity factor must be >= 0"; return false; }
+  if (c->block && (c->block % 32 || c->block < 64 || c->block > 256)) { why = "block must be 64..256, a multiple of 32"; return false; }
+  return true;
+}
+
+Geom make_geom(const pic_config *c) {
+  Geom g{};
+  g.nx = c->n[0];
+  g.ny = c->n[1];
+  g.P = c->patch[0];
+  g.Q = c->patch[1];
+  g.npx = g.nx / g.P;
+  g.npy = g.ny / g.Q;
+  g.nslots = g.npx * g.npy;
+  g.sx = ((g.nx + 2 * GX) + 31) / 32 * 32;
+  g.nys = g.ny + 2 * GY;
+  g.cs = (long long)g.sx * g.nys;
+  g.dx = c->d[0];
+  g.dy = c->d[1];
+  g.dt = c->dt;
+  g.fbc_x = c->bc_field[0];
+  g.fbc_y = c->bc_field[1];
+  for (int a = 0; a < 2; ++a)
+    for (int f = 0; f < 2; ++f) g.pbc[a][f] = c->bc_part[a][f];
+  g.q = c->q;
+  g.m = c->m;
+  return g;
+}
+
+size_t field_bytes(const Geom &g, size_t rs) { return (size_t)NCOMP * g.cs * rs; }
+size_t particle_bytes(const Geom &g, int cap, int bcap, size_t rs) {
+  return 2 * (6 * rs * ((size_t)g.nslots * cap + (size_t)g.nslots * 8 * bcap) +
+              sizeof(int) * ((size_t)g.nslots + (size_t)g.nslots * 8));
+}
+int bucket_cap(int cap) { return std::max(64, (cap / 4 + 31) / 32 * 32); }
+
+template <typename R>
+SoA<R> soa(void *const a[6]) {
+  return SoA<R>{(R *)a[0], (R *)a[1], (R *)a[2], (R *)a[3], (R *)a[4], (R *)a[5]};
+}
+
+template <typename R>
+PartView<R> view(pic_ctx *c, int segset, int bktset) {
+  PartView<R> v;
+  v.seg = soa<R>(c->seg[segset]);
+  v.cnt = c->cnt[segset];
+  v.bkt = soa<R>(c->bkt[bktset]);
+  v.bcnt = c->bcnt[bktset];
+  v.cap = c->cap;
+  v.bcap = c->bcap;
+  return v;
+}
+
+pic_status check_usable(pic_ctx *ctx) {
+  if (!ctx) return PIC_EINVAL;
+  if (ctx->sticky != PIC_OK) return fail(ctx, PIC_ESTATE, "context holds a device fault: restore a snapshot");
+  return PIC_OK;
+}
+
+// Read the sticky device word; convert it to a status.
+pic_status poll_device(pic_ctx *ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  DevState h;
+  CK(cudaMemcpy(&h, ctx->st, sizeof h, cudaMemcpyDeviceToHost));
+  if (h.err) {
+    pic_status s = PIC_ENONFINITE;
+    std::string m = "device fault:";
+    if (h.err & ERR_TIMEOUT) { s = PIC_ETIMEOUT; m += " staging wait ran out;"; }
+    if (h.err & (ERR_OVERFLOW_SEG | ERR_OVERFLOW_BKT | ERR_OVERFLOW_LOAD)) {
+      if (s != PIC_ETIMEOUT) s = PIC_EOVERFLOW;
+      m += " patch capacity exceeded (raise capacity_factor);";
+    }
+    if (h.err & ERR_NONFINITE) m += " non-finite particle;";
+    if (h.err & ERR_FAST) m += " particle moved more than one cell;";
+    if (h.err & ERR_LOAD_RANGE) { s = PIC_EINVAL; m += " particle outside the domain;"; }
+    ctx->sticky = s;
+    return fail(ctx, s, m);
+  }
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status alloc_particles(pic_ctx *ctx, int cap) {
+  ctx->cap = cap;
+  ctx->bcap = bucket_cap(cap);
+  const Geom &g = ctx->g;
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 6; ++a) {
+      CK(cudaMalloc(&ctx->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
+      CK(cudaMalloc(&ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * 8 * ctx->bcap));
+    }
+    CK(cudaMalloc(&ctx->cnt[s], sizeof(int) * g.nslots));
+    CK(cudaMalloc(&ctx->bcnt[s], sizeof(int) * g.nslots * 8));
+    CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
+    CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
+  }
+  CK(cudaMalloc(&ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
+  return PIC_OK;
+}
+
+void free_graphs(pic_ctx *c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->gexec[p]) {
+      cudaGraphExecDestroy(c->gexec[p]);
+      c->gexec[p] = nullptr;
+    }
+}
+
+template <typename R>
+pic_status build_tmap(pic_ctx *ctx) {
+  if (ctx->cfg.tma == 0) return PIC_OK;
+  auto enc = encode_fn();
+  if (!enc) return fail(ctx, PIC_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const Geom &g = ctx->g;
+  cuuint64_t dims[3] = {(cuuint64_t)g.sx, (cuuint64_t)g.nys, 6};
+  cuuint64_t strides[2] = {(cuuint64_t)g.sx * sizeof(R), (cuuint64_t)g.cs * sizeof(R)};
+  cuuint32_t box[3] = {(cuuint32_t)(g.P + 8), (cuuint32_t)(g.Q + 3), 6};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(&ctx->tmap,
+                   sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                   3, ctx->F, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, PIC_ECUDA, "cuTensorMapEncodeTiled failed");
+  ctx->tmap_ok = true;
+  return PIC_OK;
+}
+
+// One step on the context's stream: the patch particle step, then the region
+// field update.  `mid` (optional) is recorded between the two phases.
+template <typename R>
+pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
+  const Geom &g = ctx->g;
+  const int p = parity;
+  StepArgs<R> a;
+  a.g = g;
+  a.F = (const R *)ctx->F;
+  a.Jdst = (R *)ctx->F + (C_JA + 3 * p) * g.cs;
+  a.pin = soa<R>(ctx->seg[p]);
+  a.pout = soa<R>(ctx->seg[1 - p]);
+  a.cnt_in = ctx->cnt[p];
+  a.cnt_out = ctx->cnt[1 - p];
+  a.bin = soa<R>(ctx->bkt[1 - p]);
+  a.bout = soa<R>(ctx->bkt[p]);
+  a.bcnt_in = ctx->bcnt[1 - p];
+  a.bcnt_out = ctx->bcnt[p];
+  a.cap = ctx->cap;
+  a.bcap = ctx->bcap;
+  a.parity = p;
+  a.st = ctx->st;
+  const int block = ctx->cfg.block ? ctx->cfg.block : 256;
+  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, block, ctx->stream));
+  if (mid) CK(cudaEventRecord(mid, ctx->stream));
+  FieldArgs<R> f;
+  f.g = g;
+  f.F = (R *)ctx->F;
+  f.parity = p;
+  f.st = ctx->st;
+  f.laser_on = ctx->cfg.laser_on;
+  f.a0 = ctx->cfg.laser_a0;
+  f.waist = ctx->cfg.laser_waist;
+  f.tau = ctx->cfg.laser_tau;
+  f.t_peak = ctx->cfg.laser_t_peak;
+  f.yc = ctx->cfg.laser_y_center;
+  CK(launch_fields<R>(f, ctx->stream));
+  return PIC_OK;
+}
+
+int kernels_per_step(const pic_ctx *c) {
+  return 3 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0);
+}
+
+__global__ void k_window_state(DevState *st, int col0, int nshift) {
+  st->col0 = col0;
+  st->nshift = nshift;
+}
+
+template <typename R>
+pic_status window_shift(pic_ctx *ctx) {
+  const Geom &g = ctx->g;
+  const int q = (int)(ctx->step & 1);     // current segment set
+  const int bset = 1 - q;                 // current bucket set
+  const int last_j = 1 - q;               // J set of the step just taken
+  R *F = (R *)ctx->F;
+  CK(launch_shift_fields<R>(g, F, 9, ctx->stream));
+  CK(launch_shift_fields<R>(g, F + (C_JA + 3 * last_j) * g.cs, 3, ctx->stream));
+  CK(launch_shift_f64(g, ctx->rho_bg, ctx->stream));
+  const int old_col0 = ctx->col0;
+  ctx->nshift += 1;
+  ctx->col0 = (old_col0 + 1) % g.npx;
+  CK(launch_window_particles<R>(g, old_col0, ctx->nshift, soa<R>(ctx->seg[q]), ctx->cnt[q],
+                                soa<R>(ctx->bkt[bset]), ctx->bcnt[bset], ctx->cap, ctx->bcap,
+                                ctx->cfg.inj_n0, ctx->cfg.inj_x0, ctx->cfg.inj_ramp,
+                                ctx->cfg.inj_ppc[0], ctx->cfg.inj_ppc[1], ctx->rho_bg,
+                                &ctx->st->err, ctx->stream));
+  k_window_state<<<1, 1, 0, ctx->stream>>>(ctx->st, ctx->col0, ctx->nshift);
+  CK(cudaGetLastError());
+  ctx->launches += 7;
+  ctx->prev_valid = false;
+  return PIC_OK;
+}
+
+bool window_due(const pic_ctx *c) {
+  return c->cfg.moving_window && c->t > c->cfg.mw_t0 &&
+         c->t - c->cfg.mw_t0 >= (c->nshift + 1) * (double)c->g.P * c->g.dx;
+}
+
+template <typename R>
+pic_status capture_graphs(pic_ctx *ctx) {
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t gr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    pic_status s = enqueue_step<R>(ctx, p);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+    if (s != PIC_OK) return s;
+    CK(e);
+    e = cudaGraphInstantiate(&ctx->gexec[p], gr, 0);
+    cudaGraphDestroy(gr);
+    CK(e);
+  }
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status do_step(pic_ctx *ctx, int nsteps) {
+  if (!ctx->cap) return fail(ctx, PIC_ESTATE, "no particles loaded");
+  if (ctx->cfg.tma && !ctx->tmap_ok) {
+    pic_status s = build_tmap<R>(ctx);
+    if (s) return s;
+  }
+  CK(prepare_particle_step<R>(ctx->g.P, ctx->g.Q));
+  const bool timing = ctx->cfg.timing != 0;
+  const bool use_graph = ctx->cfg.use_graph && !timing;
+  if (use_graph && !ctx->gexec[0]) {
+    pic_status s = capture_graphs<R>(ctx);
+    if (s) return s;
+  }
+  // timing: three events per step (start, between phases, end) and two per
+  // window shift, read back once after the loop
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;  // 0: step triple, 1: window pair
+  auto new_event = [&](cudaEvent_t *e) -> cudaError_t { return cudaEventCreate(e); };
+  pic_status rs = PIC_OK;
+  for (int n = 0; n < nsteps && rs == PIC_OK; ++n) {
+    const int p = (int)(ctx->step & 1);
+    if (use_graph) {
+      CK(cudaGraphLaunch(ctx->gexec[p], ctx->stream));
+    } else if (timing) {
+      cudaEvent_t e[3];
+      for (int k = 0; k < 3; ++k) CK(new_event(&e[k]));
+      CK(cudaEventRecord(e[0], ctx->stream));
+      rs = enqueue_step<R>(ctx, p, e[1]);
+      CK(cudaEventRecord(e[2], ctx->stream));
+      for (int k = 0; k < 3; ++k) ev.push_back(e[k]);
+      kind.push_back(0);
+    } else {
+      rs = enqueue_step<R>(ctx, p);
+    }
+    ctx->launches += kernels_per_step(ctx);
+    ctx->ps_launches += 1;
+    ctx->step += 1;
+    ctx->t += ctx->g.dt;
+    ctx->prev_valid = true;
+    if (rs == PIC_OK && window_due(ctx)) {
+      cudaEvent_t e[2];
+      if (timing) {
+        for (int k = 0; k < 2; ++k) CK(new_event(&e[k]));
+        CK(cudaEventRecord(e[0], ctx->stream));
+      }
+      rs = window_shift<R>(ctx);
+      if (timing) {
+        CK(cudaEventRecord(e[1], ctx->stream));
+        ev.push_back(e[0]);
+        ev.push_back(e[1]);
+        kind.push_back(1);
+      }
+    }
+  }
+  if (!ev.empty()) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    size_t k = 0;
+    for (int t : kind) {
+      float a = 0, b = 0;
+      if (t == 0) {
+        CK(cudaEventElapsedTime(&a, ev[k], ev[k + 1]));
+        CK(cudaEventElapsedTime(&b, ev[k + 1], ev[k + 2]));
+        ctx->ms_particles += a;
+        ctx->ms_fields += b;
+        k += 3;
+      } else {
+        CK(cudaEventElapsedTime(&a, ev[k], ev[k + 1]));
+        ctx->ms_window += a;
+        k += 2;
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  if (rs) return rs;
+  return poll_device(ctx);
+}
+
+template <typename R>
+pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double *ux,
+                   const double *uy, const double *uz, const double *w, size_t n, int where) {
+  const Geom &g = ctx->g;
+  const double *src[6] = {x, y, ux, uy, uz, w};
+  const double *d[6];
+  double *tmp = nullptr;
+  if (where == PIC_HOST) {
+    CK(cudaMalloc(&tmp, sizeof(double) * 6 * std::max<size_t>(n, 1)));
+    for (int a = 0; a < 6; ++a) {
+      CK(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
+                         ctx->stream));
+      d[a] = tmp + a * n;
+    }
+  } else {
+    for (int a = 0; a < 6; ++a) d[a] = src[a];
+  }
+  const int q = (int)(ctx->step & 1);
+  pic_status rs = PIC_OK;
+  // validation / counting pass: particles outside the domain reject the
+  // whole call without touching the stored particles
+  int *cnt = nullptr;
+  CK(cudaMalloc(&cnt, sizeof(int) * g.nslots));
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, ctx->stream));
+  CK(launch_bin_count<R>(g, ctx->col0, d[0], d[1], n, cnt, &ctx->st->err, ctx->stream));
+  std::vector<int> h(g.nslots);
+  CK(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, ctx->stream));
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(cnt);
+  ctx->launches += 1;
+  if (hs.err & ERR_LOAD_RANGE) {
+    unsigned zero = hs.err & ~ERR_LOAD_RANGE;
+    CK(cudaMemcpy(&ctx->st->err, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    if (tmp) cudaFree(tmp);
+    return fail(ctx, PIC_EINVAL, "particle position outside the domain");
+  }
+  if (!ctx->cap) {
+    int mx = *std::max_element(h.begin(), h.end());
+    double cf = ctx->cfg.capacity_factor > 0 ? ctx->cfg.capacity_factor : 2.0;
+    int cmin = ctx->cfg.capacity_min > 0 ? ctx->cfg.capacity_min : 256;
+    if (ctx->cfg.moving_window) {
+      int inj = g.P * g.Q * ctx->cfg.inj_ppc[0] * ctx->cfg.inj_ppc[1];
+      mx = std::max(mx, inj);
+    }
+    int cap = std::max(cmin, (int)std::ceil(cf * mx));
+    cap = (cap + 31) / 32 * 32;
+    rs = alloc_particles<R>(ctx, cap);
+    if (rs) return rs;
+  }
+  CK(launch_bin_place<R>(g, ctx->col0, d[0], d[1], d[2], d[3], d[4], d[5], n,
+                         soa<R>(ctx->seg[q]), ctx->cnt[q], ctx->cap, &ctx->st->err, ctx->stream));
+  CK(launch_clamp_counts(ctx->cnt[q], g.nslots, ctx->cap, ctx->stream));
+  ctx->launches += 2;
+  // clamp counts of overflowing slots happens via the error word
+  if (tmp) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(tmp);
+  }
+  ctx->prev_valid = false;
+  free_graphs(ctx);  // capacity and buffers are baked into captured graphs
+  return poll_device(ctx);
+}
+
+template <typename R>
+pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, int where) {
+  const Geom &g = ctx->g;
+  if (!ctx->cap) {
+    *n = 0;
+    return PIC_OK;
+  }
+  const int q = (int)(ctx->step & 1);
+  std::vector<int> c(g.nslots), b((size_t)g.nslots * 8);
+  CK(cudaMemcpyAsync(c.data(), ctx->cnt[q], sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(b.data(), ctx->bcnt[1 - q], sizeof(int) * g.nslots * 8, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<long long> off((size_t)g.nslots * 9 + 1, 0);
+  long long tot = 0;
+  for (int pp = 0; pp < g.nslots; ++pp) {
+    const int slot = (pp / g.npx) * g.npx + (pp % g.npx + ctx->col0) % g.npx;
+    off[pp] = tot;
+    tot += c[slot];
+  }
+  for (int pp = 0; pp < g.nslots; ++pp) {
+    const int slot = (pp / g.npx) * g.npx + (pp % g.npx + ctx->col0) % g.npx;
+    for (int d = 0; d < 8; ++d) {
+      int ddx, ddy;
+      dir_delta(d, ddx, ddy);
+      off[g.nslots + (size_t)pp * 8 + d] = tot;
+      if (neighbour_slot(g, ctx->col0, slot, ddx, ddy) >= 0) tot += b[(size_t)slot * 8 + d];
+    }
+  }
+  *n = (size_t)tot;
+  if (!out) return PIC_OK;
+  if ((size_t)tot > cap) return fail(ctx, PIC_EINVAL, "output capacity too small");
+  CK(cudaMemcpyAsync(ctx->offsets, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  double *dst = out;
+  double *tmp = nullptr;
+  if (where == PIC_HOST) {
+    CK(cudaMalloc(&tmp, sizeof(double) * 6 * std::max<size_t>(cap, 1)));
+    dst = tmp;
+  }
+  CK(launch_get_particles<R>(g, ctx->col0, view<R>(ctx, q, 1 - q), ctx->offsets, dst, cap,
+                             ctx->stream));
+  ctx->launches += 1;
+  if (tmp) {
+    CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(tmp);
+  }
+  return poll_device(ctx);
+}
+
+pic_status ensure_staging(pic_ctx *ctx, size_t n) {
+  if (ctx->staging_n >= n) return PIC_OK;
+  if (ctx->staging) cudaFree(ctx->staging);
+  ctx->staging = nullptr;
+  CK(cudaMalloc(&ctx->staging, sizeof(double) * n));
+  ctx->staging_n = n;
+  return PIC_OK;
+}
+
+void out_shape(const Geom &g, int &nxo, int &nyo) {
+  nxo = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2;
+  nyo = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2;
+}
+
+int comp_of(int which) {
+  switch (which) {
+    case PIC_EX: return C_EX;
+    case PIC_EY: return C_EY;
+    case PIC_EZ: return C_EZ;
+    case PIC_BX: return C_BX;
+    case PIC_BY: return C_BY;
+    case PIC_BZ: return C_BZ;
+    case PIC_BMX: return C_BMX;
+    case PIC_BMY: return C_BMY;
+    case PIC_BMZ: return C_BMZ;
+    default: return -1;
+  }
+}
+
+template <typename R>
+pic_status deposit_current_rho(pic_ctx *ctx, double *rho, bool previous) {
+  const Geom &g = ctx->g;
+  CK(cudaMemsetAsync(rho, 0, sizeof(double) * g.cs, ctx->stream));
+  if (!ctx->cap) return PIC_OK;
+  const int q = (int)(ctx->step & 1);
+  const int segset = previous ? 1 - q : q;
+  const int bktset = previous ? q : 1 - q;
+  CK(launch_deposit_rho<R>(g, ctx->col0, view<R>(ctx, segset, bktset), rho, 1.0, ctx->stream));
+  ctx->launches += 1;
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status do_get_field(pic_ctx *ctx, int which, double *dst, int where) {
+  const Geom &g = ctx->g;
+  int nxo, nyo;
+  out_shape(g, nxo, nyo);
+  const size_t n = (size_t)nxo * nyo;
+  double *d = dst;
+  if (where == PIC_HOST) {
+    pic_status s = ensure_staging(ctx, n);
+    if (s) return s;
+    d = ctx->staging;
+  }
+  if (which == PIC_RHO || which == PIC_RHO_BG) {
+    const double *src = ctx->rho_bg;
+    if (which == PIC_RHO) {
+      pic_status s = deposit_current_rho<R>(ctx, ctx->rho_a, false);
+      if (s) return s;
+      src = ctx->rho_a;
+    }
+    CK(launch_get_field_f64(g, src, d, ctx->stream));
+  } else {
+    int c = comp_of(which);
+    if (which >= PIC_JX && which <= PIC_JZ) {
+      const int jset = (int)((ctx->step + 1) & 1);  // set of the last step
+      c = C_JA + 3 * jset + (which - PIC_JX);
+    }
+    if (c < 0) return fail(ctx, PIC_EINVAL, "bad field id");
+    CK(launch_get_field<R>(g, (const R *)ctx->F + c * g.cs, d, ctx->stream));
+  }
+  ctx->launches += 1;
+  if (where == PIC_HOST) {
+    CK(cudaMemcpyAsync(dst, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return poll_device(ctx);
+}
+
+template <typename R>
+pic_status do_set_field(pic_ctx *ctx, int which, const double *src, int where) {
+  const Geom &g = ctx->g;
+  int nxo, nyo;
+  out_shape(g, nxo, nyo);
+  const size_t n = (size_t)nxo * nyo;
+  const double *s = src;
+  if (where == PIC_HOST) {
+    pic_status r = ensure_staging(ctx, n);
+    if (r) return r;
+    CK(cudaMemcpyAsync(ctx->staging, src, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    s = ctx->staging;
+  }
+  if (which == PIC_RHO_BG) {
+    CK(launch_set_field_f64(g, ctx->rho_bg, s, ctx->stream));
+  } else {
+    const int c = comp_of(which);
+    if (c < 0) return fail(ctx, PIC_EINVAL, "field id not settable");
+    CK(launch_set_field<R>(g, (R *)ctx->F + c * g.cs, s, ctx->stream));
+  }
+  ctx->launches += 1;
+  ctx->prev_valid = false;
+  return poll_device(ctx);
+}
+
+template <typename R>
+pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
+  const Geom &g = ctx->g;
+  memset(out, 0, sizeof *out);
+  const int nb = ctx->npartials;
+  std::vector<double> h(3 * nb);
+  const double dV = g.dx * g.dy;
+  CK(launch_field_diag<R>(g, (const R *)ctx->F, ctx->partials, nb, ctx->stream));
+  CK(cudaMemcpyAsync(h.data(), ctx->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double ue = 0, ub = 0;
+  for (int b = 0; b < nb; ++b) {
+    ue += h[2 * b];
+    ub += h[2 * b + 1];
+  }
+  out->U_E = 0.5 * ue * dV;
+  out->U_B = 0.5 * ub * dV;
+  double ek = 0, ws = 0, cnt = 0;
+  if (ctx->cap) {
+    const int q = (int)(ctx->step & 1);
+    CK(launch_particle_diag<R>(g, ctx->col0, view<R>(ctx, q, 1 - q), ctx->partials, nb, ctx->stream));
+    CK(cudaMemcpyAsync(h.data(), ctx->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < nb; ++b) {
+      ek += h[3 * b];
+      ws += h[3 * b + 1];
+      cnt += h[3 * b + 2];
+    }
+  }
+  out->U_K = ek * g.m * dV;
+  out->charge = g.q * ws * dV;
+  out->np = (long long)llround(cnt);
+  pic_status s = deposit_current_rho<R>(ctx, ctx->rho_a, false);
+  if (s) return s;
+  const bool cont = ctx->prev_valid && ctx->cap;
+  if (cont) {
+    s = deposit_current_rho<R>(ctx, ctx->rho_b, true);
+    if (s) return s;
+  }
+  const int jset = (int)((ctx->step + 1) & 1);
+  CK(launch_gauss_diag<R>(g, (const R *)ctx->F, jset, ctx->rho_a, cont ? ctx->rho_b : nullptr,
+                          ctx->rho_bg, ctx->partials, nb, ctx->stream));
+  CK(cudaMemcpyAsync(h.data(), ctx->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double gm = 0, cm = 0;
+  for (int b = 0; b < nb; ++b) {
+    gm = std::max(gm, h[2 * b]);
+    cm = std::max(cm, h[2 * b + 1]);
+  }
+  out->gauss = gm;
+  out->continuity = cont ? cm : NAN;
+  out->step = ctx->step;
+  out->t = ctx->t;
+  out->shifts = ctx->nshift;
+  out->max_patch_count = hs.maxcnt[(ctx->step + 1) & 1];
+  out->capacity = ctx->cap;
+  out->ms_particles = ctx->ms_particles;
+  out->ms_fields = ctx->ms_fields;
+  out->ms_window = ctx->ms_window;
+  ctx->launches += 5 + (cont ? 1 : 0);
+  out->launches = ctx->launches;
+  out->particle_step_launches = ctx->ps_launches;
+  return poll_device(ctx);
+}
+
+// ---- snapshot layout: header, fields, rho_bg, segments, counts, buckets,
+// bucket counts, device state
+struct SnapHeader {
+  char magic[8];
+  int nx, ny, P, Q, fp32, cap, bcap, nshift, col0, pad;
+  long long step;
+  double t;
+  int prev_valid, sticky_pad;
+};
+
+size_t snapshot_bytes(const pic_ctx *c) {
+  const Geom &g = c->g;
+  size_t b = sizeof(SnapHeader) + field_bytes(g, c->rs) + sizeof(double) * g.cs + sizeof(DevState);
+  if (c->cap) b += particle_bytes(g, c->cap, c->bcap, c->rs);
+  return b;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char *pic_version(void) { return kVersion; }
+
+size_t pic_footprint(const pic_config *cfg, size_t np_max) {
+  std::string why;
+  if (!valid_config(cfg, why)) return 0;
+  Geom g = make_geom(cfg);
+  const size_t rs = cfg->prec == PIC_FP32 ? 4 : 8;
+  double cf = cfg->capacity_factor > 0 ? cfg->capacity_factor : 2.0;
+  int cmin = cfg->capacity_min > 0 ? cfg->capacity_min : 256;
+  // the fullest patch is not known before loading: assume a uniform load
+  size_t per = (np_max + g.nslots - 1) / g.nslots;
+  if (cfg->moving_window)
+    per = std::max(per, (size_t)g.P * g.Q * cfg->inj_ppc[0] * cfg->inj_ppc[1]);
+  int cap = std::max(cmin, (int)std::ceil(cf * (double)per));
+  cap = (cap + 31) / 32 * 32;
+  return field_bytes(g, rs) + 3 * sizeof(double) * g.cs + particle_bytes(g, cap, bucket_cap(cap), rs) +
+         sizeof(long long) * (g.nslots * 9 + 1) + sizeof(double) * 3 * 1024 + sizeof(DevState);
+}
+
+pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!valid_config(cfg, why)) {
+    // no context exists yet: report through a throw-away context-free path
+    return PIC_EINVAL;
+  }
+  pic_ctx *ctx = new (std::nothrow) pic_ctx();
+  if (!ctx) return PIC_ENOMEM;
+  ctx->cfg = *cfg;
+  if (ctx->cfg.tma < 0) ctx->cfg.tma = 1;
+  ctx->g = make_geom(cfg);
+  ctx->fp32 = cfg->prec == PIC_FP32;
+  ctx->rs = ctx->fp32 ? 4 : 8;
+  const Geom &g = ctx->g;
+  auto bail = [&](pic_status s) {
+    pic_destroy(ctx);
+    return s;
+  };
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(PIC_ECUDA);
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PIC_ECUDA);
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->F, field_bytes(g, ctx->rs)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&ctx->rho_bg, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&ctx->rho_a, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&ctx->rho_b, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&ctx->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
+  ctx->npartials = 1024;
+  if (cudaMalloc(&ctx->partials, sizeof(double) * 3 * ctx->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMemsetAsync(ctx->F, 0, field_bytes(g, ctx->rs), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->rho_bg, 0, sizeof(double) * g.cs, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return bail(PIC_ECUDA);
+  *out = ctx;
+  return PIC_OK;
+}
+
+void pic_destroy(pic_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_graphs(ctx);
+  cudaFree(ctx->F);
+  cudaFree(ctx->rho_bg);
+  cudaFree(ctx->rho_a);
+  cudaFree(ctx->rho_b);
+  cudaFree(ctx->st);
+  cudaFree(ctx->partials);
+  cudaFree(ctx->offsets);
+  cudaFree(ctx->staging);
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 6; ++a) {
+      cudaFree(ctx->seg[s][a]);
+      cudaFree(ctx->bkt[s][a]);
+    }
+    cudaFree(ctx->cnt[s]);
+    cudaFree(ctx->bcnt[s]);
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *pic_last_error(const pic_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y, const double *ux,
+                              const double *uy, const double *uz, const double *w, size_t n,
+                              int where) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (n && (!x || !y || !ux || !uy || !uz || !w)) return fail(ctx, PIC_EINVAL, "null particle array");
+  if (where != PIC_HOST && where != PIC_DEVICE) return fail(ctx, PIC_EINVAL, "bad location");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_load<float>(ctx, x, y, ux, uy, uz, w, n, where)
+                   : do_load<double>(ctx, x, y, ux, uy, uz, w, n, where);
+}
+
+pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!src || (where != PIC_HOST && where != PIC_DEVICE)) return fail(ctx, PIC_EINVAL, "bad source");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_set_field<float>(ctx, which, src, where)
+                   : do_set_field<double>(ctx, which, src, where);
+}
+
+pic_status pic_set_background(pic_ctx *ctx, int mode, double value) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  CK(cudaSetDevice(ctx->cfg.device));
+  const Geom &g = ctx->g;
+  if (mode == PIC_BG_NONE) {
+    CK(cudaMemsetAsync(ctx->rho_bg, 0, sizeof(double) * g.cs, ctx->stream));
+  } else if (mode == PIC_BG_UNIFORM) {
+    std::vector<double> h((size_t)g.cs, value);
+    CK(cudaMemcpyAsync(ctx->rho_bg, h.data(), sizeof(double) * g.cs, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else if (mode == PIC_BG_NEUTRALISING) {
+    CK(cudaMemsetAsync(ctx->rho_bg, 0, sizeof(double) * g.cs, ctx->stream));
+    if (ctx->cap) {
+      const int q = (int)(ctx->step & 1);
+      if (ctx->fp32)
+        CK(launch_deposit_rho<float>(g, ctx->col0, view<float>(ctx, q, 1 - q), ctx->rho_bg, -1.0, ctx->stream));
+      else
+        CK(launch_deposit_rho<double>(g, ctx->col0, view<double>(ctx, q, 1 - q), ctx->rho_bg, -1.0, ctx->stream));
+      ctx->launches += 1;
+    }
+  } else {
+    return fail(ctx, PIC_EINVAL, "bad background mode");
+  }
+  return poll_device(ctx);
+}
+
+pic_status pic_step(pic_ctx *ctx, int nsteps) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (nsteps < 0) return fail(ctx, PIC_EINVAL, "negative step count");
+  if (nsteps == 0) return PIC_OK;
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_step<float>(ctx, nsteps) : do_step<double>(ctx, nsteps);
+}
+
+pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!dst || which < 0 || which >= PIC_NFIELDS || (where != PIC_HOST && where != PIC_DEVICE))
+    return fail(ctx, PIC_EINVAL, "bad destination or field id");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_get_field<float>(ctx, which, dst, where)
+                   : do_get_field<double>(ctx, which, dst, where);
+}
+
+pic_status pic_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, int where) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!n || (where != PIC_HOST && where != PIC_DEVICE)) return fail(ctx, PIC_EINVAL, "bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_get_particles<float>(ctx, out, cap, n, where)
+                   : do_get_particles<double>(ctx, out, cap, n, where);
+}
+
+pic_status pic_diag(pic_ctx *ctx, pic_diag_t *out) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!out) return fail(ctx, PIC_EINVAL, "null output");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_diag<float>(ctx, out) : do_diag<double>(ctx, out);
+}
+
+pic_status pic_sync(pic_ctx *ctx) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  CK(cudaSetDevice(ctx->cfg.device));
+  return poll_device(ctx);
+}
+
+pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!bytes) return fail(ctx, PIC_EINVAL, "null size");
+  const size_t need = snapshot_bytes(ctx);
+  if (!host) {
+    *bytes = need;
+    return PIC_OK;
+  }
+  if (*bytes < need) return fail(ctx, PIC_EINVAL, "snapshot buffer too small");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const Geom &g = ctx->g;
+  char *p = (char *)host;
+  SnapHeader h{};
+  memcpy(h.magic, "PICSNAP1", 8);
+  h.nx = g.nx; h.ny = g.ny; h.P = g.P; h.Q = g.Q; h.fp32 = ctx->fp32;
+  h.cap = ctx->cap; h.bcap = ctx->bcap; h.nshift = ctx->nshift; h.col0 = ctx->col0;
+  h.step = ctx->step; h.t = ctx->t; h.prev_valid = ctx->prev_valid;
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  auto d2h = [&](const void *src, size_t n) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(p, src, n, cudaMemcpyDeviceToHost);
+    p += n;
+    return e;
+  };
+  CK(d2h(ctx->F, field_bytes(g, ctx->rs)));
+  CK(d2h(ctx->rho_bg, sizeof(double) * g.cs));
+  if (ctx->cap) {
+    for (int st = 0; st < 2; ++st) {
+      for (int a = 0; a < 6; ++a) CK(d2h(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
+      for (int a = 0; a < 6; ++a) CK(d2h(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * 8 * ctx->bcap));
+      CK(d2h(ctx->cnt[st], sizeof(int) * g.nslots));
+      CK(d2h(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
+    }
+  }
+  CK(d2h(ctx->st, sizeof(DevState)));
+  *bytes = need;
+  return PIC_OK;
+}
+
+pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
+  if (!ctx || !host) return PIC_EINVAL;
+  SnapHeader h;
+  if (bytes < sizeof h) return fail(ctx, PIC_EINVAL, "snapshot too small");
+  memcpy(&h, host, sizeof h);
+  const Geom &g = ctx->g;
+  if (memcmp(h.magic, "PICSNAP1", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
+      h.fp32 != (int)ctx->fp32)
+    return fail(ctx, PIC_EINVAL, "snapshot does not match this configuration");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h.cap != ctx->cap) {
+    if (ctx->cap) return fail(ctx, PIC_EINVAL, "snapshot capacity differs from this context's");
+    free_graphs(ctx);
+    if (h.cap) {
+      const pic_status s = ctx->fp32 ? alloc_particles<float>(ctx, h.cap) : alloc_particles<double>(ctx, h.cap);
+      if (s) return s;
+    }
+  }
+  ctx->cap = h.cap;
+  ctx->bcap = h.bcap;
+  const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
+                      (h.cap ? particle_bytes(g, h.cap, h.bcap, ctx->rs) : 0);
+  if (bytes < need) return fail(ctx, PIC_EINVAL, "snapshot truncated");
+  const char *p = (const char *)host + sizeof h;
+  auto h2d = [&](void *dst, size_t n) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);
+    p += n;
+    return e;
+  };
+  CK(h2d(ctx->F, field_bytes(g, ctx->rs)));
+  CK(h2d(ctx->rho_bg, sizeof(double) * g.cs));
+  if (h.cap) {
+    for (int st = 0; st < 2; ++st) {
+      for (int a = 0; a < 6; ++a) CK(h2d(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
+      for (int a = 0; a < 6; ++a) CK(h2d(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * 8 * ctx->bcap));
+      CK(h2d(ctx->cnt[st], sizeof(int) * g.nslots));
+      CK(h2d(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
+    }
+  }
+  DevState ds;
+  memcpy(&ds, p, sizeof ds);
+  ds.err = 0;
+  CK(cudaMemcpy(ctx->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
+  ctx->step = h.step;
+  ctx->t = h.t;
+  ctx->nshift = h.nshift;
+  ctx->col0 = h.col0;
+  ctx->prev_valid = h.prev_valid != 0;
+  ctx->sticky = PIC_OK;
+  ctx->err.clear();
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Internal definitions shared by the libpic CUDA translation units.
+//
+// Data layout in HBM (one context):
+//   fields   one allocation of NCOMP components, each a (ny + 2 GY) x sx
+//            array, x fastest; grid index (i, j) lives at
+//            (j + GY) * sx + (i + GX); sx is a multiple of 32 elements.
+//            Components: Ex Ey Ez Bmx Bmy Bmz | Bx By Bz | JA(x,y,z) |
+//            JB(x,y,z).  E and Bm are adjacent so one 3D TMA box stages all
+//            six interpolated components of a patch.  Ghost cells of a
+//            periodic axis hold mirror copies of the interior, written by
+//            the kernel that produces the value; ghost cells of an open axis
+//            hold the Silver-Mueller values.
+//   particles  per patch slot a segment of `cap` entries in six SoA arrays
+//            (x, y patch-relative in cell units; ux, uy, uz; w), two
+//            ping-pong sets; plus per slot 8 direction buckets of `bcap`
+//            entries (particles that left the slot, already rebased to the
+//            destination patch), two ping-pong sets.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr int GX = 4;  // ghost cells along x (keeps TMA box starts 16B aligned)
+constexpr int GY = 4;  // ghost cells along y
+constexpr int NCOMP = 15;
+enum {
+  C_EX = 0, C_EY, C_EZ, C_BMX, C_BMY, C_BMZ, C_BX, C_BY, C_BZ,
+  C_JA = 9, C_JB = 12
+};
+enum { FBC_PERIODIC = 0, FBC_SM = 1 };
+enum { PBC_PERIODIC = 0, PBC_REFLECT = 1, PBC_REMOVE = 2 };
+
+// Sticky device error bits.
+enum : unsigned {
+  ERR_OVERFLOW_SEG = 1u,
+  ERR_OVERFLOW_BKT = 2u,
+  ERR_NONFINITE = 4u,
+  ERR_FAST = 8u,
+  ERR_TIMEOUT = 16u,
+  ERR_LOAD_RANGE = 32u,
+  ERR_OVERFLOW_LOAD = 64u
+};
+
+// Device-resident state; t and step are double-buffered by step parity so
+// that the kernels of one step read slot p while the last one writes 1 - p.
+struct DevState {
+  double t[2];
+  long long step[2];
+  int nshift;
+  int col0;       // slot column holding physical patch column 0
+  unsigned err;
+  int maxcnt[2];  // fullest patch written by the particle step of parity p
+};
+
+struct Geom {
+  int nx, ny;       // cells
+  int P, Q;         // patch size (x, y)
+  int npx, npy, nslots;
+  int sx, nys;      // row stride, stored rows
+  long long cs;     // elements per component (sx * nys)
+  double dx, dy, dt;
+  int fbc_x, fbc_y;
+  int pbc[2][2];    // [axis][face]
+  double q, m;
+};
+
+template <typename R>
+struct SoA {
+  R *x, *y, *ux, *uy, *uz, *w;
+};
+
+// Direction k in 0..7 <-> (ddx, ddy), centre excluded.
+__host__ __device__ inline int dir_index(int ddx, int ddy) {
+  int code = (ddy + 1) * 3 + (ddx + 1);
+  return code < 4 ? code : code - 1;
+}
+__host__ __device__ inline void dir_delta(int k, int &ddx, int &ddy) {
+  int code = k < 4 ? k : k + 1;
+  ddx = code % 3 - 1;
+  ddy = code / 3 - 1;
+}
+
+// Neighbour slot of slot s in physical direction (ddx, ddy), or -1 when it
+// lies outside a non-periodic domain face.  Slot columns form a ring offset
+// by col0 (moving window); rows are not rotated.
+__host__ __device__ inline int neighbour_slot(const Geom &g, int col0, int s, int ddx,
+                                              int ddy) {
+  int sxs = s % g.npx, sy = s / g.npx;
+  int px = sxs - col0;
+  if (px < 0) px += g.npx;
+  int qx = px + ddx, qy = sy + ddy;
+  if (qx < 0 || qx >= g.npx) {
+    if (g.fbc_x != FBC_PERIODIC) return -1;
+    qx = (qx + g.npx) % g.npx;
+  }
+  if (qy < 0 || qy >= g.npy) {
+    if (g.fbc_y != FBC_PERIODIC) return -1;
+    qy = (qy + g.npy) % g.npy;
+  }
+  int qs = (qx + col0) % g.npx;
+  return qy * g.npx + qs;
+}
+
+__host__ __device__ inline long long fidx(const Geom &g, int i, int j) {
+  return (long long)(j + GY) * g.sx + (i + GX);
+}
+
+// Store v at (i, j) of component array a and at every periodic ghost image
+// of (i, j) that lies in the stored range.
+template <typename R>
+__device__ inline void store_mirrored(const Geom &g, R *a, int i, int j, R v) {
+  a[fidx(g, i, j)] = v;
+  const bool px = g.fbc_x == FBC_PERIODIC, py = g.fbc_y == FBC_PERIODIC;
+  int ix[2] = {i, i}, jy[2] = {j, j};
+  int nix = 1, njy = 1;
+  if (px) {
+    if (i < GX) ix[nix++] = i + g.nx;
+    else if (i >= g.nx - GX) ix[nix++] = i - g.nx;
+  }
+  if (py) {
+    if (j < GY) jy[njy++] = j + g.ny;
+    else if (j >= g.ny - GY) jy[njy++] = j - g.ny;
+  }
+  for (int b = 0; b < njy; ++b)
+    for (int c = 0; c < nix; ++c)
+      if (b || c) a[fidx(g, ix[c], jy[b])] = v;
+}
+
+// Quadratic B-spline weights of the nodes i0-1, i0, i0+1 for a coordinate
+// xi (in cells): i0 = floor(xi + 1/2), delta = xi - i0.
+template <typename R>
+__device__ __forceinline__ int shape2(R xi, R S[3]) {
+  R fl = floor(xi + R(0.5));
+  R d = xi - fl;
+  R a = R(0.5) - d, b = R(0.5) + d;
+  S[0] = R(0.5) * a * a;
+  S[1] = R(0.75) - d * d;
+  S[2] = R(0.5) * b * b;
+  return (int)fl;
+}
+
+// --- TMA / mbarrier helpers (inline PTX, sm_90+ forms valid on sm_103a) ---
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Bound on mbarrier polls before a wait is declared lost (each try_wait
+// suspends for up to a hardware time slice, so this is far beyond any real
+// copy latency) and the second bound used to drain an in-flight copy before
+// the block returns.
+constexpr long long WAIT_POLLS = 1ll << 24;
+constexpr long long DRAIN_POLLS = 1ll << 22;
+
+// ----------------------------------------------------------- launchers ---
+template <typename R>
+struct StepArgs {
+  Geom g;
+  const R *F;          // field base (component 0)
+  R *Jdst;             // current set deposited into (3 comps, g.cs apart)
+  SoA<R> pin, pout;    // patch segments, read / written
+  const int *cnt_in;
+  int *cnt_out;
+  SoA<R> bin, bout;    // direction buckets, read / written
+  const int *bcnt_in;
+  int *bcnt_out;
+  int cap, bcap;
+  int parity;
+  DevState *st;
+};
+
+template <typename R>
+cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
+                                 int block, cudaStream_t s);
+// Raise the dynamic shared-memory limit of the step kernels (call outside
+// stream capture).
+template <typename R>
+cudaError_t prepare_particle_step(int P, int Q);
+size_t particle_step_smem(int P, int Q, size_t rsize);
+
+template <typename R>
+struct FieldArgs {
+  Geom g;
+  R *F;
+  int parity;          // J set read = C_JA + 3 * parity, zeroed = the other
+  DevState *st;
+  // laser
+  int laser_on;
+  double a0, waist, tau, t_peak, yc;
+};
+template <typename R>
+cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s);
+
+// Field I/O and utilities.
+template <typename R>
+cudaError_t launch_set_field(const Geom &g, R *arr, const double *src, cudaStream_t s);
+template <typename R>
+cudaError_t launch_get_field(const Geom &g, const R *arr, double *dst, cudaStream_t s);
+cudaError_t launch_get_field_f64(const Geom &g, const double *arr, double *dst, cudaStream_t s);
+cudaError_t launch_set_field_f64(const Geom &g, double *arr, const double *src, cudaStream_t s);
+template <typename R>
+cudaError_t launch_shift_fields(const Geom &g, R *F, int ncomp, cudaStream_t s);
+cudaError_t launch_shift_f64(const Geom &g, double *a, cudaStream_t s);
+
+// Particles.
+template <typename R>
+cudaError_t launch_bin_count(const Geom &g, int col0, const double *x, const double *y, size_t n,
+                             int *counts, unsigned *err, cudaStream_t s);
+cudaError_t launch_clamp_counts(int *cnt, int n, int cap, cudaStream_t s);
+template <typename R>
+cudaError_t launch_bin_place(const Geom &g, int col0, const double *x, const double *y,
+                             const double *ux, const double *uy, const double *uz,
+                             const double *w, size_t n, SoA<R> seg, int *counts, int cap,
+                             unsigned *err, cudaStream_t s);
+template <typename R>
+struct PartView {
+  SoA<R> seg;
+  const int *cnt;
+  SoA<R> bkt;
+  const int *bcnt;
+  int cap, bcap;
+};
+template <typename R>
+cudaError_t launch_deposit_rho(const Geom &g, int col0, const PartView<R> &v, double *rho,
+                               double sign, cudaStream_t s);
+template <typename R>
+cudaError_t launch_particle_diag(const Geom &g, int col0, const PartView<R> &v, double *partials,
+                                 int nblocks, cudaStream_t s);
+template <typename R>
+cudaError_t launch_field_diag(const Geom &g, const R *F, double *partials, int nblocks,
+                              cudaStream_t s);
+template <typename R>
+cudaError_t launch_gauss_diag(const Geom &g, const R *F, int jset, const double *rho,
+                              const double *rho_prev, const double *rho_bg, double *partials,
+                              int nblocks, cudaStream_t s);
+template <typename R>
+cudaError_t launch_get_particles(const Geom &g, int col0, const PartView<R> &v,
+                                 const long long *offsets, double *out, size_t stride,
+                                 cudaStream_t s);
+// old_col0: ring offset before the shift; nshift: shifts including this one.
+template <typename R>
+cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,
+                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, int bcap,
+                                    double n0, double x0, double ramp, int ppcx, int ppcy,
+                                    double *rho_bg, unsigned *err, cudaStream_t s);
+
+}  // namespace pic

@@ -1,0 +1,380 @@
+// Particle storage kernels: binning of loaded particles into patch segments,
+// the float64 charge deposit used by diagnostics, particle reductions,
+// read-back in global coordinates and the moving-window bookkeeping
+// (migration of in-flight particles, removal of the leaving column and
+// injection of plasma in the new one).
+#include "common.cuh"
+
+namespace pic {
+
+namespace {
+
+__device__ __forceinline__ bool locate(const Geom &g, int col0, double x, double y, int &slot,
+                                       int &px, int &py) {
+  const double cx = x / g.dx, cy = y / g.dy;
+  if (!(cx >= 0.0 && cx < (double)g.nx && cy >= 0.0 && cy < (double)g.ny)) return false;
+  px = (int)floor(cx) / g.P;
+  py = (int)floor(cy) / g.Q;
+  if (px >= g.npx) px = g.npx - 1;
+  if (py >= g.npy) py = g.npy - 1;
+  slot = py * g.npx + (px + col0) % g.npx;
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ R rel(double c, int origin, int P) {
+  double v = c - (double)origin;
+  R r = R(v);
+  if (r < R(0)) r = R(0);
+  if (r >= R(P)) r = nextafter(R(P), R(0));
+  return r;
+}
+
+template <typename R>
+__global__ void k_bin_count(const Geom g, int col0, const double *x, const double *y, size_t n,
+                            int *counts, unsigned *err) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int slot, px, py;
+    if (!locate(g, col0, x[k], y[k], slot, px, py)) {
+      atomicOr(err, ERR_LOAD_RANGE);
+      continue;
+    }
+    atomicAdd(&counts[slot], 1);
+  }
+}
+
+template <typename R>
+__global__ void k_bin_place(const Geom g, int col0, const double *x, const double *y,
+                            const double *ux, const double *uy, const double *uz,
+                            const double *w, size_t n, SoA<R> seg, int *counts, int cap,
+                            unsigned *err) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int slot, px, py;
+    if (!locate(g, col0, x[k], y[k], slot, px, py)) continue;
+    const int pos = atomicAdd(&counts[slot], 1);
+    if (pos >= cap) {
+      atomicOr(err, ERR_OVERFLOW_LOAD);
+      continue;
+    }
+    const long long i = (long long)slot * cap + pos;
+    seg.x[i] = rel<R>(x[k] / g.dx, px * g.P, g.P);
+    seg.y[i] = rel<R>(y[k] / g.dy, py * g.Q, g.Q);
+    seg.ux[i] = R(ux[k]);
+    seg.uy[i] = R(uy[k]);
+    seg.uz[i] = R(uz[k]);
+    seg.w[i] = R(w[k]);
+  }
+}
+
+__global__ void k_clamp_counts(int *cnt, int n, int cap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cnt[i] > cap) cnt[i] = cap;
+}
+
+// Origin (in cells) of the physical patch held by a slot.
+__device__ __forceinline__ void slot_origin(const Geom &g, int col0, int slot, int &X0, int &Y0) {
+  int px = slot % g.npx - col0;
+  if (px < 0) px += g.npx;
+  X0 = px * g.P;
+  Y0 = (slot / g.npx) * g.Q;
+}
+
+// Visit every particle of a view: blocks walk slots; each slot's segment and
+// its 8 outgoing buckets (bucket particles are expressed in the frame of the
+// destination patch).
+template <typename R, typename Fn>
+__device__ void for_each_particle(const Geom &g, int col0, const PartView<R> &v, Fn fn) {
+  for (int slot = blockIdx.x; slot < g.nslots; slot += gridDim.x) {
+    int X0, Y0;
+    slot_origin(g, col0, slot, X0, Y0);
+    const int n = v.cnt[slot];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const long long i = (long long)slot * v.cap + k;
+      fn(X0, Y0, v.seg.x[i], v.seg.y[i], v.seg.ux[i], v.seg.uy[i], v.seg.uz[i], v.seg.w[i]);
+    }
+    for (int d = 0; d < 8; ++d) {
+      const int nb = v.bcnt[(long long)slot * 8 + d];
+      if (nb == 0) continue;
+      int ddx, ddy;
+      dir_delta(d, ddx, ddy);
+      const int dest = neighbour_slot(g, col0, slot, ddx, ddy);
+      if (dest < 0) continue;
+      int DX0, DY0;
+      slot_origin(g, col0, dest, DX0, DY0);
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const long long i = ((long long)slot * 8 + d) * v.bcap + k;
+        fn(DX0, DY0, v.bkt.x[i], v.bkt.y[i], v.bkt.ux[i], v.bkt.uy[i], v.bkt.uz[i], v.bkt.w[i]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void shape_d(double xi, int &i0, double S[3]) {
+  const double fl = floor(xi + 0.5);
+  const double d = xi - fl;
+  S[0] = 0.5 * (0.5 - d) * (0.5 - d);
+  S[1] = 0.75 - d * d;
+  S[2] = 0.5 * (0.5 + d) * (0.5 + d);
+  i0 = (int)fl;
+}
+
+__device__ __forceinline__ void deposit_node(const Geom &g, double *rho, int X0, int Y0, double xr,
+                                             double yr, double qw) {
+  int i0, j0;
+  double Sx[3], Sy[3];
+  shape_d(xr, i0, Sx);
+  shape_d(yr, j0, Sy);
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      int gi = X0 + i0 - 1 + a, gj = Y0 + j0 - 1 + b;
+      if (g.fbc_x == FBC_PERIODIC) gi = (gi + g.nx) % g.nx;
+      if (g.fbc_y == FBC_PERIODIC) gj = (gj + g.ny) % g.ny;
+      atomicAdd(&rho[fidx(g, gi, gj)], qw * Sx[a] * Sy[b]);
+    }
+}
+
+template <typename R>
+__global__ void k_deposit_rho(const Geom g, int col0, const PartView<R> v, double *rho,
+                              double sign) {
+  const double qs = sign * g.q;
+  for_each_particle<R>(g, col0, v, [&](int X0, int Y0, R x, R y, R, R, R, R w) {
+    deposit_node(g, rho, X0, Y0, (double)x, (double)y, qs * (double)w);
+  });
+}
+
+template <typename R>
+__global__ void k_particle_diag(const Geom g, int col0, const PartView<R> v, double *partials) {
+  __shared__ double sh[3][256];
+  double ek = 0.0, ws = 0.0, cnt = 0.0;
+  for_each_particle<R>(g, col0, v, [&](int, int, R, R, R ux, R uy, R uz, R w) {
+    const double a = ux, b = uy, c = uz;
+    ek += (double)w * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    ws += (double)w;
+    cnt += 1.0;
+  });
+  sh[0][threadIdx.x] = ek;
+  sh[1][threadIdx.x] = ws;
+  sh[2][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sh[q][0];
+}
+
+// offsets: [phys-order segment offsets (nslots)] [bucket offsets (nslots*8)]
+template <typename R>
+__global__ void k_get_particles(const Geom g, int col0, const PartView<R> v,
+                                const long long *offsets, double *out, size_t stride) {
+  const int pp = blockIdx.x;  // physical patch index
+  if (pp >= g.nslots) return;
+  const int ppx = pp % g.npx, ppy = pp / g.npx;
+  const int slot = ppy * g.npx + (ppx + col0) % g.npx;
+  auto emit = [&](long long o, int X0, int Y0, R x, R y, R ux, R uy, R uz, R w) {
+    out[o] = ((double)X0 + (double)x) * g.dx;
+    out[stride + o] = ((double)Y0 + (double)y) * g.dy;
+    out[2 * stride + o] = (double)ux;
+    out[3 * stride + o] = (double)uy;
+    out[4 * stride + o] = (double)uz;
+    out[5 * stride + o] = (double)w;
+  };
+  const int X0 = ppx * g.P, Y0 = ppy * g.Q;
+  const int n = v.cnt[slot];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const long long i = (long long)slot * v.cap + k;
+    emit(offsets[pp] + k, X0, Y0, v.seg.x[i], v.seg.y[i], v.seg.ux[i], v.seg.uy[i], v.seg.uz[i],
+         v.seg.w[i]);
+  }
+  for (int d = 0; d < 8; ++d) {
+    const int nb = v.bcnt[(long long)slot * 8 + d];
+    if (nb == 0) continue;
+    int ddx, ddy;
+    dir_delta(d, ddx, ddy);
+    const int dest = neighbour_slot(g, col0, slot, ddx, ddy);
+    if (dest < 0) continue;
+    int DX0, DY0;
+    slot_origin(g, col0, dest, DX0, DY0);
+    const long long base = offsets[g.nslots + (long long)pp * 8 + d];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      const long long i = ((long long)slot * 8 + d) * v.bcap + k;
+      emit(base + k, DX0, DY0, v.bkt.x[i], v.bkt.y[i], v.bkt.ux[i], v.bkt.uy[i], v.bkt.uz[i],
+           v.bkt.w[i]);
+    }
+  }
+}
+
+// Moving window, part 1 (old ring, col0 = old): particles that crossed from
+// the leaving column into the next one during the last step are still in the
+// leaving slots' +x buckets; append them to their destination segments, then
+// clear every bucket that points into or out of the leaving column.
+template <typename R>
+__global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, SoA<R> bkt,
+                                 int *bcnt, int cap, int bcap, unsigned *err) {
+  const int py = blockIdx.x;
+  const int sdrop = py * g.npx + col0;
+  const int snext = py * g.npx + (col0 + 1) % g.npx;
+  for (int ddy = -1; ddy <= 1; ++ddy) {
+    const int d = dir_index(1, ddy);
+    const int dest = neighbour_slot(g, col0, sdrop, 1, ddy);
+    const int nb = bcnt[(long long)sdrop * 8 + d];
+    if (dest < 0) continue;
+    __shared__ int base;
+    if (threadIdx.x == 0) base = atomicAdd(&cnt[dest], nb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      const int pos = base + k;
+      if (pos >= cap) {
+        atomicOr(err, ERR_OVERFLOW_SEG);
+        continue;
+      }
+      const long long i = ((long long)sdrop * 8 + d) * bcap + k;
+      const long long o = (long long)dest * cap + pos;
+      seg.x[o] = bkt.x[i]; seg.y[o] = bkt.y[i];
+      seg.ux[o] = bkt.ux[i]; seg.uy[o] = bkt.uy[i]; seg.uz[o] = bkt.uz[i]; seg.w[o] = bkt.w[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt[dest] > cap) cnt[dest] = cap;
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) {
+    bcnt[(long long)sdrop * 8 + threadIdx.x] = 0;
+    int ddx, ddy;
+    dir_delta(threadIdx.x, ddx, ddy);
+    if (ddx == -1) bcnt[(long long)snext * 8 + threadIdx.x] = 0;
+  }
+}
+
+// Moving window, part 2 (new ring): the leaving slots now hold the new
+// column (physical npx - 1); fill them with plasma at rest, regularly placed,
+// weight = density / ppc at the particle's x in the laboratory frame, and add
+// the co-located immobile ions to the background charge.
+template <typename R>
+__global__ void k_window_inject(const Geom g, int slot_col, int nshift, SoA<R> seg, int *cnt,
+                                int cap, double n0, double x0, double ramp, int ppcx, int ppcy,
+                                double *rho_bg, unsigned *err) {
+  const int py = blockIdx.x;
+  const int slot = py * g.npx + slot_col;
+  const int ppc = ppcx * ppcy;
+  const int total = g.P * g.Q * ppc;
+  if (total > cap) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW_SEG);
+    return;
+  }
+  const int X0 = (g.npx - 1) * g.P, Y0 = py * g.Q;
+  const double shift = __dmul_rn((double)nshift * g.P, g.dx);
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    // order: cell row, cell column, sub-row, sub-column
+    const int a = k % ppcx, b = (k / ppcx) % ppcy, cell = k / ppc;
+    const int ci = cell % g.P, cj = cell / g.P;
+    const double fx = (a + 0.5) / ppcx, fy = (b + 0.5) / ppcy;
+    const double xl = ((double)(X0 + ci) + fx) * g.dx;
+    const double xphys = __dadd_rn(xl, shift);
+    double n;
+    if (ramp <= 0.0) {
+      n = xphys >= x0 ? n0 : 0.0;
+    } else {
+      double f = (xphys - x0) / ramp;
+      f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+      n = n0 * f;
+    }
+    const double w = n / ppc;
+    const long long o = (long long)slot * cap + k;
+    seg.x[o] = R((double)ci + fx);
+    seg.y[o] = R((double)cj + fy);
+    seg.ux[o] = R(0);
+    seg.uy[o] = R(0);
+    seg.uz[o] = R(0);
+    seg.w[o] = R(w);
+    if (rho_bg) deposit_node(g, rho_bg, X0, Y0, (double)ci + fx, (double)cj + fy, -g.q * (double)R(w));
+  }
+  if (threadIdx.x == 0) cnt[slot] = total;
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_bin_count(const Geom &g, int col0, const double *x, const double *y, size_t n,
+                             int *counts, unsigned *err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+  k_bin_count<R><<<blocks, 256, 0, s>>>(g, col0, x, y, n, counts, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clamp_counts(int *cnt, int n, int cap, cudaStream_t s) {
+  k_clamp_counts<<<(n + 255) / 256, 256, 0, s>>>(cnt, n, cap);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_bin_place(const Geom &g, int col0, const double *x, const double *y,
+                             const double *ux, const double *uy, const double *uz,
+                             const double *w, size_t n, SoA<R> seg, int *counts, int cap,
+                             unsigned *err, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+  k_bin_place<R><<<blocks, 256, 0, s>>>(g, col0, x, y, ux, uy, uz, w, n, seg, counts, cap, err);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_deposit_rho(const Geom &g, int col0, const PartView<R> &v, double *rho,
+                               double sign, cudaStream_t s) {
+  k_deposit_rho<R><<<g.nslots, 256, 0, s>>>(g, col0, v, rho, sign);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_particle_diag(const Geom &g, int col0, const PartView<R> &v, double *partials,
+                                 int nblocks, cudaStream_t s) {
+  k_particle_diag<R><<<nblocks, 256, 0, s>>>(g, col0, v, partials);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_get_particles(const Geom &g, int col0, const PartView<R> &v,
+                                 const long long *offsets, double *out, size_t stride,
+                                 cudaStream_t s) {
+  k_get_particles<R><<<g.nslots, 256, 0, s>>>(g, col0, v, offsets, out, stride);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,
+                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, int bcap,
+                                    double n0, double x0, double ramp, int ppcx, int ppcy,
+                                    double *rho_bg, unsigned *err, cudaStream_t s) {
+  k_window_migrate<R><<<g.npy, 256, 0, s>>>(g, old_col0, seg, cnt, bkt, bcnt, cap, bcap, err);
+  k_window_inject<R><<<g.npy, 256, 0, s>>>(g, old_col0, nshift, seg, cnt, cap, n0, x0, ramp,
+                                            ppcx, ppcy, rho_bg, err);
+  return cudaGetLastError();
+}
+
+#define PIC_INST(R)                                                                           \
+  template cudaError_t launch_bin_count<R>(const Geom &, int, const double *, const double *, \
+                                           size_t, int *, unsigned *, cudaStream_t);          \
+  template cudaError_t launch_bin_place<R>(const Geom &, int, const double *, const double *, \
+                                           const double *, const double *, const double *,    \
+                                           const double *, size_t, SoA<R>, int *, int,        \
+                                           unsigned *, cudaStream_t);                         \
+  template cudaError_t launch_deposit_rho<R>(const Geom &, int, const PartView<R> &, double *, \
+                                             double, cudaStream_t);                           \
+  template cudaError_t launch_particle_diag<R>(const Geom &, int, const PartView<R> &,        \
+                                               double *, int, cudaStream_t);                  \
+  template cudaError_t launch_get_particles<R>(const Geom &, int, const PartView<R> &,        \
+                                               const long long *, double *, size_t,           \
+                                               cudaStream_t);                                 \
+  template cudaError_t launch_window_particles<R>(const Geom &, int, int, SoA<R>, int *,      \
+                                                  SoA<R>, int *, int, int, double, double,    \
+                                                  double, int, int, double *, unsigned *,     \
+                                                  cudaStream_t);
+PIC_INST(float)
+PIC_INST(double)
+#undef PIC_INST
+
+}  // namespace pic

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libpic (include/pic.h).
+
+Argument marshalling only: every step of the particle-in-cell path runs in
+the library's sm_103a kernels.  The functions keep the C names
+(``pic_create``, ``pic_load_particles``, ``pic_step``, ``pic_get_field``,
+``pic_diag`` ...); :class:`Pic` bundles them for one context.  Host buffers
+are numpy float64 arrays; device buffers are torch CUDA tensors (torch only
+provides device memory and streams).
+
+The library must be built (``paper_1912_04064_gb300.build.build()``); there
+is no fallback: importing the binding without ``libpic.so`` raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpic.so")
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENONFINITE, PIC_ESTATE = range(8)
+STATUS = ["PIC_OK", "PIC_EINVAL", "PIC_ENOMEM", "PIC_ECUDA", "PIC_EOVERFLOW", "PIC_ETIMEOUT",
+          "PIC_ENONFINITE", "PIC_ESTATE"]
+PIC_FP64, PIC_FP32 = 0, 1
+PIC_HOST, PIC_DEVICE = 0, 1
+FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz", "Jx", "Jy", "Jz", "rho", "rho_bg"]
+FBC = {"periodic": 0, "sm": 1}
+PBC = {"periodic": 0, "reflect": 1, "remove": 2}
+BG = {"none": 0, "uniform": 1, "neutralising": 2}
+
+
+class pic_config(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int), ("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
+        ("patch", C.c_int * 3), ("prec", C.c_int), ("bc_field", C.c_int * 3),
+        ("bc_part", (C.c_int * 2) * 3), ("q", C.c_double), ("m", C.c_double),
+        ("laser_on", C.c_int), ("laser_a0", C.c_double), ("laser_waist", C.c_double),
+        ("laser_tau", C.c_double), ("laser_t_peak", C.c_double), ("laser_y_center", C.c_double),
+        ("moving_window", C.c_int), ("mw_t0", C.c_double),
+        ("inj_n0", C.c_double), ("inj_x0", C.c_double), ("inj_ramp", C.c_double),
+        ("inj_ppc", C.c_int * 3), ("capacity_factor", C.c_double), ("capacity_min", C.c_int),
+        ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
+        ("tma", C.c_int), ("block", C.c_int),
+    ]
+
+
+class pic_diag_t(C.Structure):
+    _fields_ = [
+        ("step", C.c_longlong), ("t", C.c_double), ("np", C.c_longlong),
+        ("U_E", C.c_double), ("U_B", C.c_double), ("U_K", C.c_double),
+        ("gauss", C.c_double), ("continuity", C.c_double), ("charge", C.c_double),
+        ("shifts", C.c_int), ("max_patch_count", C.c_int), ("capacity", C.c_int),
+        ("ms_particles", C.c_double), ("ms_fields", C.c_double), ("ms_window", C.c_double),
+        ("launches", C.c_longlong), ("particle_step_launches", C.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_background", "pic_step",
+           "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync", "pic_snapshot",
+           "pic_restore", "pic_footprint", "pic_last_error", "pic_destroy", "pic_version"]
+
+_lib = None
+
+
+def lib():
+    """Load libpic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpic.so not built at {LIB_PATH}: run paper_1912_04064_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, sz = C.c_void_p, C.c_void_p, C.c_size_t
+        L.pic_create.argtypes = [C.POINTER(pic_config), C.POINTER(C.c_void_p)]
+        L.pic_load_particles.argtypes = [vp] + [dp] * 6 + [sz, C.c_int]
+        L.pic_set_field.argtypes = [vp, C.c_int, dp, C.c_int]
+        L.pic_set_background.argtypes = [vp, C.c_int, C.c_double]
+        L.pic_step.argtypes = [vp, C.c_int]
+        L.pic_get_field.argtypes = [vp, C.c_int, dp, C.c_int]
+        L.pic_get_particles.argtypes = [vp, dp, sz, C.POINTER(C.c_size_t), C.c_int]
+        L.pic_diag.argtypes = [vp, C.POINTER(pic_diag_t)]
+        L.pic_sync.argtypes = [vp]
+        L.pic_snapshot.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.pic_restore.argtypes = [vp, vp, sz]
+        L.pic_footprint.argtypes = [C.POINTER(pic_config), sz]
+        L.pic_footprint.restype = sz
+        L.pic_last_error.argtypes = [vp]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_destroy.argtypes = [vp]
+        L.pic_destroy.restype = None
+        L.pic_version.restype = C.c_char_p
+        for name in ("pic_create", "pic_load_particles", "pic_set_field", "pic_set_background",
+                     "pic_step", "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync",
+                     "pic_snapshot", "pic_restore"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
+        self.status = status
+
+
+def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
+                    use_graph: bool = True, timing: bool = False, tma: bool = True,
+                    capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0) -> pic_config:
+    """pic_config of a run dictionary (see ``workloads``)."""
+    c = pic_config()
+    c.dims = 2
+    c.n[0], c.n[1], c.n[2] = run["n"][0], run["n"][1], 1
+    c.d[0], c.d[1], c.d[2] = run["d"][0], run["d"][1], 1.0
+    c.dt = run["dt"]
+    c.patch[0], c.patch[1], c.patch[2] = run["patch"][0], run["patch"][1], 1
+    c.prec = PIC_FP32 if prec in ("fp32", PIC_FP32) else PIC_FP64
+    c.bc_field[0], c.bc_field[1] = (FBC[b] for b in run["field_bc"])
+    for a in range(2):
+        for f in range(2):
+            c.bc_part[a][f] = PBC[run["part_bc"][a][f]]
+    c.q = run.get("q", -1.0)
+    c.m = run.get("m", 1.0)
+    las = run.get("laser")
+    if las:
+        c.laser_on = 1
+        c.laser_a0, c.laser_waist, c.laser_tau = las["a0"], las["waist"], las["tau"]
+        c.laser_t_peak, c.laser_y_center = las["t_peak"], las["y_center"]
+    mw = run.get("moving_window")
+    if mw:
+        c.moving_window = 1
+        c.mw_t0 = mw["t0"]
+    inj = run.get("injection")
+    if inj:
+        c.inj_n0, c.inj_x0, c.inj_ramp = inj["n0"], inj["x0"], inj["ramp"]
+        c.inj_ppc[0], c.inj_ppc[1], c.inj_ppc[2] = inj["ppc"][0], inj["ppc"][1], 1
+    else:
+        c.inj_ppc[0] = c.inj_ppc[1] = c.inj_ppc[2] = 1
+    c.capacity_factor = capacity_factor
+    c.capacity_min = capacity_min
+    c.stream = stream
+    c.device = device
+    c.use_graph = int(use_graph)
+    c.timing = int(timing)
+    c.tma = 1 if tma else 0
+    c.block = block
+    return c
+
+
+def pic_footprint(cfg: pic_config, np_max: int) -> int:
+    return lib().pic_footprint(C.byref(cfg), np_max)
+
+
+def pic_version() -> str:
+    return lib().pic_version().decode()
+
+
+def _ptr(a):
+    """Pointer and location of a host numpy array or a CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, PIC_HOST
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), (PIC_DEVICE if a.is_cuda else PIC_HOST)
+    raise TypeError(type(a))
+
+
+class Pic:
+    """One libpic context (C-ABI calls with argument marshalling)."""
+
+    def __init__(self, cfg: pic_config):
+        self.cfg = cfg
+        self.h = C.c_void_p()
+        self._check(lib().pic_create(C.byref(cfg), C.byref(self.h)), create=True)
+        nx, ny = cfg.n[0], cfg.n[1]
+        self.shape = (ny if cfg.bc_field[1] == 0 else ny + 2, nx if cfg.bc_field[0] == 0 else nx + 2)
+
+    def _check(self, rc, create=False):
+        if rc != PIC_OK:
+            msg = "" if create or not self.h else lib().pic_last_error(self.h).decode()
+            raise PicError(rc, msg or "pic_create rejected the configuration")
+
+    def close(self):
+        if self.h:
+            lib().pic_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI calls
+    def pic_load_particles(self, p: dict):
+        """Particles as a dict of float64 arrays (numpy: host, torch CUDA: device)."""
+        arrs = []
+        for k in ("x", "y", "ux", "uy", "uz", "w"):
+            a = p[k]
+            if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+            arrs.append(a)
+        ptrs = [_ptr(a) for a in arrs]
+        where = ptrs[0][1]
+        n = int(arrs[0].shape[0])
+        self._check(lib().pic_load_particles(self.h, *[q for q, _ in ptrs], n, where))
+
+    def pic_set_field(self, name: str, a):
+        if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        if tuple(a.shape) != self.shape:
+            raise ValueError(f"{name}: shape {tuple(a.shape)} != {self.shape}")
+        q, where = _ptr(a)
+        self._check(lib().pic_set_field(self.h, FIELDS.index(name), q, where))
+
+    def pic_set_background(self, mode: str, value: float = 0.0):
+        self._check(lib().pic_set_background(self.h, BG[mode], value))
+
+    def pic_step(self, n: int = 1):
+        self._check(lib().pic_step(self.h, int(n)))
+
+    def pic_get_field(self, name: str, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        q, where = _ptr(out)
+        self._check(lib().pic_get_field(self.h, FIELDS.index(name), q, where))
+        return out
+
+    def pic_get_particles(self) -> dict:
+        n = C.c_size_t()
+        self._check(lib().pic_get_particles(self.h, None, 0, C.byref(n), PIC_HOST))
+        cap = max(n.value, 1)
+        out = np.empty((6, cap), dtype=np.float64)
+        self._check(lib().pic_get_particles(self.h, out.ctypes.data, cap, C.byref(n), PIC_HOST))
+        m = n.value
+        return {k: out[i, :m].copy() for i, k in enumerate(("x", "y", "ux", "uy", "uz", "w"))}
+
+    def pic_diag(self) -> dict:
+        d = pic_diag_t()
+        self._check(lib().pic_diag(self.h, C.byref(d)))
+        return d.as_dict()
+
+    def pic_sync(self):
+        self._check(lib().pic_sync(self.h))
+
+    def pic_snapshot(self) -> bytes:
+        n = C.c_size_t()
+        self._check(lib().pic_snapshot(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib().pic_snapshot(self.h, buf, C.byref(n)))
+        return buf.raw
+
+    def pic_restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(lib().pic_restore(self.h, buf, len(blob)))
+
+    def last_error(self) -> str:
+        return lib().pic_last_error(self.h).decode() if self.h else ""

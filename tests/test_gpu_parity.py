@@ -1,0 +1,308 @@
+"""GPU (libpic, sm_103a) against the FP64 CPU oracle, through the C-ABI.
+
+Single steps from identical states (FP64 tolerance 1e-12 relative max-norm
+per component, allowing for atomic-order differences in the current sums),
+multi-step and energy histories, the open-boundary / laser / moving-window
+path, edge cases (empty patches, one full patch, particles on patch corners
+and on the periodic seam), FP32 error bounds, and the error paths.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import poisson_periodic
+from paper_1912_04064_gb300 import pic
+from paper_1912_04064_gb300 import workloads as W
+
+from parity_utils import FIELD_NAMES, field_errors, pair, particle_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+# FP32 single step from an FP64 state: fields carry FP32 rounding (eps 6e-8)
+# plus dt x the current error; the current's relative error is bounded by
+# eps / (displacement in cells) through the S1 - S0 differences of the
+# Esirkepov weights (displacements >= 1e-2 cells here), so 2e-5 relative on
+# J and 2e-6 on E, B, Bm (max-norm relative per component).
+TOL32_J = 2e-5
+TOL32_F = 2e-6
+
+
+def _assert_fields(errs, tol, names=FIELD_NAMES):
+    bad = {k: v for k, v in errs.items() if k in names and not v <= tol}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("patch", [(4, 4), (8, 8), (16, 16), (32, 16), (16, 32)])
+def test_single_step_fp64_periodic(patch):
+    run = W.periodic_run((64, 64), (0.1, 0.1), patch)
+    parts = W.small_random_particles(run, 20000, seed=11, uth=0.5)
+    fields = W.random_fields((64, 64), seed=12, amp=0.1)
+    o, g = pair(run, parts, fields)
+    o.step(1)
+    g.pic_step(1)
+    errs = field_errors(o, g)
+    print("fp64 periodic", patch, max(errs.values()))
+    _assert_fields(errs, TOL64)
+    perr = particle_errors(o, g)
+    assert max(perr.values()) <= TOL64, perr
+
+
+@pytest.mark.parametrize("tma,graph", [(True, True), (False, True), (True, False)])
+def test_staging_and_graph_variants_agree(tma, graph):
+    run = W.periodic_run((96, 64), (0.1, 0.12), (16, 16))
+    parts = W.small_random_particles(run, 30000, seed=3, uth=0.4)
+    fields = W.random_fields((64, 96), seed=4, amp=0.1)
+    o, g = pair(run, parts, fields, tma=tma, use_graph=graph)
+    o.step(3)
+    g.pic_step(3)
+    _assert_fields(field_errors(o, g), 1e-11)
+
+
+def test_multi_step_fp64_periodic_thermal():
+    run, parts = W.thermal_2d(n=(128, 64), patch=(16, 16), seed=21)
+    o, g = pair(run, parts, background=("uniform", 1.0))
+    rho = o.field("rho") + 1.0
+    Ex, Ey = poisson_periodic(rho, *run["d"])
+    for k, v in (("Ex", Ex), ("Ey", Ey)):
+        o.set_field(k, v)
+        g.pic_set_field(k, v)
+    o.step(10)
+    g.pic_step(10)
+    errs = field_errors(o, g)
+    print("fp64 10 steps", max(errs.values()))
+    _assert_fields(errs, 1e-10)
+    do, dg = o.diag(), g.pic_diag()
+    assert dg["np"] == do["np"]
+    for k in ("U_E", "U_B", "U_K", "charge"):
+        assert abs(dg[k] - do[k]) <= 1e-11 * abs(do[k]), k
+    scale = np.max(np.abs(rho))
+    assert dg["gauss"] < 1e-10 * scale and do["gauss"] < 1e-10 * scale
+    assert dg["continuity"] < 1e-9 * scale / run["dt"]
+
+
+def test_energy_history_config1_100_steps():
+    """128x128 thermal plasma, 4 ppc, 16x16 patches, Poisson start, 100
+    steps: field and kinetic energy histories within 1e-3 of the oracle."""
+    run, parts = W.thermal_2d(seed=1)
+    o, g = pair(run, parts, background=("uniform", 1.0))
+    rho = o.field("rho") + 1.0
+    Ex, Ey = poisson_periodic(rho, *run["d"])
+    for k, v in (("Ex", Ex), ("Ey", Ey)):
+        o.set_field(k, v)
+        g.pic_set_field(k, v)
+    worst = 0.0
+    for _ in range(10):
+        o.step(10)
+        g.pic_step(10)
+        do, dg = o.diag(), g.pic_diag()
+        for k in ("U_E", "U_B", "U_K"):
+            worst = max(worst, abs(dg[k] - do[k]) / abs(do[k]))
+    print("config-1 energy history worst rel", worst)
+    assert worst <= 1e-3
+
+
+def _open_run(nx=128, ny=64, patch=(16, 16), laser=True):
+    run, _ = W.lwfa_2d(n=(nx, ny), d=(0.125, 0.5), patch=patch, ppc=(2, 2), ramp=4.0)
+    run["moving_window"] = None
+    if laser:
+        run["laser"] = {"a0": 2.0, "waist": 6.0, "tau": 4.0, "t_peak": 0.5, "y_center": ny * 0.25}
+    else:
+        run["laser"] = None
+    return run
+
+
+def test_single_step_fp64_open_laser_reflect_remove():
+    run = _open_run()
+    parts = W.small_random_particles(run, 20000, seed=5, uth=0.6)
+    shape = W.field_shape(run)
+    fields = W.random_fields(shape, seed=6, amp=0.1)
+    o, g = pair(run, parts, fields)
+    for _ in range(3):
+        o.step(1)
+        g.pic_step(1)
+        errs = field_errors(o, g)
+        _assert_fields(errs, TOL64)
+    perr = particle_errors(o, g)
+    assert max(perr.values()) <= TOL64, perr
+
+
+def test_moving_window_fp64():
+    run, parts = W.lwfa_2d(n=(128, 64), d=(0.125, 0.5), patch=(16, 16), ppc=(2, 2),
+                           ramp=6.0, t_mw=1.0, a0=1.0, waist=5.0, tau=3.0)
+    run["laser"]["t_peak"] = 6.0
+    rng = np.random.default_rng(9)
+    parts["ux"] = rng.normal(0, 0.3, parts["x"].size)
+    parts["uy"] = rng.normal(0, 0.3, parts["x"].size)
+    o, g = pair(run, parts, background=("neutralising", 0.0))
+    nsteps = 2 * math.ceil(16 * 0.125 / run["dt"]) + 12
+    for _ in range(nsteps):
+        o.step(1)
+        g.pic_step(1)
+    do, dg = o.diag(), g.pic_diag()
+    assert do["shifts"] >= 2 and dg["shifts"] == do["shifts"]
+    assert dg["np"] == do["np"]
+    errs = field_errors(o, g, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz"))
+    print("moving window", errs)
+    _assert_fields(errs, 1e-9)
+    perr = particle_errors(o, g)
+    assert max(perr.values()) <= 1e-9, perr
+    assert abs(dg["gauss"] - do["gauss"]) <= 1e-9 * max(do["gauss"], 1e-12) + 1e-12
+
+
+@pytest.mark.parametrize("case", ["empty_patches", "one_full_patch", "corners", "seam"])
+def test_edge_cases_fp64(case):
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    rng = np.random.default_rng(31)
+    if case == "empty_patches":
+        n = 3000
+        x = rng.uniform(1.6, 3.2, n)        # only patch column 1
+        y = rng.uniform(0.0, 1.6, n)        # only patch row 0
+    elif case == "one_full_patch":
+        n = 6000
+        x = rng.uniform(3.2, 4.8, n)
+        y = rng.uniform(3.2, 4.8, n)
+    elif case == "corners":
+        k = np.arange(4)
+        X, Y = np.meshgrid(k * 1.6, k * 1.6)
+        x = np.concatenate([X.ravel(), np.nextafter(X.ravel() + 1.6, 0)]) % 6.4
+        y = np.concatenate([Y.ravel(), np.nextafter(Y.ravel() + 1.6, 0)]) % 6.4
+        n = x.size
+    else:  # particles on the periodic seam, moving across it
+        n = 2000
+        x = np.concatenate([rng.uniform(0, 0.05, n // 2), rng.uniform(6.35, 6.4, n // 2)])
+        y = rng.uniform(0, 6.4, n)
+        x = np.minimum(x, np.nextafter(6.4, 0))
+    u = rng.normal(0, 0.6, (3, n))
+    parts = {"x": x, "y": y, "ux": u[0], "uy": u[1], "uz": u[2], "w": rng.uniform(0.5, 1.5, n)}
+    fields = W.random_fields((64, 64), seed=32, amp=0.1)
+    o, g = pair(run, parts, fields)
+    for _ in range(4):
+        o.step(1)
+        g.pic_step(1)
+    _assert_fields(field_errors(o, g), 1e-11)
+    assert max(particle_errors(o, g).values()) <= 1e-11
+
+
+def test_fp32_single_step_error_bounds():
+    run = W.periodic_run((128, 64), (0.1, 0.1), (16, 16))
+    parts = W.small_random_particles(run, 40000, seed=41, uth=0.5)
+    fields = W.random_fields((64, 128), seed=42, amp=0.1)
+    o, g = pair(run, parts, fields, prec="fp32")
+    o.step(1)
+    g.pic_step(1)
+    errs = field_errors(o, g)
+    print("fp32 single-step errors", errs)
+    _assert_fields(errs, TOL32_J, names=("Jx", "Jy", "Jz"))
+    _assert_fields(errs, TOL32_F, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz"))
+    perr = particle_errors(o, g)
+    print("fp32 particle errors", perr)
+    assert perr["x"] < 1e-6 and perr["y"] < 1e-6
+    assert max(perr[k] for k in ("ux", "uy", "uz")) < 1e-5
+
+
+def test_fp32_energy_history_config1():
+    run, parts = W.thermal_2d(seed=1)
+    o, g = pair(run, parts, prec="fp32", background=("uniform", 1.0))
+    rho = o.field("rho") + 1.0
+    Ex, Ey = poisson_periodic(rho, *run["d"])
+    for k, v in (("Ex", Ex), ("Ey", Ey)):
+        o.set_field(k, v)
+        g.pic_set_field(k, v)
+    worst = 0.0
+    for _ in range(10):
+        o.step(10)
+        g.pic_step(10)
+        do, dg = o.diag(), g.pic_diag()
+        for k in ("U_E", "U_K"):
+            worst = max(worst, abs(dg[k] - do[k]) / abs(do[k]))
+    print("fp32 config-1 energy history worst rel", worst)
+    assert worst <= 1e-2
+
+
+def test_snapshot_restore_resume():
+    run, parts = W.thermal_2d(n=(64, 64), patch=(16, 16), seed=51)
+    o, g = pair(run, parts, background=("uniform", 1.0))
+    g.pic_step(5)
+    blob = g.pic_snapshot()
+    g.pic_step(5)
+    ref = {k: g.pic_get_field(k) for k in ("Ex", "Ez", "Bz")}
+    g2 = pic.Pic(pic.config_from_run(run, "fp64"))
+    g2.pic_restore(blob)
+    g2.pic_step(5)
+    for k, v in ref.items():
+        assert np.max(np.abs(g2.pic_get_field(k) - v)) <= 1e-12 * np.max(np.abs(v)), k
+    assert g2.pic_diag()["step"] == 10
+
+
+def test_error_paths_are_reported_not_faulted():
+    run, parts = W.thermal_2d(n=(64, 64), patch=(16, 16), seed=61)
+    # particle outside the domain: rejected, context still usable
+    g = pic.Pic(pic.config_from_run(run, "fp64"))
+    bad = {k: np.array(v[:10]) for k, v in parts.items()}
+    bad["x"][3] = 1e6
+    with pytest.raises(pic.PicError) as e:
+        g.pic_load_particles(bad)
+    assert e.value.status == pic.PIC_EINVAL
+    g.pic_load_particles(parts)
+    blob = g.pic_snapshot()
+    # non-finite momentum: sticky ENONFINITE, then ESTATE until restore
+    g2 = pic.Pic(pic.config_from_run(run, "fp64"))
+    nan = {k: np.array(v) for k, v in parts.items()}
+    nan["ux"][7] = np.nan
+    g2.pic_load_particles(nan)
+    with pytest.raises(pic.PicError) as e:
+        g2.pic_step(1)
+    assert e.value.status == pic.PIC_ENONFINITE
+    with pytest.raises(pic.PicError) as e:
+        g2.pic_step(1)
+    assert e.value.status == pic.PIC_ESTATE
+    g2.pic_restore(blob)
+    g2.pic_step(2)
+    # capacity overflow: the first load sizes the patches, a second load
+    # crowds one patch beyond it
+    g3 = pic.Pic(pic.config_from_run(run, "fp64", capacity_factor=1.0, capacity_min=32))
+    few = {k: np.array(v[::64]) for k, v in parts.items()}
+    g3.pic_load_particles(few)
+    n = 400
+    rng = np.random.default_rng(1)
+    crowd = {"x": rng.uniform(0.1, 1.5, n), "y": rng.uniform(0.1, 1.5, n), "ux": np.zeros(n),
+             "uy": np.zeros(n), "uz": np.zeros(n), "w": np.ones(n)}
+    with pytest.raises(pic.PicError) as e:
+        g3.pic_load_particles(crowd)
+    assert e.value.status == pic.PIC_EOVERFLOW
+    with pytest.raises(pic.PicError) as e:
+        g3.pic_step(1)
+    assert e.value.status == pic.PIC_ESTATE
+
+
+def test_full_size_lwfa_single_step_fp64_and_fp32():
+    """The 2048x512, 32x32-patch, 4 ppc LWFA-shaped grid (4.19 M particles)
+    with random momenta and fields: one step through the C-ABI in the
+    launch configuration the benchmark uses, against the oracle."""
+    run, parts = W.lwfa_2d()
+    rng = np.random.default_rng(77)
+    n = parts["x"].size
+    for k in ("ux", "uy", "uz"):
+        parts[k] = rng.normal(0, 0.5, n)
+    shape = W.field_shape(run)
+    fields = W.random_fields(shape, seed=78, amp=0.05)
+    o, g = pair(run, parts, fields, background=("neutralising", 0.0))
+    o.step(1)
+    g.pic_step(1)
+    errs = field_errors(o, g)
+    print("full-size fp64", max(errs.values()))
+    _assert_fields(errs, TOL64)
+    assert g.pic_diag()["np"] == o.diag()["np"]
+    g.close()
+    g32 = pic.Pic(pic.config_from_run(run, "fp32"))
+    g32.pic_load_particles(parts)
+    for k, v in fields.items():
+        g32.pic_set_field(k, v)
+    g32.pic_step(1)
+    errs = {k: float(np.max(np.abs(g32.pic_get_field(k) - o.field(k))) / np.max(np.abs(o.field(k))))
+            for k in FIELD_NAMES}
+    print("full-size fp32", errs)
+    _assert_fields(errs, TOL32_J, names=("Jx", "Jy", "Jz"))
+    _assert_fields(errs, TOL32_F, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz"))
