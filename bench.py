@@ -1,0 +1,346 @@
+"""Benchmark of the patch-decomposed PIC hot path on GB300.
+
+Workload: the 2D3V LWFA-shaped run, 2048 x 512 cells (dx = 0.125,
+dy = 0.5 c/w0, dt = 0.95 CFL), 32 x 32-cell patches, 4 particles per cell
+(4 194 304 electrons at t = 0) on immobile ions with a 200 c/w0 linear
+ramp, Gaussian laser a0 = 2 (waist 20, 30/w0 FWHM) entering at x_min,
+moving window at c from t = 128.  The run is first advanced `--spinup`
+steps untimed (so the timed steps see the moving window and the wake, not
+a cold plasma at rest), then W warm-up steps, then exactly K timed steps.
+
+One JSON line is printed on rank 0:
+  value        particle-steps/s over all ranks (FP32 path, the headline)
+  fp64         the same for the FP64 path (its own run)
+  roofline     dominant kernel (the patch particle step): algorithmic bytes
+               per launch / mean launch time (CUDA events on the launching
+               stream) against the measured HBM copy bandwidth
+  e2e          the same metric through the C-ABI from host buffers:
+               H2D of the initial particles, K steps, D2H of fields and
+               particles inside the timed region
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the workload
+`--impl reference` times the oracle alone (the reference arm).
+
+Multi-GPU: the path is run as independent replicas (one per rank, no
+collective on the data path); value = particles x steps of all ranks /
+max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (push+deposit+FDTD) FP32 vs FP64; p50/p99 served-run latency"
+WORKLOAD = ("2D3V LWFA-shaped: 2048x512 cells, dx=0.125, dy=0.5 c/w0, dt=0.95 CFL, "
+            "32x32-cell patches, 4 ppc (4194304 electrons), immobile ions, 200 c/w0 ramp, "
+            "Gaussian laser a0=2 waist 20 tau 30, moving window at c")
+L2_BYTES = 129e6
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(npart, ncell, rsize):
+    """Bytes the method must move once per step: per particle read
+    x, y, ux, uy, uz, w and write x, y, ux, uy, uz (11 words); per cell gather
+    E and Bm (6), write J once (3), Yee read E, B, J (9), write E, B, Bm (9)."""
+    per_particle_step = 11 * rsize
+    per_cell_step = 27 * rsize
+    per_particle_kernel = 11 * rsize      # the particle step kernel alone
+    per_cell_kernel = 9 * rsize           # gather E, Bm (6) + J written once (3)
+    return (npart * per_particle_step + ncell * per_cell_step,
+            npart * per_particle_kernel + ncell * per_cell_kernel)
+
+
+def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist):
+    import torch
+
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    run, parts = W.lwfa_2d()
+    npart0 = parts["x"].size
+    ncell = run["n"][0] * run["n"][1]
+    rs = 4 if prec == "fp32" else 8
+    stream = torch.cuda.Stream(device=device)
+    cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
+                              use_graph=True, timing=False, capacity_factor=4.0)
+    g = pic.Pic(cfg)
+    g.pic_load_particles(parts)
+    g.pic_set_background("neutralising")
+    g.pic_step(spinup)
+    g.pic_step(warmup)
+    d0 = g.pic_diag()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    with ClockSampler(device) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g.pic_step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    d1 = g.pic_diag()
+    # per-kernel times over the same number of steps, CUDA events around each
+    # phase on the launching stream (no graph replay)
+    cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
+                                use_graph=False, timing=True, capacity_factor=4.0)
+    blob = g.pic_snapshot()
+    g.close()
+    gt = pic.Pic(cfg_t)
+    gt.pic_restore(blob)
+    t0 = gt.pic_diag()
+    gt.pic_step(steps)
+    t1 = gt.pic_diag()
+    gt.close()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{device}")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    np_mean = 0.5 * (d0["np"] + d1["np"])
+    total_ps = np_mean * steps * world
+    step_bytes, k_bytes = algorithmic_bytes(np_mean, ncell, rs)
+    ps_ms = (t1["ms_particles"] - t0["ms_particles"]) / steps
+    fd_ms = (t1["ms_fields"] - t0["ms_fields"]) / steps
+    return {
+        "value": total_ps / (ms_max / 1e3),
+        "ms_per_step": ms_max / steps,
+        "np": np_mean, "np0": npart0, "ncell": ncell, "rs": rs,
+        "step_bytes": step_bytes, "kernel_bytes": k_bytes,
+        "particle_step_ms": ps_ms, "fields_ms": fd_ms,
+        "window_ms": (t1["ms_window"] - t0["ms_window"]) / steps,
+        # kernels of the timed steps: the diagnostics call after them launched
+        # 5 reductions (+1 deposit when the continuity residual is available)
+        "launches": d1["launches"] - d0["launches"] - (5 + (0 if math.isnan(d1["continuity"]) else 1)),
+        "shifts": d1["shifts"], "t": d1["t"], "max_patch": d1["max_patch_count"],
+        "capacity": d1["capacity"], "clocks": clk.summary(),
+        "energy": {"U_E": d1["U_E"], "U_B": d1["U_B"], "U_K": d1["U_K"]},
+    }
+
+
+def run_e2e(prec, steps, device):
+    """Through the public C-ABI from host buffers: initial particles H2D,
+    `steps` steps, fields and particles D2H, all inside the timed region."""
+    import torch
+
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    run, parts = W.lwfa_2d()
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in parts.items()}
+    n = host["x"].size
+    cfg = pic.config_from_run(run, prec, device=device, use_graph=True, capacity_factor=4.0)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    g = pic.Pic(cfg)
+    g.pic_load_particles(host)
+    g.pic_set_background("neutralising")
+    g.pic_step(steps)
+    out = {}
+    for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz"):
+        out[k] = g.pic_get_field(k)
+    p = g.pic_get_particles()
+    t1 = time.perf_counter()
+    g.close()
+    h2d = 6 * 8 * n
+    d2h = sum(v.nbytes for v in out.values()) + 6 * 8 * p["x"].size
+    return {"value": n * steps / (t1 - t0), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "seconds": t1 - t0, "steps": steps}
+
+
+def cpu_oracle(steps, threads=0):
+    """The FP64 CPU oracle on the same workload from its initial state."""
+    from oracle.oracle import Oracle
+    from paper_1912_04064_gb300 import workloads as W
+
+    run, parts = W.lwfa_2d()
+    o = Oracle(run, nthreads=threads)
+    o.load(parts)
+    o.set_background("neutralising")
+    o.step(1)  # warm-up
+    n0 = o.diag()["np"]
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n1 = o.diag()["np"]
+    cores = threads or (os.cpu_count() or 1)
+    return {"value": 0.5 * (n0 + n1) * steps / dt, "unit": "particle-steps/s", "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{steps} steps of the full 2048x512 LWFA-shaped workload from t=0 "
+                      f"(after 1 warm-up step), FP64, OpenMP over patches"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--spinup", type=int, default=1200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        from oracle.oracle import Oracle  # noqa: F401  (builds the oracle)
+        w = max(0, min(args.warmup, 1))
+        steps = max(1, min(args.steps, args.cpu_steps))
+        cb = cpu_oracle(steps)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "particle-steps/s",
+                "n_gpus": args.gpus, "steps": steps, "warmup": w,
+                "ms_per_step": 1e3 * cb["seconds"] / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "arm": "FP64 CPU oracle, OpenMP over patches",
+                           "bounded_sample": cb["sample"]},
+                "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+                "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        dist = tdist
+    torch.cuda.set_device(local)
+    from paper_1912_04064_gb300 import build as pic_build
+    if rank == 0:
+        pic_build.build()
+    if dist:
+        dist.barrier()
+
+    r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist)
+    r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
+                  world, dist)
+    e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
+    cpu = cpu_oracle(args.cpu_steps) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    k_gbs = r32["kernel_bytes"] / (r32["particle_step_ms"] * 1e-3) / 1e9
+    step_gbs = r32["step_bytes"] / (r32["ms_per_step"] * 1e-3) / 1e9
+    ws = r32["np0"] * 3 * 6 * r32["rs"] + r32["ncell"] * 15 * r32["rs"]
+    line = {
+        "metric": METRIC, "value": r32["value"], "unit": "particle-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r32["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "prec": "fp32 (patch-relative positions, FP32 shared-memory J)",
+                   "particles_mean": r32["np"], "cells": r32["ncell"], "spinup_steps": args.spinup,
+                   "t_end": r32["t"], "window_shifts": r32["shifts"],
+                   "l2": f"no flush: working set {ws / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": "particle_step (TMA staging, gather, Boris, "
+                                                "Esirkepov, J reduction, re-binning)",
+                     "achieved": k_gbs, "peak": hbm, "unit": "GB/s", "frac": k_gbs / hbm,
+                     "peak_source": src, "traffic": None,
+                     "bytes_per_launch": r32["kernel_bytes"], "launch_ms": r32["particle_step_ms"],
+                     "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
+                                    "bytes_per_step": r32["step_bytes"]}},
+        "phases_ms": {"particle_step": r32["particle_step_ms"], "fields": r32["fields_ms"],
+                      "window": r32["window_ms"]},
+        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": args.fp64_steps,
+                 "particle_step_ms": r64["particle_step_ms"], "fields_ms": r64["fields_ms"],
+                 "speedup_fp32_over_fp64": r32["value"] / r64["value"],
+                 "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm},
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+    }
+    if e2e:
+        line["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+        line["e2e"]["note"] = (f"C-ABI from pinned host buffers: H2D of the {r32['np0']} initial particles, "
+                               f"{e2e['steps']} steps from t=0, D2H of E, B and all particles")
+    if cpu:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

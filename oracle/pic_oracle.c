@@ -504,9 +504,11 @@ static void maxwell(orc_state *s) {
 }
 
 /* Shift the window by one patch column (px cells) towards +x: every stored
- * value moves px cells down in index, the new column is vacuum, particles of
- * the leaving column are dropped and the new column is filled with plasma of
- * the configured profile, regularly placed, at rest. */
+ * value (boundary and ghost nodes included, so that the charge of particles
+ * near the old x_max keeps its whole stencil) moves px cells down in index;
+ * stored indices with no source become vacuum; particles of the leaving
+ * column are dropped and the new column is filled with plasma of the
+ * configured profile, regularly placed, at rest. */
 static void shift_window(orc_state *s) {
   const orc_config *c = &s->c;
   const int P = c->px, nx = c->nx;
@@ -518,7 +520,7 @@ static void shift_window(orc_state *s) {
     for (int j = -G; j < c->ny + G; ++j) {
       double *row = &a[(long)(j + G) * s->sx];
       for (int i = -G; i < nx + G; ++i)
-        row[i + G] = (i + P <= nx - 1) ? row[i + P + G] : 0.0;
+        row[i + G] = (i + P < nx + G) ? row[i + P + G] : 0.0;
     }
   }
   s->nshift++;

@@ -28,7 +28,8 @@ struct pic_ctx {
   int *cnt[2] = {};
   void *bkt[2][6] = {};
   int *bcnt[2] = {};
-  int cap = 0, bcap = 0;
+  int cap = 0;
+  Buckets bk{};
   DevState *st = nullptr;
   double *partials = nullptr;
   int npartials = 0;
@@ -134,11 +135,25 @@ Geom make_geom(const pic_config *c) {
 }
 
 size_t field_bytes(const Geom &g, size_t rs) { return (size_t)NCOMP * g.cs * rs; }
-size_t particle_bytes(const Geom &g, int cap, int bcap, size_t rs) {
-  return 2 * (6 * rs * ((size_t)g.nslots * cap + (size_t)g.nslots * 8 * bcap) +
+Buckets bucket_layout(int cap) {
+  Buckets b{};
+  int off = 0;
+  for (int d = 0; d < 8; ++d) {
+    int ddx, ddy;
+    dir_delta(d, ddx, ddy);
+    const int div = (ddx != 0 && ddy != 0) ? 4 : (ddx != 0 ? 1 : 2);
+    b.cap[d] = std::max(32, (cap / div + 31) / 32 * 32);
+    b.off[d] = off;
+    off += b.cap[d];
+  }
+  b.stride = off;
+  return b;
+}
+size_t particle_bytes(const Geom &g, int cap, size_t rs) {
+  const Buckets b = bucket_layout(cap);
+  return 2 * (6 * rs * ((size_t)g.nslots * cap + (size_t)g.nslots * b.stride) +
               sizeof(int) * ((size_t)g.nslots + (size_t)g.nslots * 8));
 }
-int bucket_cap(int cap) { return std::max(64, (cap / 4 + 31) / 32 * 32); }
 
 template <typename R>
 SoA<R> soa(void *const a[6]) {
@@ -153,7 +168,7 @@ PartView<R> view(pic_ctx *c, int segset, int bktset) {
   v.bkt = soa<R>(c->bkt[bktset]);
   v.bcnt = c->bcnt[bktset];
   v.cap = c->cap;
-  v.bcap = c->bcap;
+  v.bk = c->bk;
   return v;
 }
 
@@ -188,12 +203,12 @@ pic_status poll_device(pic_ctx *ctx) {
 template <typename R>
 pic_status alloc_particles(pic_ctx *ctx, int cap) {
   ctx->cap = cap;
-  ctx->bcap = bucket_cap(cap);
+  ctx->bk = bucket_layout(cap);
   const Geom &g = ctx->g;
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < 6; ++a) {
       CK(cudaMalloc(&ctx->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
-      CK(cudaMalloc(&ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * 8 * ctx->bcap));
+      CK(cudaMalloc(&ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * ctx->bk.stride));
     }
     CK(cudaMalloc(&ctx->cnt[s], sizeof(int) * g.nslots));
     CK(cudaMalloc(&ctx->bcnt[s], sizeof(int) * g.nslots * 8));
@@ -251,7 +266,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.bcnt_in = ctx->bcnt[1 - p];
   a.bcnt_out = ctx->bcnt[p];
   a.cap = ctx->cap;
-  a.bcap = ctx->bcap;
+  a.bk = ctx->bk;
   a.parity = p;
   a.st = ctx->st;
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
@@ -295,7 +310,7 @@ pic_status window_shift(pic_ctx *ctx) {
   ctx->nshift += 1;
   ctx->col0 = (old_col0 + 1) % g.npx;
   CK(launch_window_particles<R>(g, old_col0, ctx->nshift, soa<R>(ctx->seg[q]), ctx->cnt[q],
-                                soa<R>(ctx->bkt[bset]), ctx->bcnt[bset], ctx->cap, ctx->bcap,
+                                soa<R>(ctx->bkt[bset]), ctx->bcnt[bset], ctx->cap, ctx->bk,
                                 ctx->cfg.inj_n0, ctx->cfg.inj_x0, ctx->cfg.inj_ramp,
                                 ctx->cfg.inj_ppc[0], ctx->cfg.inj_ppc[1], ctx->rho_bg,
                                 &ctx->st->err, ctx->stream));
@@ -695,7 +710,7 @@ pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
 // bucket counts, device state
 struct SnapHeader {
   char magic[8];
-  int nx, ny, P, Q, fp32, cap, bcap, nshift, col0, pad;
+  int nx, ny, P, Q, fp32, cap, nshift, col0;
   long long step;
   double t;
   int prev_valid, sticky_pad;
@@ -704,7 +719,7 @@ struct SnapHeader {
 size_t snapshot_bytes(const pic_ctx *c) {
   const Geom &g = c->g;
   size_t b = sizeof(SnapHeader) + field_bytes(g, c->rs) + sizeof(double) * g.cs + sizeof(DevState);
-  if (c->cap) b += particle_bytes(g, c->cap, c->bcap, c->rs);
+  if (c->cap) b += particle_bytes(g, c->cap, c->rs);
   return b;
 }
 
@@ -729,7 +744,7 @@ size_t pic_footprint(const pic_config *cfg, size_t np_max) {
     per = std::max(per, (size_t)g.P * g.Q * cfg->inj_ppc[0] * cfg->inj_ppc[1]);
   int cap = std::max(cmin, (int)std::ceil(cf * (double)per));
   cap = (cap + 31) / 32 * 32;
-  return field_bytes(g, rs) + 3 * sizeof(double) * g.cs + particle_bytes(g, cap, bucket_cap(cap), rs) +
+  return field_bytes(g, rs) + 3 * sizeof(double) * g.cs + particle_bytes(g, cap, rs) +
          sizeof(long long) * (g.nslots * 9 + 1) + sizeof(double) * 3 * 1024 + sizeof(DevState);
 }
 
@@ -910,7 +925,7 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   SnapHeader h{};
   memcpy(h.magic, "PICSNAP1", 8);
   h.nx = g.nx; h.ny = g.ny; h.P = g.P; h.Q = g.Q; h.fp32 = ctx->fp32;
-  h.cap = ctx->cap; h.bcap = ctx->bcap; h.nshift = ctx->nshift; h.col0 = ctx->col0;
+  h.cap = ctx->cap; h.nshift = ctx->nshift; h.col0 = ctx->col0;
   h.step = ctx->step; h.t = ctx->t; h.prev_valid = ctx->prev_valid;
   memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -924,7 +939,7 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   if (ctx->cap) {
     for (int st = 0; st < 2; ++st) {
       for (int a = 0; a < 6; ++a) CK(d2h(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
-      for (int a = 0; a < 6; ++a) CK(d2h(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * 8 * ctx->bcap));
+      for (int a = 0; a < 6; ++a) CK(d2h(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * ctx->bk.stride));
       CK(d2h(ctx->cnt[st], sizeof(int) * g.nslots));
       CK(d2h(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
     }
@@ -954,9 +969,9 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
     }
   }
   ctx->cap = h.cap;
-  ctx->bcap = h.bcap;
+  ctx->bk = bucket_layout(h.cap);
   const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
-                      (h.cap ? particle_bytes(g, h.cap, h.bcap, ctx->rs) : 0);
+                      (h.cap ? particle_bytes(g, h.cap, ctx->rs) : 0);
   if (bytes < need) return fail(ctx, PIC_EINVAL, "snapshot truncated");
   const char *p = (const char *)host + sizeof h;
   auto h2d = [&](void *dst, size_t n) -> cudaError_t {
@@ -969,7 +984,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (h.cap) {
     for (int st = 0; st < 2; ++st) {
       for (int a = 0; a < 6; ++a) CK(h2d(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
-      for (int a = 0; a < 6; ++a) CK(h2d(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * 8 * ctx->bcap));
+      for (int a = 0; a < 6; ++a) CK(h2d(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * ctx->bk.stride));
       CK(h2d(ctx->cnt[st], sizeof(int) * g.nslots));
       CK(h2d(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
     }

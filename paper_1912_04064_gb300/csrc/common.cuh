@@ -72,6 +72,17 @@ struct SoA {
   R *x, *y, *ux, *uy, *uz, *w;
 };
 
+// Direction buckets of one slot: bucket d holds up to cap[d] particles at
+// elements [s * stride + off[d], ... + cap[d]).  A particle sheet moving
+// along x (a laser-driven front) can carry a whole patch across an x edge in
+// one step, so x-edge buckets get the full patch capacity, y-edge buckets
+// half of it and corner buckets a quarter.
+struct Buckets {
+  int cap[8];
+  int off[8];
+  int stride;
+};
+
 // Direction k in 0..7 <-> (ddx, ddy), centre excluded.
 __host__ __device__ inline int dir_index(int ddx, int ddy) {
   int code = (ddy + 1) * 3 + (ddx + 1);
@@ -197,7 +208,8 @@ struct StepArgs {
   SoA<R> bin, bout;    // direction buckets, read / written
   const int *bcnt_in;
   int *bcnt_out;
-  int cap, bcap;
+  int cap;
+  Buckets bk;
   int parity;
   DevState *st;
 };
@@ -251,7 +263,8 @@ struct PartView {
   const int *cnt;
   SoA<R> bkt;
   const int *bcnt;
-  int cap, bcap;
+  int cap;
+  Buckets bk;
 };
 template <typename R>
 cudaError_t launch_deposit_rho(const Geom &g, int col0, const PartView<R> &v, double *rho,
@@ -273,7 +286,7 @@ cudaError_t launch_get_particles(const Geom &g, int col0, const PartView<R> &v,
 // old_col0: ring offset before the shift; nshift: shifts including this one.
 template <typename R>
 cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,
-                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, int bcap,
+                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, Buckets bk,
                                     double n0, double x0, double ramp, int ppcx, int ppcy,
                                     double *rho_bg, unsigned *err, cudaStream_t s);
 

@@ -222,8 +222,9 @@ __global__ void k_get_field(const Geom g, const R *arr, double *dst) {
   dst[(long long)b * nxo + a] = (double)arr[fidx(g, lx + a, ly + b)];
 }
 
-// Moving-window shift of whole rows: value at i <- value at i + P when
-// i + P <= nx - 1, else 0 (vacuum), for every stored row.
+// Moving-window shift of whole rows: the value at stored index i takes the
+// value at i + P when that index is stored (boundary and ghost nodes
+// included), else 0 (vacuum), for every stored row.
 template <typename R>
 __global__ void k_shift_rows(const Geom g, R *base, long long comp_stride) {
   extern __shared__ unsigned char row_raw[];
@@ -234,7 +235,7 @@ __global__ void k_shift_rows(const Geom g, R *base, long long comp_stride) {
   __syncthreads();
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const int i = e - GX;
-    a[e] = (i + g.P <= g.nx - 1) ? row[e + g.P] : R(0);
+    a[e] = (i + g.P < g.nx + GX) ? row[e + g.P] : R(0);
   }
 }
 

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
         x = a.pin.x[i]; y = a.pin.y[i];
         ux = a.pin.ux[i]; uy = a.pin.uy[i]; uz = a.pin.uz[i]; w = a.pin.w[i];
       } else {
-        const long long i = ((long long)s_src[src] * 8 + (src - 1)) * a.bcap + kk;
+        const long long i = (long long)s_src[src] * a.bk.stride + a.bk.off[src - 1] + kk;
         x = a.bin.x[i]; y = a.bin.y[i];
         ux = a.bin.ux[i]; uy = a.bin.uy[i]; uz = a.bin.uz[i]; w = a.bin.w[i];
       }
@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
     } else if (alive) {
       const int dir = dir_index(ddx, ddy);
       const int pos = atomicAdd(&s_bcnt[dir], 1);
-      if (pos < a.bcap) {
-        const long long i = ((long long)s * 8 + dir) * a.bcap + pos;
+      if (pos < a.bk.cap[dir]) {
+        const long long i = (long long)s * a.bk.stride + a.bk.off[dir] + pos;
         a.bout.x[i] = x; a.bout.y[i] = y;
         a.bout.ux[i] = ux; a.bout.uy[i] = uy; a.bout.uz[i] = uz; a.bout.w[i] = w;
       } else {
@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
     a.cnt_out[s] = n;
     atomicMax(&a.st->maxcnt[a.parity], s_out);
   }
-  if (tid < 8) a.bcnt_out[(long long)s * 8 + tid] = s_bcnt[tid] < a.bcap ? s_bcnt[tid] : a.bcap;
+  if (tid < 8)
+    a.bcnt_out[(long long)s * 8 + tid] = s_bcnt[tid] < a.bk.cap[tid] ? s_bcnt[tid] : a.bk.cap[tid];
 }
 
 }  // namespace

@@ -104,7 +104,7 @@ __device__ void for_each_particle(const Geom &g, int col0, const PartView<R> &v,
       int DX0, DY0;
       slot_origin(g, col0, dest, DX0, DY0);
       for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const long long i = ((long long)slot * 8 + d) * v.bcap + k;
+        const long long i = (long long)slot * v.bk.stride + v.bk.off[d] + k;
         fn(DX0, DY0, v.bkt.x[i], v.bkt.y[i], v.bkt.ux[i], v.bkt.uy[i], v.bkt.uz[i], v.bkt.w[i]);
       }
     }
@@ -201,7 +201,7 @@ __global__ void k_get_particles(const Geom g, int col0, const PartView<R> v,
     slot_origin(g, col0, dest, DX0, DY0);
     const long long base = offsets[g.nslots + (long long)pp * 8 + d];
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-      const long long i = ((long long)slot * 8 + d) * v.bcap + k;
+      const long long i = (long long)slot * v.bk.stride + v.bk.off[d] + k;
       emit(base + k, DX0, DY0, v.bkt.x[i], v.bkt.y[i], v.bkt.ux[i], v.bkt.uy[i], v.bkt.uz[i],
            v.bkt.w[i]);
     }
@@ -214,7 +214,7 @@ __global__ void k_get_particles(const Geom g, int col0, const PartView<R> v,
 // clear every bucket that points into or out of the leaving column.
 template <typename R>
 __global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, SoA<R> bkt,
-                                 int *bcnt, int cap, int bcap, unsigned *err) {
+                                 int *bcnt, int cap, Buckets bk, unsigned *err) {
   const int py = blockIdx.x;
   const int sdrop = py * g.npx + col0;
   const int snext = py * g.npx + (col0 + 1) % g.npx;
@@ -232,7 +232,7 @@ __global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, S
         atomicOr(err, ERR_OVERFLOW_SEG);
         continue;
       }
-      const long long i = ((long long)sdrop * 8 + d) * bcap + k;
+      const long long i = (long long)sdrop * bk.stride + bk.off[d] + k;
       const long long o = (long long)dest * cap + pos;
       seg.x[o] = bkt.x[i]; seg.y[o] = bkt.y[i];
       seg.ux[o] = bkt.ux[i]; seg.uy[o] = bkt.uy[i]; seg.uz[o] = bkt.uz[i]; seg.w[o] = bkt.w[i];
@@ -346,10 +346,10 @@ cudaError_t launch_get_particles(const Geom &g, int col0, const PartView<R> &v,
 
 template <typename R>
 cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,
-                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, int bcap,
+                                    int *cnt, SoA<R> bkt, int *bcnt, int cap, Buckets bk,
                                     double n0, double x0, double ramp, int ppcx, int ppcy,
                                     double *rho_bg, unsigned *err, cudaStream_t s) {
-  k_window_migrate<R><<<g.npy, 256, 0, s>>>(g, old_col0, seg, cnt, bkt, bcnt, cap, bcap, err);
+  k_window_migrate<R><<<g.npy, 256, 0, s>>>(g, old_col0, seg, cnt, bkt, bcnt, cap, bk, err);
   k_window_inject<R><<<g.npy, 256, 0, s>>>(g, old_col0, nshift, seg, cnt, cap, n0, x0, ramp,
                                             ppcx, ppcy, rho_bg, err);
   return cudaGetLastError();
@@ -370,7 +370,7 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
                                                const long long *, double *, size_t,           \
                                                cudaStream_t);                                 \
   template cudaError_t launch_window_particles<R>(const Geom &, int, int, SoA<R>, int *,      \
-                                                  SoA<R>, int *, int, int, double, double,    \
+                                                  SoA<R>, int *, int, Buckets, double, double, \
                                                   double, int, int, double *, unsigned *,     \
                                                   cudaStream_t);
 PIC_INST(float)

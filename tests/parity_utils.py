@@ -39,16 +39,30 @@ def field_errors(o, g, names=FIELD_NAMES):
     return {k: rel_err(g.pic_get_field(k), o.field(k)) for k in names}
 
 
-def sorted_particles(p):
-    order = np.lexsort((p["y"], p["x"]))
-    return {k: v[order] for k, v in p.items()}
+def match_particles(a, b):
+    """Pair every particle of `a` with its nearest particle of `b` in
+    (x, y, ux, uy, uz, w) space; particles are unordered sets and regularly
+    injected ones share exact positions, so sorting alone is ambiguous.
+    Returns b re-ordered to match a; asserts the pairing is one-to-one."""
+    from scipy.spatial import cKDTree
+
+    keys = ("x", "y", "ux", "uy", "uz", "w")
+    A = np.stack([a[k] for k in keys], 1)
+    B = np.stack([b[k] for k in keys], 1)
+    scale = np.maximum(np.max(np.abs(B), 0), 1e-30)
+    _, idx = cKDTree(B / scale).query(A / scale, k=1)
+    assert np.unique(idx).size == idx.size, "particle pairing is not one-to-one"
+    return {k: b[k][idx] for k in keys}
 
 
 def particle_errors(o, g):
-    a, b = sorted_particles(g.pic_get_particles()), sorted_particles(o.particles())
+    a, b = g.pic_get_particles(), o.particles()
     assert a["x"].size == b["x"].size, (a["x"].size, b["x"].size)
+    if a["x"].size == 0:
+        return {k: 0.0 for k in a}
+    b = match_particles(a, b)
     out = {}
     for k in a:
-        scale = max(np.max(np.abs(b[k])) if b[k].size else 0.0, 1e-300)
-        out[k] = float(np.max(np.abs(a[k] - b[k])) / scale) if a[k].size else 0.0
+        scale = max(np.max(np.abs(b[k])), 1e-300)
+        out[k] = float(np.max(np.abs(a[k] - b[k])) / scale)
     return out
