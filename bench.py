@@ -123,7 +123,7 @@ def algorithmic_bytes(npart, ncell, rsize):
             npart * per_particle_kernel + ncell * per_cell_kernel)
 
 
-def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist):
+def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1):
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -135,13 +135,14 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist):
     rs = 4 if prec == "fp32" else 8
     stream = torch.cuda.Stream(device=device)
     cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                              use_graph=True, timing=False, capacity_factor=4.0)
+                              use_graph=True, timing=False, capacity_factor=cf, merge=merge)
     g = pic.Pic(cfg)
     g.pic_load_particles(parts)
     g.pic_set_background("neutralising")
     g.pic_step(spinup)
     g.pic_step(warmup)
     d0 = g.pic_diag()
+    blob = g.pic_snapshot()   # the per-kernel timing pass replays the same steps
     if dist:
         dist.barrier()
     torch.cuda.synchronize(device)
@@ -154,11 +155,11 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist):
         torch.cuda.synchronize(device)
     ms = ev0.elapsed_time(ev1)
     d1 = g.pic_diag()
-    # per-kernel times over the same number of steps, CUDA events around each
-    # phase on the launching stream (no graph replay)
+    # per-kernel times over the same steps (replayed from the snapshot taken
+    # before the timed region), CUDA events around each phase on the
+    # launching stream (no graph replay)
     cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                                use_graph=False, timing=True, capacity_factor=4.0)
-    blob = g.pic_snapshot()
+                                use_graph=False, timing=True, capacity_factor=cf, merge=merge)
     g.close()
     gt = pic.Pic(cfg_t)
     gt.pic_restore(blob)
@@ -202,7 +203,7 @@ def run_e2e(prec, steps, device):
     run, parts = W.lwfa_2d()
     host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in parts.items()}
     n = host["x"].size
-    cfg = pic.config_from_run(run, prec, device=device, use_graph=True, capacity_factor=4.0)
+    cfg = pic.config_from_run(run, prec, device=device, use_graph=True, capacity_factor=2.0)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     g = pic.Pic(cfg)
@@ -254,6 +255,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--merge", type=int, default=-1,
+                    help="deposit merging in registers: 1 on, 0 off, -1 library default")
+    ap.add_argument("--capacity-factor", type=float, default=2.0,
+                    help="patch capacity / fullest initial patch")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -294,11 +299,14 @@ def main():
     if dist:
         dist.barrier()
 
-    r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist)
-    r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
-                  world, dist)
+    r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist,
+                  args.capacity_factor, args.merge)
+    r64 = None
+    if args.fp64_steps > 0:
+        r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
+                      world, dist, args.capacity_factor)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
-    cpu = cpu_oracle(args.cpu_steps) if rank == 0 else None
+    cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
         dist.barrier()
     if rank != 0:
@@ -326,10 +334,11 @@ def main():
                                     "bytes_per_step": r32["step_bytes"]}},
         "phases_ms": {"particle_step": r32["particle_step_ms"], "fields": r32["fields_ms"],
                       "window": r32["window_ms"]},
-        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": args.fp64_steps,
-                 "particle_step_ms": r64["particle_step_ms"], "fields_ms": r64["fields_ms"],
-                 "speedup_fp32_over_fp64": r32["value"] / r64["value"],
-                 "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm},
+        "fp64": None if r64 is None else {
+            "value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": args.fp64_steps,
+            "particle_step_ms": r64["particle_step_ms"], "fields_ms": r64["fields_ms"],
+            "speedup_fp32_over_fp64": r32["value"] / r64["value"],
+            "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm},
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }

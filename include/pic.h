@@ -105,6 +105,13 @@ typedef struct pic_config {
   int tma;                /* 1 (default if >= 0): stage field tiles with TMA;
                              0: plain coalesced loads */
   int block;              /* threads per patch block (0 = default 256) */
+  int merge;              /* deposition: sum consecutive particles sharing a
+                             current window in registers before the shared
+                             atomics: 1 on, 0 off, -1 (default) on for FP32 */
+  int auto_grow;          /* 1: pic_step keeps a device copy of the state at
+                             entry; a patch or re-binning capacity overflow
+                             grows the capacity (x1.5 or more) and replays the
+                             steps instead of failing (up to 4 times) */
 } pic_config;
 
 typedef struct pic_diag_t {
@@ -125,6 +132,7 @@ typedef struct pic_diag_t {
   double ms_particles, ms_fields, ms_window; /* timers (timing = 1) */
   long long launches;     /* kernels launched by this context so far */
   long long particle_step_launches;
+  int grows;              /* capacity growths done by auto_grow */
 } pic_diag_t;
 
 typedef struct pic_ctx pic_ctx;

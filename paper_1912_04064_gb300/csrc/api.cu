@@ -48,6 +48,21 @@ struct pic_ctx {
   long long launches = 0, ps_launches = 0;
   int sticky = PIC_OK;
   std::string err;
+  // device copy of the live state taken at the start of pic_step when the
+  // capacity may grow (auto_grow): replayed after an overflow
+  struct Backup {
+    void *F = nullptr;        // components 0..8 (E, Bm, B)
+    double *rho_bg = nullptr;
+    void *seg[6] = {}, *bkt[6] = {};
+    int *cnt = nullptr, *bcnt = nullptr;
+    DevState *st = nullptr;
+    int cap = 0;
+    Buckets bk{};
+    long long step = 0;
+    double t = 0;
+    int nshift = 0, col0 = 0;
+  } bak;
+  int grows = 0;
 };
 
 namespace {
@@ -270,7 +285,8 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.parity = p;
   a.st = ctx->st;
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
-  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, block, ctx->stream));
+  const bool merge = ctx->cfg.merge < 0 ? sizeof(R) == 4 : ctx->cfg.merge != 0;
+  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->stream));
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
   FieldArgs<R> f;
   f.g = g;
@@ -342,8 +358,136 @@ pic_status capture_graphs(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+void free_backup(pic_ctx *c) {
+  auto &b = c->bak;
+  cudaFree(b.F);
+  cudaFree(b.rho_bg);
+  for (int a = 0; a < 6; ++a) {
+    cudaFree(b.seg[a]);
+    cudaFree(b.bkt[a]);
+  }
+  cudaFree(b.cnt);
+  cudaFree(b.bcnt);
+  cudaFree(b.st);
+  b = pic_ctx::Backup{};
+}
+
+void free_particles(pic_ctx *c) {
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 6; ++a) {
+      cudaFree(c->seg[s][a]);
+      cudaFree(c->bkt[s][a]);
+      c->seg[s][a] = c->bkt[s][a] = nullptr;
+    }
+    cudaFree(c->cnt[s]);
+    cudaFree(c->bcnt[s]);
+    c->cnt[s] = c->bcnt[s] = nullptr;
+  }
+  cudaFree(c->offsets);
+  c->offsets = nullptr;
+}
+
+// Copy the live state (current particle set and in-flight buckets, E, Bm,
+// B, background charge, device scalars) into the backup.
+template <typename R>
+pic_status take_backup(pic_ctx *ctx) {
+  auto &b = ctx->bak;
+  const Geom &g = ctx->g;
+  if (b.cap != ctx->cap) free_backup(ctx);
+  if (!b.F) {
+    b.cap = ctx->cap;
+    b.bk = ctx->bk;
+    CK(cudaMalloc(&b.F, 9 * g.cs * sizeof(R)));
+    CK(cudaMalloc(&b.rho_bg, g.cs * sizeof(double)));
+    for (int a = 0; a < 6; ++a) {
+      CK(cudaMalloc(&b.seg[a], sizeof(R) * (size_t)g.nslots * b.cap));
+      CK(cudaMalloc(&b.bkt[a], sizeof(R) * (size_t)g.nslots * b.bk.stride));
+    }
+    CK(cudaMalloc(&b.cnt, sizeof(int) * g.nslots));
+    CK(cudaMalloc(&b.bcnt, sizeof(int) * g.nslots * 8));
+    CK(cudaMalloc(&b.st, sizeof(DevState)));
+  }
+  const int q = (int)(ctx->step & 1);
+  CK(cudaMemcpyAsync(b.F, ctx->F, 9 * g.cs * sizeof(R), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(b.rho_bg, ctx->rho_bg, g.cs * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CK(launch_repack<R>(g, soa<R>(ctx->seg[q]), ctx->cnt[q], ctx->cap, soa<R>(ctx->bkt[1 - q]),
+                      ctx->bcnt[1 - q], ctx->bk, soa<R>(b.seg), b.cnt, b.cap, soa<R>(b.bkt),
+                      b.bcnt, b.bk, ctx->stream));
+  CK(cudaMemcpyAsync(b.st, ctx->st, sizeof(DevState), cudaMemcpyDeviceToDevice, ctx->stream));
+  b.step = ctx->step;
+  b.t = ctx->t;
+  b.nshift = ctx->nshift;
+  b.col0 = ctx->col0;
+  ctx->launches += 1;
+  return PIC_OK;
+}
+
+// Return to the backup with a patch capacity of new_cap (particle storage
+// reallocated and repacked when it changes); clears the device fault.
+template <typename R>
+pic_status restore_backup(pic_ctx *ctx, int new_cap) {
+  auto &b = ctx->bak;
+  const Geom &g = ctx->g;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (new_cap != ctx->cap) {
+    free_graphs(ctx);
+    free_particles(ctx);
+    pic_status s = alloc_particles<R>(ctx, new_cap);
+    if (s) return s;
+  }
+  const int q = (int)(b.step & 1);
+  CK(cudaMemcpyAsync(ctx->F, b.F, 9 * g.cs * sizeof(R), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemsetAsync((R *)ctx->F + C_JA * g.cs, 0, 6 * g.cs * sizeof(R), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->rho_bg, b.rho_bg, g.cs * sizeof(double), cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->cnt[1 - q], 0, sizeof(int) * g.nslots, ctx->stream));
+  CK(cudaMemsetAsync(ctx->bcnt[q], 0, sizeof(int) * g.nslots * 8, ctx->stream));
+  CK(launch_repack<R>(g, soa<R>(b.seg), b.cnt, b.cap, soa<R>(b.bkt), b.bcnt, b.bk,
+                      soa<R>(ctx->seg[q]), ctx->cnt[q], ctx->cap, soa<R>(ctx->bkt[1 - q]),
+                      ctx->bcnt[1 - q], ctx->bk, ctx->stream));
+  DevState ds;
+  CK(cudaMemcpyAsync(&ds, b.st, sizeof ds, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ds.err = 0;
+  CK(cudaMemcpy(ctx->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
+  ctx->step = b.step;
+  ctx->t = b.t;
+  ctx->nshift = b.nshift;
+  ctx->col0 = b.col0;
+  ctx->prev_valid = false;
+  ctx->sticky = PIC_OK;
+  ctx->launches += 1;
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status run_steps(pic_ctx *ctx, int nsteps);
+
+// Advance nsteps; with auto_grow, an overflow of a patch or bucket capacity
+// grows the capacity and replays the steps from the state at entry.
 template <typename R>
 pic_status do_step(pic_ctx *ctx, int nsteps) {
+  if (!ctx->cap) return fail(ctx, PIC_ESTATE, "no particles loaded");
+  if (!ctx->cfg.auto_grow) return run_steps<R>(ctx, nsteps);
+  pic_status s = take_backup<R>(ctx);
+  if (s) return s;
+  for (int attempt = 0;; ++attempt) {
+    s = run_steps<R>(ctx, nsteps);
+    if (s != PIC_EOVERFLOW || attempt >= 4) return s;
+    DevState h;
+    CK(cudaMemcpy(&h, ctx->st, sizeof h, cudaMemcpyDeviceToHost));
+    const int seen = std::max(h.maxcnt[0], h.maxcnt[1]);
+    int cap = std::max((int)(1.5 * ctx->cap), (int)(1.25 * seen));
+    cap = (cap + 31) / 32 * 32;
+    s = restore_backup<R>(ctx, cap);
+    if (s) return s;
+    ctx->grows += 1;
+  }
+}
+
+template <typename R>
+pic_status run_steps(pic_ctx *ctx, int nsteps) {
   if (!ctx->cap) return fail(ctx, PIC_ESTATE, "no particles loaded");
   if (ctx->cfg.tma && !ctx->tmap_ok) {
     pic_status s = build_tmap<R>(ctx);
@@ -697,6 +841,7 @@ pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
   out->shifts = ctx->nshift;
   out->max_patch_count = hs.maxcnt[(ctx->step + 1) & 1];
   out->capacity = ctx->cap;
+  out->grows = ctx->grows;
   out->ms_particles = ctx->ms_particles;
   out->ms_fields = ctx->ms_fields;
   out->ms_window = ctx->ms_window;
@@ -811,6 +956,7 @@ void pic_destroy(pic_ctx *ctx) {
     cudaFree(ctx->cnt[s]);
     cudaFree(ctx->bcnt[s]);
   }
+  free_backup(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

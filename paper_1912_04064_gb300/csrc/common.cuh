@@ -119,25 +119,28 @@ __host__ __device__ inline long long fidx(const Geom &g, int i, int j) {
   return (long long)(j + GY) * g.sx + (i + GX);
 }
 
+// Write v at the periodic ghost images of stored element o = grid (i, j)
+// (those that lie in the stored range); o itself is not written.
+template <typename R>
+__device__ __forceinline__ void mirror(const Geom &g, R *a, long long o, int i, int j, R v) {
+  int mx = 0, my = 0;
+  if (g.fbc_x == FBC_PERIODIC) mx = i < GX ? g.nx : (i >= g.nx - GX ? -g.nx : 0);
+  if (g.fbc_y == FBC_PERIODIC) my = j < GY ? g.ny : (j >= g.ny - GY ? -g.ny : 0);
+  if (mx) a[o + mx] = v;
+  if (my) {
+    const long long oy = o + (long long)my * g.sx;
+    a[oy] = v;
+    if (mx) a[oy + mx] = v;
+  }
+}
+
 // Store v at (i, j) of component array a and at every periodic ghost image
 // of (i, j) that lies in the stored range.
 template <typename R>
 __device__ inline void store_mirrored(const Geom &g, R *a, int i, int j, R v) {
-  a[fidx(g, i, j)] = v;
-  const bool px = g.fbc_x == FBC_PERIODIC, py = g.fbc_y == FBC_PERIODIC;
-  int ix[2] = {i, i}, jy[2] = {j, j};
-  int nix = 1, njy = 1;
-  if (px) {
-    if (i < GX) ix[nix++] = i + g.nx;
-    else if (i >= g.nx - GX) ix[nix++] = i - g.nx;
-  }
-  if (py) {
-    if (j < GY) jy[njy++] = j + g.ny;
-    else if (j >= g.ny - GY) jy[njy++] = j - g.ny;
-  }
-  for (int b = 0; b < njy; ++b)
-    for (int c = 0; c < nix; ++c)
-      if (b || c) a[fidx(g, ix[c], jy[b])] = v;
+  const long long o = fidx(g, i, j);
+  a[o] = v;
+  mirror(g, a, o, i, j, v);
 }
 
 // Quadratic B-spline weights of the nodes i0-1, i0, i0+1 for a coordinate
@@ -216,7 +219,7 @@ struct StepArgs {
 
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 int block, cudaStream_t s);
+                                 bool merge, int block, cudaStream_t s);
 // Raise the dynamic shared-memory limit of the step kernels (call outside
 // stream capture).
 template <typename R>
@@ -283,6 +286,15 @@ template <typename R>
 cudaError_t launch_get_particles(const Geom &g, int col0, const PartView<R> &v,
                                  const long long *offsets, double *out, size_t stride,
                                  cudaStream_t s);
+// Copy the live particles of every slot (segment and 8 buckets) between two
+// storage layouts (capacities may differ); counts are copied, clamped to the
+// destination capacities.
+template <typename R>
+cudaError_t launch_repack(const Geom &g, SoA<R> src, const int *cnt_src, int cap_src,
+                          SoA<R> bsrc, const int *bcnt_src, Buckets bk_src, SoA<R> dst,
+                          int *cnt_dst, int cap_dst, SoA<R> bdst, int *bcnt_dst, Buckets bk_dst,
+                          cudaStream_t s);
+
 // old_col0: ring offset before the shift; nshift: shifts including this one.
 template <typename R>
 cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,

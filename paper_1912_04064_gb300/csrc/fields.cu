@@ -29,91 +29,131 @@ __device__ __forceinline__ Ranges ranges(const Geom &g) {
   return r;
 }
 
+constexpr int RY = 8;      // rows per thread in the Yee kernels
+constexpr int YEE_BX = 128;
+
+// True when any cell of the block's tile lies in a periodic mirror band.
+__device__ __forceinline__ bool block_mirrors(const Geom &g, int i0, int i1, int j0, int j1) {
+  return (g.fbc_x == FBC_PERIODIC && (i0 < GX || i1 > g.nx - GX)) ||
+         (g.fbc_y == FBC_PERIODIC && (j0 < GY || j1 > g.ny - GY));
+}
+
+// E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}); one thread per column
+// segment of RY rows, the previous row's B carried in registers.
 template <typename R>
-__global__ void k_update_E(const FieldArgs<R> a) {
+__global__ void __launch_bounds__(YEE_BX) k_update_E(const FieldArgs<R> a) {
   const Geom &g = a.g;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const Ranges rg = ranges(g);
-  if (i >= rg.nxp || j >= rg.nyp) return;
-  R *F = a.F;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * RY;
+  const int j1 = min(j0 + RY, rg.nyp);
+  const int ib0 = blockIdx.x * blockDim.x;
+  const bool mir = block_mirrors(g, ib0, ib0 + blockDim.x, j0, j1);
+  if (i >= rg.nxp) return;
   const long long cs = g.cs;
+  const int sx = g.sx;
+  R *F = a.F;
   R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
   const R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   const R *J = F + (C_JA + 3 * a.parity) * cs;
   const R dt = R(g.dt), idx = R(1.0 / g.dx), idy = R(1.0 / g.dy);
-  const long long o = fidx(g, i, j);
-  const long long oxm = o - 1, oym = o - g.sx;
-  if (i < rg.nxd) {
-    const R v = Ex[o] + dt * ((Bz[o] - Bz[oym]) * idy - J[o]);
-    store_mirrored(g, Ex, i, j, v);
-  }
-  if (j < rg.nyd) {
-    const R v = Ey[o] + dt * (-(Bz[o] - Bz[oxm]) * idx - J[cs + o]);
-    store_mirrored(g, Ey, i, j, v);
-  }
-  {
-    const R v = Ez[o] + dt * ((By[o] - By[oxm]) * idx - (Bx[o] - Bx[oym]) * idy - J[2 * cs + o]);
-    store_mirrored(g, Ez, i, j, v);
+  long long o = fidx(g, i, j0);
+  R bzp = Bz[o - sx], bxp = Bx[o - sx];
+  for (int j = j0; j < j1; ++j, o += sx) {
+    const R bz = Bz[o], bx = Bx[o], by = By[o];
+    const R bzl = Bz[o - 1], byl = By[o - 1];
+    if (i < rg.nxd) {
+      const R v = Ex[o] + dt * ((bz - bzp) * idy - J[o]);
+      Ex[o] = v;
+      if (mir) mirror(g, Ex, o, i, j, v);
+    }
+    if (j < rg.nyd) {
+      const R v = Ey[o] + dt * (-(bz - bzl) * idx - J[cs + o]);
+      Ey[o] = v;
+      if (mir) mirror(g, Ey, o, i, j, v);
+    }
+    {
+      const R v = Ez[o] + dt * ((by - byl) * idx - (bx - bxp) * idy - J[2 * cs + o]);
+      Ez[o] = v;
+      if (mir) mirror(g, Ez, o, i, j, v);
+    }
+    bzp = bz;
+    bxp = bx;
   }
 }
 
+// B^{n+3/2} = B^{n+1/2} - dt curl_h E^{n+1}, Bm^{n+1} = (B^{n+1/2} +
+// B^{n+3/2}) / 2 (= B at stored cells that are not updated), and the
+// current set of the next step cleared.  Covers every stored column and row.
 template <typename R>
-__global__ void k_update_B(const FieldArgs<R> a) {
+__global__ void __launch_bounds__(YEE_BX) k_update_B(const FieldArgs<R> a) {
   const Geom &g = a.g;
-  const int ii = blockIdx.x * blockDim.x + threadIdx.x;
-  const int jj = blockIdx.y * blockDim.y + threadIdx.y;
-  if (ii == 0 && jj == 0) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     const int p = a.parity;
     a.st->t[1 - p] = a.st->t[p] + g.dt;
     a.st->step[1 - p] = a.st->step[p] + 1;
     a.st->maxcnt[1 - p] = 0;  // the next particle step starts a new maximum
   }
-  if (ii >= g.sx || jj >= g.nys) return;
-  R *F = a.F;
-  const long long cs = g.cs;
-  const long long o = (long long)jj * g.sx + ii;
-  R *Jn = F + (C_JA + 3 * (1 - a.parity)) * cs;
-  Jn[o] = R(0);
-  Jn[cs + o] = R(0);
-  Jn[2 * cs + o] = R(0);
-  const int i = ii - GX, j = jj - GY;
-  if (i >= g.nx + GX) return;  // row padding
-  if ((g.fbc_x == FBC_PERIODIC && (i < 0 || i >= g.nx)) ||
-      (g.fbc_y == FBC_PERIODIC && (j < 0 || j >= g.ny)))
-    return;  // periodic ghost: written as a mirror by its owner
   const Ranges rg = ranges(g);
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GX;
+  const int j0 = (int)(blockIdx.y * RY) - GY;
+  const int j1 = min(j0 + RY, g.ny + GY);
+  const int ib0 = (int)(blockIdx.x * blockDim.x) - GX;
+  const bool mir = block_mirrors(g, ib0, ib0 + blockDim.x, j0, j1);
+  if (i >= g.nx + GX) return;
+  const bool perx = g.fbc_x == FBC_PERIODIC, pery = g.fbc_y == FBC_PERIODIC;
+  const bool ghost_x = i < 0 || i >= g.nx;
+  const long long cs = g.cs;
+  const int sx = g.sx;
+  R *F = a.F;
   const R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
   R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   R *Bmx = F + C_BMX * cs, *Bmy = F + C_BMY * cs, *Bmz = F + C_BMZ * cs;
+  R *Jn = F + (C_JA + 3 * (1 - a.parity)) * cs;
   const R dt = R(g.dt), idx = R(1.0 / g.dx), idy = R(1.0 / g.dy);
-  const bool in_x = i >= 0, in_y = j >= 0;
-  {
-    const R b0 = Bx[o];
-    R b1 = b0;
-    if (in_x && in_y && i < rg.nxp && j < rg.nyd) {
-      b1 = b0 - dt * (Ez[o + g.sx] - Ez[o]) * idy;
-      store_mirrored(g, Bx, i, j, b1);
+  long long o = fidx(g, i, j0);
+  for (int j = j0; j < j1; ++j, o += sx) {
+    Jn[o] = R(0);
+    Jn[cs + o] = R(0);
+    Jn[2 * cs + o] = R(0);
+    if ((perx && ghost_x) || (pery && (j < 0 || j >= g.ny))) continue;  // mirror cells
+    const bool in = i >= 0 && j >= 0;
+    {
+      const R b0 = Bx[o];
+      R b1 = b0;
+      if (in && i < rg.nxp && j < rg.nyd) {
+        b1 = b0 - dt * (Ez[o + sx] - Ez[o]) * idy;
+        Bx[o] = b1;
+        if (mir) mirror(g, Bx, o, i, j, b1);
+      }
+      const R m = R(0.5) * (b0 + b1);
+      Bmx[o] = m;
+      if (mir) mirror(g, Bmx, o, i, j, m);
     }
-    store_mirrored(g, Bmx, i, j, R(0.5) * (b0 + b1));
-  }
-  {
-    const R b0 = By[o];
-    R b1 = b0;
-    if (in_x && in_y && i < rg.nxd && j < rg.nyp) {
-      b1 = b0 + dt * (Ez[o + 1] - Ez[o]) * idx;
-      store_mirrored(g, By, i, j, b1);
+    {
+      const R b0 = By[o];
+      R b1 = b0;
+      if (in && i < rg.nxd && j < rg.nyp) {
+        b1 = b0 + dt * (Ez[o + 1] - Ez[o]) * idx;
+        By[o] = b1;
+        if (mir) mirror(g, By, o, i, j, b1);
+      }
+      const R m = R(0.5) * (b0 + b1);
+      Bmy[o] = m;
+      if (mir) mirror(g, Bmy, o, i, j, m);
     }
-    store_mirrored(g, Bmy, i, j, R(0.5) * (b0 + b1));
-  }
-  {
-    const R b0 = Bz[o];
-    R b1 = b0;
-    if (in_x && in_y && i < rg.nxd && j < rg.nyd) {
-      b1 = b0 - dt * ((Ey[o + 1] - Ey[o]) * idx - (Ex[o + g.sx] - Ex[o]) * idy);
-      store_mirrored(g, Bz, i, j, b1);
+    {
+      const R b0 = Bz[o];
+      R b1 = b0;
+      if (in && i < rg.nxd && j < rg.nyd) {
+        b1 = b0 - dt * ((Ey[o + 1] - Ey[o]) * idx - (Ex[o + sx] - Ex[o]) * idy);
+        Bz[o] = b1;
+        if (mir) mirror(g, Bz, o, i, j, b1);
+      }
+      const R m = R(0.5) * (b0 + b1);
+      Bmz[o] = m;
+      if (mir) mirror(g, Bmz, o, i, j, m);
     }
-    store_mirrored(g, Bmz, i, j, R(0.5) * (b0 + b1));
   }
 }
 
@@ -322,17 +362,10 @@ __global__ void k_gauss(const Geom g, const R *F, int jset, const double *rho,
 template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   const Geom &g = a.g;
-  {
-    dim3 blk(64, 4);
-    const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
-    dim3 grd((nxp + blk.x - 1) / blk.x, (nyp + blk.y - 1) / blk.y);
-    k_update_E<R><<<grd, blk, 0, s>>>(a);
-  }
-  {
-    dim3 blk(64, 4);
-    dim3 grd((g.sx + blk.x - 1) / blk.x, (g.nys + blk.y - 1) / blk.y);
-    k_update_B<R><<<grd, blk, 0, s>>>(a);
-  }
+  const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
+  k_update_E<R><<<dim3((nxp + YEE_BX - 1) / YEE_BX, (nyp + RY - 1) / RY), YEE_BX, 0, s>>>(a);
+  const int ncol = g.nx + 2 * GX, nrow = g.ny + 2 * GY;
+  k_update_B<R><<<dim3((ncol + YEE_BX - 1) / YEE_BX, (nrow + RY - 1) / RY), YEE_BX, 0, s>>>(a);
   if (g.fbc_x == FBC_SM || g.fbc_y == FBC_SM) {
     const int n = (g.nx > g.ny ? g.nx : g.ny) + 1;
     k_silver_mueller<R><<<(n + 127) / 128, 128, 0, s>>>(a);

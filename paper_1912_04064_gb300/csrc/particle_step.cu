@@ -8,13 +8,23 @@
 //      interpolated with the quadratic shape, pushed with the Boris scheme
 //      and moved;
 //   3. Esirkepov deposition (second-order shape, Section 3.2) into a shared
-//      memory current tile with a 2-node halo, 40 shared atomics per
-//      particle on the 4-node window that covers both shapes;
+//      memory current tile with a 2-node halo, on the 4-node window that
+//      covers both shapes (at most 40 shared atomics per particle, exact
+//      zeros skipped);
 //   4. SDMD step (i): the tile is added into the region current;
 //   5. re-binning: particles that stay are compacted into the output
 //      segment, particles that left are appended to the direction bucket
 //      read by the destination patch at the next step (positions already
 //      rebased to it), boundary conditions applied at the domain faces.
+//
+// The Esirkepov weights are evaluated as outer products of 1D factors:
+// with DS = S1 - S0 and A = S0 + DS/2 on each axis,
+//   W_x = DSx (x) A_y,  W_y = A_x (x) DSy,  W_z = A_x (x) A_y + DSx (x) DSy / 12
+// (the last identity: S0xS0y + DSxS0y/2 + S0xDSy/2 + DSxDSy/3 =
+// (S0x + DSx/2)(S0y + DSy/2) + DSxDSy/12), and the prefix sums of DS along
+// the window end at exactly zero (sum DS = 0), written as -DS[3].
+#include <cstring>
+
 #include "common.cuh"
 
 namespace pic {
@@ -32,37 +42,120 @@ __device__ __forceinline__ double below<double>(double v) {
   return __longlong_as_double(__double_as_longlong(v) - 1);
 }
 
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+
 template <typename R>
-__device__ __forceinline__ R gather(const R *T, int BX, int cx, const R Sx[3], int ry,
-                                    const R Sy[3]) {
-  const R *r0 = T + ry * BX + cx;
-  R v = R(0);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const R *r = r0 + b * BX;
-    v += Sy[b] * (Sx[0] * r[0] + Sx[1] * r[1] + Sx[2] * r[2]);
-  }
-  return v;
+struct Vec;
+template <>
+struct Vec<float> {
+  using T = float4;
+};
+template <>
+struct Vec<double> {
+  using T = double2;
+};
+
+// Quadratic B-spline weights of the primal (node) and dual (half-node)
+// stencils of one coordinate xi (cells): primal nearest node ip =
+// floor(xi + 1/2), dual nearest id = floor(xi), both from one floor.
+template <typename R>
+__device__ __forceinline__ void shapes(R xi, int &ip, R Sp[3], int &id, R Sd[3]) {
+  const R fl = floor(xi);
+  const R fr = xi - fl;
+  const bool up = fr >= R(0.5);
+  id = (int)fl;
+  ip = id + (up ? 1 : 0);
+  const R dp = up ? fr - R(1) : fr;
+  const R dd = fr - R(0.5);
+  R a = R(0.5) - dp, b = R(0.5) + dp;
+  Sp[0] = R(0.5) * a * a;
+  Sp[1] = R(0.75) - dp * dp;
+  Sp[2] = R(0.5) * b * b;
+  a = R(0.5) - dd;
+  b = R(0.5) + dd;
+  Sd[0] = R(0.5) * a * a;
+  Sd[1] = R(0.75) - dd * dd;
+  Sd[2] = R(0.5) * b * b;
 }
 
-// Place the three shape weights into a 4-node window: shifted by one node
-// when `sh` is set.
 template <typename R>
-__device__ __forceinline__ void window4(const R S3[3], int sh, R S[4]) {
+__device__ __forceinline__ int shape_primal(R xi, R S[3]) {
+  const R fl = floor(xi);
+  const R fr = xi - fl;
+  const bool up = fr >= R(0.5);
+  const R d = up ? fr - R(1) : fr;
+  const R a = R(0.5) - d, b = R(0.5) + d;
+  S[0] = R(0.5) * a * a;
+  S[1] = R(0.75) - d * d;
+  S[2] = R(0.5) * b * b;
+  return (int)fl + (up ? 1 : 0);
+}
+
+// Sum of a 3 x 3 stencil at tile offset o (row stride BX).
+template <typename R, int BXc>
+__device__ __forceinline__ R gather(const R *T, int BXr, int o, const R Sx[3], const R Sy[3]) {
+  const int BX = BXc ? BXc : BXr;
+  const R *r = T + o;
+  return Sy[0] * (Sx[0] * r[0] + Sx[1] * r[1] + Sx[2] * r[2]) +
+         Sy[1] * (Sx[0] * r[BX] + Sx[1] * r[BX + 1] + Sx[2] * r[BX + 2]) +
+         Sy[2] * (Sx[0] * r[2 * BX] + Sx[1] * r[2 * BX + 1] + Sx[2] * r[2 * BX + 2]);
+}
+
+// Place three shape weights in a 4-node window, shifted one node when sh.
+template <typename R>
+__device__ __forceinline__ void window4(const R S3[3], bool sh, R S[4]) {
   S[0] = sh ? R(0) : S3[0];
   S[1] = sh ? S3[0] : S3[1];
   S[2] = sh ? S3[1] : S3[2];
   S[3] = sh ? S3[2] : R(0);
 }
 
-template <typename R, bool TMA>
-__global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ CUtensorMap tmap,
-                                                       const StepArgs<R> a) {
+// The 40 current contributions of one window: Jx rows l (4) x dual columns
+// q (3); Jy columns q (4) x dual rows l (3); Jz 4 x 4.
+template <typename R>
+struct Win {
+  R x[4][3], y[4][3], z[4][4];
+};
+
+template <typename R, int JWc>
+__device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<R> &w) {
+  const int JW = JWc ? JWc : JWr;
+  R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (w.x[l][q] != R(0)) atomicAdd(&Jx[l * JW + q], w.x[l][q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (w.y[q][l] != R(0)) atomicAdd(&Jy[l * JW + q], w.y[q][l]);
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (w.z[l][q] != R(0)) atomicAdd(&Jz[l * JW + q], w.z[l][q]);
+}
+
+// Particle step kernel.  PT, QT: patch size known at compile time (0 =
+// runtime).  MERGE: consecutive particles of a thread that share a window
+// are summed in registers before one set of shared atomics.
+template <typename R, int PT, int QT, bool TMA, bool MERGE>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
+    k_particle_step(const __grid_constant__ CUtensorMap tmap, const StepArgs<R> a) {
+  constexpr int M = 16 / sizeof(R);  // particles per thread: one 128-bit load per array
+  constexpr int BXc = PT ? PT + 8 : 0, BYc = QT ? QT + 3 : 0;
+  constexpr int JWc = PT ? PT + 5 : 0, JHc = QT ? QT + 5 : 0;
+  using V = typename Vec<R>::T;
   extern __shared__ unsigned char dsm_raw[];
   __shared__ uint64_t mbar;
-  __shared__ int s_off[10];
+  __shared__ int s_qoff[10];
   __shared__ int s_cnt[9];
-  __shared__ int s_src[9];
+  __shared__ long long s_base[9];
   __shared__ int s_out;
   __shared__ int s_bcnt[8];
   __shared__ int s_ok;
@@ -70,12 +163,13 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
   const Geom &g = a.g;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int s = blockIdx.x;
-  const int P = g.P, Q = g.Q;
-  const int BX = P + 8, BY = Q + 3;   // field tile
-  const int JW = P + 5, JH = Q + 5;   // current tile
+  const int P = PT ? PT : g.P, Q = QT ? QT : g.Q;
+  const int BX = BXc ? BXc : P + 8, BY = BYc ? BYc : Q + 3;  // field tile
+  const int JW = JWc ? JWc : P + 5, JH = JHc ? JHc : Q + 5;  // current tile
+  const int FT = BY * BX, JT = JH * JW;
   const uint32_t pad = (128u - (smem_u32(dsm_raw) & 127u)) & 127u;
   R *Ft = reinterpret_cast<R *>(dsm_raw + pad);
-  R *Jt = Ft + 6 * BY * BX;
+  R *Jt = Ft + 6 * FT;
 
   const int col0 = a.st->col0;
   const int sxs = s % g.npx, sy = s / g.npx;
@@ -92,35 +186,40 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
     }
     __syncthreads();
     if (tid == 0) {
-      mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * BY * BX * sizeof(R)));
+      mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
       tma_load_3d(Ft, &tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
     }
   } else {
-    for (int e = tid; e < 6 * BY * BX; e += nth) {
-      int c = e / (BY * BX), r = e - c * (BY * BX), yy = r / BX, xx = r - yy * BX;
+    for (int e = tid; e < 6 * FT; e += nth) {
+      int c = e / FT, r = e - c * FT, yy = r / BX, xx = r - yy * BX;
       Ft[e] = a.F[c * g.cs + fidx(g, X0 - 4 + xx, Y0 - 1 + yy)];
     }
   }
-  for (int e = tid; e < 3 * JH * JW; e += nth) Jt[e] = R(0);
+  for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
   if (tid < 9) {
-    int cnt = 0, src = s;
+    int cnt = 0;
+    long long base = 0;
     if (tid == 0) {
       cnt = a.cnt_in[s];
+      base = (long long)s * a.cap;
     } else {
       int k = tid - 1, ddx, ddy;
       dir_delta(k, ddx, ddy);
-      src = neighbour_slot(g, col0, s, -ddx, -ddy);
-      cnt = src >= 0 ? a.bcnt_in[(long long)src * 8 + k] : 0;
+      const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
+      if (src >= 0) {
+        cnt = a.bcnt_in[(long long)src * 8 + k];
+        base = (long long)src * a.bk.stride + a.bk.off[k];
+      }
     }
-    s_src[tid] = src;
     s_cnt[tid] = cnt;
+    s_base[tid] = base;
   }
   if (tid < 8) s_bcnt[tid] = 0;
   if (tid == 0) s_out = 0;
   __syncthreads();
   if (tid == 0) {
-    s_off[0] = 0;
-    for (int i = 0; i < 9; ++i) s_off[i + 1] = s_off[i] + s_cnt[i];
+    s_qoff[0] = 0;
+    for (int i = 0; i < 9; ++i) s_qoff[i + 1] = s_qoff[i] + (s_cnt[i] + M - 1) / M;
     int ok = 1;
     if (TMA) {
       ok = 0;
@@ -137,188 +236,228 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
   __syncthreads();
   if (!s_ok) return;
 
-  // ---- 2..5. particles
-  const int total = s_off[9];
+  // ---- 2..5. particles, M per thread
+  const int totalq = s_qoff[9];
   const R rdx = R(g.dt / g.dx), rdy = R(g.dt / g.dy);
   const R eps = R(g.q * g.dt / (2.0 * g.m));
   const R cjx = R(-g.q * g.dx / g.dt), cjy = R(-g.q * g.dy / g.dt), cjz = R(g.q);
   const R RP = R(P), RQ = R(Q);
   const int lane = tid & 31;
-  R *Jx = Jt, *Jy = Jt + JH * JW, *Jz = Jt + 2 * JH * JW;
-  const R *TEx = Ft, *TEy = Ft + BY * BX, *TEz = Ft + 2 * BY * BX;
-  const R *TBx = Ft + 3 * BY * BX, *TBy = Ft + 4 * BY * BX, *TBz = Ft + 5 * BY * BX;
   unsigned err = 0;
 
-  for (int b0 = 0; b0 < total; b0 += nth) {
-    const int k = b0 + tid;
-    bool alive = k < total;
-    R x = 0, y = 0, ux = 0, uy = 0, uz = 0, w = 0;
-    if (alive) {
+  for (int qb = 0; qb < totalq; qb += nth) {
+    const int qi = qb + tid;
+    int nval = 0;
+    R x[M], y[M], ux[M], uy[M], uz[M], w[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) x[m] = y[m] = ux[m] = uy[m] = uz[m] = w[m] = R(0);
+    if (qi < totalq) {
       int src = 0;
-      while (src < 8 && k >= s_off[src + 1]) ++src;
-      const int kk = k - s_off[src];
-      if (src == 0) {
-        const long long i = (long long)s * a.cap + kk;
-        x = a.pin.x[i]; y = a.pin.y[i];
-        ux = a.pin.ux[i]; uy = a.pin.uy[i]; uz = a.pin.uz[i]; w = a.pin.w[i];
+      while (src < 8 && qi >= s_qoff[src + 1]) ++src;
+      const int k0 = (qi - s_qoff[src]) * M;
+      nval = min(M, s_cnt[src] - k0);
+      const SoA<R> &A = src == 0 ? a.pin : a.bin;
+      const long long b = s_base[src] + k0;
+      if (nval == M) {
+        const V vx = *reinterpret_cast<const V *>(A.x + b);
+        const V vy = *reinterpret_cast<const V *>(A.y + b);
+        const V vux = *reinterpret_cast<const V *>(A.ux + b);
+        const V vuy = *reinterpret_cast<const V *>(A.uy + b);
+        const V vuz = *reinterpret_cast<const V *>(A.uz + b);
+        const V vw = *reinterpret_cast<const V *>(A.w + b);
+        memcpy(x, &vx, sizeof vx);
+        memcpy(y, &vy, sizeof vy);
+        memcpy(ux, &vux, sizeof vux);
+        memcpy(uy, &vuy, sizeof vuy);
+        memcpy(uz, &vuz, sizeof vuz);
+        memcpy(w, &vw, sizeof vw);
       } else {
-        const long long i = (long long)s_src[src] * a.bk.stride + a.bk.off[src - 1] + kk;
-        x = a.bin.x[i]; y = a.bin.y[i];
-        ux = a.bin.ux[i]; uy = a.bin.uy[i]; uz = a.bin.uz[i]; w = a.bin.w[i];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+          if (m < nval) {
+            x[m] = A.x[b + m]; y[m] = A.y[b + m];
+            ux[m] = A.ux[b + m]; uy[m] = A.uy[b + m]; uz[m] = A.uz[b + m]; w[m] = A.w[b + m];
+          }
       }
     }
-    int ddx = 0, ddy = 0;
-    if (alive) {
-      // interpolation at x^n with the shape of each component's stagger
-      R Sxp[3], Sxd[3], Syp[3], Syd[3];
-      const int ip = shape2(x, Sxp);
-      const int id = shape2(x - R(0.5), Sxd);
-      const int jp = shape2(y, Syp);
-      const int jd = shape2(y - R(0.5), Syd);
-      const R Ex = gather(TEx, BX, id + 3, Sxd, jp, Syp);
-      const R Ey = gather(TEy, BX, ip + 3, Sxp, jd, Syd);
-      const R Ez = gather(TEz, BX, ip + 3, Sxp, jp, Syp);
-      const R Bx = gather(TBx, BX, ip + 3, Sxp, jd, Syd);
-      const R By = gather(TBy, BX, id + 3, Sxd, jp, Syp);
-      const R Bz = gather(TBz, BX, id + 3, Sxd, jd, Syd);
-      // Boris push u^{n-1/2} -> u^{n+1/2}
-      const R umx = ux + eps * Ex, umy = uy + eps * Ey, umz = uz + eps * Ez;
-      const R gm = sqrt(R(1) + umx * umx + umy * umy + umz * umz);
-      const R ig = eps / gm;
-      const R tx = ig * Bx, ty = ig * By, tz = ig * Bz;
-      const R f = R(2) / (R(1) + tx * tx + ty * ty + tz * tz);
-      const R sx_ = f * tx, sy_ = f * ty, sz_ = f * tz;
-      const R upx = umx + (umy * tz - umz * ty);
-      const R upy = umy + (umz * tx - umx * tz);
-      const R upz = umz + (umx * ty - umy * tx);
-      ux = umx + (upy * sz_ - upz * sy_) + eps * Ex;
-      uy = umy + (upz * sx_ - upx * sz_) + eps * Ey;
-      uz = umz + (upx * sy_ - upy * sx_) + eps * Ez;
-      const R gam = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-      const R inv = R(1) / gam;
-      R x1 = x + rdx * ux * inv;
-      R y1 = y + rdy * uy * inv;
-      // Esirkepov deposition on the 4-node window covering S(x^n), S(x^{n+1})
-      R S1x3[3], S1y3[3];
-      const int i1 = shape2(x1, S1x3);
-      const int j1 = shape2(y1, S1y3);
-      const int di = i1 - ip, dj = j1 - jp;
-      if (!(isfinite(x1) && isfinite(y1) && isfinite(ux) && isfinite(uy) && isfinite(uz))) {
-        err |= ERR_NONFINITE;
-        alive = false;
-      } else if (di < -1 || di > 1 || dj < -1 || dj > 1) {
-        err |= ERR_FAST;
-        alive = false;
-      } else {
-        const int shx = di < 0, shy = dj < 0;
-        R S0x[4], S1x[4], S0y[4], S1y[4], DSx[4], DSy[4];
-        window4(Sxp, shx, S0x);
-        window4(S1x3, di + shx, S1x);
-        window4(Syp, shy, S0y);
-        window4(S1y3, dj + shy, S1y);
+    Win<R> acc;
+    int key = -1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          DSx[q] = S1x[q] - S0x[q];
-          DSy[q] = S1y[q] - S0y[q];
-        }
-        const int cx = ip - 1 - shx + 2, cy = jp - 1 - shy + 2;  // tile coords
-        const R wjx = cjx * w, wjy = cjy * w, wjz = cjz * w * uz * inv;
+    for (int m = 0; m < M; ++m) {
+      int dir = -2;  // -1 stay, -2 gone / invalid, 0..7 bucket
+      R x1 = R(0), y1 = R(0), nux = R(0), nuy = R(0), nuz = R(0);
+      if (m < nval) {
+        // interpolation at x^n with the shape of each component's stagger
+        int ip, id, jp, jd;
+        R Sxp[3], Sxd[3], Syp[3], Syd[3];
+        shapes(x[m], ip, Sxp, id, Sxd);
+        shapes(y[m], jp, Syp, jd, Syd);
+        // tile offsets: column node n -> n + 3 (tile starts at node -4,
+        // stencil at n - 1); row node n -> n (tile starts at node -1)
+        const int opp = jp * BX + ip + 3, opd = jd * BX + ip + 3;
+        const int odp = jp * BX + id + 3, odd = jd * BX + id + 3;
+        const R Ex = gather<R, BXc>(Ft, BX, odp, Sxd, Syp);
+        const R Ey = gather<R, BXc>(Ft + FT, BX, opd, Sxp, Syd);
+        const R Ez = gather<R, BXc>(Ft + 2 * FT, BX, opp, Sxp, Syp);
+        const R Bx = gather<R, BXc>(Ft + 3 * FT, BX, opd, Sxp, Syd);
+        const R By = gather<R, BXc>(Ft + 4 * FT, BX, odp, Sxd, Syp);
+        const R Bz = gather<R, BXc>(Ft + 5 * FT, BX, odd, Sxd, Syd);
+        // Boris push u^{n-1/2} -> u^{n+1/2}
+        const R umx = ux[m] + eps * Ex, umy = uy[m] + eps * Ey, umz = uz[m] + eps * Ez;
+        const R ig = eps * rsq(R(1) + umx * umx + umy * umy + umz * umz);
+        const R tx = ig * Bx, ty = ig * By, tz = ig * Bz;
+        const R f = quot(R(2), R(1) + tx * tx + ty * ty + tz * tz);
+        const R upx = umx + (umy * tz - umz * ty);
+        const R upy = umy + (umz * tx - umx * tz);
+        const R upz = umz + (umx * ty - umy * tx);
+        nux = umx + f * (upy * tz - upz * ty) + eps * Ex;
+        nuy = umy + f * (upz * tx - upx * tz) + eps * Ey;
+        nuz = umz + f * (upx * ty - upy * tx) + eps * Ez;
+        const R inv = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+        x1 = x[m] + rdx * nux * inv;
+        y1 = y[m] + rdy * nuy * inv;
+        R S1x3[3], S1y3[3];
+        const int i1 = shape_primal(x1, S1x3);
+        const int j1 = shape_primal(y1, S1y3);
+        const int di = i1 - ip, dj = j1 - jp;
+        const bool finite = isfinite(x1) && isfinite(y1) && isfinite(nux) && isfinite(nuy) &&
+                            isfinite(nuz);
+        const bool slow = di >= -1 && di <= 1 && dj >= -1 && dj <= 1;
+        if (!finite) err |= ERR_NONFINITE;
+        else if (!slow) err |= ERR_FAST;
+        if (finite && slow) {
+          // Esirkepov weights on the 4-node window covering S(x^n), S(x^{n+1})
+          const bool shx = di < 0, shy = dj < 0;
+          R S0x[4], S1x[4], S0y[4], S1y[4], DSx[4], DSy[4], Ax[4], Ay[4];
+          window4(Sxp, shx, S0x);
+          window4(S1x3, di + (shx ? 1 : 0) != 0, S1x);
+          window4(Syp, shy, S0y);
+          window4(S1y3, dj + (shy ? 1 : 0) != 0, S1y);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          const R Ay = S0y[l] + R(0.5) * DSy[l];
-          R acc = R(0);
+          for (int c = 0; c < 4; ++c) {
+            DSx[c] = S1x[c] - S0x[c];
+            DSy[c] = S1y[c] - S0y[c];
+            Ax[c] = S0x[c] + R(0.5) * DSx[c];
+            Ay[c] = S0y[c] + R(0.5) * DSy[c];
+          }
+          const R wx = cjx * w[m], wy = cjy * w[m], wz = cjz * w[m] * nuz * inv;
+          const R Px[3] = {wx * DSx[0], wx * (DSx[0] + DSx[1]), -wx * DSx[3]};
+          const R Py[3] = {wy * DSy[0], wy * (DSy[0] + DSy[1]), -wy * DSy[3]};
+          R zA[4], zD[4];
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            acc += DSx[q] * Ay;
-            atomicAdd(&Jx[(cy + l) * JW + cx + q], wjx * acc);
+          for (int c = 0; c < 4; ++c) {
+            zA[c] = wz * Ax[c];
+            zD[c] = (wz * R(1.0 / 12.0)) * DSx[c];
+          }
+          Win<R> cur;
+#pragma unroll
+          for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cur.x[l][q] = Px[q] * Ay[l];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) cur.y[q][l] = Py[l] * Ax[q];
+#pragma unroll
+          for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur.z[l][q] = zA[q] * Ay[l] + zD[q] * DSy[l];
+          // window origin in the current tile (tile starts at node -2)
+          const int o = (jp - 1 - (shy ? 1 : 0) + 2) * JW + ip - 1 - (shx ? 1 : 0) + 2;
+          if (MERGE) {
+            if (o == key) {
+#pragma unroll
+              for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  acc.x[l][q] += cur.x[l][q];
+                  acc.y[l][q] += cur.y[l][q];
+                }
+#pragma unroll
+              for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc.z[l][q] += cur.z[l][q];
+            } else {
+              if (key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc);
+              acc = cur;
+              key = o;
+            }
+          } else {
+            flush<R, JWc>(Jt, JW, JT, o, cur);
+          }
+          // boundary conditions at domain faces, then destination patch
+          int ddx = 0, ddy = 0;
+          if (x1 < R(0)) ddx = -1; else if (x1 >= RP) ddx = 1;
+          if (y1 < R(0)) ddy = -1; else if (y1 >= RQ) ddy = 1;
+          bool gone = false;
+          if (ddx != 0 && (px + ddx < 0 || px + ddx >= g.npx)) {
+            const int bc = g.pbc[0][ddx > 0];
+            if (bc == PBC_REFLECT) {
+              x1 = ddx < 0 ? -x1 : R(2 * P) - x1;
+              if (x1 >= RP) x1 = below(RP);
+              nux = -nux;
+              ddx = 0;
+            } else if (bc == PBC_REMOVE) {
+              gone = true;
+            }
+          }
+          if (ddy != 0 && (py + ddy < 0 || py + ddy >= g.npy)) {
+            const int bc = g.pbc[1][ddy > 0];
+            if (bc == PBC_REFLECT) {
+              y1 = ddy < 0 ? -y1 : R(2 * Q) - y1;
+              if (y1 >= RQ) y1 = below(RQ);
+              nuy = -nuy;
+              ddy = 0;
+            } else if (bc == PBC_REMOVE) {
+              gone = true;
+            }
+          }
+          if (!gone) {
+            if (ddx < 0) { x1 += RP; if (x1 >= RP) x1 = below(RP); }
+            else if (ddx > 0) x1 -= RP;
+            if (ddy < 0) { y1 += RQ; if (y1 >= RQ) y1 = below(RQ); }
+            else if (ddy > 0) y1 -= RQ;
+            dir = (ddx == 0 && ddy == 0) ? -1 : dir_index(ddx, ddy);
           }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const R Ax = S0x[q] + R(0.5) * DSx[q];
-          R acc = R(0);
-#pragma unroll
-          for (int l = 0; l < 3; ++l) {
-            acc += DSy[l] * Ax;
-            atomicAdd(&Jy[(cy + l) * JW + cx + q], wjy * acc);
-          }
+      }
+      // compaction of the particles that stay (warp ballot, one shared
+      // atomic per warp), exits appended to their direction bucket
+      const bool stay = dir == -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, stay);
+      int wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(&s_out, __popc(bal));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (stay) {
+        const int pos = wbase + __popc(bal & ((1u << lane) - 1u));
+        if (pos < a.cap) {
+          const long long i = (long long)s * a.cap + pos;
+          a.pout.x[i] = x1; a.pout.y[i] = y1;
+          a.pout.ux[i] = nux; a.pout.uy[i] = nuy; a.pout.uz[i] = nuz; a.pout.w[i] = w[m];
+        } else {
+          err |= ERR_OVERFLOW_SEG;
         }
-#pragma unroll
-        for (int l = 0; l < 4; ++l)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const R Wz = S0x[q] * S0y[l] + R(0.5) * DSx[q] * S0y[l] +
-                         R(0.5) * S0x[q] * DSy[l] + R(1.0 / 3.0) * DSx[q] * DSy[l];
-            atomicAdd(&Jz[(cy + l) * JW + cx + q], wjz * Wz);
-          }
-        // boundary conditions at domain faces, then destination patch
-        if (x1 < R(0)) ddx = -1; else if (x1 >= RP) ddx = 1;
-        if (y1 < R(0)) ddy = -1; else if (y1 >= RQ) ddy = 1;
-        if (ddx != 0 && (px + ddx < 0 || px + ddx >= g.npx)) {
-          const int bc = g.pbc[0][ddx > 0];
-          if (bc == PBC_REFLECT) {
-            x1 = ddx < 0 ? -x1 : R(2 * P) - x1;
-            if (x1 >= RP) x1 = below(RP);
-            ux = -ux;
-            ddx = 0;
-          } else if (bc == PBC_REMOVE) {
-            alive = false;
-          }
+      } else if (dir >= 0) {
+        const int bp = atomicAdd(&s_bcnt[dir], 1);
+        if (bp < a.bk.cap[dir]) {
+          const long long i = (long long)s * a.bk.stride + a.bk.off[dir] + bp;
+          a.bout.x[i] = x1; a.bout.y[i] = y1;
+          a.bout.ux[i] = nux; a.bout.uy[i] = nuy; a.bout.uz[i] = nuz; a.bout.w[i] = w[m];
+        } else {
+          err |= ERR_OVERFLOW_BKT;
         }
-        if (ddy != 0 && (py + ddy < 0 || py + ddy >= g.npy)) {
-          const int bc = g.pbc[1][ddy > 0];
-          if (bc == PBC_REFLECT) {
-            y1 = ddy < 0 ? -y1 : R(2 * Q) - y1;
-            if (y1 >= RQ) y1 = below(RQ);
-            uy = -uy;
-            ddy = 0;
-          } else if (bc == PBC_REMOVE) {
-            alive = false;
-          }
-        }
-        if (ddx < 0) { x1 += RP; if (x1 >= RP) x1 = below(RP); }
-        else if (ddx > 0) x1 -= RP;
-        if (ddy < 0) { y1 += RQ; if (y1 >= RQ) y1 = below(RQ); }
-        else if (ddy > 0) y1 -= RQ;
-        x = x1;
-        y = y1;
       }
     }
-    // compaction of the particles that stay
-    const bool stay = alive && ddx == 0 && ddy == 0;
-    const unsigned m = __ballot_sync(0xffffffffu, stay);
-    int wbase = 0;
-    if (lane == 0 && m) wbase = atomicAdd(&s_out, __popc(m));
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (stay) {
-      const int pos = wbase + __popc(m & ((1u << lane) - 1u));
-      if (pos < a.cap) {
-        const long long i = (long long)s * a.cap + pos;
-        a.pout.x[i] = x; a.pout.y[i] = y;
-        a.pout.ux[i] = ux; a.pout.uy[i] = uy; a.pout.uz[i] = uz; a.pout.w[i] = w;
-      } else {
-        err |= ERR_OVERFLOW_SEG;
-      }
-    } else if (alive) {
-      const int dir = dir_index(ddx, ddy);
-      const int pos = atomicAdd(&s_bcnt[dir], 1);
-      if (pos < a.bk.cap[dir]) {
-        const long long i = (long long)s * a.bk.stride + a.bk.off[dir] + pos;
-        a.bout.x[i] = x; a.bout.y[i] = y;
-        a.bout.ux[i] = ux; a.bout.uy[i] = uy; a.bout.uz[i] = uz; a.bout.w[i] = w;
-      } else {
-        err |= ERR_OVERFLOW_BKT;
-      }
-    }
+    if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc);
   }
   if (err) atomicOr(&a.st->err, err);
   __syncthreads();
 
   // ---- SDMD step (i): patch current tile -> region current
-  for (int e = tid; e < 3 * JH * JW; e += nth) {
+  for (int e = tid; e < 3 * JT; e += nth) {
     const R v = Jt[e];
     if (v != R(0)) {
-      const int c = e / (JH * JW), r = e - c * (JH * JW), l = r / JW, q = r - l * JW;
+      const int c = e / JT, r = e - c * JT, l = r / JW, q = r - l * JW;
       int gi = X0 - 2 + q, gj = Y0 - 2 + l;
       if (g.fbc_x == FBC_PERIODIC) gi = gi < 0 ? gi + g.nx : (gi >= g.nx ? gi - g.nx : gi);
       if (g.fbc_y == FBC_PERIODIC) gj = gj < 0 ? gj + g.ny : (gj >= g.ny ? gj - g.ny : gj);
@@ -334,6 +473,27 @@ __global__ void __launch_bounds__(256) k_particle_step(const __grid_constant__ C
     a.bcnt_out[(long long)s * 8 + tid] = s_bcnt[tid] < a.bk.cap[tid] ? s_bcnt[tid] : a.bk.cap[tid];
 }
 
+template <typename R, int PT, int QT, bool TMA, bool MERGE>
+const void *kernel_ptr() {
+  return (const void *)k_particle_step<R, PT, QT, TMA, MERGE>;
+}
+
+// Kernel for a patch shape: compile-time tile sizes for the common square
+// patches, a runtime-size kernel otherwise; plain loads always runtime-size.
+template <typename R, bool MERGE>
+const void *pick(int P, int Q, bool tma) {
+  if (!tma) return kernel_ptr<R, 0, 0, false, MERGE>();
+  if (P == 32 && Q == 32) return kernel_ptr<R, 32, 32, true, MERGE>();
+  if (P == 16 && Q == 16) return kernel_ptr<R, 16, 16, true, MERGE>();
+  if (P == 8 && Q == 8) return kernel_ptr<R, 8, 8, true, MERGE>();
+  return kernel_ptr<R, 0, 0, true, MERGE>();
+}
+
+template <typename R>
+const void *pick_kernel(int P, int Q, bool tma, bool merge) {
+  return merge ? pick<R, true>(P, Q, tma) : pick<R, false>(P, Q, tma);
+}
+
 }  // namespace
 
 size_t particle_step_smem(int P, int Q, size_t rsize) {
@@ -343,27 +503,30 @@ size_t particle_step_smem(int P, int Q, size_t rsize) {
 template <typename R>
 cudaError_t prepare_particle_step(int P, int Q) {
   const int smem = (int)particle_step_smem(P, Q, sizeof(R));
-  cudaError_t e = cudaFuncSetAttribute(k_particle_step<R, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_particle_step<R, false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int t = 0; t < 2; ++t)
+    for (int mg = 0; mg < 2; ++mg) {
+      cudaError_t e = cudaFuncSetAttribute(pick_kernel<R>(P, Q, t != 0, mg != 0),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 int block, cudaStream_t s) {
+                                 bool merge, int block, cudaStream_t s) {
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
-  auto kern = tma ? k_particle_step<R, true> : k_particle_step<R, false>;
-  kern<<<a.g.nslots, block, smem, s>>>(*tmap, a);
-  return cudaGetLastError();
+  const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge);
+  void *args[] = {(void *)tmap, (void *)&a};
+  return cudaLaunchKernel(k, dim3(a.g.nslots), dim3(block), args, smem, s);
 }
 
 template cudaError_t prepare_particle_step<float>(int, int);
 template cudaError_t prepare_particle_step<double>(int, int);
 template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const CUtensorMap *,
-                                                 bool, int, cudaStream_t);
+                                                 bool, bool, int, cudaStream_t);
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
-                                                  const CUtensorMap *, bool, int, cudaStream_t);
+                                                  const CUtensorMap *, bool, bool, int,
+                                                  cudaStream_t);
 
 }  // namespace pic

@@ -295,7 +295,43 @@ __global__ void k_window_inject(const Geom g, int slot_col, int nshift, SoA<R> s
   if (threadIdx.x == 0) cnt[slot] = total;
 }
 
+template <typename R>
+__global__ void k_repack(const Geom g, SoA<R> src, const int *cnt_src, int cap_src, SoA<R> bsrc,
+                         const int *bcnt_src, Buckets bk_src, SoA<R> dst, int *cnt_dst,
+                         int cap_dst, SoA<R> bdst, int *bcnt_dst, Buckets bk_dst) {
+  const int slot = blockIdx.x;
+  const int n = min(cnt_src[slot], cap_dst);
+  const long long so = (long long)slot * cap_src, dof = (long long)slot * cap_dst;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    dst.x[dof + k] = src.x[so + k]; dst.y[dof + k] = src.y[so + k];
+    dst.ux[dof + k] = src.ux[so + k]; dst.uy[dof + k] = src.uy[so + k];
+    dst.uz[dof + k] = src.uz[so + k]; dst.w[dof + k] = src.w[so + k];
+  }
+  for (int d = 0; d < 8; ++d) {
+    const int nb = min(bcnt_src[(long long)slot * 8 + d], bk_dst.cap[d]);
+    const long long bs = (long long)slot * bk_src.stride + bk_src.off[d];
+    const long long bd = (long long)slot * bk_dst.stride + bk_dst.off[d];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      bdst.x[bd + k] = bsrc.x[bs + k]; bdst.y[bd + k] = bsrc.y[bs + k];
+      bdst.ux[bd + k] = bsrc.ux[bs + k]; bdst.uy[bd + k] = bsrc.uy[bs + k];
+      bdst.uz[bd + k] = bsrc.uz[bs + k]; bdst.w[bd + k] = bsrc.w[bs + k];
+    }
+    if (threadIdx.x == 0) bcnt_dst[(long long)slot * 8 + d] = nb;
+  }
+  if (threadIdx.x == 0) cnt_dst[slot] = n;
+}
+
 }  // namespace
+
+template <typename R>
+cudaError_t launch_repack(const Geom &g, SoA<R> src, const int *cnt_src, int cap_src,
+                          SoA<R> bsrc, const int *bcnt_src, Buckets bk_src, SoA<R> dst,
+                          int *cnt_dst, int cap_dst, SoA<R> bdst, int *bcnt_dst, Buckets bk_dst,
+                          cudaStream_t s) {
+  k_repack<R><<<g.nslots, 256, 0, s>>>(g, src, cnt_src, cap_src, bsrc, bcnt_src, bk_src, dst,
+                                        cnt_dst, cap_dst, bdst, bcnt_dst, bk_dst);
+  return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_bin_count(const Geom &g, int col0, const double *x, const double *y, size_t n,
@@ -356,6 +392,9 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
 }
 
 #define PIC_INST(R)                                                                           \
+  template cudaError_t launch_repack<R>(const Geom &, SoA<R>, const int *, int, SoA<R>,        \
+                                        const int *, Buckets, SoA<R>, int *, int, SoA<R>,      \
+                                        int *, Buckets, cudaStream_t);                         \
   template cudaError_t launch_bin_count<R>(const Geom &, int, const double *, const double *, \
                                            size_t, int *, unsigned *, cudaStream_t);          \
   template cudaError_t launch_bin_place<R>(const Geom &, int, const double *, const double *, \

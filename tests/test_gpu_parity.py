@@ -306,3 +306,30 @@ def test_full_size_lwfa_single_step_fp64_and_fp32():
     print("full-size fp32", errs)
     _assert_fields(errs, TOL32_J, names=("Jx", "Jy", "Jz"))
     _assert_fields(errs, TOL32_F, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz"))
+
+
+def test_auto_grow_replays_overflowing_steps():
+    """Converging flows pile particles into the central patches; with a
+    patch capacity sized exactly to the initial load, pic_step grows the
+    capacity and replays: results equal a run that never overflowed."""
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    rng = np.random.default_rng(5)
+    n = 20000
+    x = rng.uniform(0, 6.4, n)
+    y = rng.uniform(0, 6.4, n)
+    parts = {"x": x, "y": y, "ux": -2.0 * np.sign(x - 3.2), "uy": -2.0 * np.sign(y - 3.2),
+             "uz": np.zeros(n), "w": np.full(n, 0.01)}
+    small = pic.Pic(pic.config_from_run(run, "fp64", capacity_factor=1.0, capacity_min=32))
+    big = pic.Pic(pic.config_from_run(run, "fp64", capacity_factor=8.0))
+    for g in (small, big):
+        g.pic_load_particles(parts)
+    cap0 = small.pic_diag()["capacity"]
+    small.pic_step(20)
+    big.pic_step(20)
+    d = small.pic_diag()
+    assert d["grows"] >= 1 and d["capacity"] > cap0
+    assert d["max_patch_count"] > cap0
+    for k in ("Ex", "Ey", "Jx", "Jy", "Bz"):
+        a, b = small.pic_get_field(k), big.pic_get_field(k)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), k
+    assert small.pic_diag()["np"] == big.pic_diag()["np"] == n
