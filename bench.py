@@ -123,7 +123,7 @@ def algorithmic_bytes(npart, ncell, rsize):
             npart * per_particle_kernel + ncell * per_cell_kernel)
 
 
-def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1):
+def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1, sort=0):
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -135,7 +135,8 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     rs = 4 if prec == "fp32" else 8
     stream = torch.cuda.Stream(device=device)
     cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                              use_graph=True, timing=False, capacity_factor=cf, merge=merge)
+                              use_graph=True, timing=False, capacity_factor=cf, merge=merge,
+                              sort_every=sort)
     g = pic.Pic(cfg)
     g.pic_load_particles(parts)
     g.pic_set_background("neutralising")
@@ -159,7 +160,8 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     # before the timed region), CUDA events around each phase on the
     # launching stream (no graph replay)
     cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                                use_graph=False, timing=True, capacity_factor=cf, merge=merge)
+                                use_graph=False, timing=True, capacity_factor=cf, merge=merge,
+                                sort_every=sort)
     g.close()
     gt = pic.Pic(cfg_t)
     gt.pic_restore(blob)
@@ -183,6 +185,7 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
         "step_bytes": step_bytes, "kernel_bytes": k_bytes,
         "particle_step_ms": ps_ms, "fields_ms": fd_ms,
         "window_ms": (t1["ms_window"] - t0["ms_window"]) / steps,
+        "sort_ms": (t1["ms_sort"] - t0["ms_sort"]) / steps,
         # kernels of the timed steps: the diagnostics call after them launched
         # 5 reductions (+1 deposit when the continuity residual is available)
         "launches": d1["launches"] - d0["launches"] - (5 + (0 if math.isnan(d1["continuity"]) else 1)),
@@ -255,6 +258,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="re-order particles into the interleaved cell order every N steps")
     ap.add_argument("--merge", type=int, default=-1,
                     help="deposit merging in registers: 1 on, 0 off, -1 library default")
     ap.add_argument("--capacity-factor", type=float, default=2.0,
@@ -300,11 +305,11 @@ def main():
         dist.barrier()
 
     r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist,
-                  args.capacity_factor, args.merge)
+                  args.capacity_factor, args.merge, args.sort_every)
     r64 = None
     if args.fp64_steps > 0:
         r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
-                      world, dist, args.capacity_factor)
+                      world, dist, args.capacity_factor, -1, args.sort_every)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
@@ -333,7 +338,7 @@ def main():
                      "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
                                     "bytes_per_step": r32["step_bytes"]}},
         "phases_ms": {"particle_step": r32["particle_step_ms"], "fields": r32["fields_ms"],
-                      "window": r32["window_ms"]},
+                      "window": r32["window_ms"], "sort": r32["sort_ms"]},
         "fp64": None if r64 is None else {
             "value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": args.fp64_steps,
             "particle_step_ms": r64["particle_step_ms"], "fields_ms": r64["fields_ms"],

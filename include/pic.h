@@ -105,13 +105,19 @@ typedef struct pic_config {
   int tma;                /* 1 (default if >= 0): stage field tiles with TMA;
                              0: plain coalesced loads */
   int block;              /* threads per patch block (0 = default 256) */
-  int merge;              /* deposition: sum consecutive particles sharing a
-                             current window in registers before the shared
-                             atomics: 1 on, 0 off, -1 (default) on for FP32 */
+  int merge;              /* deposition: 1 = each thread takes 4 (FP32) or 2
+                             (FP64) consecutive particles with 128-bit loads
+                             and sums those sharing a current window in
+                             registers before the shared atomics; otherwise
+                             (default) one particle per thread per slice */
   int auto_grow;          /* 1: pic_step keeps a device copy of the state at
                              entry; a patch or re-binning capacity overflow
                              grows the capacity (x1.5 or more) and replays the
                              steps instead of failing (up to 4 times) */
+  int sort_every;         /* > 0: every sort_every steps (and after loading)
+                             re-order each patch's particles so that a warp's
+                             32 lanes hold particles of 32 distinct
+                             neighbouring cells; 0: never */
 } pic_config;
 
 typedef struct pic_diag_t {
@@ -133,6 +139,8 @@ typedef struct pic_diag_t {
   long long launches;     /* kernels launched by this context so far */
   long long particle_step_launches;
   int grows;              /* capacity growths done by auto_grow */
+  long long sorts;        /* cell-order sorts done */
+  double ms_sort;         /* timer of the sorts (timing = 1) */
 } pic_diag_t;
 
 typedef struct pic_ctx pic_ctx;

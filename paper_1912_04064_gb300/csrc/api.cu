@@ -44,7 +44,7 @@ struct pic_ctx {
   CUtensorMap tmap;
   bool tmap_ok = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  double ms_particles = 0, ms_fields = 0, ms_window = 0;
+  double ms_particles = 0, ms_fields = 0, ms_window = 0, ms_sort = 0;
   long long launches = 0, ps_launches = 0;
   int sticky = PIC_OK;
   std::string err;
@@ -63,6 +63,8 @@ struct pic_ctx {
     int nshift = 0, col0 = 0;
   } bak;
   int grows = 0;
+  long long sorts = 0;
+  long long since_sort = 0;
 };
 
 namespace {
@@ -285,7 +287,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.parity = p;
   a.st = ctx->st;
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
-  const bool merge = ctx->cfg.merge < 0 ? sizeof(R) == 4 : ctx->cfg.merge != 0;
+  const bool merge = ctx->cfg.merge > 0;
   CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->stream));
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
   FieldArgs<R> f;
@@ -461,6 +463,21 @@ pic_status restore_backup(pic_ctx *ctx, int new_cap) {
   return PIC_OK;
 }
 
+// Sort the live particles into the interleaved cell order (the other
+// segment set is scratch at this point; in-flight buckets are absorbed).
+template <typename R>
+pic_status sort_particles(pic_ctx *ctx) {
+  const int q = (int)(ctx->step & 1);
+  CK(launch_sort_cells<R>(ctx->g, ctx->col0, soa<R>(ctx->seg[q]), ctx->cnt[q],
+                          soa<R>(ctx->seg[1 - q]), ctx->cnt[1 - q], ctx->cap,
+                          soa<R>(ctx->bkt[1 - q]), ctx->bcnt[1 - q], ctx->bk, &ctx->st->err,
+                          ctx->stream));
+  ctx->launches += 2;
+  ctx->sorts += 1;
+  ctx->prev_valid = false;
+  return PIC_OK;
+}
+
 template <typename R>
 pic_status run_steps(pic_ctx *ctx, int nsteps);
 
@@ -503,11 +520,28 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
   // timing: three events per step (start, between phases, end) and two per
   // window shift, read back once after the loop
   std::vector<cudaEvent_t> ev;
-  std::vector<int> kind;  // 0: step triple, 1: window pair
+  std::vector<int> kind;  // 0: step triple, 1: window pair, 2: sort pair
   auto new_event = [&](cudaEvent_t *e) -> cudaError_t { return cudaEventCreate(e); };
   pic_status rs = PIC_OK;
   for (int n = 0; n < nsteps && rs == PIC_OK; ++n) {
     const int p = (int)(ctx->step & 1);
+    if (ctx->cfg.sort_every > 0 && ctx->since_sort >= ctx->cfg.sort_every) {
+      cudaEvent_t e[2];
+      if (timing) {
+        for (int k = 0; k < 2; ++k) CK(new_event(&e[k]));
+        CK(cudaEventRecord(e[0], ctx->stream));
+      }
+      rs = sort_particles<R>(ctx);
+      if (timing) {
+        CK(cudaEventRecord(e[1], ctx->stream));
+        ev.push_back(e[0]);
+        ev.push_back(e[1]);
+        kind.push_back(2);
+      }
+      if (rs) break;
+      ctx->since_sort = 0;
+    }
+    ctx->since_sort += 1;
     if (use_graph) {
       CK(cudaGraphLaunch(ctx->gexec[p], ctx->stream));
     } else if (timing) {
@@ -554,7 +588,7 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
         k += 3;
       } else {
         CK(cudaEventElapsedTime(&a, ev[k], ev[k + 1]));
-        ctx->ms_window += a;
+        (t == 1 ? ctx->ms_window : ctx->ms_sort) += a;
         k += 2;
       }
     }
@@ -619,6 +653,11 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
                          soa<R>(ctx->seg[q]), ctx->cnt[q], ctx->cap, &ctx->st->err, ctx->stream));
   CK(launch_clamp_counts(ctx->cnt[q], g.nslots, ctx->cap, ctx->stream));
   ctx->launches += 2;
+  if (ctx->cfg.sort_every > 0) {
+    pic_status ss = sort_particles<R>(ctx);
+    if (ss) return ss;
+    ctx->since_sort = 0;
+  }
   // clamp counts of overflowing slots happens via the error word
   if (tmp) {
     CK(cudaStreamSynchronize(ctx->stream));
@@ -842,9 +881,11 @@ pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
   out->max_patch_count = hs.maxcnt[(ctx->step + 1) & 1];
   out->capacity = ctx->cap;
   out->grows = ctx->grows;
+  out->sorts = ctx->sorts;
   out->ms_particles = ctx->ms_particles;
   out->ms_fields = ctx->ms_fields;
   out->ms_window = ctx->ms_window;
+  out->ms_sort = ctx->ms_sort;
   ctx->launches += 5 + (cont ? 1 : 0);
   out->launches = ctx->launches;
   out->particle_step_launches = ctx->ps_launches;

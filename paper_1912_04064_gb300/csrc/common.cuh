@@ -295,6 +295,13 @@ cudaError_t launch_repack(const Geom &g, SoA<R> src, const int *cnt_src, int cap
                           int *cnt_dst, int cap_dst, SoA<R> bdst, int *bcnt_dst, Buckets bk_dst,
                           cudaStream_t s);
 
+// Sort every patch's particles (segment plus incoming buckets, which are
+// absorbed) into the interleaved cell order, through the scratch set.
+template <typename R>
+cudaError_t launch_sort_cells(const Geom &g, int col0, SoA<R> seg, int *cnt, SoA<R> scratch,
+                              int *cnt_scratch, int cap, SoA<R> bkt, int *bcnt, Buckets bk,
+                              unsigned *err, cudaStream_t s);
+
 // old_col0: ring offset before the shift; nshift: shifts including this one.
 template <typename R>
 cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA<R> seg,

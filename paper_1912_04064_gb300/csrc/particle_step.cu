@@ -145,9 +145,14 @@ __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<
 // runtime).  MERGE: consecutive particles of a thread that share a window
 // are summed in registers before one set of shared atomics.
 template <typename R, int PT, int QT, bool TMA, bool MERGE>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     k_particle_step(const __grid_constant__ CUtensorMap tmap, const StepArgs<R> a) {
-  constexpr int M = 16 / sizeof(R);  // particles per thread: one 128-bit load per array
+  // MERGE: M = 16 / sizeof(R) consecutive particles per thread, one 128-bit
+  // load per array; otherwise one particle per thread per slice, lanes on
+  // consecutive particles (coalesced 32/64-bit loads), which keeps the 32
+  // lanes of a warp on 32 distinct, neighbouring cells for particles stored
+  // in the interleaved cell order (conflict-free gathers and atomics).
+  constexpr int M = MERGE ? 16 / sizeof(R) : 1;
   constexpr int BXc = PT ? PT + 8 : 0, BYc = QT ? QT + 3 : 0;
   constexpr int JWc = PT ? PT + 5 : 0, JHc = QT ? QT + 5 : 0;
   using V = typename Vec<R>::T;
@@ -245,10 +250,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
   const int lane = tid & 31;
   unsigned err = 0;
 
-  for (int qb = 0; qb < totalq; qb += nth) {
-    const int qi = qb + tid;
+  // particles of work item qi (M consecutive of one source) -> registers
+  auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
     int nval = 0;
-    R x[M], y[M], ux[M], uy[M], uz[M], w[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) x[m] = y[m] = ux[m] = uy[m] = uz[m] = w[m] = R(0);
     if (qi < totalq) {
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
       nval = min(M, s_cnt[src] - k0);
       const SoA<R> &A = src == 0 ? a.pin : a.bin;
       const long long b = s_base[src] + k0;
-      if (nval == M) {
+      if (M > 1 && nval == M) {
         const V vx = *reinterpret_cast<const V *>(A.x + b);
         const V vy = *reinterpret_cast<const V *>(A.y + b);
         const V vux = *reinterpret_cast<const V *>(A.ux + b);
@@ -280,6 +284,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
           }
       }
     }
+    return nval;
+  };
+  R x[M], y[M], ux[M], uy[M], uz[M], w[M];
+  int nval = load(tid, x, y, ux, uy, uz, w);
+  for (int qb = 0; qb < totalq; qb += nth) {
+    // prefetch the next work item so its global loads overlap this one
+    R nx_[M], ny_[M], nux_[M], nuy_[M], nuz_[M], nw_[M];
+    const int nnval = load(qb + nth + tid, nx_, ny_, nux_, nuy_, nuz_, nw_);
     Win<R> acc;
     int key = -1;
 #pragma unroll
@@ -449,6 +461,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
       }
     }
     if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      x[m] = nx_[m]; y[m] = ny_[m]; ux[m] = nux_[m]; uy[m] = nuy_[m]; uz[m] = nuz_[m];
+      w[m] = nw_[m];
+    }
+    nval = nnval;
   }
   if (err) atomicOr(&a.st->err, err);
   __syncthreads();

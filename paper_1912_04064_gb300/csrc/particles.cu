@@ -321,7 +321,171 @@ __global__ void k_repack(const Geom g, SoA<R> src, const int *cnt_src, int cap_s
   if (threadIdx.x == 0) cnt_dst[slot] = n;
 }
 
+// Interleaved cell order of one patch.  Each row of cells is cut into
+// segments of at most 32 cells; inside a segment particles are laid out rank
+// slice by rank slice: slice r holds, in column order, the r-th particle of
+// every cell of the segment that has more than r particles.  A warp then
+// processes 32 particles in 32 distinct neighbouring cells.  Ranks >= SORT_R
+// (dense cells) go to a tail after all segments.  Incoming bucket particles
+// are absorbed (their counts cleared by the one reader).
+constexpr int SORT_R = 64;
+
+template <typename R>
+__global__ void k_sort_cells(const Geom g, int col0, SoA<R> src, const int *cnt_src, int cap,
+                             SoA<R> bsrc, int *bcnt, Buckets bk, SoA<R> dst, int *cnt_dst,
+                             unsigned *err) {
+  extern __shared__ int sm[];
+  const int P = g.P, Q = g.Q;
+  const int spr = (P + 31) / 32;      // segments per row
+  const int nseg = Q * spr;
+  int *hist = sm;                     // P*Q
+  int *rank = hist + P * Q;           // P*Q
+  int *segoff = rank + P * Q;         // nseg + 1
+  int *sliceoff = segoff + nseg + 1;  // nseg * SORT_R
+  unsigned *mask = (unsigned *)(sliceoff + nseg * SORT_R);  // nseg * SORT_R
+  __shared__ int s_cnt[9];
+  __shared__ long long s_base[9];
+  __shared__ int s_off[10];
+  __shared__ int s_tail;
+  const int slot = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  for (int e = tid; e < 2 * P * Q; e += nth) sm[e] = 0;
+  if (tid < 9) {
+    int cnt = 0;
+    long long base = 0;
+    if (tid == 0) {
+      cnt = cnt_src[slot];
+      base = (long long)slot * cap;
+    } else {
+      int k = tid - 1, ddx, ddy;
+      dir_delta(k, ddx, ddy);
+      const int sv = neighbour_slot(g, col0, slot, -ddx, -ddy);
+      if (sv >= 0) {
+        cnt = bcnt[(long long)sv * 8 + k];
+        base = (long long)sv * bk.stride + bk.off[k];
+      }
+    }
+    s_cnt[tid] = cnt;
+    s_base[tid] = base;
+  }
+  if (tid == 0) s_tail = 0;
+  __syncthreads();
+  if (tid == 0) {
+    s_off[0] = 0;
+    for (int i = 0; i < 9; ++i) s_off[i + 1] = s_off[i] + s_cnt[i];
+  }
+  __syncthreads();
+  const int total = s_off[9];
+  auto cell_of = [&](int k, long long &idx, const SoA<R> *&A) {
+    int sidx = 0;
+    while (sidx < 8 && k >= s_off[sidx + 1]) ++sidx;
+    idx = s_base[sidx] + (k - s_off[sidx]);
+    A = sidx == 0 ? &src : &bsrc;
+    int cx = (int)A->x[idx], cy = (int)A->y[idx];
+    cx = cx < 0 ? 0 : (cx >= P ? P - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= Q ? Q - 1 : cy);
+    return cy * P + cx;
+  };
+  for (int k = tid; k < total; k += nth) {
+    long long idx;
+    const SoA<R> *A;
+    atomicAdd(&hist[cell_of(k, idx, A)], 1);
+  }
+  __syncthreads();
+  // per segment: rank slices (warp ballots over the segment's columns)
+  for (int sg = warp; sg < nseg; sg += nwarp) {
+    const int row = sg / spr, c = (sg % spr) * 32 + lane;
+    const int cnt = c < P ? hist[row * P + c] : 0;
+    int mx = cnt;
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int run = 0;
+    for (int r = 0; r < SORT_R; ++r) {
+      const unsigned m = __ballot_sync(0xffffffffu, cnt > r);
+      if (lane == 0) {
+        mask[sg * SORT_R + r] = m;
+        sliceoff[sg * SORT_R + r] = run;
+      }
+      run += __popc(m);
+      if (r + 1 >= mx) {
+        for (int rr = r + 1 + lane; rr < SORT_R; rr += 32) mask[sg * SORT_R + rr] = 0u;
+        break;
+      }
+    }
+    if (lane == 0) segoff[sg + 1] = run;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    segoff[0] = 0;
+    for (int sg = 0; sg < nseg; ++sg) segoff[sg + 1] += segoff[sg];
+  }
+  __syncthreads();
+  const int tail0 = segoff[nseg];
+  for (int k = tid; k < total; k += nth) {
+    long long idx;
+    const SoA<R> *A;
+    const int c = cell_of(k, idx, A);
+    const int r = atomicAdd(&rank[c], 1);
+    const int row = c / P, col = c - row * P;
+    const int sg = row * spr + col / 32, bit = col % 32;
+    int pos;
+    if (r < SORT_R)
+      pos = segoff[sg] + sliceoff[sg * SORT_R + r] +
+            __popc(mask[sg * SORT_R + r] & ((1u << bit) - 1u));
+    else
+      pos = tail0 + atomicAdd(&s_tail, 1);
+    if (pos >= cap) {
+      atomicOr(err, ERR_OVERFLOW_SEG);
+      continue;
+    }
+    const long long o = (long long)slot * cap + pos;
+    dst.x[o] = A->x[idx]; dst.y[o] = A->y[idx];
+    dst.ux[o] = A->ux[idx]; dst.uy[o] = A->uy[idx]; dst.uz[o] = A->uz[idx]; dst.w[o] = A->w[idx];
+  }
+  __syncthreads();
+  if (tid == 0) cnt_dst[slot] = min(total, cap);
+  // the incoming buckets have been absorbed: this block is their one reader
+  if (tid >= 1 && tid < 9) {
+    int k = tid - 1, ddx, ddy;
+    dir_delta(k, ddx, ddy);
+    const int sv = neighbour_slot(g, col0, slot, -ddx, -ddy);
+    if (sv >= 0) bcnt[(long long)sv * 8 + k] = 0;
+  }
+}
+
+template <typename R>
+__global__ void k_copy_segments(const Geom g, SoA<R> src, const int *cnt_src, SoA<R> dst,
+                                int *cnt_dst, int cap) {
+  const int slot = blockIdx.x;
+  const int n = cnt_src[slot];
+  const long long o = (long long)slot * cap;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    dst.x[o + k] = src.x[o + k]; dst.y[o + k] = src.y[o + k];
+    dst.ux[o + k] = src.ux[o + k]; dst.uy[o + k] = src.uy[o + k];
+    dst.uz[o + k] = src.uz[o + k]; dst.w[o + k] = src.w[o + k];
+  }
+  if (threadIdx.x == 0) cnt_dst[slot] = n;
+}
+
 }  // namespace
+
+size_t sort_smem(int P, int Q) {
+  const int nseg = Q * ((P + 31) / 32);
+  return sizeof(int) * (2 * (size_t)P * Q + nseg + 1 + 2 * (size_t)nseg * SORT_R);
+}
+
+template <typename R>
+cudaError_t launch_sort_cells(const Geom &g, int col0, SoA<R> seg, int *cnt, SoA<R> scratch,
+                              int *cnt_scratch, int cap, SoA<R> bkt, int *bcnt, Buckets bk,
+                              unsigned *err, cudaStream_t s) {
+  const size_t smem = sort_smem(g.P, g.Q);
+  cudaError_t e = cudaFuncSetAttribute(k_sort_cells<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_sort_cells<R><<<g.nslots, 256, smem, s>>>(g, col0, seg, cnt, cap, bkt, bcnt, bk, scratch,
+                                              cnt_scratch, err);
+  k_copy_segments<R><<<g.nslots, 256, 0, s>>>(g, scratch, cnt_scratch, seg, cnt, cap);
+  return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_repack(const Geom &g, SoA<R> src, const int *cnt_src, int cap_src,
@@ -392,6 +556,9 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
 }
 
 #define PIC_INST(R)                                                                           \
+  template cudaError_t launch_sort_cells<R>(const Geom &, int, SoA<R>, int *, SoA<R>, int *,   \
+                                            int, SoA<R>, int *, Buckets, unsigned *,           \
+                                            cudaStream_t);                                     \
   template cudaError_t launch_repack<R>(const Geom &, SoA<R>, const int *, int, SoA<R>,        \
                                         const int *, Buckets, SoA<R>, int *, int, SoA<R>,      \
                                         int *, Buckets, cudaStream_t);                         \

@@ -41,6 +41,7 @@ class pic_config(C.Structure):
         ("inj_ppc", C.c_int * 3), ("capacity_factor", C.c_double), ("capacity_min", C.c_int),
         ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
+        ("sort_every", C.c_int),
     ]
 
 
@@ -52,7 +53,7 @@ class pic_diag_t(C.Structure):
         ("shifts", C.c_int), ("max_patch_count", C.c_int), ("capacity", C.c_int),
         ("ms_particles", C.c_double), ("ms_fields", C.c_double), ("ms_window", C.c_double),
         ("launches", C.c_longlong), ("particle_step_launches", C.c_longlong),
-        ("grows", C.c_int),
+        ("grows", C.c_int), ("sorts", C.c_longlong), ("ms_sort", C.c_double),
     ]
 
     def as_dict(self):
@@ -109,7 +110,7 @@ class PicError(RuntimeError):
 def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     use_graph: bool = True, timing: bool = False, tma: bool = True,
                     capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0,
-                    merge: int = -1, auto_grow: bool = True) -> pic_config:
+                    merge: int = -1, auto_grow: bool = True, sort_every: int = 0) -> pic_config:
     """pic_config of a run dictionary (see ``workloads``)."""
     c = pic_config()
     c.dims = 2
@@ -149,6 +150,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     c.block = block
     c.merge = merge
     c.auto_grow = int(auto_grow)
+    c.sort_every = sort_every
     return c
 
 

@@ -333,3 +333,35 @@ def test_auto_grow_replays_overflowing_steps():
         a, b = small.pic_get_field(k), big.pic_get_field(k)
         assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), k
     assert small.pic_diag()["np"] == big.pic_diag()["np"] == n
+
+
+@pytest.mark.parametrize("sort_every", [1, 3])
+def test_cell_order_sort_keeps_parity(sort_every):
+    """Re-ordering particles into the interleaved cell order (and absorbing
+    in-flight particles) changes only summation order: FP64 parity holds."""
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    parts = W.small_random_particles(run, 30000, seed=17, uth=0.5)
+    fields = W.random_fields((64, 64), seed=18, amp=0.1)
+    o, g = pair(run, parts, fields, sort_every=sort_every)
+    for _ in range(3):
+        o.step(2)
+        g.pic_step(2)
+    _assert_fields(field_errors(o, g), 1e-11)
+    assert max(particle_errors(o, g).values()) <= 1e-11
+    d = g.pic_diag()
+    assert d["sorts"] >= 2 and d["np"] == 30000
+
+
+def test_cell_order_sort_fp32_open_window():
+    """FP32 LWFA-shaped run with the window moving and periodic sorting:
+    particle count and energies follow the oracle."""
+    run, parts = W.lwfa_2d(n=(128, 64), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2),
+                           ramp=6.0, t_mw=1.0, a0=1.0, waist=5.0, tau=3.0)
+    run["laser"]["t_peak"] = 6.0
+    o, g = pair(run, parts, prec="fp32", background=("neutralising", 0.0), sort_every=4)
+    for _ in range(6):
+        o.step(10)
+        g.pic_step(10)
+    do, dg = o.diag(), g.pic_diag()
+    assert dg["np"] == do["np"] and dg["shifts"] == do["shifts"] >= 1
+    assert abs(dg["U_E"] - do["U_E"]) <= 1e-3 * do["U_E"]
