@@ -205,6 +205,29 @@ void pic_destroy(pic_ctx *ctx);
 /* Library version string. */
 const char *pic_version(void);
 
+/* Allocation-free field energy (the paper has no counterpart: this is a
+ * library service).  For callers that cannot let the library call
+ * cudaMalloc -- an application that owns the device memory budget through
+ * its own allocator, or a serving loop where a device allocation would
+ * synchronise the device under live requests -- this computes
+ * out[0] = 1/2 sum (Ex^2 + Ey^2 + Ez^2) dV and out[1] = 1/2 sum (Bmx^2 +
+ * Bmy^2 + Bmz^2) dV over float64 cell arrays of shape (ny, nx), row-major,
+ * all in device memory of the current device (out: 2 doubles, device).
+ * It allocates nothing: its scratch is a fixed file-scope device array of
+ * PIC_NOALLOC_MAX_ROWS x 2 doubles (1 MiB) that every GPU loading the library
+ * holds until exit.  ny > PIC_NOALLOC_MAX_ROWS, nx or ny <= 0, or a null
+ * pointer gives PIC_EINVAL.  The first call on a device looks up the
+ * scratch array's device address (so make it before any stream capture on
+ * that device).  Calls share the scratch array: calls that overlap on the
+ * GPU race; a call rewrites every row it reads.  Runs asynchronously on
+ * `stream` (a cudaStream_t; NULL = the default stream). */
+#define PIC_NOALLOC_MAX_ROWS 65536
+pic_status pic_field_energy_noalloc(const double *Ex, const double *Ey,
+                                    const double *Ez, const double *Bmx,
+                                    const double *Bmy, const double *Bmz,
+                                    int nx, int ny, double dV, double *out,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

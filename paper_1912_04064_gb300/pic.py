@@ -62,7 +62,8 @@ class pic_diag_t(C.Structure):
 
 EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_background", "pic_step",
            "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync", "pic_snapshot",
-           "pic_restore", "pic_footprint", "pic_last_error", "pic_destroy", "pic_version"]
+           "pic_restore", "pic_footprint", "pic_last_error", "pic_destroy", "pic_version",
+           "pic_field_energy_noalloc"]
 
 _lib = None
 
@@ -93,6 +94,8 @@ def lib():
         L.pic_destroy.argtypes = [vp]
         L.pic_destroy.restype = None
         L.pic_version.restype = C.c_char_p
+        L.pic_field_energy_noalloc.argtypes = [vp] * 6 + [C.c_int, C.c_int, C.c_double, vp, vp]
+        L.pic_field_energy_noalloc.restype = C.c_int
         for name in ("pic_create", "pic_load_particles", "pic_set_field", "pic_set_background",
                      "pic_step", "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync",
                      "pic_snapshot", "pic_restore"):
