@@ -24,6 +24,7 @@ struct pic_ctx {
   bool own_stream = false;
   void *F = nullptr;
   double *rho_bg = nullptr, *rho_a = nullptr, *rho_b = nullptr;
+  double *laser_g = nullptr;  // transverse laser profile at y = (j + 1/2) dy
   void *seg[2][6] = {};
   int *cnt[2] = {};
   void *bkt[2][6] = {};
@@ -286,6 +287,14 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.bk = ctx->bk;
   a.parity = p;
   a.st = ctx->st;
+  a.rdx = R(g.dt / g.dx);
+  a.rdy = R(g.dt / g.dy);
+  a.eps = R(g.q * g.dt / (2.0 * g.m));
+  a.cjx = R(-g.q * g.dx / g.dt);
+  a.cjy = R(-g.q * g.dy / g.dt);
+  a.cjz = R(g.q);
+  a.RP = R(g.P);
+  a.RQ = R(g.Q);
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
   const bool merge = ctx->cfg.merge > 0;
   CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->stream));
@@ -295,12 +304,20 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   f.F = (R *)ctx->F;
   f.parity = p;
   f.st = ctx->st;
+  f.dt = R(g.dt);
+  f.idx = R(1.0 / g.dx);
+  f.idy = R(1.0 / g.dy);
+  const double rx = g.dt / g.dx, ry = g.dt / g.dy;
+  f.smx_inv1pr = R(1.0 / (1.0 + rx));
+  f.smx_1mr = R(1.0 - rx);
+  f.smx_dtt = R(g.dt / g.dy);
+  f.smy_inv1pr = R(1.0 / (1.0 + ry));
+  f.smy_1mr = R(1.0 - ry);
+  f.smy_dtt = R(g.dt / g.dx);
   f.laser_on = ctx->cfg.laser_on;
-  f.a0 = ctx->cfg.laser_a0;
-  f.waist = ctx->cfg.laser_waist;
+  f.laser_g = ctx->laser_g;
   f.tau = ctx->cfg.laser_tau;
   f.t_peak = ctx->cfg.laser_t_peak;
-  f.yc = ctx->cfg.laser_y_center;
   CK(launch_fields<R>(f, ctx->stream));
   return PIC_OK;
 }
@@ -968,6 +985,17 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
   if (cudaMalloc(&ctx->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
   ctx->npartials = 1024;
   if (cudaMalloc(&ctx->partials, sizeof(double) * 3 * ctx->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cfg->laser_on) {
+    std::vector<double> prof(g.ny + 1);
+    for (int j = 0; j <= g.ny; ++j) {
+      const double r = ((j + 0.5) * g.dy - cfg->laser_y_center) / cfg->laser_waist;
+      prof[j] = cfg->laser_a0 * std::exp(-r * r);
+    }
+    if (cudaMalloc(&ctx->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cudaMemcpy(ctx->laser_g, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return bail(PIC_ECUDA);
+  }
   if (cudaMemsetAsync(ctx->F, 0, field_bytes(g, ctx->rs), ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->rho_bg, 0, sizeof(double) * g.cs, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->st, 0, sizeof(DevState), ctx->stream) != cudaSuccess ||
@@ -985,6 +1013,7 @@ void pic_destroy(pic_ctx *ctx) {
   cudaFree(ctx->rho_bg);
   cudaFree(ctx->rho_a);
   cudaFree(ctx->rho_b);
+  cudaFree(ctx->laser_g);
   cudaFree(ctx->st);
   cudaFree(ctx->partials);
   cudaFree(ctx->offsets);

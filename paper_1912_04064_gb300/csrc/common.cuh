@@ -215,6 +215,12 @@ struct StepArgs {
   Buckets bk;
   int parity;
   DevState *st;
+  // per-step constants in the working precision, computed on the host (the
+  // device's FP64 unit is slow: no per-thread double arithmetic)
+  R rdx, rdy;          // dt / dx, dt / dy (cell units per unit velocity)
+  R eps;               // q dt / (2 m)
+  R cjx, cjy, cjz;     // -q dx / dt, -q dy / dt, q
+  R RP, RQ;            // patch size as reals
 };
 
 template <typename R>
@@ -232,9 +238,14 @@ struct FieldArgs {
   R *F;
   int parity;          // J set read = C_JA + 3 * parity, zeroed = the other
   DevState *st;
-  // laser
+  R dt, idx, idy;      // dt, 1/dx, 1/dy in the working precision
+  // Silver-Mueller coefficients per open axis: 1/(1+r), 1-r, dt/d_transverse
+  R smx_inv1pr, smx_1mr, smx_dtt, smy_inv1pr, smy_1mr, smy_dtt;
+  // laser: transverse profile a0 exp(-((y-yc)/w)^2) at y = (j+1/2) dy
+  // (device array) and the temporal factor's parameters
   int laser_on;
-  double a0, waist, tau, t_peak, yc;
+  const double *laser_g;
+  double tau, t_peak;
 };
 template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s);

@@ -29,8 +29,7 @@ __device__ __forceinline__ Ranges ranges(const Geom &g) {
   return r;
 }
 
-constexpr int RY = 8;      // rows per thread in the Yee kernels
-constexpr int YEE_BX = 128;
+constexpr int YBX = 32, YBY = 8;  // Yee block: 32 x 8 cells, one cell per thread
 
 // True when any cell of the block's tile lies in a periodic mirror band.
 __device__ __forceinline__ bool block_mirrors(const Geom &g, int i0, int i1, int j0, int j1) {
@@ -38,47 +37,43 @@ __device__ __forceinline__ bool block_mirrors(const Geom &g, int i0, int i1, int
          (g.fbc_y == FBC_PERIODIC && (j0 < GY || j1 > g.ny - GY));
 }
 
-// E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}); one thread per column
-// segment of RY rows, the previous row's B carried in registers.
+// E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}); one cell per thread so
+// that every thread issues its loads at once.
 template <typename R>
-__global__ void __launch_bounds__(YEE_BX) k_update_E(const FieldArgs<R> a) {
+__global__ void __launch_bounds__(YBX * YBY) k_update_E(const FieldArgs<R> a) {
   const Geom &g = a.g;
   const Ranges rg = ranges(g);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j0 = blockIdx.y * RY;
-  const int j1 = min(j0 + RY, rg.nyp);
-  const int ib0 = blockIdx.x * blockDim.x;
-  const bool mir = block_mirrors(g, ib0, ib0 + blockDim.x, j0, j1);
-  if (i >= rg.nxp) return;
+  const int i0 = blockIdx.x * YBX, j0 = blockIdx.y * YBY;
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const bool mir = block_mirrors(g, i0, i0 + YBX, j0, j0 + YBY);
+  if (i >= rg.nxp || j >= rg.nyp) return;
   const long long cs = g.cs;
   const int sx = g.sx;
   R *F = a.F;
   R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
   const R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   const R *J = F + (C_JA + 3 * a.parity) * cs;
-  const R dt = R(g.dt), idx = R(1.0 / g.dx), idy = R(1.0 / g.dy);
-  long long o = fidx(g, i, j0);
-  R bzp = Bz[o - sx], bxp = Bx[o - sx];
-  for (int j = j0; j < j1; ++j, o += sx) {
-    const R bz = Bz[o], bx = Bx[o], by = By[o];
-    const R bzl = Bz[o - 1], byl = By[o - 1];
-    if (i < rg.nxd) {
-      const R v = Ex[o] + dt * ((bz - bzp) * idy - J[o]);
-      Ex[o] = v;
-      if (mir) mirror(g, Ex, o, i, j, v);
-    }
-    if (j < rg.nyd) {
-      const R v = Ey[o] + dt * (-(bz - bzl) * idx - J[cs + o]);
-      Ey[o] = v;
-      if (mir) mirror(g, Ey, o, i, j, v);
-    }
-    {
-      const R v = Ez[o] + dt * ((by - byl) * idx - (bx - bxp) * idy - J[2 * cs + o]);
-      Ez[o] = v;
-      if (mir) mirror(g, Ez, o, i, j, v);
-    }
-    bzp = bz;
-    bxp = bx;
+  const R dt = a.dt, idx = a.idx, idy = a.idy;
+  const long long o = (long long)(j + GY) * sx + (i + GX);
+  const R bz = Bz[o], bzl = Bz[o - 1], bzd = Bz[o - sx];
+  const R by = By[o], byl = By[o - 1];
+  const R bx = Bx[o], bxd = Bx[o - sx];
+  const R jx = J[o], jy = J[cs + o], jz = J[2 * cs + o];
+  const R ex = Ex[o], ey = Ey[o], ez = Ez[o];
+  if (i < rg.nxd) {
+    const R v = ex + dt * ((bz - bzd) * idy - jx);
+    Ex[o] = v;
+    if (mir) mirror(g, Ex, o, i, j, v);
+  }
+  if (j < rg.nyd) {
+    const R v = ey + dt * (-(bz - bzl) * idx - jy);
+    Ey[o] = v;
+    if (mir) mirror(g, Ey, o, i, j, v);
+  }
+  {
+    const R v = ez + dt * ((by - byl) * idx - (bx - bxd) * idy - jz);
+    Ez[o] = v;
+    if (mir) mirror(g, Ez, o, i, j, v);
   }
 }
 
@@ -86,96 +81,114 @@ __global__ void __launch_bounds__(YEE_BX) k_update_E(const FieldArgs<R> a) {
 // B^{n+3/2}) / 2 (= B at stored cells that are not updated), and the
 // current set of the next step cleared.  Covers every stored column and row.
 template <typename R>
-__global__ void __launch_bounds__(YEE_BX) k_update_B(const FieldArgs<R> a) {
+__global__ void __launch_bounds__(YBX * YBY) k_update_B(const FieldArgs<R> a) {
   const Geom &g = a.g;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     const int p = a.parity;
     a.st->t[1 - p] = a.st->t[p] + g.dt;
     a.st->step[1 - p] = a.st->step[p] + 1;
     a.st->maxcnt[1 - p] = 0;  // the next particle step starts a new maximum
   }
   const Ranges rg = ranges(g);
-  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GX;
-  const int j0 = (int)(blockIdx.y * RY) - GY;
-  const int j1 = min(j0 + RY, g.ny + GY);
-  const int ib0 = (int)(blockIdx.x * blockDim.x) - GX;
-  const bool mir = block_mirrors(g, ib0, ib0 + blockDim.x, j0, j1);
-  if (i >= g.nx + GX) return;
-  const bool perx = g.fbc_x == FBC_PERIODIC, pery = g.fbc_y == FBC_PERIODIC;
-  const bool ghost_x = i < 0 || i >= g.nx;
+  const int i0 = (int)(blockIdx.x * YBX) - GX, j0 = (int)(blockIdx.y * YBY) - GY;
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const bool mir = block_mirrors(g, i0, i0 + YBX, j0, j0 + YBY);
+  if (i >= g.nx + GX || j >= g.ny + GY) return;
   const long long cs = g.cs;
   const int sx = g.sx;
   R *F = a.F;
+  const long long o = (long long)(j + GY) * sx + (i + GX);
+  R *Jn = F + (C_JA + 3 * (1 - a.parity)) * cs;
+  Jn[o] = R(0);
+  Jn[cs + o] = R(0);
+  Jn[2 * cs + o] = R(0);
+  if ((g.fbc_x == FBC_PERIODIC && (i < 0 || i >= g.nx)) ||
+      (g.fbc_y == FBC_PERIODIC && (j < 0 || j >= g.ny)))
+    return;  // mirror cell: written by its owner
   const R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
   R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   R *Bmx = F + C_BMX * cs, *Bmy = F + C_BMY * cs, *Bmz = F + C_BMZ * cs;
-  R *Jn = F + (C_JA + 3 * (1 - a.parity)) * cs;
-  const R dt = R(g.dt), idx = R(1.0 / g.dx), idy = R(1.0 / g.dy);
-  long long o = fidx(g, i, j0);
-  for (int j = j0; j < j1; ++j, o += sx) {
-    Jn[o] = R(0);
-    Jn[cs + o] = R(0);
-    Jn[2 * cs + o] = R(0);
-    if ((perx && ghost_x) || (pery && (j < 0 || j >= g.ny))) continue;  // mirror cells
-    const bool in = i >= 0 && j >= 0;
-    {
-      const R b0 = Bx[o];
-      R b1 = b0;
-      if (in && i < rg.nxp && j < rg.nyd) {
-        b1 = b0 - dt * (Ez[o + sx] - Ez[o]) * idy;
-        Bx[o] = b1;
-        if (mir) mirror(g, Bx, o, i, j, b1);
-      }
-      const R m = R(0.5) * (b0 + b1);
-      Bmx[o] = m;
-      if (mir) mirror(g, Bmx, o, i, j, m);
-    }
-    {
-      const R b0 = By[o];
-      R b1 = b0;
-      if (in && i < rg.nxd && j < rg.nyp) {
-        b1 = b0 + dt * (Ez[o + 1] - Ez[o]) * idx;
-        By[o] = b1;
-        if (mir) mirror(g, By, o, i, j, b1);
-      }
-      const R m = R(0.5) * (b0 + b1);
-      Bmy[o] = m;
-      if (mir) mirror(g, Bmy, o, i, j, m);
-    }
-    {
-      const R b0 = Bz[o];
-      R b1 = b0;
-      if (in && i < rg.nxd && j < rg.nyd) {
-        b1 = b0 - dt * ((Ey[o + 1] - Ey[o]) * idx - (Ex[o + sx] - Ex[o]) * idy);
-        Bz[o] = b1;
-        if (mir) mirror(g, Bz, o, i, j, b1);
-      }
-      const R m = R(0.5) * (b0 + b1);
-      Bmz[o] = m;
-      if (mir) mirror(g, Bmz, o, i, j, m);
-    }
+  const R dt = a.dt, idx = a.idx, idy = a.idy;
+  const bool in = i >= 0 && j >= 0;
+  const bool ux = in && i < rg.nxp && j < rg.nyd;
+  const bool uy = in && i < rg.nxd && j < rg.nyp;
+  const bool uz = in && i < rg.nxd && j < rg.nyd;
+  const R bx0 = Bx[o], by0 = By[o], bz0 = Bz[o];
+  R ez = R(0), ezu = R(0), ezr = R(0), ey = R(0), eyr = R(0), ex = R(0), exu = R(0);
+  if (ux || uy) ez = Ez[o];
+  if (ux) ezu = Ez[o + sx];
+  if (uy) ezr = Ez[o + 1];
+  if (uz) {
+    ey = Ey[o];
+    eyr = Ey[o + 1];
+    ex = Ex[o];
+    exu = Ex[o + sx];
   }
-}
-
-template <typename R>
-__device__ __forceinline__ double laser_field(const FieldArgs<R> &a, double y, double t,
-                                              int nshift) {
-  const double tr = t - (double)(nshift * a.g.P) * a.g.dx - a.t_peak;
-  const double r = (y - a.yc) / a.waist;
-  return a.a0 * exp(-r * r) * exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
+  {
+    R b1 = bx0;
+    if (ux) {
+      b1 = bx0 - dt * (ezu - ez) * idy;
+      Bx[o] = b1;
+      if (mir) mirror(g, Bx, o, i, j, b1);
+    }
+    const R m = R(0.5) * (bx0 + b1);
+    Bmx[o] = m;
+    if (mir) mirror(g, Bmx, o, i, j, m);
+  }
+  {
+    R b1 = by0;
+    if (uy) {
+      b1 = by0 + dt * (ezr - ez) * idx;
+      By[o] = b1;
+      if (mir) mirror(g, By, o, i, j, b1);
+    }
+    const R m = R(0.5) * (by0 + b1);
+    Bmy[o] = m;
+    if (mir) mirror(g, Bmy, o, i, j, m);
+  }
+  {
+    R b1 = bz0;
+    if (uz) {
+      b1 = bz0 - dt * ((eyr - ey) * idx - (exu - ex) * idy);
+      Bz[o] = b1;
+      if (mir) mirror(g, Bz, o, i, j, b1);
+    }
+    const R m = R(0.5) * (bz0 + b1);
+    Bmz[o] = m;
+    if (mir) mirror(g, Bmz, o, i, j, m);
+  }
 }
 
 template <typename R>
 __device__ __forceinline__ void set_ghost(const Geom &g, R *B, R *Bm, int i, int j, R v) {
   const long long o = fidx(g, i, j);
   const R old = Bm[o];  // = B^{n+1/2} at this ghost after k_update_B
-  store_mirrored(g, B, i, j, v);
-  store_mirrored(g, Bm, i, j, R(0.5) * (old + v));
+  B[o] = v;
+  mirror(g, B, o, i, j, v);
+  const R m = R(0.5) * (old + v);
+  Bm[o] = m;
+  mirror(g, Bm, o, i, j, m);
 }
 
+// Ghost B on open faces from the discrete Silver-Mueller condition; the
+// coefficients 1/(1+r), 1-r and the transverse dt/d are precomputed.  The
+// laser Ey_inc(y, t) = profile(y) * envelope(t) carrier(t): the transverse
+// profile is a precomputed array, the temporal factor is evaluated once per
+// block at t_{n+3/2} (retarded by the window's displacement).
 template <typename R>
 __global__ void k_silver_mueller(const FieldArgs<R> a) {
   const Geom &g = a.g;
+  __shared__ double s_h;
+  if (threadIdx.x == 0) {
+    double h = 0.0;
+    if (a.laser_on) {
+      const double t = a.st->t[a.parity] + 1.5 * g.dt;
+      const double tr = t - (double)(a.st->nshift * g.P) * g.dx - a.t_peak;
+      h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
+    }
+    s_h = h;
+  }
+  __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   R *F = a.F;
   const long long cs = g.cs;
@@ -183,55 +196,45 @@ __global__ void k_silver_mueller(const FieldArgs<R> a) {
   R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   R *Bmx = F + C_BMX * cs, *Bmy = F + C_BMY * cs, *Bmz = F + C_BMZ * cs;
   const Ranges rg = ranges(g);
-  const double dt = g.dt;
   if (g.fbc_x == FBC_SM && t < rg.nyp) {
     const int j = t, nx = g.nx;
-    const double r = dt / g.dx;
+    const R ia = a.smx_inv1pr, b = a.smx_1mr, c = a.smx_dtt;
     const bool inter = g.fbc_y == FBC_PERIODIC || (j >= 1 && j <= g.ny - 1);
-    double dBx0 = 0.0, dBxn = 0.0;
+    R dBx0 = R(0), dBxn = R(0);
     if (inter) {
-      dBx0 = (double)Bx[fidx(g, 0, j)] - (double)Bx[fidx(g, 0, j - 1)];
-      dBxn = (double)Bx[fidx(g, nx, j)] - (double)Bx[fidx(g, nx, j - 1)];
+      dBx0 = Bx[fidx(g, 0, j)] - Bx[fidx(g, 0, j - 1)];
+      dBxn = Bx[fidx(g, nx, j)] - Bx[fidx(g, nx, j - 1)];
     }
-    const double by_lo = (2.0 * Ez[fidx(g, 0, j)] - (1.0 - r) * By[fidx(g, 0, j)] -
-                          (dt / g.dy) * dBx0) / (1.0 + r);
-    const double by_hi = (-2.0 * Ez[fidx(g, nx, j)] - (1.0 - r) * By[fidx(g, nx - 1, j)] +
-                          (dt / g.dy) * dBxn) / (1.0 + r);
-    set_ghost(g, By, Bmy, -1, j, R(by_lo));
-    set_ghost(g, By, Bmy, nx, j, R(by_hi));
+    const R by_lo = (R(2) * Ez[fidx(g, 0, j)] - b * By[fidx(g, 0, j)] - c * dBx0) * ia;
+    const R by_hi = (R(-2) * Ez[fidx(g, nx, j)] - b * By[fidx(g, nx - 1, j)] + c * dBxn) * ia;
+    set_ghost(g, By, Bmy, -1, j, by_lo);
+    set_ghost(g, By, Bmy, nx, j, by_hi);
     if (j < rg.nyd) {
-      double eyinc = 0.0;
-      if (a.laser_on)
-        eyinc = laser_field(a, (j + 0.5) * g.dy, a.st->t[a.parity] + 1.5 * dt, a.st->nshift);
-      const double bz_lo =
-          (4.0 * eyinc - 2.0 * Ey[fidx(g, 0, j)] - (1.0 - r) * Bz[fidx(g, 0, j)]) / (1.0 + r);
-      const double bz_hi =
-          (2.0 * Ey[fidx(g, nx, j)] - (1.0 - r) * Bz[fidx(g, nx - 1, j)]) / (1.0 + r);
-      set_ghost(g, Bz, Bmz, -1, j, R(bz_lo));
-      set_ghost(g, Bz, Bmz, nx, j, R(bz_hi));
+      const R eyinc = a.laser_on ? R(a.laser_g[j] * s_h) : R(0);
+      const R bz_lo = (R(4) * eyinc - R(2) * Ey[fidx(g, 0, j)] - b * Bz[fidx(g, 0, j)]) * ia;
+      const R bz_hi = (R(2) * Ey[fidx(g, nx, j)] - b * Bz[fidx(g, nx - 1, j)]) * ia;
+      set_ghost(g, Bz, Bmz, -1, j, bz_lo);
+      set_ghost(g, Bz, Bmz, nx, j, bz_hi);
     }
   }
   if (g.fbc_y == FBC_SM && t < rg.nxp) {
     const int i = t, ny = g.ny;
-    const double r = dt / g.dy;
+    const R ia = a.smy_inv1pr, b = a.smy_1mr, c = a.smy_dtt;
     const bool inter = g.fbc_x == FBC_PERIODIC || (i >= 1 && i <= g.nx - 1);
-    double dBy0 = 0.0, dByn = 0.0;
+    R dBy0 = R(0), dByn = R(0);
     if (inter) {
-      dBy0 = (double)By[fidx(g, i, 0)] - (double)By[fidx(g, i - 1, 0)];
-      dByn = (double)By[fidx(g, i, ny)] - (double)By[fidx(g, i - 1, ny)];
+      dBy0 = By[fidx(g, i, 0)] - By[fidx(g, i - 1, 0)];
+      dByn = By[fidx(g, i, ny)] - By[fidx(g, i - 1, ny)];
     }
-    const double bx_lo = (-2.0 * Ez[fidx(g, i, 0)] - (1.0 - r) * Bx[fidx(g, i, 0)] -
-                          (dt / g.dx) * dBy0) / (1.0 + r);
-    const double bx_hi = (2.0 * Ez[fidx(g, i, ny)] - (1.0 - r) * Bx[fidx(g, i, ny - 1)] +
-                          (dt / g.dx) * dByn) / (1.0 + r);
-    set_ghost(g, Bx, Bmx, i, -1, R(bx_lo));
-    set_ghost(g, Bx, Bmx, i, ny, R(bx_hi));
+    const R bx_lo = (R(-2) * Ez[fidx(g, i, 0)] - b * Bx[fidx(g, i, 0)] - c * dBy0) * ia;
+    const R bx_hi = (R(2) * Ez[fidx(g, i, ny)] - b * Bx[fidx(g, i, ny - 1)] + c * dByn) * ia;
+    set_ghost(g, Bx, Bmx, i, -1, bx_lo);
+    set_ghost(g, Bx, Bmx, i, ny, bx_hi);
     if (i < rg.nxd) {
-      const double bz_lo = (2.0 * Ex[fidx(g, i, 0)] - (1.0 - r) * Bz[fidx(g, i, 0)]) / (1.0 + r);
-      const double bz_hi =
-          (-2.0 * Ex[fidx(g, i, ny)] - (1.0 - r) * Bz[fidx(g, i, ny - 1)]) / (1.0 + r);
-      set_ghost(g, Bz, Bmz, i, -1, R(bz_lo));
-      set_ghost(g, Bz, Bmz, i, ny, R(bz_hi));
+      const R bz_lo = (R(2) * Ex[fidx(g, i, 0)] - b * Bz[fidx(g, i, 0)]) * ia;
+      const R bz_hi = (R(-2) * Ex[fidx(g, i, ny)] - b * Bz[fidx(g, i, ny - 1)]) * ia;
+      set_ghost(g, Bz, Bmz, i, -1, bz_lo);
+      set_ghost(g, Bz, Bmz, i, ny, bz_hi);
     }
   }
 }
@@ -363,12 +366,13 @@ template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   const Geom &g = a.g;
   const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
-  k_update_E<R><<<dim3((nxp + YEE_BX - 1) / YEE_BX, (nyp + RY - 1) / RY), YEE_BX, 0, s>>>(a);
+  const dim3 blk(YBX, YBY);
+  k_update_E<R><<<dim3((nxp + YBX - 1) / YBX, (nyp + YBY - 1) / YBY), blk, 0, s>>>(a);
   const int ncol = g.nx + 2 * GX, nrow = g.ny + 2 * GY;
-  k_update_B<R><<<dim3((ncol + YEE_BX - 1) / YEE_BX, (nrow + RY - 1) / RY), YEE_BX, 0, s>>>(a);
+  k_update_B<R><<<dim3((ncol + YBX - 1) / YBX, (nrow + YBY - 1) / YBY), blk, 0, s>>>(a);
   if (g.fbc_x == FBC_SM || g.fbc_y == FBC_SM) {
     const int n = (g.nx > g.ny ? g.nx : g.ny) + 1;
-    k_silver_mueller<R><<<(n + 127) / 128, 128, 0, s>>>(a);
+    k_silver_mueller<R><<<(n + 63) / 64, 64, 0, s>>>(a);
   }
   return cudaGetLastError();
 }

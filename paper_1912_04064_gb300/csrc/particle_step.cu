@@ -58,40 +58,49 @@ struct Vec<double> {
   using T = double2;
 };
 
-// Quadratic B-spline weights of the primal (node) and dual (half-node)
-// stencils of one coordinate xi (cells): primal nearest node ip =
-// floor(xi + 1/2), dual nearest id = floor(xi), both from one floor.
-template <typename R>
-__device__ __forceinline__ void shapes(R xi, int &ip, R Sp[3], int &id, R Sd[3]) {
-  const R fl = floor(xi);
-  const R fr = xi - fl;
-  const bool up = fr >= R(0.5);
-  id = (int)fl;
-  ip = id + (up ? 1 : 0);
-  const R dp = up ? fr - R(1) : fr;
-  const R dd = fr - R(0.5);
-  R a = R(0.5) - dp, b = R(0.5) + dp;
-  Sp[0] = R(0.5) * a * a;
-  Sp[1] = R(0.75) - dp * dp;
-  Sp[2] = R(0.5) * b * b;
-  a = R(0.5) - dd;
-  b = R(0.5) + dd;
-  Sd[0] = R(0.5) * a * a;
-  Sd[1] = R(0.75) - dd * dd;
-  Sd[2] = R(0.5) * b * b;
+// Nearest integer of v (|v| < 2^22 for float, 2^51 for double) and v minus
+// it, without float-to-integer conversion instructions: adding 1.5 * 2^23
+// (2^52) rounds v to an integer held in the low mantissa bits.  A tie
+// (v = k + 1/2) may go to either neighbour; the quadratic shape has the same
+// weights on both node sets there.
+__device__ __forceinline__ int nearest(float v, float &d) {
+  const float t = v + 12582912.0f;
+  d = v - (t - 12582912.0f);
+  return __float_as_int(t) - 0x4B400000;
+}
+__device__ __forceinline__ int nearest(double v, double &d) {
+  const double t = v + 6755399441055744.0;
+  d = v - (t - 6755399441055744.0);
+  return (int)(__double_as_longlong(t) - 0x4338000000000000ll);
 }
 
+// Quadratic B-spline weights of the nodes i0-1, i0, i0+1 for offset d of a
+// coordinate from its nearest node i0 (|d| <= 1/2).
 template <typename R>
-__device__ __forceinline__ int shape_primal(R xi, R S[3]) {
-  const R fl = floor(xi);
-  const R fr = xi - fl;
-  const bool up = fr >= R(0.5);
-  const R d = up ? fr - R(1) : fr;
+__device__ __forceinline__ void bspline(R d, R S[3]) {
   const R a = R(0.5) - d, b = R(0.5) + d;
   S[0] = R(0.5) * a * a;
   S[1] = R(0.75) - d * d;
   S[2] = R(0.5) * b * b;
-  return (int)fl + (up ? 1 : 0);
+}
+
+// Primal (node) and dual (half-node) stencils of one coordinate xi (cells):
+// ip = nearest node of xi, id = nearest node of xi - 1/2.
+template <typename R>
+__device__ __forceinline__ void shapes(R xi, int &ip, R Sp[3], int &id, R Sd[3]) {
+  R dp, dd;
+  ip = nearest(xi, dp);
+  id = nearest(xi - R(0.5), dd);
+  bspline(dp, Sp);
+  bspline(dd, Sd);
+}
+
+template <typename R>
+__device__ __forceinline__ int shape_primal(R xi, R S[3]) {
+  R d;
+  const int i = nearest(xi, d);
+  bspline(d, S);
+  return i;
 }
 
 // Sum of a 3 x 3 stencil at tile offset o (row stride BX).
@@ -243,10 +252,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 
   // ---- 2..5. particles, M per thread
   const int totalq = s_qoff[9];
-  const R rdx = R(g.dt / g.dx), rdy = R(g.dt / g.dy);
-  const R eps = R(g.q * g.dt / (2.0 * g.m));
-  const R cjx = R(-g.q * g.dx / g.dt), cjy = R(-g.q * g.dy / g.dt), cjz = R(g.q);
-  const R RP = R(P), RQ = R(Q);
+  const R rdx = a.rdx, rdy = a.rdy, eps = a.eps;
+  const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
+  const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
   const int lane = tid & 31;
   unsigned err = 0;
 
