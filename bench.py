@@ -124,7 +124,8 @@ def algorithmic_bytes(npart, ncell, rsize):
             npart * per_particle_kernel + ncell * per_cell_kernel)
 
 
-def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1, sort=0):
+def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1, sort=0,
+            chunk=0):
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -137,7 +138,7 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     stream = torch.cuda.Stream(device=device)
     cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                               use_graph=True, timing=False, capacity_factor=cf, merge=merge,
-                              sort_every=sort)
+                              sort_every=sort, task_chunk=chunk)
     g = pic.Pic(cfg)
     g.pic_load_particles(parts)
     g.pic_set_background("neutralising")
@@ -162,7 +163,7 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     # launching stream (no graph replay)
     cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                                 use_graph=False, timing=True, capacity_factor=cf, merge=merge,
-                                sort_every=sort)
+                                sort_every=sort, task_chunk=chunk)
     g.close()
     gt = pic.Pic(cfg_t)
     gt.pic_restore(blob)
@@ -260,6 +261,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--task-chunk", type=int, default=0,
+                    help="particles per work item of the particle step (0 = library default)")
     ap.add_argument("--sort-every", type=int, default=0,
                     help="re-order particles into the interleaved cell order every N steps")
     ap.add_argument("--merge", type=int, default=-1,
@@ -307,11 +310,11 @@ def main():
         dist.barrier()
 
     r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist,
-                  args.capacity_factor, args.merge, args.sort_every)
+                  args.capacity_factor, args.merge, args.sort_every, args.task_chunk)
     r64 = None
     if args.fp64_steps > 0:
         r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
-                      world, dist, args.capacity_factor, -1, args.sort_every)
+                      world, dist, args.capacity_factor, -1, args.sort_every, args.task_chunk)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:

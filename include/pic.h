@@ -118,6 +118,10 @@ typedef struct pic_config {
                              re-order each patch's particles so that a warp's
                              32 lanes hold particles of 32 distinct
                              neighbouring cells; 0: never */
+  int task_chunk;         /* particles per work item of the particle step: a
+                             patch holding more is split over several
+                             blocks, each with its own current tile
+                             (0 = 2048) */
 } pic_config;
 
 typedef struct pic_diag_t {

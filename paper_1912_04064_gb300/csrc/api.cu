@@ -31,6 +31,8 @@ struct pic_ctx {
   int *bcnt[2] = {};
   int cap = 0;
   Buckets bk{};
+  Plan plan{};
+  int ps_grid = 0;
   DevState *st = nullptr;
   double *partials = nullptr;
   int npartials = 0;
@@ -234,6 +236,20 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
     CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
   }
   CK(cudaMalloc(&ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
+  // work plan: a slot holds at most cap + bucket stride particles per step
+  const bool merge = ctx->cfg.merge > 0;
+  Plan &pl = ctx->plan;
+  pl.unit = merge ? (int)(16 / sizeof(R)) : 1;
+  const int chunk_particles = ctx->cfg.task_chunk > 0 ? ctx->cfg.task_chunk : 2048;
+  pl.chunk = std::max(1, chunk_particles / pl.unit);
+  const long long units_max = (long long)(cap + ctx->bk.stride) / pl.unit + 9;
+  pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
+                                          1ll << 30);
+  CK(cudaMalloc(&pl.item_slot, sizeof(int) * pl.max_items));
+  CK(cudaMalloc(&pl.item_first, sizeof(int) * pl.max_items));
+  CK(cudaMalloc(&pl.n_items, sizeof(int) * 2));
+  pl.next = pl.n_items + 1;
+  CK(cudaMalloc(&pl.units, sizeof(int) * g.nslots));
   return PIC_OK;
 }
 
@@ -295,9 +311,15 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.cjz = R(g.q);
   a.RP = R(g.P);
   a.RQ = R(g.Q);
+  a.plan = ctx->plan;
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
   const bool merge = ctx->cfg.merge > 0;
-  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->stream));
+  if (!ctx->ps_grid) {
+    ctx->ps_grid = particle_step_grid<R>(g.P, g.Q, ctx->cfg.tma != 0, merge, block);
+    if (ctx->ps_grid <= 0) return fail(ctx, PIC_ECUDA, "particle step occupancy query failed");
+  }
+  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,
+                             ctx->stream));
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
   FieldArgs<R> f;
   f.g = g;
@@ -323,7 +345,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
 }
 
 int kernels_per_step(const pic_ctx *c) {
-  return 3 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0);
+  return 4 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0);
 }
 
 __global__ void k_window_state(DevState *st, int col0, int nshift) {
@@ -404,6 +426,11 @@ void free_particles(pic_ctx *c) {
   }
   cudaFree(c->offsets);
   c->offsets = nullptr;
+  cudaFree(c->plan.item_slot);
+  cudaFree(c->plan.item_first);
+  cudaFree(c->plan.n_items);
+  cudaFree(c->plan.units);
+  c->plan = Plan{};
 }
 
 // Copy the live state (current particle set and in-flight buckets, E, Bm,
@@ -703,7 +730,7 @@ pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, in
   for (int pp = 0; pp < g.nslots; ++pp) {
     const int slot = (pp / g.npx) * g.npx + (pp % g.npx + ctx->col0) % g.npx;
     off[pp] = tot;
-    tot += c[slot];
+    tot += std::min(c[slot], ctx->cap);
   }
   for (int pp = 0; pp < g.nslots; ++pp) {
     const int slot = (pp / g.npx) * g.npx + (pp % g.npx + ctx->col0) % g.npx;
@@ -711,7 +738,8 @@ pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, in
       int ddx, ddy;
       dir_delta(d, ddx, ddy);
       off[g.nslots + (size_t)pp * 8 + d] = tot;
-      if (neighbour_slot(g, ctx->col0, slot, ddx, ddy) >= 0) tot += b[(size_t)slot * 8 + d];
+      if (neighbour_slot(g, ctx->col0, slot, ddx, ddy) >= 0)
+        tot += std::min(b[(size_t)slot * 8 + d], ctx->bk.cap[d]);
     }
   }
   *n = (size_t)tot;
@@ -1016,16 +1044,8 @@ void pic_destroy(pic_ctx *ctx) {
   cudaFree(ctx->laser_g);
   cudaFree(ctx->st);
   cudaFree(ctx->partials);
-  cudaFree(ctx->offsets);
   cudaFree(ctx->staging);
-  for (int s = 0; s < 2; ++s) {
-    for (int a = 0; a < 6; ++a) {
-      cudaFree(ctx->seg[s][a]);
-      cudaFree(ctx->bkt[s][a]);
-    }
-    cudaFree(ctx->cnt[s]);
-    cudaFree(ctx->bcnt[s]);
-  }
+  free_particles(ctx);
   free_backup(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

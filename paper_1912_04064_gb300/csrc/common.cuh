@@ -200,6 +200,19 @@ constexpr long long WAIT_POLLS = 1ll << 24;
 constexpr long long DRAIN_POLLS = 1ll << 22;
 
 // ----------------------------------------------------------- launchers ---
+// Work plan of one particle step: items (patch slot, first work unit), a
+// work unit being the particles one thread takes at once; patches holding
+// more than `chunk` units are split into several items (task decomposition
+// below the patch), ordered heaviest patch first.
+struct Plan {
+  int *item_slot, *item_first;  // [max_items]
+  int *n_items, *next;          // device scalars: items, work counter
+  int *units;                   // [nslots] scratch: units per slot
+  int chunk;                    // units per item
+  int unit;                     // particles per unit
+  int max_items;
+};
+
 template <typename R>
 struct StepArgs {
   Geom g;
@@ -221,11 +234,17 @@ struct StepArgs {
   R eps;               // q dt / (2 m)
   R cjx, cjy, cjz;     // -q dx / dt, -q dy / dt, q
   R RP, RQ;            // patch size as reals
+  Plan plan;
 };
 
+// Build the plan (and clear the output counts), then run the persistent
+// particle step with `grid` blocks.
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 bool merge, int block, cudaStream_t s);
+                                 bool merge, int block, int grid, cudaStream_t s);
+// Blocks of the particle step resident on the device at once.
+template <typename R>
+int particle_step_grid(int P, int Q, bool tma, bool merge, int block);
 // Raise the dynamic shared-memory limit of the step kernels (call outside
 // stream capture).
 template <typename R>

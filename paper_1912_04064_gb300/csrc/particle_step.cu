@@ -170,13 +170,11 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
   __shared__ int s_qoff[10];
   __shared__ int s_cnt[9];
   __shared__ long long s_base[9];
-  __shared__ int s_out;
-  __shared__ int s_bcnt[8];
+  __shared__ int s_item;
   __shared__ int s_ok;
 
   const Geom &g = a.g;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int s = blockIdx.x;
   const int P = PT ? PT : g.P, Q = QT ? QT : g.Q;
   const int BX = BXc ? BXc : P + 8, BY = BYc ? BYc : Q + 3;  // field tile
   const int JW = JWc ? JWc : P + 5, JH = JHc ? JHc : Q + 5;  // current tile
@@ -184,79 +182,87 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
   const uint32_t pad = (128u - (smem_u32(dsm_raw) & 127u)) & 127u;
   R *Ft = reinterpret_cast<R *>(dsm_raw + pad);
   R *Jt = Ft + 6 * FT;
-
-  const int col0 = a.st->col0;
-  const int sxs = s % g.npx, sy = s / g.npx;
-  int px = sxs - col0;
-  if (px < 0) px += g.npx;
-  const int py = sy;
-  const int X0 = px * P, Y0 = py * Q;
-
-  // ---- 1. region -> patch field staging (SDMD step ii)
-  if (TMA) {
-    if (tid == 0) {
-      mbar_init(&mbar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-      mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
-      tma_load_3d(Ft, &tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
-    }
-  } else {
-    for (int e = tid; e < 6 * FT; e += nth) {
-      int c = e / FT, r = e - c * FT, yy = r / BX, xx = r - yy * BX;
-      Ft[e] = a.F[c * g.cs + fidx(g, X0 - 4 + xx, Y0 - 1 + yy)];
-    }
-  }
-  for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
-  if (tid < 9) {
-    int cnt = 0;
-    long long base = 0;
-    if (tid == 0) {
-      cnt = a.cnt_in[s];
-      base = (long long)s * a.cap;
-    } else {
-      int k = tid - 1, ddx, ddy;
-      dir_delta(k, ddx, ddy);
-      const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
-      if (src >= 0) {
-        cnt = a.bcnt_in[(long long)src * 8 + k];
-        base = (long long)src * a.bk.stride + a.bk.off[k];
-      }
-    }
-    s_cnt[tid] = cnt;
-    s_base[tid] = base;
-  }
-  if (tid < 8) s_bcnt[tid] = 0;
-  if (tid == 0) s_out = 0;
-  __syncthreads();
-  if (tid == 0) {
-    s_qoff[0] = 0;
-    for (int i = 0; i < 9; ++i) s_qoff[i + 1] = s_qoff[i] + (s_cnt[i] + M - 1) / M;
-    int ok = 1;
-    if (TMA) {
-      ok = 0;
-      for (long long it = 0; it < WAIT_POLLS; ++it)
-        if (mbar_try_wait(&mbar, 0)) { ok = 1; break; }
-      if (!ok) {
-        atomicOr(&a.st->err, ERR_TIMEOUT);
-        for (long long it = 0; it < DRAIN_POLLS; ++it)
-          if (mbar_try_wait(&mbar, 0)) break;
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (!s_ok) return;
-
-  // ---- 2..5. particles, M per thread
-  const int totalq = s_qoff[9];
   const R rdx = a.rdx, rdy = a.rdy, eps = a.eps;
   const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
   const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
   const int lane = tid & 31;
+  const int col0 = a.st->col0;
+  const int n_items = *a.plan.n_items;
   unsigned err = 0;
+  uint32_t phase = 0;
+  if (TMA && tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+
+  // Persistent loop over work items: (patch slot, chunk of its particles),
+  // heaviest patches first, fetched from a global counter.
+  for (;;) {
+    __syncthreads();  // the previous item is done with the tiles
+    if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int s = a.plan.item_slot[item];
+    const int ufirst = a.plan.item_first[item];
+    const int sxs = s % g.npx, sy = s / g.npx;
+    int px = sxs - col0;
+    if (px < 0) px += g.npx;
+    const int py = sy;
+    const int X0 = px * P, Y0 = py * Q;
+
+    // ---- 1. region -> patch field staging (SDMD step ii)
+    if (TMA) {
+      if (tid == 0) {
+        mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
+        tma_load_3d(Ft, &tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
+      }
+    } else {
+      for (int e = tid; e < 6 * FT; e += nth) {
+        int c = e / FT, r = e - c * FT, yy = r / BX, xx = r - yy * BX;
+        Ft[e] = a.F[c * g.cs + fidx(g, X0 - 4 + xx, Y0 - 1 + yy)];
+      }
+    }
+    for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
+    if (tid < 9) {
+      int cnt = 0;
+      long long base = 0;
+      if (tid == 0) {
+        cnt = min(a.cnt_in[s], a.cap);
+        base = (long long)s * a.cap;
+      } else {
+        int k = tid - 1, ddx, ddy;
+        dir_delta(k, ddx, ddy);
+        const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
+        if (src >= 0) {
+          cnt = min(a.bcnt_in[(long long)src * 8 + k], a.bk.cap[k]);
+          base = (long long)src * a.bk.stride + a.bk.off[k];
+        }
+      }
+      s_cnt[tid] = cnt;
+      s_base[tid] = base;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_qoff[0] = 0;
+      for (int i = 0; i < 9; ++i) s_qoff[i + 1] = s_qoff[i] + (s_cnt[i] + M - 1) / M;
+      int ok = 1;
+      if (TMA) {
+        ok = 0;
+        for (long long it = 0; it < WAIT_POLLS; ++it)
+          if (mbar_try_wait(&mbar, phase)) { ok = 1; break; }
+        if (!ok) {
+          atomicOr(&a.st->err, ERR_TIMEOUT);
+          for (long long it = 0; it < DRAIN_POLLS; ++it)
+            if (mbar_try_wait(&mbar, phase)) break;
+        }
+      }
+      s_ok = ok;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (!s_ok) break;
+    const int totalq = min(ufirst + a.plan.chunk, s_qoff[9]);
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -295,8 +301,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     return nval;
   };
   R x[M], y[M], ux[M], uy[M], uz[M], w[M];
-  int nval = load(tid, x, y, ux, uy, uz, w);
-  for (int qb = 0; qb < totalq; qb += nth) {
+  int nval = load(ufirst + tid, x, y, ux, uy, uz, w);
+  for (int qb = ufirst; qb < totalq; qb += nth) {
     // prefetch the next work item so its global loads overlap this one
     R nx_[M], ny_[M], nux_[M], nuy_[M], nuz_[M], nw_[M];
     const int nnval = load(qb + nth + tid, nx_, ny_, nux_, nuy_, nuz_, nw_);
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
       const bool stay = dir == -1;
       const unsigned bal = __ballot_sync(0xffffffffu, stay);
       int wbase = 0;
-      if (lane == 0 && bal) wbase = atomicAdd(&s_out, __popc(bal));
+      if (lane == 0 && bal) wbase = atomicAdd(&a.cnt_out[s], __popc(bal));
       wbase = __shfl_sync(0xffffffffu, wbase, 0);
       if (stay) {
         const int pos = wbase + __popc(bal & ((1u << lane) - 1u));
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
           err |= ERR_OVERFLOW_SEG;
         }
       } else if (dir >= 0) {
-        const int bp = atomicAdd(&s_bcnt[dir], 1);
+        const int bp = atomicAdd(&a.bcnt_out[(long long)s * 8 + dir], 1);
         if (bp < a.bk.cap[dir]) {
           const long long i = (long long)s * a.bk.stride + a.bk.off[dir] + bp;
           a.bout.x[i] = x1; a.bout.y[i] = y1;
@@ -476,27 +482,72 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     }
     nval = nnval;
   }
+    __syncthreads();
+    // ---- SDMD step (i): patch current tile -> region current
+    for (int e = tid; e < 3 * JT; e += nth) {
+      const R v = Jt[e];
+      if (v != R(0)) {
+        const int c = e / JT, r = e - c * JT, l = r / JW, q = r - l * JW;
+        int gi = X0 - 2 + q, gj = Y0 - 2 + l;
+        if (g.fbc_x == FBC_PERIODIC) gi = gi < 0 ? gi + g.nx : (gi >= g.nx ? gi - g.nx : gi);
+        if (g.fbc_y == FBC_PERIODIC) gj = gj < 0 ? gj + g.ny : (gj >= g.ny ? gj - g.ny : gj);
+        atomicAdd(&a.Jdst[c * g.cs + fidx(g, gi, gj)], v);
+      }
+    }
+    if (tid == 0) atomicMax(&a.st->maxcnt[a.parity], atomicAdd(&a.cnt_out[s], 0));
+  }
   if (err) atomicOr(&a.st->err, err);
-  __syncthreads();
+}
 
-  // ---- SDMD step (i): patch current tile -> region current
-  for (int e = tid; e < 3 * JT; e += nth) {
-    const R v = Jt[e];
-    if (v != R(0)) {
-      const int c = e / JT, r = e - c * JT, l = r / JW, q = r - l * JW;
-      int gi = X0 - 2 + q, gj = Y0 - 2 + l;
-      if (g.fbc_x == FBC_PERIODIC) gi = gi < 0 ? gi + g.nx : (gi >= g.nx ? gi - g.nx : gi);
-      if (g.fbc_y == FBC_PERIODIC) gj = gj < 0 ? gj + g.ny : (gj >= g.ny ? gj - g.ny : gj);
-      atomicAdd(&a.Jdst[c * g.cs + fidx(g, gi, gj)], v);
+// Plan of one step: units per slot (segment plus incoming buckets, counts
+// clamped to the capacities), items per slot, items ordered by decreasing
+// item count of their slot (classes of one item count, heaviest first);
+// the output counts of the step are cleared here.
+constexpr int PLAN_CLASSES = 64;
+
+__global__ void __launch_bounds__(1024) k_plan(const Geom g, const int *cnt_in,
+                                               const int *bcnt_in, int cap, Buckets bk,
+                                               Plan plan, int *cnt_out, int *bcnt_out,
+                                               const DevState *st) {
+  __shared__ int hist[PLAN_CLASSES], off[PLAN_CLASSES];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int col0 = st->col0, u = plan.unit;
+  for (int c = tid; c < PLAN_CLASSES; c += nth) hist[c] = 0;
+  __syncthreads();
+  for (int s = tid; s < g.nslots; s += nth) {
+    int units = (min(cnt_in[s], cap) + u - 1) / u;
+    for (int d = 0; d < 8; ++d) {
+      int ddx, ddy;
+      dir_delta(d, ddx, ddy);
+      const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
+      if (src >= 0) units += (min(bcnt_in[(long long)src * 8 + d], bk.cap[d]) + u - 1) / u;
+    }
+    plan.units[s] = units;
+    cnt_out[s] = 0;
+    for (int d = 0; d < 8; ++d) bcnt_out[(long long)s * 8 + d] = 0;
+    const int items = (units + plan.chunk - 1) / plan.chunk;
+    if (items) atomicAdd(&hist[min(items, PLAN_CLASSES) - 1], items);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int c = PLAN_CLASSES - 1; c >= 0; --c) {
+      off[c] = run;
+      run += hist[c];
+    }
+    *plan.n_items = min(run, plan.max_items);
+    *plan.next = 0;
+  }
+  __syncthreads();
+  for (int s = tid; s < g.nslots; s += nth) {
+    const int items = (plan.units[s] + plan.chunk - 1) / plan.chunk;
+    if (!items) continue;
+    const int base = atomicAdd(&off[min(items, PLAN_CLASSES) - 1], items);
+    for (int k = 0; k < items && base + k < plan.max_items; ++k) {
+      plan.item_slot[base + k] = s;
+      plan.item_first[base + k] = k * plan.chunk;
     }
   }
-  if (tid == 0) {
-    const int n = s_out < a.cap ? s_out : a.cap;
-    a.cnt_out[s] = n;
-    atomicMax(&a.st->maxcnt[a.parity], s_out);
-  }
-  if (tid < 8)
-    a.bcnt_out[(long long)s * 8 + tid] = s_bcnt[tid] < a.bk.cap[tid] ? s_bcnt[tid] : a.bk.cap[tid];
 }
 
 template <typename R, int PT, int QT, bool TMA, bool MERGE>
@@ -539,20 +590,36 @@ cudaError_t prepare_particle_step(int P, int Q) {
 }
 
 template <typename R>
+int particle_step_grid(int P, int Q, bool tma, bool merge, int block) {
+  const int smem = (int)particle_step_smem(P, Q, sizeof(R));
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel<R>(P, Q, tma, merge),
+                                                    block, smem) != cudaSuccess)
+    return 0;
+  return per_sm * nsm;
+}
+
+template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 bool merge, int block, cudaStream_t s) {
+                                 bool merge, int block, int grid, cudaStream_t s) {
+  k_plan<<<1, 1024, 0, s>>>(a.g, a.cnt_in, a.bcnt_in, a.cap, a.bk, a.plan, a.cnt_out,
+                            a.bcnt_out, a.st);
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
   const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge);
   void *args[] = {(void *)tmap, (void *)&a};
-  return cudaLaunchKernel(k, dim3(a.g.nslots), dim3(block), args, smem, s);
+  return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
 }
 
+template int particle_step_grid<float>(int, int, bool, bool, int);
+template int particle_step_grid<double>(int, int, bool, bool, int);
 template cudaError_t prepare_particle_step<float>(int, int);
 template cudaError_t prepare_particle_step<double>(int, int);
 template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const CUtensorMap *,
-                                                 bool, bool, int, cudaStream_t);
+                                                 bool, bool, int, int, cudaStream_t);
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
-                                                  const CUtensorMap *, bool, bool, int,
+                                                  const CUtensorMap *, bool, bool, int, int,
                                                   cudaStream_t);
 
 }  // namespace pic

@@ -89,13 +89,13 @@ __device__ void for_each_particle(const Geom &g, int col0, const PartView<R> &v,
   for (int slot = blockIdx.x; slot < g.nslots; slot += gridDim.x) {
     int X0, Y0;
     slot_origin(g, col0, slot, X0, Y0);
-    const int n = v.cnt[slot];
+    const int n = min(v.cnt[slot], v.cap);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const long long i = (long long)slot * v.cap + k;
       fn(X0, Y0, v.seg.x[i], v.seg.y[i], v.seg.ux[i], v.seg.uy[i], v.seg.uz[i], v.seg.w[i]);
     }
     for (int d = 0; d < 8; ++d) {
-      const int nb = v.bcnt[(long long)slot * 8 + d];
+      const int nb = min(v.bcnt[(long long)slot * 8 + d], v.bk.cap[d]);
       if (nb == 0) continue;
       int ddx, ddy;
       dir_delta(d, ddx, ddy);
@@ -184,14 +184,14 @@ __global__ void k_get_particles(const Geom g, int col0, const PartView<R> v,
     out[5 * stride + o] = (double)w;
   };
   const int X0 = ppx * g.P, Y0 = ppy * g.Q;
-  const int n = v.cnt[slot];
+  const int n = min(v.cnt[slot], v.cap);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const long long i = (long long)slot * v.cap + k;
     emit(offsets[pp] + k, X0, Y0, v.seg.x[i], v.seg.y[i], v.seg.ux[i], v.seg.uy[i], v.seg.uz[i],
          v.seg.w[i]);
   }
   for (int d = 0; d < 8; ++d) {
-    const int nb = v.bcnt[(long long)slot * 8 + d];
+    const int nb = min(v.bcnt[(long long)slot * 8 + d], v.bk.cap[d]);
     if (nb == 0) continue;
     int ddx, ddy;
     dir_delta(d, ddx, ddy);
@@ -221,7 +221,7 @@ __global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, S
   for (int ddy = -1; ddy <= 1; ++ddy) {
     const int d = dir_index(1, ddy);
     const int dest = neighbour_slot(g, col0, sdrop, 1, ddy);
-    const int nb = bcnt[(long long)sdrop * 8 + d];
+    const int nb = min(bcnt[(long long)sdrop * 8 + d], bk.cap[d]);
     if (dest < 0) continue;
     __shared__ int base;
     if (threadIdx.x == 0) base = atomicAdd(&cnt[dest], nb);
@@ -300,7 +300,7 @@ __global__ void k_repack(const Geom g, SoA<R> src, const int *cnt_src, int cap_s
                          const int *bcnt_src, Buckets bk_src, SoA<R> dst, int *cnt_dst,
                          int cap_dst, SoA<R> bdst, int *bcnt_dst, Buckets bk_dst) {
   const int slot = blockIdx.x;
-  const int n = min(cnt_src[slot], cap_dst);
+  const int n = min(min(cnt_src[slot], cap_src), cap_dst);
   const long long so = (long long)slot * cap_src, dof = (long long)slot * cap_dst;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     dst.x[dof + k] = src.x[so + k]; dst.y[dof + k] = src.y[so + k];
@@ -308,7 +308,7 @@ __global__ void k_repack(const Geom g, SoA<R> src, const int *cnt_src, int cap_s
     dst.uz[dof + k] = src.uz[so + k]; dst.w[dof + k] = src.w[so + k];
   }
   for (int d = 0; d < 8; ++d) {
-    const int nb = min(bcnt_src[(long long)slot * 8 + d], bk_dst.cap[d]);
+    const int nb = min(min(bcnt_src[(long long)slot * 8 + d], bk_src.cap[d]), bk_dst.cap[d]);
     const long long bs = (long long)slot * bk_src.stride + bk_src.off[d];
     const long long bd = (long long)slot * bk_dst.stride + bk_dst.off[d];
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
@@ -354,14 +354,14 @@ __global__ void k_sort_cells(const Geom g, int col0, SoA<R> src, const int *cnt_
     int cnt = 0;
     long long base = 0;
     if (tid == 0) {
-      cnt = cnt_src[slot];
+      cnt = min(cnt_src[slot], cap);
       base = (long long)slot * cap;
     } else {
       int k = tid - 1, ddx, ddy;
       dir_delta(k, ddx, ddy);
       const int sv = neighbour_slot(g, col0, slot, -ddx, -ddy);
       if (sv >= 0) {
-        cnt = bcnt[(long long)sv * 8 + k];
+        cnt = min(bcnt[(long long)sv * 8 + k], bk.cap[k]);
         base = (long long)sv * bk.stride + bk.off[k];
       }
     }
@@ -456,7 +456,7 @@ template <typename R>
 __global__ void k_copy_segments(const Geom g, SoA<R> src, const int *cnt_src, SoA<R> dst,
                                 int *cnt_dst, int cap) {
   const int slot = blockIdx.x;
-  const int n = cnt_src[slot];
+  const int n = min(cnt_src[slot], cap);
   const long long o = (long long)slot * cap;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     dst.x[o + k] = src.x[o + k]; dst.y[o + k] = src.y[o + k];

@@ -41,7 +41,7 @@ class pic_config(C.Structure):
         ("inj_ppc", C.c_int * 3), ("capacity_factor", C.c_double), ("capacity_min", C.c_int),
         ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
-        ("sort_every", C.c_int),
+        ("sort_every", C.c_int), ("task_chunk", C.c_int),
     ]
 
 
@@ -113,7 +113,8 @@ class PicError(RuntimeError):
 def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     use_graph: bool = True, timing: bool = False, tma: bool = True,
                     capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0,
-                    merge: int = -1, auto_grow: bool = True, sort_every: int = 0) -> pic_config:
+                    merge: int = -1, auto_grow: bool = True, sort_every: int = 0,
+                    task_chunk: int = 0) -> pic_config:
     """pic_config of a run dictionary (see ``workloads``)."""
     c = pic_config()
     c.dims = 2
@@ -154,6 +155,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     c.merge = merge
     c.auto_grow = int(auto_grow)
     c.sort_every = sort_every
+    c.task_chunk = task_chunk
     return c
 
 

@@ -365,3 +365,24 @@ def test_cell_order_sort_fp32_open_window():
     do, dg = o.diag(), g.pic_diag()
     assert dg["np"] == do["np"] and dg["shifts"] == do["shifts"] >= 1
     assert abs(dg["U_E"] - do["U_E"]) <= 1e-3 * do["U_E"]
+
+
+@pytest.mark.parametrize("chunk", [128, 1000])
+def test_patch_split_into_tasks_keeps_parity(chunk):
+    """A patch holding more particles than the task chunk is processed by
+    several blocks, each with its own current tile and shared output
+    counters: FP64 parity with the oracle still holds."""
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    rng = np.random.default_rng(23)
+    n = 12000
+    x = np.concatenate([rng.uniform(1.6, 3.2, n // 2), rng.uniform(0, 6.4, n // 2)])
+    y = np.concatenate([rng.uniform(1.6, 3.2, n // 2), rng.uniform(0, 6.4, n // 2)])
+    u = rng.normal(0, 0.5, (3, n))
+    parts = {"x": x, "y": y, "ux": u[0], "uy": u[1], "uz": u[2], "w": rng.uniform(0.5, 1.5, n)}
+    fields = W.random_fields((64, 64), seed=24, amp=0.1)
+    o, g = pair(run, parts, fields, task_chunk=chunk)
+    for _ in range(3):
+        o.step(1)
+        g.pic_step(1)
+    _assert_fields(field_errors(o, g), 1e-11)
+    assert max(particle_errors(o, g).values()) <= 1e-11
