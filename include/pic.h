@@ -122,6 +122,10 @@ typedef struct pic_config {
                              patch holding more is split over several
                              blocks, each with its own current tile
                              (0 = 2048) */
+  int filter_passes;      /* binomial current filter (Section 3.2): 0 off, 1 or
+                             2 passes of (1,2,1)/4 along x then y applied to
+                             J before the field update; pic_get_field(J*)
+                             still returns the deposited current */
 } pic_config;
 
 typedef struct pic_diag_t {

@@ -41,7 +41,8 @@ class _Cfg(C.Structure):
                 ("mw_on", C.c_int), ("mw_t0", C.c_double),
                 ("inj_n0", C.c_double), ("inj_x0", C.c_double), ("inj_ramp", C.c_double),
                 ("inj_ppcx", C.c_int), ("inj_ppcy", C.c_int),
-                ("track_continuity", C.c_int), ("nthreads", C.c_int)]
+                ("track_continuity", C.c_int), ("filter_passes", C.c_int),
+                ("nthreads", C.c_int)]
 
 
 _lib = None
@@ -71,6 +72,7 @@ def lib():
         L.orc_esirkepov.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.c_double, C.c_double,
                                     C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.orc_apply_filter.argtypes = [C.c_void_p]
         L.orc_gather.restype = C.c_double
         L.orc_gather.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
         L.orc_laser_field.argtypes = [C.c_void_p, C.c_double, C.c_double, dp]
@@ -108,6 +110,7 @@ def make_config(run: dict, nthreads: int = 0, track_continuity: bool = False) ->
     else:
         c.inj_ppcx = c.inj_ppcy = 1
     c.track_continuity = int(track_continuity)
+    c.filter_passes = int(run.get("filter_passes", 0))
     c.nthreads = nthreads
     return c
 
@@ -173,6 +176,9 @@ class Oracle:
         v = C.c_double()
         lib().orc_laser_field(self.h, y, t, C.byref(v))
         return v.value
+
+    def apply_filter(self):
+        lib().orc_apply_filter(self.h)
 
     def gather(self, name: str, x: float, y: float) -> float:
         return lib().orc_gather(self.h, FIELDS.index(name), x, y)

@@ -375,6 +375,35 @@ static void upd_range(int fbc, int n, int dual, int *lo, int *hi) {
   *hi = (fbc == ORC_FBC_PERIODIC) ? n : (dual ? n : n + 1);
 }
 
+/* Binomial current filter (Section 3.2: "two-pass binomial filter" on the
+ * current densities every iteration): each pass replaces J(i) by
+ * (J(i-1) + 2 J(i) + J(i+1)) / 4 along x, then the same along y, for every
+ * stored index; periodic axes wrap, open axes read zero outside the stored
+ * range. */
+static void filter_current(orc_state *s) {
+  const orc_config *c = &s->c;
+  double *tmp = malloc(s->ntot * sizeof(double));
+  const int xl = c->fbc_x == ORC_FBC_PERIODIC ? 0 : -G, xh = c->fbc_x == ORC_FBC_PERIODIC ? c->nx : c->nx + G;
+  const int yl = c->fbc_y == ORC_FBC_PERIODIC ? 0 : -G, yh = c->fbc_y == ORC_FBC_PERIODIC ? c->ny : c->ny + G;
+  for (int pass = 0; pass < c->filter_passes; ++pass)
+    for (int k = ORC_JX; k <= ORC_JZ; ++k)
+      for (int axis = 0; axis < 2; ++axis) {
+        double *J = s->F[k];
+        memcpy(tmp, J, s->ntot * sizeof(double));
+        for (int j = yl; j < yh; ++j)
+          for (int i = xl; i < xh; ++i) {
+            const int di = axis == 0, dj = axis == 1;
+            double lo = 0.0, hi = 0.0;
+            if (in_store(s, i - di, j - dj)) lo = *at(s, tmp, i - di, j - dj);
+            if (in_store(s, i + di, j + dj)) hi = *at(s, tmp, i + di, j + dj);
+            *at(s, J, i, j) = 0.25 * (lo + 2.0 * *at(s, tmp, i, j) + hi);
+          }
+      }
+  free(tmp);
+}
+
+void orc_apply_filter(orc_state *s) { filter_current(s); }
+
 /* Yee finite-difference update of the region (Section 3.2):
  * E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2}),
  * B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}, Bm^{n+1} = (B^{n+1/2}+B^{n+3/2})/2,
@@ -655,6 +684,7 @@ int orc_step(orc_state *s, int nsteps) {
     }
     apply_particle_bc(s);
     rebin(s);
+    if (c->filter_passes > 0) filter_current(s);
     maxwell(s);
     s->step++;
     s->t += c->dt;

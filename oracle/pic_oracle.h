@@ -49,6 +49,7 @@ typedef struct {
   double inj_n0, inj_x0, inj_ramp; /* density profile of injected plasma */
   int inj_ppcx, inj_ppcy;
   int track_continuity;  /* keep rho^n of the last step for the residual */
+  int filter_passes;     /* binomial (1,2,1)/4 passes on J, each along x then y */
   int nthreads;          /* OpenMP threads for the patch loop (0 = default) */
 } orc_config;
 
@@ -81,6 +82,8 @@ void orc_boris(double q, double m, double dt, const double E[3],
 int orc_esirkepov(const orc_state *s, double x0, double y0, double x1,
                   double y1, double w, double vz, int *ix, int *iy,
                   double Jw[3][5][5]);
+/* Apply the configured binomial filter passes to the stored J (test hook). */
+void orc_apply_filter(orc_state *s);
 /* Interpolated value of component comp (< ORC_RHO) at (x, y). */
 double orc_gather(const orc_state *s, int comp, double x, double y);
 int orc_laser_field(const orc_state *s, double y, double t, double *ey);

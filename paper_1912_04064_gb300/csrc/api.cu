@@ -127,6 +127,7 @@ bool valid_config(const pic_config *c, std::string &why) {
   }
   if (c->capacity_factor < 0) { why = "capacity factor must be >= 0"; return false; }
   if (c->block && (c->block % 32 || c->block < 64 || c->block > 256)) { why = "block must be 64..256, a multiple of 32"; return false; }
+  if (c->filter_passes < 0 || c->filter_passes > 2) { why = "filter_passes must be 0, 1 or 2"; return false; }
   return true;
 }
 
@@ -340,12 +341,14 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   f.laser_g = ctx->laser_g;
   f.tau = ctx->cfg.laser_tau;
   f.t_peak = ctx->cfg.laser_t_peak;
+  f.filter_passes = ctx->cfg.filter_passes;
   CK(launch_fields<R>(f, ctx->stream));
   return PIC_OK;
 }
 
 int kernels_per_step(const pic_ctx *c) {
-  return 4 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0);
+  return 4 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0) +
+         (c->cfg.filter_passes > 0 ? 1 : 0);
 }
 
 __global__ void k_window_state(DevState *st, int col0, int nshift) {

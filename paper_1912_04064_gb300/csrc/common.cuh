@@ -265,6 +265,7 @@ struct FieldArgs {
   int laser_on;
   const double *laser_g;
   double tau, t_peak;
+  int filter_passes;   // 0: E reads the deposited J; 1, 2: the filtered copy
 };
 template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s);

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(YBX * YBY) k_update_E(const FieldArgs<R> a) {
   R *F = a.F;
   R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
   const R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
-  const R *J = F + (C_JA + 3 * a.parity) * cs;
+  const R *J = F + (C_JA + 3 * (a.filter_passes > 0 ? 1 - a.parity : a.parity)) * cs;
   const R dt = a.dt, idx = a.idx, idy = a.idy;
   const long long o = (long long)(j + GY) * sx + (i + GX);
   const R bz = Bz[o], bzl = Bz[o - 1], bzd = Bz[o - sx];
@@ -239,6 +239,57 @@ __global__ void k_silver_mueller(const FieldArgs<R> a) {
   }
 }
 
+// Binomial current filter (Section 3.2): NP passes of (1,2,1)/4 along x then
+// y, applied as the separable stencil (1,2,1)/4 (NP = 1) or (1,4,6,4,1)/16
+// (NP = 2) per axis, from the deposited set into the other current set.
+// Periodic axes wrap; open axes read zero outside the stored range (the
+// deposit never reaches the outer two stored layers, so this equals the
+// pass-by-pass definition).
+template <typename R, int NP>
+__global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R> a, int src,
+                                                              int dst) {
+  const Geom &g = a.g;
+  const bool px = g.fbc_x == FBC_PERIODIC, py = g.fbc_y == FBC_PERIODIC;
+  const int ilo = px ? 0 : -GX, jlo = py ? 0 : -GY;
+  const int ihi = px ? g.nx : g.nx + GX, jhi = py ? g.ny : g.ny + GY;
+  const int i = ilo + (int)(blockIdx.x * YBX + threadIdx.x);
+  const int j = jlo + (int)(blockIdx.y * YBY + threadIdx.y);
+  if (i >= ihi || j >= jhi) return;
+  constexpr int W = 2 * NP + 1;
+  const R c1[3] = {R(0.25), R(0.5), R(0.25)};
+  const R c2[5] = {R(1.0 / 16), R(4.0 / 16), R(6.0 / 16), R(4.0 / 16), R(1.0 / 16)};
+  const R *cw = NP == 1 ? c1 : c2;
+  int ii[W], jj[W];
+  bool okx[W], oky[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    int u = i + k - NP, v = j + k - NP;
+    okx[k] = true;
+    oky[k] = true;
+    if (px) u = u < 0 ? u + g.nx : (u >= g.nx ? u - g.nx : u);
+    else okx[k] = u >= -GX && u < g.nx + GX;
+    if (py) v = v < 0 ? v + g.ny : (v >= g.ny ? v - g.ny : v);
+    else oky[k] = v >= -GY && v < g.ny + GY;
+    ii[k] = u;
+    jj[k] = v;
+  }
+  const long long o = fidx(g, i, j);
+  for (int c = 0; c < 3; ++c) {
+    const R *J = a.F + (C_JA + 3 * src + c) * g.cs;
+    R acc = R(0);
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      if (!oky[b]) continue;
+      R row = R(0);
+#pragma unroll
+      for (int k = 0; k < W; ++k)
+        if (okx[k]) row += cw[k] * J[fidx(g, ii[k], jj[b])];
+      acc += cw[b] * row;
+    }
+    a.F[(C_JA + 3 * dst + c) * g.cs + o] = acc;
+  }
+}
+
 // ---------------------------------------------------------------- I/O ----
 __host__ __device__ inline void out_layout(const Geom &g, int &lx, int &nxo, int &ly, int &nyo) {
   lx = g.fbc_x == FBC_PERIODIC ? 0 : -1;
@@ -367,6 +418,15 @@ cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   const Geom &g = a.g;
   const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
   const dim3 blk(YBX, YBY);
+  if (a.filter_passes > 0) {
+    const int fw = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
+    const int fh = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
+    const dim3 fgrid((fw + YBX - 1) / YBX, (fh + YBY - 1) / YBY);
+    if (a.filter_passes == 1)
+      k_filter_current<R, 1><<<fgrid, blk, 0, s>>>(a, a.parity, 1 - a.parity);
+    else
+      k_filter_current<R, 2><<<fgrid, blk, 0, s>>>(a, a.parity, 1 - a.parity);
+  }
   k_update_E<R><<<dim3((nxp + YBX - 1) / YBX, (nyp + YBY - 1) / YBY), blk, 0, s>>>(a);
   const int ncol = g.nx + 2 * GX, nrow = g.ny + 2 * GY;
   k_update_B<R><<<dim3((ncol + YBX - 1) / YBX, (nrow + YBY - 1) / YBY), blk, 0, s>>>(a);

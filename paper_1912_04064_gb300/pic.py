@@ -41,7 +41,7 @@ class pic_config(C.Structure):
         ("inj_ppc", C.c_int * 3), ("capacity_factor", C.c_double), ("capacity_min", C.c_int),
         ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
-        ("sort_every", C.c_int), ("task_chunk", C.c_int),
+        ("sort_every", C.c_int), ("task_chunk", C.c_int), ("filter_passes", C.c_int),
     ]
 
 
@@ -156,6 +156,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     c.auto_grow = int(auto_grow)
     c.sort_every = sort_every
     c.task_chunk = task_chunk
+    c.filter_passes = int(run.get("filter_passes", 0))
     return c
 
 

@@ -386,3 +386,24 @@ def test_patch_split_into_tasks_keeps_parity(chunk):
         g.pic_step(1)
     _assert_fields(field_errors(o, g), 1e-11)
     assert max(particle_errors(o, g).values()) <= 1e-11
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("openbc", [False, True])
+def test_binomial_filter_parity(passes, openbc):
+    """Binomial current filter (1 or 2 passes) on periodic and open grids:
+    fields after several steps match the oracle (FP64)."""
+    if openbc:
+        run = _open_run(laser=False)
+        parts = W.small_random_particles(run, 20000, seed=33, uth=0.6)
+    else:
+        run = W.periodic_run((64, 48), (0.1, 0.1), (16, 16))
+        parts = W.small_random_particles(run, 20000, seed=33, uth=0.6)
+    run["filter_passes"] = passes
+    fields = W.random_fields(W.field_shape(run), seed=34, amp=0.1)
+    o, g = pair(run, parts, fields)
+    for _ in range(3):
+        o.step(1)
+        g.pic_step(1)
+    errs = field_errors(o, g, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz"))
+    _assert_fields(errs, 1e-11, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz"))

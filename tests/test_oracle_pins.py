@@ -637,3 +637,47 @@ def test_moving_window_keeps_neutral_plasma_neutral():
     d = o.diag()
     assert d["shifts"] >= 2
     assert d["gauss"] < 1e-15, d["gauss"]
+
+
+# ------------------------------------------------------- current filter ----
+
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("mx,my", [(1, 0), (3, 2), (8, 0), (16, 5)])
+def test_binomial_filter_fourier_eigenvalue(passes, mx, my):
+    """(1,2,1)/4 along an axis multiplies a Fourier mode of wavenumber k by
+    cos^2(k d / 2); `passes` passes along x and y give
+    cos^(2 passes)(pi mx / nx) cos^(2 passes)(pi my / ny); the Nyquist mode
+    (mx = nx / 2) is removed and the sum of J is conserved."""
+    run = W.periodic_run((32, 24), (0.1, 0.1), (8, 8))
+    run["filter_passes"] = passes
+    o = Oracle(run)
+    nx, ny = 32, 24
+    i = np.arange(nx)[None, :]
+    j = np.arange(ny)[:, None]
+    J = np.cos(2 * np.pi * mx * i / nx + 0.3) * np.cos(2 * np.pi * my * j / ny - 0.7) + 0.2
+    for k in ("Jx", "Jy", "Jz"):
+        o.set_field(k, J)
+    o.apply_filter()
+    g = (math.cos(math.pi * mx / nx) ** 2 * math.cos(math.pi * my / ny) ** 2) ** passes
+    expect = g * (J - 0.2) + 0.2
+    for k in ("Jx", "Jy", "Jz"):
+        out = o.field(k)
+        assert np.max(np.abs(out - expect)) < 1e-14, k
+        assert abs(out.sum() - J.sum()) < 1e-12
+
+
+def test_binomial_filter_two_pass_impulse_response_open_axes():
+    """On open axes, far from the edges, two passes turn a unit impulse into
+    the binomial 5 x 5 stencil (1,4,6,4,1) x (1,4,6,4,1) / 256."""
+    run, _ = W.lwfa_2d(n=(32, 32), d=(0.125, 0.5), patch=(16, 16))
+    run["filter_passes"] = 2
+    o = Oracle(run)
+    J = np.zeros(o.shape)
+    J[17, 15] = 1.0
+    o.set_field("Jz", J)
+    o.apply_filter()
+    out = o.field("Jz")
+    b = np.array([1, 4, 6, 4, 1]) / 16.0
+    expect = np.zeros_like(J)
+    expect[15:20, 13:18] = np.outer(b, b)
+    assert np.max(np.abs(out - expect)) < 1e-16
