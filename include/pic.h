@@ -180,8 +180,9 @@ pic_status pic_set_background(pic_ctx *ctx, int mode, double value);
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Read one field component (PIC_EX..PIC_RHO_BG) into dst (layout above).
- * PIC_JX..PIC_JZ give the current of the last step; PIC_RHO deposits the
- * particles' charge in float64. */
+ * PIC_JX..PIC_JZ give the current of the last step as the field update used
+ * it (after the binomial filter when filter_passes > 0); PIC_RHO deposits
+ * the particles' charge in float64. */
 pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where);
 
 /* Copy the particles out as 6 x n float64 rows (x, y, ux, uy, uz, w), global
@@ -209,6 +210,55 @@ size_t pic_footprint(const pic_config *cfg, size_t np_max);
 
 const char *pic_last_error(const pic_ctx *ctx);
 void pic_destroy(pic_ctx *ctx);
+
+/* ---- Batches ---------------------------------------------------------
+ * Many independent runs (contexts) advanced together, one launch per kernel
+ * per step for the whole batch: one work plan over the patches of every
+ * run, one persistent particle-step launch whose work items carry their run
+ * (the patch-level task decomposition of Section 2.2 applied across runs),
+ * and one launch per field kernel whose blocks cover every run's region.
+ * Each run keeps its own state and gives the same results, step for step,
+ * as when stepped alone (the order of its floating-point atomic sums aside).
+ *
+ * Rules: the runs of a batch share a precision and the batch's device, have
+ * particles loaded and hold no device fault; at most PIC_BATCH_MAX runs.  A
+ * run may still be used alone between batched steps (its stream and the
+ * batch's are ordered by events); a run whose capacity, storage or step
+ * parity changed since the batch last built its device arguments makes the
+ * next pic_batch_step rebuild them.  Inside a batch a run's capacity is
+ * fixed (no auto_grow replay) and sort_every is not applied; a run that
+ * faults (capacity overflow, non-finite particle, ...) holds the sticky
+ * status that pic_step would give, leaves the batch, and pic_batch_step
+ * returns that status (the other runs have stepped normally).
+ * The batch does not own its runs: destroy it before them, or remove them
+ * with pic_batch_set first. */
+#define PIC_BATCH_MAX 64
+typedef struct pic_batch pic_batch;
+typedef struct pic_batch_config {
+  void *stream;    /* cudaStream_t of the batch; NULL = library-owned */
+  int device;      /* CUDA device ordinal (every run's) */
+  int use_graph;   /* 1: each step replays a captured CUDA graph */
+  int task_chunk;  /* particles per work item (0 = 2048) */
+} pic_batch_config;
+typedef struct pic_batch_diag_t {
+  long long steps;     /* batched steps taken */
+  long long launches;  /* kernels launched by them (window shifts included) */
+  long long builds;    /* device-argument (and graph) rebuilds */
+  int nruns;           /* runs currently in the batch */
+  int grid;            /* blocks of the persistent particle step */
+} pic_batch_diag_t;
+
+pic_status pic_batch_create(const pic_batch_config *cfg, pic_batch **out);
+/* Replace the batch's runs (n = 0 empties it); PIC_EINVAL / PIC_ESTATE when
+ * a run breaks a rule above, leaving the batch unchanged. */
+pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n);
+/* Advance every run nsteps steps (moving-window shifts of each run applied
+ * as they fall due).  Synchronises at the end. */
+pic_status pic_batch_step(pic_batch *b, int nsteps);
+int pic_batch_size(const pic_batch *b);
+pic_status pic_batch_get_diag(const pic_batch *b, pic_batch_diag_t *out);
+const char *pic_batch_last_error(const pic_batch *b);
+void pic_batch_destroy(pic_batch *b);
 
 /* Library version string. */
 const char *pic_version(void);

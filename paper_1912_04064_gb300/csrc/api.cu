@@ -282,12 +282,11 @@ pic_status build_tmap(pic_ctx *ctx) {
   return PIC_OK;
 }
 
-// One step on the context's stream: the patch particle step, then the region
-// field update.  `mid` (optional) is recorded between the two phases.
+// Arguments of the particle step of parity p: reads segment set p and the
+// bucket set 1 - p, writes segment set 1 - p, bucket set p and current set p.
 template <typename R>
-pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
+StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   const Geom &g = ctx->g;
-  const int p = parity;
   StepArgs<R> a;
   a.g = g;
   a.F = (const R *)ctx->F;
@@ -313,15 +312,14 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   a.RP = R(g.P);
   a.RQ = R(g.Q);
   a.plan = ctx->plan;
-  const int block = ctx->cfg.block ? ctx->cfg.block : 256;
-  const bool merge = ctx->cfg.merge > 0;
-  if (!ctx->ps_grid) {
-    ctx->ps_grid = particle_step_grid<R>(g.P, g.Q, ctx->cfg.tma != 0, merge, block);
-    if (ctx->ps_grid <= 0) return fail(ctx, PIC_ECUDA, "particle step occupancy query failed");
-  }
-  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,
-                             ctx->stream));
-  if (mid) CK(cudaEventRecord(mid, ctx->stream));
+  return a;
+}
+
+// Arguments of the field update of parity p (constants in the working
+// precision computed here, on the host).
+template <typename R>
+FieldArgs<R> field_args(const pic_ctx *ctx, int p) {
+  const Geom &g = ctx->g;
   FieldArgs<R> f;
   f.g = g;
   f.F = (R *)ctx->F;
@@ -342,7 +340,25 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
   f.tau = ctx->cfg.laser_tau;
   f.t_peak = ctx->cfg.laser_t_peak;
   f.filter_passes = ctx->cfg.filter_passes;
-  CK(launch_fields<R>(f, ctx->stream));
+  return f;
+}
+
+// One step on the context's stream: the patch particle step, then the region
+// field update.  `mid` (optional) is recorded between the two phases.
+template <typename R>
+pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
+  const Geom &g = ctx->g;
+  const StepArgs<R> a = step_args<R>(ctx, parity);
+  const int block = ctx->cfg.block ? ctx->cfg.block : 256;
+  const bool merge = ctx->cfg.merge > 0;
+  if (!ctx->ps_grid) {
+    ctx->ps_grid = particle_step_grid<R>(g.P, g.Q, ctx->cfg.tma != 0, merge, block);
+    if (ctx->ps_grid <= 0) return fail(ctx, PIC_ECUDA, "particle step occupancy query failed");
+  }
+  CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,
+                             ctx->stream));
+  if (mid) CK(cudaEventRecord(mid, ctx->stream));
+  CK(launch_fields<R>(field_args<R>(ctx, parity), ctx->stream));
   return PIC_OK;
 }
 
@@ -831,12 +847,25 @@ pic_status do_get_field(pic_ctx *ctx, int which, double *dst, int where) {
     CK(launch_get_field_f64(g, src, d, ctx->stream));
   } else {
     int c = comp_of(which);
+    int filtered = -1;
     if (which >= PIC_JX && which <= PIC_JZ) {
       const int jset = (int)((ctx->step + 1) & 1);  // set of the last step
       c = C_JA + 3 * jset + (which - PIC_JX);
+      if (ctx->cfg.filter_passes > 0) {
+        // the field update used the filtered current, which the step does
+        // not keep: filter the deposited set again into the other set (zero
+        // between steps), read it, and clear it again
+        filtered = 1 - jset;
+        CK(launch_filter<R>(field_args<R>(ctx, jset), jset, filtered, ctx->stream));
+        c = C_JA + 3 * filtered + (which - PIC_JX);
+        ctx->launches += 1;
+      }
     }
     if (c < 0) return fail(ctx, PIC_EINVAL, "bad field id");
     CK(launch_get_field<R>(g, (const R *)ctx->F + c * g.cs, d, ctx->stream));
+    if (filtered >= 0)
+      CK(cudaMemsetAsync((R *)ctx->F + (C_JA + 3 * filtered) * g.cs, 0, 3 * g.cs * sizeof(R),
+                         ctx->stream));
   }
   ctx->launches += 1;
   if (where == PIC_HOST) {
@@ -955,6 +984,269 @@ size_t snapshot_bytes(const pic_ctx *c) {
   size_t b = sizeof(SnapHeader) + field_bytes(g, c->rs) + sizeof(double) * g.cs + sizeof(DevState);
   if (c->cap) b += particle_bytes(g, c->cap, c->rs);
   return b;
+}
+
+// ================================================================ batches
+//
+// A batch advances several independent contexts with one launch per kernel
+// per step: one plan over the flattened patch slots of every run, one
+// persistent particle step over the work items of every run (each item
+// names its run; the run's arguments come from a device array and its
+// tensor map from the launch's TmapSet parameter), then one launch per
+// field kernel whose blocks map to (run, block) through BatchGrid.  Every
+// run flips its step parity each step, so the device argument arrays are
+// built for two phases and the step of phase k uses set k.
+
+}  // namespace
+
+struct pic_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int use_graph = 1;
+  int task_chunk = 0;
+  std::vector<pic_ctx *> runs;
+  bool fp32 = false;
+  // state of the last build: membership, per-run capacity / storage / parity
+  bool dirty = true;
+  std::vector<int> cap_built;
+  std::vector<void *> seg_built;
+  std::vector<int> parity0;  // run parity at phase 0
+  int phase = 0;
+  // device arrays: step / field arguments per phase, plan
+  void *sargs[2] = {nullptr, nullptr};
+  void *fargs[2] = {nullptr, nullptr};
+  Plan plan{};
+  int *item_run = nullptr;
+  int plan_items_alloc = 0, plan_slots_alloc = 0;
+  BatchGrid slots{};
+  BatchGrid fgrid[4]{};
+  TmapSet<kBatchMax> *tm = nullptr;  // host copy: the launch parameter
+  int P = 0, Q = 0;                  // common patch shape, 0 when mixed
+  bool tma = true;
+  size_t smem = 0;
+  int grid = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaEvent_t ev = nullptr;
+  long long steps = 0, launches = 0, builds = 0;
+  std::string err;
+};
+
+namespace {
+
+pic_status bfail(pic_batch *b, pic_status s, const std::string &m) {
+  b->err = m;
+  return s;
+}
+
+#define BCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return bfail(b, PIC_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_));     \
+  } while (0)
+
+void batch_free_graphs(pic_batch *b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->gexec[p]) {
+      cudaGraphExecDestroy(b->gexec[p]);
+      b->gexec[p] = nullptr;
+    }
+}
+
+// True when a run changed since the last build (capacity regrown, storage
+// reallocated, or stepped alone so that its parity no longer follows the
+// batch's phase).
+bool batch_stale(const pic_batch *b) {
+  if (b->dirty) return true;
+  for (size_t r = 0; r < b->runs.size(); ++r) {
+    const pic_ctx *c = b->runs[r];
+    if (c->cap != b->cap_built[r] || c->seg[0][0] != b->seg_built[r]) return true;
+    if ((int)(c->step & 1) != (b->parity0[r] ^ b->phase)) return true;
+  }
+  return false;
+}
+
+template <typename R>
+pic_status batch_enqueue(pic_batch *b, int k) {
+  BatchRef<R> br;
+  br.args = (const StepArgs<R> *)b->sargs[k];
+  br.item_run = b->item_run;
+  br.slots = b->slots;
+  br.plan = b->plan;
+  BCK(launch_particle_step_batch<R>(br, b->tm, b->P, b->Q, b->tma, 256, b->grid, b->smem,
+                                    b->stream));
+  BCK(launch_fields_batch<R>((const FieldArgs<R> *)b->fargs[k], b->fgrid, b->stream));
+  return PIC_OK;
+}
+
+int batch_kernels_per_step(const pic_batch *b) {
+  int n = 4;  // plan, particle step, E, B
+  if (b->fgrid[0].off[b->fgrid[0].n] > 0) ++n;
+  if (b->fgrid[3].off[b->fgrid[3].n] > 0) ++n;
+  return n;
+}
+
+template <typename R>
+pic_status batch_build(pic_batch *b) {
+  const int n = (int)b->runs.size();
+  BCK(cudaStreamSynchronize(b->stream));  // argument arrays may be in use
+  batch_free_graphs(b);
+  b->cap_built.assign(n, 0);
+  b->seg_built.assign(n, nullptr);
+  b->parity0.assign(n, 0);
+  b->phase = 0;
+  b->P = b->runs[0]->g.P;
+  b->Q = b->runs[0]->g.Q;
+  b->tma = true;
+  b->smem = 0;
+  std::vector<StepArgs<R>> sa[2];
+  std::vector<FieldArgs<R>> fa[2];
+  BatchGrid slots{};
+  BatchGrid fg[4]{};
+  slots.n = n;
+  for (int k = 0; k < 4; ++k) fg[k].n = n;
+  long long max_items = 0;
+  const int chunk = std::max(1, b->task_chunk > 0 ? b->task_chunk : 2048);
+  for (int r = 0; r < n; ++r) {
+    pic_ctx *c = b->runs[r];
+    const Geom &g = c->g;
+    if (g.P != b->P || g.Q != b->Q) b->P = b->Q = 0;
+    if (!c->cfg.tma) b->tma = false;
+    b->smem = std::max(b->smem, particle_step_smem(g.P, g.Q, sizeof(R)));
+    const int p0 = (int)(c->step & 1);
+    b->parity0[r] = p0;
+    b->cap_built[r] = c->cap;
+    b->seg_built[r] = c->seg[0][0];
+    for (int k = 0; k < 2; ++k) {
+      sa[k].push_back(step_args<R>(c, p0 ^ k));
+      fa[k].push_back(field_args<R>(c, p0 ^ k));
+    }
+    slots.off[r + 1] = slots.off[r] + g.nslots;
+    int gx[4], gy[4];
+    field_batch_blocks(g, c->cfg.filter_passes, gx, gy);
+    for (int k = 0; k < 4; ++k) {
+      fg[k].gx[r] = std::max(gx[k], 1);
+      fg[k].off[r + 1] = fg[k].off[r] + gx[k] * gy[k];
+    }
+    const long long units_max = (long long)c->cap + c->bk.stride + 9;
+    max_items += (long long)g.nslots * ((units_max + chunk - 1) / chunk);
+  }
+  if (b->tma) {
+    for (int r = 0; r < n; ++r) {
+      pic_ctx *c = b->runs[r];
+      if (!c->tmap_ok) {
+        pic_status s = build_tmap<R>(c);
+        if (s) return bfail(b, s, c->err);
+      }
+      b->tm->m[r] = c->tmap;
+    }
+  }
+  if (max_items > (1ll << 30)) return bfail(b, PIC_EINVAL, "batch too large");
+  // plan storage: grows, never shrinks
+  if (max_items > b->plan_items_alloc || slots.off[n] > b->plan_slots_alloc) {
+    cudaFree(b->plan.item_slot);
+    cudaFree(b->plan.item_first);
+    cudaFree(b->plan.units);
+    cudaFree(b->item_run);
+    b->plan_items_alloc = (int)std::max<long long>(max_items, b->plan_items_alloc);
+    b->plan_slots_alloc = std::max(slots.off[n], b->plan_slots_alloc);
+    BCK(cudaMalloc(&b->plan.item_slot, sizeof(int) * b->plan_items_alloc));
+    BCK(cudaMalloc(&b->plan.item_first, sizeof(int) * b->plan_items_alloc));
+    BCK(cudaMalloc(&b->item_run, sizeof(int) * b->plan_items_alloc));
+    BCK(cudaMalloc(&b->plan.units, sizeof(int) * b->plan_slots_alloc));
+  }
+  b->plan.unit = 1;
+  b->plan.chunk = chunk;
+  b->plan.max_items = (int)max_items;
+  b->slots = slots;
+  for (int k = 0; k < 4; ++k) b->fgrid[k] = fg[k];
+  for (int k = 0; k < 2; ++k) {
+    BCK(cudaMemcpy(b->sargs[k], sa[k].data(), sizeof(StepArgs<R>) * n, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->fargs[k], fa[k].data(), sizeof(FieldArgs<R>) * n, cudaMemcpyHostToDevice));
+  }
+  BCK(prepare_particle_step_batch<R>(b->P, b->Q, b->smem));
+  b->grid = particle_step_batch_grid<R>(b->P, b->Q, b->tma, 256, b->smem);
+  if (b->grid <= 0) return bfail(b, PIC_ECUDA, "particle step occupancy query failed");
+  if (b->use_graph) {
+    for (int k = 0; k < 2; ++k) {
+      cudaGraph_t gr;
+      BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      pic_status s = batch_enqueue<R>(b, k);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+      if (s != PIC_OK) return s;
+      BCK(e);
+      e = cudaGraphInstantiate(&b->gexec[k], gr, 0);
+      cudaGraphDestroy(gr);
+      BCK(e);
+    }
+  }
+  b->dirty = false;
+  b->builds += 1;
+  return PIC_OK;
+}
+
+// Make `waiter` wait for the work queued so far on `on`.
+pic_status order_after(pic_batch *b, cudaStream_t waiter, cudaStream_t on) {
+  if (waiter == on) return PIC_OK;
+  BCK(cudaEventRecord(b->ev, on));
+  BCK(cudaStreamWaitEvent(waiter, b->ev, 0));
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status batch_step(pic_batch *b, int nsteps) {
+  if (batch_stale(b)) {
+    pic_status s = batch_build<R>(b);
+    if (s) return s;
+  }
+  for (pic_ctx *c : b->runs) {
+    pic_status s = order_after(b, b->stream, c->stream);
+    if (s) return s;
+  }
+  pic_status rs = PIC_OK;
+  for (int it = 0; it < nsteps && rs == PIC_OK; ++it) {
+    const int k = b->phase;
+    if (b->use_graph) BCK(cudaGraphLaunch(b->gexec[k], b->stream));
+    else rs = batch_enqueue<R>(b, k);
+    b->launches += batch_kernels_per_step(b);
+    b->steps += 1;
+    b->phase ^= 1;
+    for (pic_ctx *c : b->runs) {
+      c->step += 1;
+      c->t += c->g.dt;
+      c->prev_valid = true;
+      c->ps_launches += 1;
+      if (rs == PIC_OK && window_due(c)) {
+        // the shift runs on the batch's stream, between batched steps
+        cudaStream_t own = c->stream;
+        c->stream = b->stream;
+        rs = window_shift<R>(c);
+        c->stream = own;
+        if (rs) rs = bfail(b, rs, c->err);
+        b->launches += 7;
+      }
+    }
+  }
+  BCK(cudaStreamSynchronize(b->stream));
+  // per-run device faults: sticky on the run, which leaves the batch
+  pic_status first = rs;
+  std::vector<pic_ctx *> keep;
+  for (pic_ctx *c : b->runs) {
+    pic_status s = order_after(b, c->stream, b->stream);
+    if (s) return s;
+    s = poll_device(c);
+    if (s == PIC_OK) {
+      keep.push_back(c);
+    } else if (first == PIC_OK) {
+      first = bfail(b, s, c->err);
+    }
+  }
+  if (keep.size() != b->runs.size()) {
+    b->runs = keep;
+    b->dirty = true;
+  }
+  return first;
 }
 
 }  // namespace
@@ -1240,6 +1532,107 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   ctx->sticky = PIC_OK;
   ctx->err.clear();
   return PIC_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+pic_status pic_batch_create(const pic_batch_config *cfg, pic_batch **out) {
+  if (!out || !cfg) return PIC_EINVAL;
+  *out = nullptr;
+  if (cfg->task_chunk < 0) return PIC_EINVAL;
+  pic_batch *b = new (std::nothrow) pic_batch();
+  if (!b) return PIC_ENOMEM;
+  b->device = cfg->device;
+  b->use_graph = cfg->use_graph;
+  b->task_chunk = cfg->task_chunk;
+  auto bail = [&](pic_status s) {
+    pic_batch_destroy(b);
+    return s;
+  };
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(PIC_ECUDA);
+  if (cfg->stream) {
+    b->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(PIC_ECUDA);
+    b->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) return bail(PIC_ECUDA);
+  const size_t sa = std::max(sizeof(StepArgs<double>), sizeof(StepArgs<float>));
+  const size_t fa = std::max(sizeof(FieldArgs<double>), sizeof(FieldArgs<float>));
+  for (int k = 0; k < 2; ++k) {
+    if (cudaMalloc(&b->sargs[k], sa * kBatchMax) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cudaMalloc(&b->fargs[k], fa * kBatchMax) != cudaSuccess) return bail(PIC_ENOMEM);
+  }
+  if (cudaMalloc(&b->plan.n_items, sizeof(int) * 2) != cudaSuccess) return bail(PIC_ENOMEM);
+  b->plan.next = b->plan.n_items + 1;
+  b->tm = new (std::nothrow) TmapSet<kBatchMax>();
+  if (!b->tm) return bail(PIC_ENOMEM);
+  *out = b;
+  return PIC_OK;
+}
+
+pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n) {
+  if (!b) return PIC_EINVAL;
+  if (n < 0 || n > kBatchMax || (n && !runs)) return bfail(b, PIC_EINVAL, "bad run count");
+  for (int r = 0; r < n; ++r) {
+    const pic_ctx *c = runs[r];
+    if (!c) return bfail(b, PIC_EINVAL, "null run");
+    for (int q = 0; q < r; ++q)
+      if (runs[q] == c) return bfail(b, PIC_EINVAL, "a run appears twice");
+    if (c->sticky != PIC_OK) return bfail(b, PIC_ESTATE, "a run holds a device fault");
+    if (!c->cap) return bfail(b, PIC_ESTATE, "a run has no particles loaded");
+    if (c->cfg.device != b->device) return bfail(b, PIC_EINVAL, "a run lives on another device");
+    if (c->fp32 != runs[0]->fp32) return bfail(b, PIC_EINVAL, "runs of one batch share a precision");
+  }
+  b->runs.assign(runs, runs + n);
+  b->fp32 = n ? runs[0]->fp32 : false;
+  b->dirty = true;
+  return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch *b, int nsteps) {
+  if (!b) return PIC_EINVAL;
+  if (nsteps < 0) return bfail(b, PIC_EINVAL, "negative step count");
+  if (nsteps == 0 || b->runs.empty()) return PIC_OK;
+  for (pic_ctx *c : b->runs)
+    if (c->sticky != PIC_OK || !c->cap)
+      return bfail(b, PIC_ESTATE, "a run holds a device fault or lost its particles");
+  BCK(cudaSetDevice(b->device));
+  return b->fp32 ? batch_step<float>(b, nsteps) : batch_step<double>(b, nsteps);
+}
+
+int pic_batch_size(const pic_batch *b) { return b ? (int)b->runs.size() : 0; }
+
+pic_status pic_batch_get_diag(const pic_batch *b, pic_batch_diag_t *out) {
+  if (!b || !out) return PIC_EINVAL;
+  out->steps = b->steps;
+  out->launches = b->launches;
+  out->builds = b->builds;
+  out->nruns = (int)b->runs.size();
+  out->grid = b->grid;
+  return PIC_OK;
+}
+
+const char *pic_batch_last_error(const pic_batch *b) { return b ? b->err.c_str() : "no batch"; }
+
+void pic_batch_destroy(pic_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free_graphs(b);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(b->sargs[k]);
+    cudaFree(b->fargs[k]);
+  }
+  cudaFree(b->plan.n_items);
+  cudaFree(b->plan.item_slot);
+  cudaFree(b->plan.item_first);
+  cudaFree(b->plan.units);
+  cudaFree(b->item_run);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b->tm;
+  delete b;
 }
 
 }  // extern "C"

@@ -245,6 +245,46 @@ cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, 
 // Blocks of the particle step resident on the device at once.
 template <typename R>
 int particle_step_grid(int P, int Q, bool tma, bool merge, int block);
+
+// ---- batches: several independent runs advanced by one launch per kernel.
+// Runs per batch; the tensor maps of a batch travel as one kernel parameter
+// (128 B each), the per-run argument structs live in device arrays.
+constexpr int kBatchMax = 64;
+template <int N>
+struct TmapSet {
+  CUtensorMap m[N];
+};
+// Linear block index -> (run, block x, block y) of a batched 2D launch:
+// run r owns blocks [off[r], off[r + 1]) laid out gx[r] per row.
+struct BatchGrid {
+  int n;
+  int off[kBatchMax + 1];
+  int gx[kBatchMax];
+};
+__host__ __device__ inline int batch_run(const int *off, int n, int b) {
+  int lo = 0, hi = n;  // last r with off[r] <= b
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+template <typename R>
+struct BatchRef {
+  const StepArgs<R> *args;  // [n] this step's arguments of each run
+  int *item_run;            // [max_items] run of each work item
+  BatchGrid slots;          // run r owns flattened slots [off[r], off[r + 1])
+  Plan plan;                // the batch's plan (units indexed by flat slot)
+};
+// Batched plan + persistent particle step over every run of `b`.
+template <typename R>
+cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatchMax> *tm,
+                                       int P, int Q, bool tma, int block, int grid,
+                                       size_t smem, cudaStream_t s);
+template <typename R>
+int particle_step_batch_grid(int P, int Q, bool tma, int block, size_t smem);
+template <typename R>
+cudaError_t prepare_particle_step_batch(int P, int Q, size_t smem);
 // Raise the dynamic shared-memory limit of the step kernels (call outside
 // stream capture).
 template <typename R>
@@ -269,6 +309,17 @@ struct FieldArgs {
 };
 template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s);
+// The binomial filter alone (a.filter_passes passes): current set src -> dst.
+template <typename R>
+cudaError_t launch_filter(const FieldArgs<R> &a, int src, int dst, cudaStream_t s);
+// Field update of every run of a batch: `fa` holds each run's arguments,
+// grid[k] maps the blocks of the filter (k = 0), E (1), B (2) and
+// Silver-Mueller (3) kernels to runs; kernels with no block are skipped.
+template <typename R>
+cudaError_t launch_fields_batch(const FieldArgs<R> *fa, const BatchGrid grid[4], cudaStream_t s);
+// Blocks per run of the batched field kernels (gx, gy for k = 0..2; the
+// Silver-Mueller kernel is 1D: gx blocks, gy = 1).
+void field_batch_blocks(const Geom &g, int filter_passes, int gx[4], int gy[4]);
 
 // Field I/O and utilities.
 template <typename R>

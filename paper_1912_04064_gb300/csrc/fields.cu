@@ -40,10 +40,10 @@ __device__ __forceinline__ bool block_mirrors(const Geom &g, int i0, int i1, int
 // E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}); one cell per thread so
 // that every thread issues its loads at once.
 template <typename R>
-__global__ void __launch_bounds__(YBX * YBY) k_update_E(const FieldArgs<R> a) {
+__device__ __forceinline__ void update_E(const FieldArgs<R> &a, int blk_x, int blk_y) {
   const Geom &g = a.g;
   const Ranges rg = ranges(g);
-  const int i0 = blockIdx.x * YBX, j0 = blockIdx.y * YBY;
+  const int i0 = blk_x * YBX, j0 = blk_y * YBY;
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   const bool mir = block_mirrors(g, i0, i0 + YBX, j0, j0 + YBY);
   if (i >= rg.nxp || j >= rg.nyp) return;
@@ -81,16 +81,16 @@ __global__ void __launch_bounds__(YBX * YBY) k_update_E(const FieldArgs<R> a) {
 // B^{n+3/2}) / 2 (= B at stored cells that are not updated), and the
 // current set of the next step cleared.  Covers every stored column and row.
 template <typename R>
-__global__ void __launch_bounds__(YBX * YBY) k_update_B(const FieldArgs<R> a) {
+__device__ __forceinline__ void update_B(const FieldArgs<R> &a, int blk_x, int blk_y) {
   const Geom &g = a.g;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+  if (blk_x == 0 && blk_y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     const int p = a.parity;
     a.st->t[1 - p] = a.st->t[p] + g.dt;
     a.st->step[1 - p] = a.st->step[p] + 1;
     a.st->maxcnt[1 - p] = 0;  // the next particle step starts a new maximum
   }
   const Ranges rg = ranges(g);
-  const int i0 = (int)(blockIdx.x * YBX) - GX, j0 = (int)(blockIdx.y * YBY) - GY;
+  const int i0 = blk_x * YBX - GX, j0 = blk_y * YBY - GY;
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   const bool mir = block_mirrors(g, i0, i0 + YBX, j0, j0 + YBY);
   if (i >= g.nx + GX || j >= g.ny + GY) return;
@@ -176,9 +176,8 @@ __device__ __forceinline__ void set_ghost(const Geom &g, R *B, R *Bm, int i, int
 // profile is a precomputed array, the temporal factor is evaluated once per
 // block at t_{n+3/2} (retarded by the window's displacement).
 template <typename R>
-__global__ void k_silver_mueller(const FieldArgs<R> a) {
+__device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, double &s_h) {
   const Geom &g = a.g;
-  __shared__ double s_h;
   if (threadIdx.x == 0) {
     double h = 0.0;
     if (a.laser_on) {
@@ -189,7 +188,7 @@ __global__ void k_silver_mueller(const FieldArgs<R> a) {
     s_h = h;
   }
   __syncthreads();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = bx * blockDim.x + threadIdx.x;
   R *F = a.F;
   const long long cs = g.cs;
   const R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
@@ -246,14 +245,14 @@ __global__ void k_silver_mueller(const FieldArgs<R> a) {
 // deposit never reaches the outer two stored layers, so this equals the
 // pass-by-pass definition).
 template <typename R, int NP>
-__global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R> a, int src,
-                                                              int dst) {
+__device__ __forceinline__ void filter_current(const FieldArgs<R> &a, int src, int dst, int bx,
+                                               int by) {
   const Geom &g = a.g;
   const bool px = g.fbc_x == FBC_PERIODIC, py = g.fbc_y == FBC_PERIODIC;
   const int ilo = px ? 0 : -GX, jlo = py ? 0 : -GY;
   const int ihi = px ? g.nx : g.nx + GX, jhi = py ? g.ny : g.ny + GY;
-  const int i = ilo + (int)(blockIdx.x * YBX + threadIdx.x);
-  const int j = jlo + (int)(blockIdx.y * YBY + threadIdx.y);
+  const int i = ilo + bx * YBX + (int)threadIdx.x;
+  const int j = jlo + by * YBY + (int)threadIdx.y;
   if (i >= ihi || j >= jhi) return;
   constexpr int W = 2 * NP + 1;
   const R c1[3] = {R(0.25), R(0.5), R(0.25)};
@@ -288,6 +287,67 @@ __global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R>
     }
     a.F[(C_JA + 3 * dst + c) * g.cs + o] = acc;
   }
+}
+
+// Single-run kernels: one 2D grid per kernel.
+template <typename R>
+__global__ void __launch_bounds__(YBX * YBY) k_update_E(const FieldArgs<R> a) {
+  update_E(a, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void __launch_bounds__(YBX * YBY) k_update_B(const FieldArgs<R> a) {
+  update_B(a, blockIdx.x, blockIdx.y);
+}
+template <typename R>
+__global__ void k_silver_mueller(const FieldArgs<R> a) {
+  __shared__ double s_h;
+  silver_mueller(a, blockIdx.x, s_h);
+}
+template <typename R, int NP>
+__global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R> a, int src,
+                                                              int dst) {
+  filter_current<R, NP>(a, src, dst, blockIdx.x, blockIdx.y);
+}
+
+// Batched kernels: a 1D grid over the blocks of every run (BatchGrid); each
+// block reads its run's arguments and works as the block (bx, by) of that
+// run's own grid.
+__device__ __forceinline__ int batch_block(const BatchGrid &bg, int &bx, int &by) {
+  const int b = blockIdx.x;
+  const int r = batch_run(bg.off, bg.n, b);
+  const int k = b - bg.off[r];
+  by = k / bg.gx[r];
+  bx = k - by * bg.gx[r];
+  return r;
+}
+template <typename R>
+__global__ void __launch_bounds__(YBX * YBY) k_update_E_batch(const FieldArgs<R> *fa,
+                                                              const BatchGrid bg) {
+  int bx, by;
+  const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
+  update_E(a, bx, by);
+}
+template <typename R>
+__global__ void __launch_bounds__(YBX * YBY) k_update_B_batch(const FieldArgs<R> *fa,
+                                                              const BatchGrid bg) {
+  int bx, by;
+  const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
+  update_B(a, bx, by);
+}
+template <typename R>
+__global__ void k_silver_mueller_batch(const FieldArgs<R> *fa, const BatchGrid bg) {
+  __shared__ double s_h;
+  int bx, by;
+  const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
+  silver_mueller(a, bx, s_h);
+}
+template <typename R>
+__global__ void __launch_bounds__(YBX * YBY) k_filter_current_batch(const FieldArgs<R> *fa,
+                                                                    const BatchGrid bg) {
+  int bx, by;
+  const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
+  if (a.filter_passes == 1) filter_current<R, 1>(a, a.parity, 1 - a.parity, bx, by);
+  else filter_current<R, 2>(a, a.parity, 1 - a.parity, bx, by);
 }
 
 // ---------------------------------------------------------------- I/O ----
@@ -414,18 +474,29 @@ __global__ void k_gauss(const Geom g, const R *F, int jset, const double *rho,
 }  // namespace
 
 template <typename R>
+cudaError_t launch_filter(const FieldArgs<R> &a, int src, int dst, cudaStream_t s) {
+  const Geom &g = a.g;
+  const dim3 blk(YBX, YBY);
+  const int fw = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
+  const int fh = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
+  const dim3 fgrid((fw + YBX - 1) / YBX, (fh + YBY - 1) / YBY);
+  if (a.filter_passes == 1)
+    k_filter_current<R, 1><<<fgrid, blk, 0, s>>>(a, src, dst);
+  else if (a.filter_passes == 2)
+    k_filter_current<R, 2><<<fgrid, blk, 0, s>>>(a, src, dst);
+  return cudaGetLastError();
+}
+template cudaError_t launch_filter<float>(const FieldArgs<float> &, int, int, cudaStream_t);
+template cudaError_t launch_filter<double>(const FieldArgs<double> &, int, int, cudaStream_t);
+
+template <typename R>
 cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   const Geom &g = a.g;
   const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
   const dim3 blk(YBX, YBY);
   if (a.filter_passes > 0) {
-    const int fw = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
-    const int fh = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
-    const dim3 fgrid((fw + YBX - 1) / YBX, (fh + YBY - 1) / YBY);
-    if (a.filter_passes == 1)
-      k_filter_current<R, 1><<<fgrid, blk, 0, s>>>(a, a.parity, 1 - a.parity);
-    else
-      k_filter_current<R, 2><<<fgrid, blk, 0, s>>>(a, a.parity, 1 - a.parity);
+    const cudaError_t e = launch_filter(a, a.parity, 1 - a.parity, s);
+    if (e != cudaSuccess) return e;
   }
   k_update_E<R><<<dim3((nxp + YBX - 1) / YBX, (nyp + YBY - 1) / YBY), blk, 0, s>>>(a);
   const int ncol = g.nx + 2 * GX, nrow = g.ny + 2 * GY;
@@ -436,6 +507,42 @@ cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   }
   return cudaGetLastError();
 }
+
+void field_batch_blocks(const Geom &g, int filter_passes, int gx[4], int gy[4]) {
+  const int nxp = g.nx + (g.fbc_x == FBC_SM), nyp = g.ny + (g.fbc_y == FBC_SM);
+  gx[0] = gy[0] = 0;
+  if (filter_passes > 0) {
+    const int fw = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
+    const int fh = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
+    gx[0] = (fw + YBX - 1) / YBX;
+    gy[0] = (fh + YBY - 1) / YBY;
+  }
+  gx[1] = (nxp + YBX - 1) / YBX;
+  gy[1] = (nyp + YBY - 1) / YBY;
+  gx[2] = (g.nx + 2 * GX + YBX - 1) / YBX;
+  gy[2] = (g.ny + 2 * GY + YBY - 1) / YBY;
+  gx[3] = gy[3] = 0;
+  if (g.fbc_x == FBC_SM || g.fbc_y == FBC_SM) {
+    gx[3] = ((g.nx > g.ny ? g.nx : g.ny) + 1 + 63) / 64;
+    gy[3] = 1;
+  }
+}
+
+template <typename R>
+cudaError_t launch_fields_batch(const FieldArgs<R> *fa, const BatchGrid grid[4], cudaStream_t s) {
+  const dim3 blk(YBX, YBY);
+  if (grid[0].off[grid[0].n] > 0)
+    k_filter_current_batch<R><<<grid[0].off[grid[0].n], blk, 0, s>>>(fa, grid[0]);
+  k_update_E_batch<R><<<grid[1].off[grid[1].n], blk, 0, s>>>(fa, grid[1]);
+  k_update_B_batch<R><<<grid[2].off[grid[2].n], blk, 0, s>>>(fa, grid[2]);
+  if (grid[3].off[grid[3].n] > 0)
+    k_silver_mueller_batch<R><<<grid[3].off[grid[3].n], 64, 0, s>>>(fa, grid[3]);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fields_batch<float>(const FieldArgs<float> *, const BatchGrid[4],
+                                                cudaStream_t);
+template cudaError_t launch_fields_batch<double>(const FieldArgs<double> *, const BatchGrid[4],
+                                                 cudaStream_t);
 
 template <typename R>
 cudaError_t launch_set_field(const Geom &g, R *arr, const double *src, cudaStream_t s) {

@@ -152,10 +152,13 @@ __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<
 
 // Particle step kernel.  PT, QT: patch size known at compile time (0 =
 // runtime).  MERGE: consecutive particles of a thread that share a window
-// are summed in registers before one set of shared atomics.
-template <typename R, int PT, int QT, bool TMA, bool MERGE>
+// are summed in registers before one set of shared atomics.  BATCH: the
+// work items of several independent runs in one launch; each item names its
+// run, whose arguments and tensor map are read from device arrays.
+template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
-    k_particle_step(const __grid_constant__ CUtensorMap tmap, const StepArgs<R> a) {
+    k_particle_step(const __grid_constant__ TmapSet<BATCH ? kBatchMax : 1> tm,
+                    const StepArgs<R> a0, const BatchRef<R> br) {
   // MERGE: M = 16 / sizeof(R) consecutive particles per thread, one 128-bit
   // load per array; otherwise one particle per thread per slice, lanes on
   // consecutive particles (coalesced 32/64-bit loads), which keeps the 32
@@ -172,39 +175,52 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
   __shared__ long long s_base[9];
   __shared__ int s_item;
   __shared__ int s_ok;
+  // BATCH: the current item's run arguments, copied from the device array
+  __shared__ __align__(16) StepArgs<R> s_args[1];
 
-  const Geom &g = a.g;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int P = PT ? PT : g.P, Q = QT ? QT : g.Q;
-  const int BX = BXc ? BXc : P + 8, BY = BYc ? BYc : Q + 3;  // field tile
-  const int JW = JWc ? JWc : P + 5, JH = JHc ? JHc : Q + 5;  // current tile
-  const int FT = BY * BX, JT = JH * JW;
   const uint32_t pad = (128u - (smem_u32(dsm_raw) & 127u)) & 127u;
-  R *Ft = reinterpret_cast<R *>(dsm_raw + pad);
-  R *Jt = Ft + 6 * FT;
-  const R rdx = a.rdx, rdy = a.rdy, eps = a.eps;
-  const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
-  const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
   const int lane = tid & 31;
-  const int col0 = a.st->col0;
-  const int n_items = *a.plan.n_items;
-  unsigned err = 0;
+  const Plan &plan = BATCH ? br.plan : a0.plan;
+  const int n_items = *plan.n_items;
   uint32_t phase = 0;
   if (TMA && tid == 0) {
     mbar_init(&mbar, 1);
     fence_mbar_init();
   }
 
-  // Persistent loop over work items: (patch slot, chunk of its particles),
-  // heaviest patches first, fetched from a global counter.
+  // Persistent loop over work items: (run, patch slot, chunk of its
+  // particles), heaviest patches first, fetched from a global counter.
   for (;;) {
     __syncthreads();  // the previous item is done with the tiles
-    if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
+    if (tid == 0) s_item = atomicAdd(plan.next, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= n_items) break;
-    const int s = a.plan.item_slot[item];
-    const int ufirst = a.plan.item_first[item];
+    const int run = BATCH ? br.item_run[item] : 0;
+    if (BATCH) {
+      constexpr int NW = sizeof(StepArgs<R>) / 4;
+      const int *src = reinterpret_cast<const int *>(br.args + run);
+      int *dst = reinterpret_cast<int *>(s_args);
+      for (int e = tid; e < NW; e += nth) dst[e] = src[e];
+      __syncthreads();
+    }
+    const StepArgs<R> &a = BATCH ? s_args[0] : a0;
+    const CUtensorMap *tmap = &tm.m[BATCH ? run : 0];
+    const Geom &g = a.g;
+    const int P = PT ? PT : g.P, Q = QT ? QT : g.Q;
+    const int BX = BXc ? BXc : P + 8, BY = BYc ? BYc : Q + 3;  // field tile
+    const int JW = JWc ? JWc : P + 5, JH = JHc ? JHc : Q + 5;  // current tile
+    const int FT = BY * BX, JT = JH * JW;
+    R *Ft = reinterpret_cast<R *>(dsm_raw + pad);
+    R *Jt = Ft + 6 * FT;
+    const R rdx = a.rdx, rdy = a.rdy, eps = a.eps;
+    const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
+    const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
+    const int col0 = a.st->col0;
+    unsigned err = 0;
+    const int s = plan.item_slot[item];
+    const int ufirst = plan.item_first[item];
     const int sxs = s % g.npx, sy = s / g.npx;
     int px = sxs - col0;
     if (px < 0) px += g.npx;
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     if (TMA) {
       if (tid == 0) {
         mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
-        tma_load_3d(Ft, &tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
+        tma_load_3d(Ft, tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
       }
     } else {
       for (int e = tid; e < 6 * FT; e += nth) {
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     phase ^= 1u;
     __syncthreads();
     if (!s_ok) break;
-    const int totalq = min(ufirst + a.plan.chunk, s_qoff[9]);
+    const int totalq = min(ufirst + plan.chunk, s_qoff[9]);
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -495,36 +511,41 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
       }
     }
     if (tid == 0) atomicMax(&a.st->maxcnt[a.parity], atomicAdd(&a.cnt_out[s], 0));
+    if (err) atomicOr(&a.st->err, err);
   }
-  if (err) atomicOr(&a.st->err, err);
 }
 
 // Plan of one step: units per slot (segment plus incoming buckets, counts
 // clamped to the capacities), items per slot, items ordered by decreasing
 // item count of their slot (classes of one item count, heaviest first);
-// the output counts of the step are cleared here.
+// the output counts of the step are cleared here.  BATCH: the slots of all
+// runs, flattened (run r owns flat slots [br.slots.off[r], off[r + 1])).
 constexpr int PLAN_CLASSES = 64;
 
-__global__ void __launch_bounds__(1024) k_plan(const Geom g, const int *cnt_in,
-                                               const int *bcnt_in, int cap, Buckets bk,
-                                               Plan plan, int *cnt_out, int *bcnt_out,
-                                               const DevState *st) {
+template <typename R, bool BATCH>
+__global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const BatchRef<R> br) {
   __shared__ int hist[PLAN_CLASSES], off[PLAN_CLASSES];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int col0 = st->col0, u = plan.unit;
+  const Plan &plan = BATCH ? br.plan : a0.plan;
+  const int u = plan.unit;
+  const int nflat = BATCH ? br.slots.off[br.slots.n] : a0.g.nslots;
   for (int c = tid; c < PLAN_CLASSES; c += nth) hist[c] = 0;
   __syncthreads();
-  for (int s = tid; s < g.nslots; s += nth) {
-    int units = (min(cnt_in[s], cap) + u - 1) / u;
+  for (int f = tid; f < nflat; f += nth) {
+    const int run = BATCH ? batch_run(br.slots.off, br.slots.n, f) : 0;
+    const StepArgs<R> &a = BATCH ? br.args[run] : a0;
+    const int s = BATCH ? f - br.slots.off[run] : f;
+    const int col0 = a.st->col0;
+    int units = (min(a.cnt_in[s], a.cap) + u - 1) / u;
     for (int d = 0; d < 8; ++d) {
       int ddx, ddy;
       dir_delta(d, ddx, ddy);
-      const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
-      if (src >= 0) units += (min(bcnt_in[(long long)src * 8 + d], bk.cap[d]) + u - 1) / u;
+      const int src = neighbour_slot(a.g, col0, s, -ddx, -ddy);
+      if (src >= 0) units += (min(a.bcnt_in[(long long)src * 8 + d], a.bk.cap[d]) + u - 1) / u;
     }
-    plan.units[s] = units;
-    cnt_out[s] = 0;
-    for (int d = 0; d < 8; ++d) bcnt_out[(long long)s * 8 + d] = 0;
+    plan.units[f] = units;
+    a.cnt_out[s] = 0;
+    for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
     const int items = (units + plan.chunk - 1) / plan.chunk;
     if (items) atomicAdd(&hist[min(items, PLAN_CLASSES) - 1], items);
   }
@@ -539,36 +560,42 @@ __global__ void __launch_bounds__(1024) k_plan(const Geom g, const int *cnt_in,
     *plan.next = 0;
   }
   __syncthreads();
-  for (int s = tid; s < g.nslots; s += nth) {
-    const int items = (plan.units[s] + plan.chunk - 1) / plan.chunk;
+  for (int f = tid; f < nflat; f += nth) {
+    const int items = (plan.units[f] + plan.chunk - 1) / plan.chunk;
     if (!items) continue;
+    const int run = BATCH ? batch_run(br.slots.off, br.slots.n, f) : 0;
+    const int s = BATCH ? f - br.slots.off[run] : f;
     const int base = atomicAdd(&off[min(items, PLAN_CLASSES) - 1], items);
     for (int k = 0; k < items && base + k < plan.max_items; ++k) {
       plan.item_slot[base + k] = s;
       plan.item_first[base + k] = k * plan.chunk;
+      if (BATCH) br.item_run[base + k] = run;
     }
   }
 }
 
-template <typename R, int PT, int QT, bool TMA, bool MERGE>
+template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH>
 const void *kernel_ptr() {
-  return (const void *)k_particle_step<R, PT, QT, TMA, MERGE>;
+  return (const void *)k_particle_step<R, PT, QT, TMA, MERGE, BATCH>;
 }
 
 // Kernel for a patch shape: compile-time tile sizes for the common square
 // patches, a runtime-size kernel otherwise; plain loads always runtime-size.
-template <typename R, bool MERGE>
+// Batched launches (runs may differ in patch size) use runtime sizes unless
+// every run shares the patch shape.
+template <typename R, bool MERGE, bool BATCH>
 const void *pick(int P, int Q, bool tma) {
-  if (!tma) return kernel_ptr<R, 0, 0, false, MERGE>();
-  if (P == 32 && Q == 32) return kernel_ptr<R, 32, 32, true, MERGE>();
-  if (P == 16 && Q == 16) return kernel_ptr<R, 16, 16, true, MERGE>();
-  if (P == 8 && Q == 8) return kernel_ptr<R, 8, 8, true, MERGE>();
-  return kernel_ptr<R, 0, 0, true, MERGE>();
+  if (!tma) return kernel_ptr<R, 0, 0, false, MERGE, BATCH>();
+  if (P == 32 && Q == 32) return kernel_ptr<R, 32, 32, true, MERGE, BATCH>();
+  if (P == 16 && Q == 16) return kernel_ptr<R, 16, 16, true, MERGE, BATCH>();
+  if (P == 8 && Q == 8) return kernel_ptr<R, 8, 8, true, MERGE, BATCH>();
+  return kernel_ptr<R, 0, 0, true, MERGE, BATCH>();
 }
 
 template <typename R>
-const void *pick_kernel(int P, int Q, bool tma, bool merge) {
-  return merge ? pick<R, true>(P, Q, tma) : pick<R, false>(P, Q, tma);
+const void *pick_kernel(int P, int Q, bool tma, bool merge, bool batch = false) {
+  if (batch) return pick<R, false, true>(P, Q, tma);  // batches: one particle per thread
+  return merge ? pick<R, true, false>(P, Q, tma) : pick<R, false, false>(P, Q, tma);
 }
 
 }  // namespace
@@ -590,36 +617,81 @@ cudaError_t prepare_particle_step(int P, int Q) {
 }
 
 template <typename R>
-int particle_step_grid(int P, int Q, bool tma, bool merge, int block) {
-  const int smem = (int)particle_step_smem(P, Q, sizeof(R));
+cudaError_t prepare_particle_step_batch(int P, int Q, size_t smem) {
+  for (int t = 0; t < 2; ++t) {
+    cudaError_t e = cudaFuncSetAttribute(pick_kernel<R>(P, Q, t != 0, false, true),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+namespace {
+int resident_grid(const void *k, int block, size_t smem) {
   int per_sm = 0, dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel<R>(P, Q, tma, merge),
-                                                    block, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess)
     return 0;
   return per_sm * nsm;
+}
+}  // namespace
+
+template <typename R>
+int particle_step_grid(int P, int Q, bool tma, bool merge, int block) {
+  return resident_grid(pick_kernel<R>(P, Q, tma, merge), block,
+                       particle_step_smem(P, Q, sizeof(R)));
+}
+
+template <typename R>
+int particle_step_batch_grid(int P, int Q, bool tma, int block, size_t smem) {
+  return resident_grid(pick_kernel<R>(P, Q, tma, false, true), block, smem);
 }
 
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
                                  bool merge, int block, int grid, cudaStream_t s) {
-  k_plan<<<1, 1024, 0, s>>>(a.g, a.cnt_in, a.bcnt_in, a.cap, a.bk, a.plan, a.cnt_out,
-                            a.bcnt_out, a.st);
+  BatchRef<R> none{};
+  k_plan<R, false><<<1, 1024, 0, s>>>(a, none);
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
   const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge);
-  void *args[] = {(void *)tmap, (void *)&a};
+  TmapSet<1> tm;
+  tm.m[0] = *tmap;
+  void *args[] = {(void *)&tm, (void *)&a, (void *)&none};
+  return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
+}
+
+// P, Q: the runs' common patch shape (0 when they differ: runtime sizes);
+// smem: the largest tile footprint of the runs.
+template <typename R>
+cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatchMax> *tm,
+                                       int P, int Q, bool tma, int block, int grid,
+                                       size_t smem, cudaStream_t s) {
+  StepArgs<R> none{};
+  k_plan<R, true><<<1, 1024, 0, s>>>(none, b);
+  const void *k = pick_kernel<R>(P, Q, tma, false, true);
+  void *args[] = {(void *)tm, (void *)&none, (void *)&b};
   return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
 }
 
 template int particle_step_grid<float>(int, int, bool, bool, int);
 template int particle_step_grid<double>(int, int, bool, bool, int);
+template int particle_step_batch_grid<float>(int, int, bool, int, size_t);
+template int particle_step_batch_grid<double>(int, int, bool, int, size_t);
 template cudaError_t prepare_particle_step<float>(int, int);
 template cudaError_t prepare_particle_step<double>(int, int);
+template cudaError_t prepare_particle_step_batch<float>(int, int, size_t);
+template cudaError_t prepare_particle_step_batch<double>(int, int, size_t);
 template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const CUtensorMap *,
                                                  bool, bool, int, int, cudaStream_t);
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
                                                   const CUtensorMap *, bool, bool, int, int,
                                                   cudaStream_t);
+template cudaError_t launch_particle_step_batch<float>(const BatchRef<float> &,
+                                                       const TmapSet<kBatchMax> *, int, int,
+                                                       bool, int, int, size_t, cudaStream_t);
+template cudaError_t launch_particle_step_batch<double>(const BatchRef<double> &,
+                                                        const TmapSet<kBatchMax> *, int, int,
+                                                        bool, int, int, size_t, cudaStream_t);
 
 }  // namespace pic

@@ -60,10 +60,26 @@ class pic_diag_t(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pic_batch_config(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int),
+                ("task_chunk", C.c_int)]
+
+
+class pic_batch_diag_t(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("launches", C.c_longlong), ("builds", C.c_longlong),
+                ("nruns", C.c_int), ("grid", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PIC_BATCH_MAX = 64
+
 EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_background", "pic_step",
            "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync", "pic_snapshot",
            "pic_restore", "pic_footprint", "pic_last_error", "pic_destroy", "pic_version",
-           "pic_field_energy_noalloc"]
+           "pic_field_energy_noalloc", "pic_batch_create", "pic_batch_set", "pic_batch_step",
+           "pic_batch_size", "pic_batch_get_diag", "pic_batch_last_error", "pic_batch_destroy"]
 
 _lib = None
 
@@ -96,9 +112,19 @@ def lib():
         L.pic_version.restype = C.c_char_p
         L.pic_field_energy_noalloc.argtypes = [vp] * 6 + [C.c_int, C.c_int, C.c_double, vp, vp]
         L.pic_field_energy_noalloc.restype = C.c_int
+        L.pic_batch_create.argtypes = [C.POINTER(pic_batch_config), C.POINTER(C.c_void_p)]
+        L.pic_batch_set.argtypes = [vp, C.POINTER(C.c_void_p), C.c_int]
+        L.pic_batch_step.argtypes = [vp, C.c_int]
+        L.pic_batch_size.argtypes = [vp]
+        L.pic_batch_get_diag.argtypes = [vp, C.POINTER(pic_batch_diag_t)]
+        L.pic_batch_last_error.argtypes = [vp]
+        L.pic_batch_last_error.restype = C.c_char_p
+        L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_destroy.restype = None
         for name in ("pic_create", "pic_load_particles", "pic_set_field", "pic_set_background",
                      "pic_step", "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync",
-                     "pic_snapshot", "pic_restore"):
+                     "pic_snapshot", "pic_restore", "pic_batch_create", "pic_batch_set",
+                     "pic_batch_step", "pic_batch_size", "pic_batch_get_diag"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -268,3 +294,47 @@ class Pic:
 
     def last_error(self) -> str:
         return lib().pic_last_error(self.h).decode() if self.h else ""
+
+
+class Batch:
+    """A batch of contexts advanced together (pic_batch_* calls)."""
+
+    def __init__(self, stream=None, device: int = 0, use_graph: bool = True, task_chunk: int = 0):
+        cfg = pic_batch_config(stream, device, int(use_graph), int(task_chunk))
+        self.h = C.c_void_p()
+        self.runs = []
+        rc = lib().pic_batch_create(C.byref(cfg), C.byref(self.h))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_batch_create failed")
+
+    def _check(self, rc):
+        if rc != PIC_OK:
+            raise PicError(rc, lib().pic_batch_last_error(self.h).decode())
+
+    def pic_batch_set(self, runs):
+        arr = (C.c_void_p * max(len(runs), 1))(*[r.h.value for r in runs])
+        self._check(lib().pic_batch_set(self.h, arr, len(runs)))
+        self.runs = list(runs)
+
+    def pic_batch_step(self, n: int = 1):
+        self._check(lib().pic_batch_step(self.h, int(n)))
+
+    def pic_batch_size(self) -> int:
+        return lib().pic_batch_size(self.h)
+
+    def pic_batch_get_diag(self) -> dict:
+        d = pic_batch_diag_t()
+        self._check(lib().pic_batch_get_diag(self.h, C.byref(d)))
+        return d.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().pic_batch_destroy(self.h)
+            self.h = C.c_void_p()
+            self.runs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

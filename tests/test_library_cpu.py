@@ -49,14 +49,18 @@ def test_struct_layout_matches_header(tmp_path):
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_config),"
         " sizeof(pic_diag_t), offsetof(pic_config, stream), offsetof(pic_config, block),"
         " offsetof(pic_config, inj_ppc), offsetof(pic_diag_t, ms_particles),"
-        " offsetof(pic_diag_t, particle_step_launches));return 0;}\n")
+        " offsetof(pic_diag_t, particle_step_launches));"
+        "printf(\"%zu %zu %zu %zu\\n\", sizeof(pic_batch_config), offsetof(pic_batch_config, task_chunk),"
+        " sizeof(pic_batch_diag_t), offsetof(pic_batch_diag_t, grid));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     want = [C.sizeof(pic.pic_config), C.sizeof(pic.pic_diag_t), pic.pic_config.stream.offset,
             pic.pic_config.block.offset, pic.pic_config.inj_ppc.offset,
-            pic.pic_diag_t.ms_particles.offset, pic.pic_diag_t.particle_step_launches.offset]
+            pic.pic_diag_t.ms_particles.offset, pic.pic_diag_t.particle_step_launches.offset,
+            C.sizeof(pic.pic_batch_config), pic.pic_batch_config.task_chunk.offset,
+            C.sizeof(pic.pic_batch_diag_t), pic.pic_batch_diag_t.grid.offset]
     assert got == want
 
 
@@ -118,6 +122,13 @@ def test_null_arguments(libpic):
     assert libpic.pic_sync(None) == pic.PIC_EINVAL
     assert b"no context" in libpic.pic_last_error(None)
     libpic.pic_destroy(None)
+    assert libpic.pic_batch_create(None, None) == pic.PIC_EINVAL
+    assert libpic.pic_batch_set(None, None, 0) == pic.PIC_EINVAL
+    assert libpic.pic_batch_step(None, 1) == pic.PIC_EINVAL
+    assert libpic.pic_batch_size(None) == 0
+    assert libpic.pic_batch_get_diag(None, None) == pic.PIC_EINVAL
+    assert b"no batch" in libpic.pic_batch_last_error(None)
+    libpic.pic_batch_destroy(None)
 
 
 def test_create_without_gpu_fails_loudly(libpic):
