@@ -167,6 +167,16 @@ pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y,
                               const double *uz, const double *w, size_t n,
                               int where);
 
+/* Fill the domain, on the device, with the configuration's plasma profile
+ * (inj_n0, inj_x0, inj_ramp, inj_ppc: the profile the moving window
+ * injects): inj_ppc[0] x inj_ppc[1] particles per cell at rest, regularly
+ * placed, weight = density at the particle's x / particles per cell; the
+ * charge of the co-located immobile ions is added to the background.  Only
+ * before any particles are loaded (PIC_ESTATE otherwise); sizes the patch
+ * capacity like the first pic_load_particles (a full patch x
+ * capacity_factor). */
+pic_status pic_load_plasma(pic_ctx *ctx);
+
 /* Overwrite one field component (PIC_EX..PIC_BMZ or PIC_RHO_BG) from an
  * array in the layout above.  B is taken at t + dt/2, Bm at t. */
 pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where);
@@ -259,6 +269,99 @@ int pic_batch_size(const pic_batch *b);
 pic_status pic_batch_get_diag(const pic_batch *b, pic_batch_diag_t *out);
 const char *pic_batch_last_error(const pic_batch *b);
 void pic_batch_destroy(pic_batch *b);
+
+/* ---- Autotuner ---------------------------------------------------------
+ * Chooses the launch shape of a workload by timing: square patch sizes
+ * {8, 16, 32} (only the configured patch size when the moving window is on,
+ * since the window advances by one patch column), particle-step blocks of
+ * {128, 256} threads and work items of {1024, 2048, 4096} particles, plus the
+ * configuration as given.  Each candidate is a fresh context loaded with the
+ * caller's particles (float64, PIC_HOST or PIC_DEVICE), stepped 2 steps to
+ * warm up and then `steps` steps, timed on the host around pic_step (which
+ * synchronises); the fastest wins.  The choice changes only the rounding
+ * order of the current sums, never the method.  Results are cached per
+ * process by (grid, boundaries, laser, window, filter, precision, particles
+ * per cell); a cached key returns without timing (candidates = 0).
+ * On success *tuned is cfg with patch, block and task_chunk replaced. */
+typedef struct pic_tune_t {
+  int patch[3];        /* chosen patch size */
+  int block;           /* chosen particle-step block size */
+  int task_chunk;      /* chosen particles per work item */
+  double ms_per_step;  /* its measured time per step */
+  double ms_given;     /* time per step of the configuration as given */
+  int candidates;      /* candidates timed (0: taken from the cache) */
+} pic_tune_t;
+pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
+                        const double *ux, const double *uy, const double *uz,
+                        const double *w, size_t n, int where, int steps,
+                        pic_config *tuned, pic_tune_t *out);
+void pic_autotune_clear_cache(void);
+
+/* ---- Serving ------------------------------------------------------------
+ * A request loop over many PIC runs with continuous batching.  A request is
+ * a configuration plus its initial plasma (the configuration's injection
+ * profile, filled on the device by pic_load_plasma, with its ions as the
+ * background) and a step count.  Each pic_server_tick:
+ *  1. admits queued requests in arrival order while the run slots
+ *     (max_runs) and the device-memory budget (the sum of the admitted runs'
+ *     pic_footprint estimates) allow; an admitted run's state stays
+ *     resident until it completes;
+ *  2. advances every admitted run by k = min(steps_per_tick, the fewest
+ *     steps any of them has left) batched steps (pic_batch_*: one launch per
+ *     kernel for all runs, whatever their grid sizes);
+ *  3. retires the runs that reached their step count (final diagnostics
+ *     recorded; the context destroyed, or kept for pic_server_take).
+ * A request that arrives while others run joins at the next tick in which
+ * a slot and memory are free.  Times are seconds on the server's clock
+ * (pic_server_clock).  FP32 and FP64 requests may be mixed: the server
+ * keeps one batch per precision and steps both in every tick.  Not
+ * thread-safe: one host thread drives a server. */
+typedef struct pic_server pic_server;
+typedef struct pic_server_config {
+  void *stream;          /* cudaStream_t of the batches; NULL = library-owned */
+  int device;
+  size_t hbm_budget;     /* bytes the admitted runs may hold; 0 = 90% of the
+                            device memory free at creation */
+  int max_runs;          /* runs admitted at once (1..PIC_BATCH_MAX; 0 = max) */
+  int steps_per_tick;    /* batched steps per tick at most (0 = 10) */
+  int use_graph;         /* batches replay captured CUDA graphs */
+} pic_server_config;
+enum { PIC_REQ_QUEUED = 0, PIC_REQ_RUNNING = 1, PIC_REQ_DONE = 2, PIC_REQ_FAILED = 3 };
+typedef struct pic_request_info {
+  int state;             /* PIC_REQ_* */
+  int status;            /* pic_status of a failed request */
+  long long steps_done, steps_total;
+  long long np0;         /* particles at admission */
+  long long np;          /* particles at completion */
+  size_t footprint;      /* admission estimate (pic_footprint) */
+  double t_submit, t_admit, t_done;  /* server clock, seconds */
+  double U_E, U_B, U_K;  /* diagnostics at completion */
+} pic_request_info;
+typedef struct pic_server_stats {
+  long long submitted, done, failed, queued, running;
+  long long ticks, batched_steps;
+  double particle_steps; /* sum over runs of particles at admission x steps */
+  size_t hbm_in_use;     /* footprint estimates of the runs held */
+  double busy_s;         /* time spent inside pic_server_tick */
+} pic_server_stats;
+
+pic_status pic_server_create(const pic_server_config *cfg, pic_server **out);
+/* Queue a request (cfg is copied; plasma from cfg's inj_* fields, which
+ * must give at least one particle per cell); *id receives its handle.
+ * keep = 1: the finished context is kept for pic_server_take.  The
+ * configuration is validated here (PIC_EINVAL). */
+pic_status pic_server_submit(pic_server *s, const pic_config *cfg, long long nsteps, int keep,
+                             long long *id);
+/* Admit, step, retire (see above); *running (optional) receives the runs
+ * on the device after the tick. */
+pic_status pic_server_tick(pic_server *s, int *running);
+pic_status pic_server_info(const pic_server *s, long long id, pic_request_info *out);
+/* Hand a finished, kept run's context to the caller, who destroys it
+ * (before the server: the context runs on the server's stream). */
+pic_status pic_server_take(pic_server *s, long long id, pic_ctx **out);
+pic_status pic_server_get_stats(const pic_server *s, pic_server_stats *out);
+double pic_server_clock(const pic_server *s);
+void pic_server_destroy(pic_server *s);
 
 /* Library version string. */
 const char *pic_version(void);

@@ -731,6 +731,34 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   return poll_device(ctx);
 }
 
+// Initial plasma filled on the device (the moving window's injection profile
+// over every patch column); capacity sized like the first load.
+template <typename R>
+pic_status do_fill(pic_ctx *ctx) {
+  const Geom &g = ctx->g;
+  const pic_config &c = ctx->cfg;
+  const int total = g.P * g.Q * c.inj_ppc[0] * c.inj_ppc[1];
+  const double cf = c.capacity_factor > 0 ? c.capacity_factor : 2.0;
+  const int cmin = c.capacity_min > 0 ? c.capacity_min : 256;
+  int cap = std::max(cmin, (int)std::ceil(cf * total));
+  cap = (cap + 31) / 32 * 32;
+  pic_status rs = alloc_particles<R>(ctx, cap);
+  if (rs) return rs;
+  const int q = (int)(ctx->step & 1);
+  CK(launch_fill_plasma<R>(g, ctx->col0, ctx->nshift, soa<R>(ctx->seg[q]), ctx->cnt[q], ctx->cap,
+                           c.inj_n0, c.inj_x0, c.inj_ramp, c.inj_ppc[0], c.inj_ppc[1],
+                           ctx->rho_bg, &ctx->st->err, ctx->stream));
+  ctx->launches += 1;
+  if (c.sort_every > 0) {
+    pic_status ss = sort_particles<R>(ctx);
+    if (ss) return ss;
+    ctx->since_sort = 0;
+  }
+  ctx->prev_valid = false;
+  free_graphs(ctx);
+  return poll_device(ctx);
+}
+
 template <typename R>
 pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, int where) {
   const Geom &g = ctx->g;
@@ -1358,6 +1386,16 @@ pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y, co
   CK(cudaSetDevice(ctx->cfg.device));
   return ctx->fp32 ? do_load<float>(ctx, x, y, ux, uy, uz, w, n, where)
                    : do_load<double>(ctx, x, y, ux, uy, uz, w, n, where);
+}
+
+pic_status pic_load_plasma(pic_ctx *ctx) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (ctx->cap) return fail(ctx, PIC_ESTATE, "particles are already loaded");
+  if (ctx->cfg.inj_ppc[0] < 1 || ctx->cfg.inj_ppc[1] < 1 || !(ctx->cfg.inj_n0 >= 0))
+    return fail(ctx, PIC_EINVAL, "plasma needs inj_ppc >= 1 and inj_n0 >= 0");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return ctx->fp32 ? do_fill<float>(ctx) : do_fill<double>(ctx);
 }
 
 pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where) {

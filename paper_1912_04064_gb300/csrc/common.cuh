@@ -390,5 +390,11 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
                                     int *cnt, SoA<R> bkt, int *bcnt, int cap, Buckets bk,
                                     double n0, double x0, double ramp, int ppcx, int ppcy,
                                     double *rho_bg, unsigned *err, cudaStream_t s);
+// Initial plasma of a run: every patch filled as the window fills its new
+// column (the same placement, weights and ion background).
+template <typename R>
+cudaError_t launch_fill_plasma(const Geom &g, int col0, int nshift, SoA<R> seg, int *cnt, int cap,
+                               double n0, double x0, double ramp, int ppcx, int ppcy,
+                               double *rho_bg, unsigned *err, cudaStream_t s);
 
 }  // namespace pic

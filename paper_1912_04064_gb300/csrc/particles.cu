@@ -249,15 +249,19 @@ __global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, S
   }
 }
 
-// Moving window, part 2 (new ring): the leaving slots now hold the new
-// column (physical npx - 1); fill them with plasma at rest, regularly placed,
-// weight = density / ppc at the particle's x in the laboratory frame, and add
-// the co-located immobile ions to the background charge.
+// Plasma at rest, regularly placed (ppcx x ppcy per cell), weight =
+// density / ppc at the particle's x in the laboratory frame, with the
+// co-located immobile ions added to the background charge.  Block (py, c)
+// fills physical patch column phys0 + c, held by slot column
+// (slot_col0 + c) mod npx.  Moving window, part 2: after the ring advanced,
+// the leaving slots (slot_col0 = old col0) hold the new column
+// (phys0 = npx - 1); loading a run's initial plasma fills every column.
 template <typename R>
-__global__ void k_window_inject(const Geom g, int slot_col, int nshift, SoA<R> seg, int *cnt,
-                                int cap, double n0, double x0, double ramp, int ppcx, int ppcy,
-                                double *rho_bg, unsigned *err) {
+__global__ void k_window_inject(const Geom g, int slot_col0, int phys0, int nshift, SoA<R> seg,
+                                int *cnt, int cap, double n0, double x0, double ramp, int ppcx,
+                                int ppcy, double *rho_bg, unsigned *err) {
   const int py = blockIdx.x;
+  const int slot_col = (slot_col0 + (int)blockIdx.y) % g.npx;
   const int slot = py * g.npx + slot_col;
   const int ppc = ppcx * ppcy;
   const int total = g.P * g.Q * ppc;
@@ -265,7 +269,7 @@ __global__ void k_window_inject(const Geom g, int slot_col, int nshift, SoA<R> s
     if (threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW_SEG);
     return;
   }
-  const int X0 = (g.npx - 1) * g.P, Y0 = py * g.Q;
+  const int X0 = (phys0 + (int)blockIdx.y) * g.P, Y0 = py * g.Q;
   const double shift = __dmul_rn((double)nshift * g.P, g.dx);
   for (int k = threadIdx.x; k < total; k += blockDim.x) {
     // order: cell row, cell column, sub-row, sub-column
@@ -550,8 +554,17 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
                                     double n0, double x0, double ramp, int ppcx, int ppcy,
                                     double *rho_bg, unsigned *err, cudaStream_t s) {
   k_window_migrate<R><<<g.npy, 256, 0, s>>>(g, old_col0, seg, cnt, bkt, bcnt, cap, bk, err);
-  k_window_inject<R><<<g.npy, 256, 0, s>>>(g, old_col0, nshift, seg, cnt, cap, n0, x0, ramp,
-                                            ppcx, ppcy, rho_bg, err);
+  k_window_inject<R><<<g.npy, 256, 0, s>>>(g, old_col0, g.npx - 1, nshift, seg, cnt, cap, n0,
+                                            x0, ramp, ppcx, ppcy, rho_bg, err);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_fill_plasma(const Geom &g, int col0, int nshift, SoA<R> seg, int *cnt, int cap,
+                               double n0, double x0, double ramp, int ppcx, int ppcy,
+                               double *rho_bg, unsigned *err, cudaStream_t s) {
+  k_window_inject<R><<<dim3(g.npy, g.npx), 256, 0, s>>>(g, col0, 0, nshift, seg, cnt, cap, n0,
+                                                         x0, ramp, ppcx, ppcy, rho_bg, err);
   return cudaGetLastError();
 }
 
@@ -578,7 +591,10 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
   template cudaError_t launch_window_particles<R>(const Geom &, int, int, SoA<R>, int *,      \
                                                   SoA<R>, int *, int, Buckets, double, double, \
                                                   double, int, int, double *, unsigned *,     \
-                                                  cudaStream_t);
+                                                  cudaStream_t);                              \
+  template cudaError_t launch_fill_plasma<R>(const Geom &, int, int, SoA<R>, int *, int, double, \
+                                             double, double, int, int, double *, unsigned *,  \
+                                             cudaStream_t);
 PIC_INST(float)
 PIC_INST(double)
 #undef PIC_INST

@@ -60,6 +60,11 @@ class pic_diag_t(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pic_tune_t(C.Structure):
+    _fields_ = [("patch", C.c_int * 3), ("block", C.c_int), ("task_chunk", C.c_int),
+                ("ms_per_step", C.c_double), ("ms_given", C.c_double), ("candidates", C.c_int)]
+
+
 class pic_batch_config(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int),
                 ("task_chunk", C.c_int)]
@@ -74,12 +79,42 @@ class pic_batch_diag_t(C.Structure):
 
 
 PIC_BATCH_MAX = 64
+PIC_REQ_QUEUED, PIC_REQ_RUNNING, PIC_REQ_DONE, PIC_REQ_FAILED = range(4)
+
+
+class pic_server_config(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("device", C.c_int), ("hbm_budget", C.c_size_t),
+                ("max_runs", C.c_int), ("steps_per_tick", C.c_int), ("use_graph", C.c_int)]
+
+
+class pic_request_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("steps_done", C.c_longlong),
+                ("steps_total", C.c_longlong), ("np0", C.c_longlong), ("np", C.c_longlong),
+                ("footprint", C.c_size_t), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("U_E", C.c_double), ("U_B", C.c_double),
+                ("U_K", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class pic_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("done", C.c_longlong), ("failed", C.c_longlong),
+                ("queued", C.c_longlong), ("running", C.c_longlong), ("ticks", C.c_longlong),
+                ("batched_steps", C.c_longlong), ("particle_steps", C.c_double),
+                ("hbm_in_use", C.c_size_t), ("busy_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_background", "pic_step",
            "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync", "pic_snapshot",
            "pic_restore", "pic_footprint", "pic_last_error", "pic_destroy", "pic_version",
            "pic_field_energy_noalloc", "pic_batch_create", "pic_batch_set", "pic_batch_step",
-           "pic_batch_size", "pic_batch_get_diag", "pic_batch_last_error", "pic_batch_destroy"]
+           "pic_batch_size", "pic_batch_get_diag", "pic_batch_last_error", "pic_batch_destroy",
+           "pic_load_plasma", "pic_autotune", "pic_autotune_clear_cache", "pic_server_create",
+           "pic_server_submit", "pic_server_tick", "pic_server_info", "pic_server_take",
+           "pic_server_get_stats", "pic_server_clock", "pic_server_destroy"]
 
 _lib = None
 
@@ -112,6 +147,21 @@ def lib():
         L.pic_version.restype = C.c_char_p
         L.pic_field_energy_noalloc.argtypes = [vp] * 6 + [C.c_int, C.c_int, C.c_double, vp, vp]
         L.pic_field_energy_noalloc.restype = C.c_int
+        L.pic_load_plasma.argtypes = [vp]
+        L.pic_autotune.argtypes = ([C.POINTER(pic_config)] + [dp] * 6 +
+                                   [sz, C.c_int, C.c_int, C.POINTER(pic_config), C.POINTER(pic_tune_t)])
+        L.pic_autotune_clear_cache.restype = None
+        L.pic_server_create.argtypes = [C.POINTER(pic_server_config), C.POINTER(C.c_void_p)]
+        L.pic_server_submit.argtypes = [vp, C.POINTER(pic_config), C.c_longlong, C.c_int,
+                                        C.POINTER(C.c_longlong)]
+        L.pic_server_tick.argtypes = [vp, C.POINTER(C.c_int)]
+        L.pic_server_info.argtypes = [vp, C.c_longlong, C.POINTER(pic_request_info)]
+        L.pic_server_take.argtypes = [vp, C.c_longlong, C.POINTER(C.c_void_p)]
+        L.pic_server_get_stats.argtypes = [vp, C.POINTER(pic_server_stats)]
+        L.pic_server_clock.argtypes = [vp]
+        L.pic_server_clock.restype = C.c_double
+        L.pic_server_destroy.argtypes = [vp]
+        L.pic_server_destroy.restype = None
         L.pic_batch_create.argtypes = [C.POINTER(pic_batch_config), C.POINTER(C.c_void_p)]
         L.pic_batch_set.argtypes = [vp, C.POINTER(C.c_void_p), C.c_int]
         L.pic_batch_step.argtypes = [vp, C.c_int]
@@ -124,7 +174,9 @@ def lib():
         for name in ("pic_create", "pic_load_particles", "pic_set_field", "pic_set_background",
                      "pic_step", "pic_get_field", "pic_get_particles", "pic_diag", "pic_sync",
                      "pic_snapshot", "pic_restore", "pic_batch_create", "pic_batch_set",
-                     "pic_batch_step", "pic_batch_size", "pic_batch_get_diag"):
+                     "pic_batch_step", "pic_batch_size", "pic_batch_get_diag", "pic_load_plasma",
+                     "pic_autotune", "pic_server_create", "pic_server_submit", "pic_server_tick",
+                     "pic_server_info", "pic_server_take", "pic_server_get_stats"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -213,6 +265,16 @@ class Pic:
         nx, ny = cfg.n[0], cfg.n[1]
         self.shape = (ny if cfg.bc_field[1] == 0 else ny + 2, nx if cfg.bc_field[0] == 0 else nx + 2)
 
+    @classmethod
+    def adopt(cls, h, cfg: pic_config) -> "Pic":
+        """Wrap a context created elsewhere (e.g. handed over by a server)."""
+        self = cls.__new__(cls)
+        self.cfg = cfg
+        self.h = h
+        nx, ny = cfg.n[0], cfg.n[1]
+        self.shape = (ny if cfg.bc_field[1] == 0 else ny + 2, nx if cfg.bc_field[0] == 0 else nx + 2)
+        return self
+
     def _check(self, rc, create=False):
         if rc != PIC_OK:
             msg = "" if create or not self.h else lib().pic_last_error(self.h).decode()
@@ -242,6 +304,10 @@ class Pic:
         where = ptrs[0][1]
         n = int(arrs[0].shape[0])
         self._check(lib().pic_load_particles(self.h, *[q for q, _ in ptrs], n, where))
+
+    def pic_load_plasma(self):
+        """Fill the domain with the configuration's plasma profile on the device."""
+        self._check(lib().pic_load_plasma(self.h))
 
     def pic_set_field(self, name: str, a):
         if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
@@ -296,6 +362,22 @@ class Pic:
         return lib().pic_last_error(self.h).decode() if self.h else ""
 
 
+def pic_autotune(cfg: pic_config, parts: dict, steps: int = 5):
+    """Time candidate launch shapes on `parts` (host float64 arrays); returns
+    (tuned pic_config, dict of the choice and timings)."""
+    arrs = [np.ascontiguousarray(parts[k], dtype=np.float64)
+            for k in ("x", "y", "ux", "uy", "uz", "w")]
+    tuned, res = pic_config(), pic_tune_t()
+    rc = lib().pic_autotune(C.byref(cfg), *[a.ctypes.data for a in arrs], int(arrs[0].size),
+                            PIC_HOST, int(steps), C.byref(tuned), C.byref(res))
+    if rc != PIC_OK:
+        raise PicError(rc, "pic_autotune failed")
+    info = {"patch": (res.patch[0], res.patch[1]), "block": res.block,
+            "task_chunk": res.task_chunk, "ms_per_step": res.ms_per_step,
+            "ms_given": res.ms_given, "candidates": res.candidates}
+    return tuned, info
+
+
 class Batch:
     """A batch of contexts advanced together (pic_batch_* calls)."""
 
@@ -332,6 +414,69 @@ class Batch:
             lib().pic_batch_destroy(self.h)
             self.h = C.c_void_p()
             self.runs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (pic_server_* calls)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, max_runs: int = 0,
+                 steps_per_tick: int = 0, use_graph: bool = True, stream=None):
+        cfg = pic_server_config(stream, device, int(hbm_budget), int(max_runs),
+                                int(steps_per_tick), int(use_graph))
+        self.h = C.c_void_p()
+        rc = lib().pic_server_create(C.byref(cfg), C.byref(self.h))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_server_create failed")
+
+    def pic_server_submit(self, cfg: pic_config, nsteps: int, keep: bool = False) -> int:
+        rid = C.c_longlong()
+        rc = lib().pic_server_submit(self.h, C.byref(cfg), int(nsteps), int(keep), C.byref(rid))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_server_submit rejected the request")
+        return rid.value
+
+    def pic_server_tick(self) -> int:
+        running = C.c_int()
+        rc = lib().pic_server_tick(self.h, C.byref(running))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_server_tick failed")
+        return running.value
+
+    def pic_server_info(self, rid: int) -> dict:
+        info = pic_request_info()
+        rc = lib().pic_server_info(self.h, int(rid), C.byref(info))
+        if rc != PIC_OK:
+            raise PicError(rc, "unknown request")
+        return info.as_dict()
+
+    def pic_server_take(self, rid: int, cfg: pic_config) -> "Pic":
+        """The finished context of a kept request, wrapped as a Pic."""
+        h = C.c_void_p()
+        rc = lib().pic_server_take(self.h, int(rid), C.byref(h))
+        if rc != PIC_OK:
+            raise PicError(rc, "request not finished or not kept")
+        return Pic.adopt(h, cfg)
+
+    def pic_server_get_stats(self) -> dict:
+        st = pic_server_stats()
+        rc = lib().pic_server_get_stats(self.h, C.byref(st))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_server_get_stats failed")
+        return st.as_dict()
+
+    def pic_server_clock(self) -> float:
+        return lib().pic_server_clock(self.h)
+
+    def close(self):
+        if self.h:
+            lib().pic_server_destroy(self.h)
+            self.h = C.c_void_p()
 
     def __del__(self):
         try:

@@ -51,7 +51,11 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(pic_config, inj_ppc), offsetof(pic_diag_t, ms_particles),"
         " offsetof(pic_diag_t, particle_step_launches));"
         "printf(\"%zu %zu %zu %zu\\n\", sizeof(pic_batch_config), offsetof(pic_batch_config, task_chunk),"
-        " sizeof(pic_batch_diag_t), offsetof(pic_batch_diag_t, grid));return 0;}\n")
+        " sizeof(pic_batch_diag_t), offsetof(pic_batch_diag_t, grid));"
+        "printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_tune_t), offsetof(pic_tune_t, candidates),"
+        " sizeof(pic_server_config), offsetof(pic_server_config, use_graph),"
+        " sizeof(pic_request_info), offsetof(pic_request_info, t_done),"
+        " sizeof(pic_server_stats), offsetof(pic_server_stats, busy_s));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
@@ -60,7 +64,11 @@ def test_struct_layout_matches_header(tmp_path):
             pic.pic_config.block.offset, pic.pic_config.inj_ppc.offset,
             pic.pic_diag_t.ms_particles.offset, pic.pic_diag_t.particle_step_launches.offset,
             C.sizeof(pic.pic_batch_config), pic.pic_batch_config.task_chunk.offset,
-            C.sizeof(pic.pic_batch_diag_t), pic.pic_batch_diag_t.grid.offset]
+            C.sizeof(pic.pic_batch_diag_t), pic.pic_batch_diag_t.grid.offset,
+            C.sizeof(pic.pic_tune_t), pic.pic_tune_t.candidates.offset,
+            C.sizeof(pic.pic_server_config), pic.pic_server_config.use_graph.offset,
+            C.sizeof(pic.pic_request_info), pic.pic_request_info.t_done.offset,
+            C.sizeof(pic.pic_server_stats), pic.pic_server_stats.busy_s.offset]
     assert got == want
 
 
@@ -129,6 +137,18 @@ def test_null_arguments(libpic):
     assert libpic.pic_batch_get_diag(None, None) == pic.PIC_EINVAL
     assert b"no batch" in libpic.pic_batch_last_error(None)
     libpic.pic_batch_destroy(None)
+    assert libpic.pic_load_plasma(None) == pic.PIC_EINVAL
+    assert libpic.pic_autotune(None, None, None, None, None, None, None, 0, 0, 1, None,
+                               None) == pic.PIC_EINVAL
+    libpic.pic_autotune_clear_cache()
+    assert libpic.pic_server_create(None, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_submit(None, None, 1, 0, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_tick(None, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_info(None, 1, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_take(None, 1, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_get_stats(None, None) == pic.PIC_EINVAL
+    assert libpic.pic_server_clock(None) == 0.0
+    libpic.pic_server_destroy(None)
 
 
 def test_create_without_gpu_fails_loudly(libpic):
@@ -145,3 +165,7 @@ def test_create_without_gpu_fails_loudly(libpic):
     with pytest.raises(pic.PicError) as e:
         pic.Pic(pic.config_from_run(run, "fp64"))
     assert e.value.status == pic.PIC_ECUDA
+    for make in (pic.Batch, pic.Server):
+        with pytest.raises(pic.PicError) as e:
+            make()
+        assert e.value.status == pic.PIC_ECUDA
