@@ -18,6 +18,9 @@ One JSON line is printed on rank 0:
   e2e          the same metric through the C-ABI from host buffers:
                H2D of the initial particles, K steps, D2H of fields and
                particles inside the timed region
+  serving      the served ensemble (FP32 runs of four grid sizes, Poisson
+               arrivals at 70% of the measured capacity, continuous
+               batching): p50/p99 latency from arrival, throughput
   cpu_baseline the FP64 CPU oracle on a bounded sample of the workload
 `--impl reference` times the oracle alone (the reference arm).
 
@@ -229,6 +232,87 @@ def run_e2e(prec, steps, device):
             "seconds": t1 - t0, "steps": steps}
 
 
+def run_serving(device, seconds, seed=5, probe=16, load=0.7, cf=4.0, steps_per_tick=10):
+    """The served ensemble (FP32): first `probe` requests submitted at once
+    and run to completion give the service capacity (requests/s); then
+    requests arrive as a Poisson process at `load` x that capacity for
+    `seconds` and the server drains.  Latency = completion - arrival."""
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    def cfg_of(run):
+        return pic.config_from_run(run, "fp32", device=device, capacity_factor=cf)
+
+    srv = pic.Server(device=device, steps_per_tick=steps_per_tick)
+    # capacity probe
+    probe_reqs = W.served_requests(probe, seed)
+    t0 = srv.pic_server_clock()
+    ps0 = srv.pic_server_get_stats()["particle_steps"]
+    for run, steps, _ in probe_reqs:
+        srv.pic_server_submit(cfg_of(run), steps)
+    while True:
+        srv.pic_server_tick()
+        st = srv.pic_server_get_stats()
+        if st["done"] + st["failed"] >= probe:
+            break
+    t_probe = srv.pic_server_clock() - t0
+    cap_rps = probe / t_probe
+    cap_ps = (st["particle_steps"] - ps0) / t_probe
+    # Poisson arrivals at load x capacity
+    lam = load * cap_rps
+    rng = np.random.default_rng(seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * seconds * 3) + 10))
+    arrivals = arrivals[arrivals < seconds]
+    reqs = W.served_requests(arrivals.size, seed + 2)
+    ids = []
+    base_done = st["done"] + st["failed"]
+    ps1 = st["particle_steps"]
+    t_start = srv.pic_server_clock()
+    i = 0
+    running = []
+    while True:
+        now = srv.pic_server_clock() - t_start
+        while i < arrivals.size and arrivals[i] <= now:
+            run, steps, _ = reqs[i]
+            ids.append(srv.pic_server_submit(cfg_of(run), steps))
+            i += 1
+        st = srv.pic_server_get_stats()
+        if i == arrivals.size and st["done"] + st["failed"] - base_done >= arrivals.size:
+            break
+        if st["running"] == 0 and st["queued"] == 0:
+            time.sleep(max(0.0, min(arrivals[i] - now, 0.05)))
+            continue
+        running.append(srv.pic_server_tick())
+    t_end = srv.pic_server_clock() - t_start
+    lat, failed = [], 0
+    for k, rid in enumerate(ids):
+        info = srv.pic_server_info(rid)
+        if info["state"] != pic.PIC_REQ_DONE:
+            failed += 1
+            continue
+        lat.append(info["t_done"] - t_start - arrivals[k])
+    st = srv.pic_server_get_stats()
+    srv.close()
+    lat = np.array(lat)
+    return {
+        "workload": ("served ensemble, FP32: grids {256x256, 512x256, 1024x512, 2048x512} "
+                     "(32x32 patches), 1-8 ppc, 0.001-0.02 n_c uniform or ramped, laser a0 "
+                     "0.5-4 with moving window in half, 200-2000 steps; plasma filled on the "
+                     "device at admission; Poisson arrivals"),
+        "arrival_rate_per_s": lam, "load_vs_capacity": load,
+        "capacity_runs_per_s": cap_rps, "capacity_particle_steps_per_s": cap_ps,
+        "probe_requests": probe, "requests": int(arrivals.size), "failed": failed,
+        "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+        "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+        "mean_s": float(lat.mean()) if lat.size else None,
+        "throughput_particle_steps_per_s": (st["particle_steps"] - ps1) / t_end,
+        "runs_per_s": (lat.size) / t_end, "window_s": t_end,
+        "max_concurrent_runs": max(running) if running else 0,
+        "mean_concurrent_runs": float(np.mean(running)) if running else 0.0,
+        "steps_per_tick": steps_per_tick, "capacity_factor": cf,
+    }
+
+
 def cpu_oracle(steps, threads=0):
     """The FP64 CPU oracle on the same workload from its initial state."""
     from oracle.oracle import Oracle
@@ -269,6 +353,8 @@ def main():
                     help="deposit merging in registers: 1 on, 0 off, -1 library default")
     ap.add_argument("--capacity-factor", type=float, default=4.0,
                     help="patch capacity / fullest initial patch")
+    ap.add_argument("--serve-seconds", type=float, default=20.0,
+                    help="arrival window of the served-ensemble measurement (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -316,6 +402,7 @@ def main():
         r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
                       world, dist, args.capacity_factor, -1, args.sort_every, args.task_chunk)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
+    serving = run_serving(local, args.serve_seconds) if args.serve_seconds > 0 else None
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
         dist.barrier()
@@ -358,6 +445,8 @@ def main():
         line["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
         line["e2e"]["note"] = (f"C-ABI from pinned host buffers: H2D of the {r32['np0']} initial particles, "
                                f"{e2e['steps']} steps from t=0, D2H of E, B and all particles")
+    if serving:
+        line["serving"] = serving
     if cpu:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)

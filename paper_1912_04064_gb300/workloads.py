@@ -99,6 +99,18 @@ def lwfa_2d(n=(2048, 512), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2), n0=0.01,
     cold electrons on immobile ions with a linear density ramp, moving
     window at c, Silver-Mueller fields on every face, particles removed
     through the x faces and reflected at the y faces."""
+    run = lwfa_run(n, d, patch, ppc, n0, ramp, a0, waist, tau, t_mw, frac)
+    nx, ny = n
+    dx, dy = d
+    parts = regular_particles(nx, ny, dx, dy, ppc,
+                              lambda x: density_profile(x, n0, 0.0, ramp))
+    return run, parts
+
+
+def lwfa_run(n=(2048, 512), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2), n0=0.01,
+             ramp=200.0, a0=2.0, waist=20.0, tau=30.0, t_mw=None, frac=0.95):
+    """The run dictionary of lwfa_2d without its particles (the plasma is
+    the injection profile; a context can fill it on the device)."""
     nx, ny = n
     dx, dy = d
     Lx, Ly = nx * dx, ny * dy
@@ -112,9 +124,33 @@ def lwfa_2d(n=(2048, 512), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2), n0=0.01,
         "moving_window": {"t0": Lx / 2.0 if t_mw is None else t_mw},
         "injection": {"n0": n0, "x0": 0.0, "ramp": ramp, "ppc": tuple(ppc)},
     }
-    parts = regular_particles(nx, ny, dx, dy, ppc,
-                              lambda x: density_profile(x, n0, 0.0, ramp))
-    return run, parts
+    return run
+
+
+def served_requests(count, seed):
+    """Requests of the served ensemble: grid uniform over {256x256,
+    512x256, 1024x512, 2048x512} (dx = 0.125, dy = 0.5, 32x32 patches),
+    1-8 particles per cell, density 0.001-0.02 n_c uniform or ramped
+    (20-200 c/w0), a Gaussian laser (a0 0.5-4, with the moving window) in
+    half of them, 200-2000 steps.  Returns [(run, steps, particles)]."""
+    rng = np.random.default_rng(seed)
+    grids = [(256, 256), (512, 256), (1024, 512), (2048, 512)]
+    out = []
+    for _ in range(count):
+        nx, ny = grids[int(rng.integers(len(grids)))]
+        ppc_total = int(rng.integers(1, 9))
+        ppc = (2, ppc_total // 2) if ppc_total % 2 == 0 and ppc_total > 2 else (ppc_total, 1)
+        n0 = float(rng.uniform(0.001, 0.02))
+        ramp = 0.0 if rng.random() < 0.5 else float(rng.uniform(20.0, 200.0))
+        laser = rng.random() < 0.5
+        a0 = float(rng.uniform(0.5, 4.0))
+        steps = int(rng.integers(200, 2001))
+        run = lwfa_run(n=(nx, ny), ppc=ppc, n0=n0, ramp=ramp, a0=a0)
+        if not laser:
+            run["laser"] = None
+            run["moving_window"] = None
+        out.append((run, steps, nx * ny * ppc_total))
+    return out
 
 
 def random_fields(shape, seed, amp=0.05, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz",
