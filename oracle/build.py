@@ -8,11 +8,12 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, "pic_oracle.c")]
+SRC = [os.path.join(HERE, "pic_oracle.c"), os.path.join(HERE, "pic_oracle3d.c")]
 
 
 def build(force: bool = False) -> str:
-    newest = max(os.path.getmtime(p) for p in SRC + [os.path.join(HERE, "pic_oracle.h")])
+    newest = max(os.path.getmtime(p) for p in SRC + [os.path.join(HERE, "pic_oracle.h"),
+                                                      os.path.join(HERE, "pic_oracle3d.h")])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()

@@ -178,3 +178,56 @@ def field_shape(run):
     nx, ny = run["n"]
     fx, fy = run["field_bc"]
     return (ny if fy == "periodic" else ny + 2, nx if fx == "periodic" else nx + 2)
+
+
+# ------------------------------------------------------------------ 3D3V --
+
+def periodic_run3(n, d, patch, dt=None, frac=0.95):
+    """Fully periodic 3D3V run (fields and particles), electrons."""
+    return {"n": tuple(n), "d": tuple(d), "dt": dt if dt is not None else cfl_dt(d, frac),
+            "patch": tuple(patch), "field_bc": ("periodic",) * 3,
+            "part_bc": (("periodic", "periodic"),) * 3, "q": -1.0, "m": 1.0}
+
+
+def lwfa_3d(n=(1024, 256, 256), d=(0.125, 0.5, 0.5), patch=(16, 16, 16), ppc=(2, 1, 1),
+            n0=0.005, ramp=0.0, a0=3.0, waist=15.0, tau=30.0, t_mw=None, frac=0.95,
+            upper_half=True):
+    """3D3V LWFA-shaped run: y-polarised Gaussian laser through x_min,
+    cold electrons on immobile ions filling the upper half of the transverse
+    box (y >= Ly/2, all x and z) when upper_half, moving window at c,
+    Silver-Mueller on every face, particles removed through the x faces and
+    reflected at the y and z faces.  The plasma is the injection profile
+    (a context fills it on the device)."""
+    nx, ny, nz = n
+    dx, dy, dz = d
+    Lx, Ly, Lz = nx * dx, ny * dy, nz * dz
+    return {
+        "n": tuple(n), "d": tuple(d), "dt": cfl_dt(d, frac), "patch": tuple(patch),
+        "field_bc": ("sm", "sm", "sm"),
+        "part_bc": (("remove", "remove"), ("reflect", "reflect"), ("reflect", "reflect")),
+        "q": -1.0, "m": 1.0,
+        "laser": {"a0": a0, "waist": waist, "tau": tau, "t_peak": 2.0 * tau,
+                  "y_center": Ly / 2.0, "z_center": Lz / 2.0},
+        "moving_window": {"t0": Lx / 2.0 if t_mw is None else t_mw},
+        "injection": {"n0": n0, "x0": 0.0, "ramp": ramp, "ppc": tuple(ppc),
+                      "ymin": Ly / 2.0 if upper_half else 0.0},
+    }
+
+
+def field_shape3(run):
+    """(nz_e, ny_e, nx_e) of 3D field arrays: per axis n (periodic) or
+    n + 2 (open)."""
+    return tuple(run["n"][a] + (0 if run["field_bc"][a] == "periodic" else 2) for a in (2, 1, 0))
+
+
+def small_random_particles3(run, n, seed, uth=0.3):
+    """n particles uniformly over the 3D box, momenta N(0, uth^2)."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for a, k in enumerate(("x", "y", "z")):
+        L = run["n"][a] * run["d"][a]
+        out[k] = np.minimum(rng.random(n) * L, np.nextafter(L, 0))
+    u = rng.normal(0.0, uth, size=(3, n))
+    out["ux"], out["uy"], out["uz"] = u[0], u[1], u[2]
+    out["w"] = 0.5 + rng.random(n)
+    return out
