@@ -115,6 +115,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(name):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary profiles/<name>, if the kernel sources
+    it names still hash to the value recorded at capture time; else None."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
+        files = re.findall(r"`([^`]+)`", m.group(2))
+        h = hashlib.sha256()
+        for f in files:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if not h.hexdigest().startswith(m.group(1)):
+            return None
+        t = re.search(r"traffic = DRAM read \+ write per launch \| (\d+) bytes", text)
+        return int(t.group(1)) if t else None
+    except Exception:
+        return None
+
+
 def algorithmic_bytes(npart, ncell, rsize):
     """Bytes the method must move once per step: per particle read
     x, y, ux, uy, uz, w and write x, y, ux, uy, uz (11 words); per cell gather
@@ -427,7 +449,11 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "particle_step (TMA staging, gather, Boris, "
                                                 "Esirkepov, J reduction, re-binning)",
                      "achieved": k_gbs, "peak": hbm, "unit": "GB/s", "frac": k_gbs / hbm,
-                     "peak_source": src, "traffic": None,
+                     "peak_source": src,
+                     "traffic": profiled_traffic("particle_step_fp32_lwfa2048.md"),
+                     "traffic_source": "ncu capture of one launch at step 1005 "
+                                       "(profiles/particle_step_fp32_lwfa2048.md); null when "
+                                       "the kernel sources changed since",
                      "bytes_per_launch": r32["kernel_bytes"], "launch_ms": r32["particle_step_ms"],
                      "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
                                     "bytes_per_step": r32["step_bytes"]}},
