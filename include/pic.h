@@ -34,6 +34,10 @@
  * A component staggered (dual) along an axis has grid index i at (i + 1/2) d,
  * otherwise at i d (Yee lattice: Ex (1/2,0), Ey (0,1/2), Ez (0,0),
  * Bx (0,1/2), By (1/2,0), Bz (1/2,1/2); J like E; rho at nodes).
+ * 3D contexts (dims = 3) exchange (nz_e, ny_e, nx_e) arrays with the same
+ * per-axis rule on the 3D Yee lattice: Ex (1/2,0,0), Ey (0,1/2,0),
+ * Ez (0,0,1/2), Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0).  A 3D context
+ * has no current filter, snapshot, auto-grow replay or batch membership.
  */
 #ifndef PIC_H
 #define PIC_H
@@ -71,11 +75,14 @@ enum {
 enum { PIC_BG_NONE = 0, PIC_BG_UNIFORM = 1, PIC_BG_NEUTRALISING = 2 };
 
 typedef struct pic_config {
-  int dims;              /* 2 (2D3V) */
+  int dims;              /* 2 (2D3V) or 3 (3D3V) */
   int n[3];              /* cells per axis; n[i] % patch[i] == 0 */
   double d[3];           /* cell size per axis */
-  double dt;             /* time step; must satisfy dt < min(d) (CFL) */
-  int patch[3];          /* patch size in cells, multiple of 4, 4..64 */
+  double dt;             /* time step; 2D: dt < min(d); 3D: the Courant
+                            condition dt sqrt(sum 1/d^2) < 1 */
+  int patch[3];          /* patch size in cells, multiple of 4: 4..64 (2D),
+                            4..32 with the current tile in shared memory
+                            (3D) */
   int prec;              /* pic_precision */
   int bc_field[3];       /* PIC_BC_* per axis */
   int bc_part[3][2];     /* PIC_PBC_* per face (lo, hi); periodic must pair
@@ -83,7 +90,9 @@ typedef struct pic_config {
   double q, m;           /* charge and mass of the mobile species */
   /* Laser entering through x_min (requires an open x axis): Ey_inc(y, t) =
    * a0 exp(-((y-yc)/waist)^2) exp(-2 ln2 (tr/tau)^2) sin(tr),
-   * tr = t - x_shift - t_peak, x_shift the moving window's displacement. */
+   * tr = t - x_shift - t_peak, x_shift the moving window's displacement;
+   * 3D: the transverse factor is exp(-((y-yc)^2 + (z-zc)^2)/waist^2) with
+   * zc = laser_z_center. */
   int laser_on;
   double laser_a0, laser_waist, laser_tau, laser_t_peak, laser_y_center;
   /* Moving window at c along +x: after a step that brings t - mw_t0 to at
@@ -91,8 +100,9 @@ typedef struct pic_config {
   int moving_window;
   double mw_t0;
   /* Plasma injected in the new column: density n0 min(1, max(0,
-   * (x - x0) / ramp)) (a step at x0 if ramp <= 0), ppc[0] x ppc[1] particles
-   * per cell placed regularly, at rest. */
+   * (x - x0) / ramp)) (a step at x0 if ramp <= 0), ppc[0] x ppc[1]
+   * (x ppc[2] in 3D) particles per cell placed regularly, at rest; in 3D
+   * only in cells whose centre has y >= inj_ymin. */
   double inj_n0, inj_x0, inj_ramp;
   int inj_ppc[3];
   double capacity_factor; /* patch capacity = factor x the fullest patch at
@@ -124,8 +134,9 @@ typedef struct pic_config {
                              (0 = 2048) */
   int filter_passes;      /* binomial current filter (Section 3.2): 0 off, 1 or
                              2 passes of (1,2,1)/4 along x then y applied to
-                             J before the field update; pic_get_field(J*)
-                             still returns the deposited current */
+                             J before the field update (2D only) */
+  double inj_ymin;        /* 3D plasma: lower y bound of the filled cells */
+  double laser_z_center;  /* 3D laser: z of the beam axis */
 } pic_config;
 
 typedef struct pic_diag_t {
@@ -161,11 +172,17 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out);
 /* Append n particles (global positions x, y in c/w; momenta u; weights w =
  * local density / particles per cell), float64, PIC_HOST or PIC_DEVICE.
  * They are binned into patches on the device; positions outside the domain
- * give PIC_EINVAL.  The first call sizes the patch capacity. */
+ * give PIC_EINVAL.  The first call sizes the patch capacity.  2D contexts
+ * only (PIC_EINVAL for dims = 3). */
 pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y,
                               const double *ux, const double *uy,
                               const double *uz, const double *w, size_t n,
                               int where);
+/* The same with z positions, for 3D contexts (PIC_EINVAL for dims = 2). */
+pic_status pic_load_particles3(pic_ctx *ctx, const double *x, const double *y,
+                               const double *z, const double *ux,
+                               const double *uy, const double *uz,
+                               const double *w, size_t n, int where);
 
 /* Fill the domain, on the device, with the configuration's plasma profile
  * (inj_n0, inj_x0, inj_ramp, inj_ppc: the profile the moving window
@@ -196,8 +213,9 @@ pic_status pic_step(pic_ctx *ctx, int nsteps);
 pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where);
 
 /* Copy the particles out as 6 x n float64 rows (x, y, ux, uy, uz, w), global
- * positions, in patch order.  cap is the row length of out; *n receives the
- * count (PIC_EINVAL if it exceeds cap). */
+ * positions, in patch order; 3D contexts give 7 rows (x, y, z, ux, uy, uz,
+ * w).  cap is the row length of out; *n receives the count (PIC_EINVAL if
+ * it exceeds cap). */
 pic_status pic_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n,
                              int where);
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpic.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["api", "particle_step", "fields", "particles", "noalloc", "runtime"]
+UNITS = ["api", "particle_step", "fields", "particles", "noalloc", "runtime", "pic3d"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

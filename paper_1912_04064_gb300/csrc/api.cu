@@ -12,6 +12,7 @@
 
 #include "../../include/pic.h"
 #include "common.cuh"
+#include "pic3d.h"
 
 using namespace pic;
 
@@ -68,6 +69,7 @@ struct pic_ctx {
   int grows = 0;
   long long sorts = 0;
   long long since_sort = 0;
+  Ctx3 *c3 = nullptr;  // dims = 3: the 3D context (pic3d.cu)
 };
 
 namespace {
@@ -101,7 +103,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 bool valid_config(const pic_config *c, std::string &why) {
   if (!c) { why = "null config"; return false; }
-  if (c->dims != 2) { why = "only dims = 2 (2D3V) is supported"; return false; }
+  if (c->dims != 2 && c->dims != 3) { why = "dims must be 2 (2D3V) or 3 (3D3V)"; return false; }
+  if (c->dims == 3) {
+    if (!valid_config3(c, why)) return false;
+    if (c->prec != PIC_FP64 && c->prec != PIC_FP32) { why = "bad precision"; return false; }
+    if (!(c->m > 0) || c->q == 0) { why = "mass must be positive and charge nonzero"; return false; }
+    if (c->laser_on && c->bc_field[0] != PIC_BC_SILVER_MULLER) { why = "the laser needs an open x axis"; return false; }
+    if (c->laser_on && !(c->laser_waist > 0 && c->laser_tau > 0)) { why = "laser waist and duration must be positive"; return false; }
+    if (c->moving_window) {
+      if (c->bc_field[0] != PIC_BC_SILVER_MULLER) { why = "the moving window needs an open x axis"; return false; }
+      if (c->n[0] / c->patch[0] < 2) { why = "the moving window needs two patch columns"; return false; }
+      if (c->inj_ppc[0] < 1 || c->inj_ppc[1] < 1 || c->inj_ppc[2] < 1) { why = "injected particles per cell must be >= 1"; return false; }
+    }
+    if (c->capacity_factor < 0) { why = "capacity factor must be >= 0"; return false; }
+    return true;
+  }
   for (int a = 0; a < 2; ++a) {
     if (c->n[a] <= 0 || c->patch[a] <= 0) { why = "cells and patch sizes must be positive"; return false; }
     if (c->patch[a] % 4 || c->patch[a] < 4 || c->patch[a] > 64) { why = "patch sizes must be multiples of 4 in [4, 64]"; return false; }
@@ -1288,6 +1304,7 @@ const char *pic_version(void) { return kVersion; }
 size_t pic_footprint(const pic_config *cfg, size_t np_max) {
   std::string why;
   if (!valid_config(cfg, why)) return 0;
+  if (cfg->dims == 3) return footprint3(cfg, np_max);
   Geom g = make_geom(cfg);
   const size_t rs = cfg->prec == PIC_FP32 ? 4 : 8;
   double cf = cfg->capacity_factor > 0 ? cfg->capacity_factor : 2.0;
@@ -1329,6 +1346,12 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(PIC_ECUDA);
     ctx->own_stream = true;
   }
+  if (cfg->dims == 3) {
+    const pic_status s = c3_create(cfg, ctx->stream, &ctx->c3, ctx->err);
+    if (s) return bail(s);
+    *out = ctx;
+    return PIC_OK;
+  }
   if (cudaMalloc(&ctx->F, field_bytes(g, ctx->rs)) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&ctx->rho_bg, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&ctx->rho_a, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
@@ -1359,6 +1382,8 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
 void pic_destroy(pic_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  c3_destroy(ctx->c3);
+  ctx->c3 = nullptr;
   free_graphs(ctx);
   cudaFree(ctx->F);
   cudaFree(ctx->rho_bg);
@@ -1374,7 +1399,10 @@ void pic_destroy(pic_ctx *ctx) {
   delete ctx;
 }
 
-const char *pic_last_error(const pic_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+const char *pic_last_error(const pic_ctx *ctx) {
+  if (!ctx) return "no context";
+  return ctx->c3 ? c3_error(ctx->c3) : ctx->err.c_str();
+}
 
 pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y, const double *ux,
                               const double *uy, const double *uz, const double *w, size_t n,
@@ -1383,14 +1411,31 @@ pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y, co
   if (s) return s;
   if (n && (!x || !y || !ux || !uy || !uz || !w)) return fail(ctx, PIC_EINVAL, "null particle array");
   if (where != PIC_HOST && where != PIC_DEVICE) return fail(ctx, PIC_EINVAL, "bad location");
+  if (ctx->c3) return fail(ctx, PIC_EINVAL, "3D contexts load particles with pic_load_particles3");
   CK(cudaSetDevice(ctx->cfg.device));
   return ctx->fp32 ? do_load<float>(ctx, x, y, ux, uy, uz, w, n, where)
                    : do_load<double>(ctx, x, y, ux, uy, uz, w, n, where);
 }
 
+pic_status pic_load_particles3(pic_ctx *ctx, const double *x, const double *y, const double *z,
+                               const double *ux, const double *uy, const double *uz,
+                               const double *w, size_t n, int where) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (!ctx->c3) return fail(ctx, PIC_EINVAL, "pic_load_particles3 needs a 3D context");
+  if (n && (!x || !y || !z || !ux || !uy || !uz || !w)) return fail(ctx, PIC_EINVAL, "null particle array");
+  if (where != PIC_HOST && where != PIC_DEVICE) return fail(ctx, PIC_EINVAL, "bad location");
+  CK(cudaSetDevice(ctx->cfg.device));
+  return c3_load(ctx->c3, x, y, z, ux, uy, uz, w, n, where);
+}
+
 pic_status pic_load_plasma(pic_ctx *ctx) {
   pic_status s = check_usable(ctx);
   if (s) return s;
+  if (ctx->c3) {
+    CK(cudaSetDevice(ctx->cfg.device));
+    return c3_fill_plasma(ctx->c3);
+  }
   if (ctx->cap) return fail(ctx, PIC_ESTATE, "particles are already loaded");
   if (ctx->cfg.inj_ppc[0] < 1 || ctx->cfg.inj_ppc[1] < 1 || !(ctx->cfg.inj_n0 >= 0))
     return fail(ctx, PIC_EINVAL, "plasma needs inj_ppc >= 1 and inj_n0 >= 0");
@@ -1403,6 +1448,7 @@ pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where) 
   if (s) return s;
   if (!src || (where != PIC_HOST && where != PIC_DEVICE)) return fail(ctx, PIC_EINVAL, "bad source");
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_set_field(ctx->c3, which, src, where);
   return ctx->fp32 ? do_set_field<float>(ctx, which, src, where)
                    : do_set_field<double>(ctx, which, src, where);
 }
@@ -1411,6 +1457,7 @@ pic_status pic_set_background(pic_ctx *ctx, int mode, double value) {
   pic_status s = check_usable(ctx);
   if (s) return s;
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_set_background(ctx->c3, mode, value);
   const Geom &g = ctx->g;
   if (mode == PIC_BG_NONE) {
     CK(cudaMemsetAsync(ctx->rho_bg, 0, sizeof(double) * g.cs, ctx->stream));
@@ -1440,6 +1487,7 @@ pic_status pic_step(pic_ctx *ctx, int nsteps) {
   if (nsteps < 0) return fail(ctx, PIC_EINVAL, "negative step count");
   if (nsteps == 0) return PIC_OK;
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_step(ctx->c3, nsteps);
   return ctx->fp32 ? do_step<float>(ctx, nsteps) : do_step<double>(ctx, nsteps);
 }
 
@@ -1449,6 +1497,7 @@ pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where) {
   if (!dst || which < 0 || which >= PIC_NFIELDS || (where != PIC_HOST && where != PIC_DEVICE))
     return fail(ctx, PIC_EINVAL, "bad destination or field id");
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_get_field(ctx->c3, which, dst, where);
   return ctx->fp32 ? do_get_field<float>(ctx, which, dst, where)
                    : do_get_field<double>(ctx, which, dst, where);
 }
@@ -1458,6 +1507,7 @@ pic_status pic_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, i
   if (s) return s;
   if (!n || (where != PIC_HOST && where != PIC_DEVICE)) return fail(ctx, PIC_EINVAL, "bad arguments");
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_get_particles(ctx->c3, out, cap, n, where);
   return ctx->fp32 ? do_get_particles<float>(ctx, out, cap, n, where)
                    : do_get_particles<double>(ctx, out, cap, n, where);
 }
@@ -1467,6 +1517,7 @@ pic_status pic_diag(pic_ctx *ctx, pic_diag_t *out) {
   if (s) return s;
   if (!out) return fail(ctx, PIC_EINVAL, "null output");
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_diag(ctx->c3, out);
   return ctx->fp32 ? do_diag<float>(ctx, out) : do_diag<double>(ctx, out);
 }
 
@@ -1474,12 +1525,14 @@ pic_status pic_sync(pic_ctx *ctx) {
   pic_status s = check_usable(ctx);
   if (s) return s;
   CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_sync(ctx->c3);
   return poll_device(ctx);
 }
 
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   pic_status s = check_usable(ctx);
   if (s) return s;
+  if (ctx->c3) return fail(ctx, PIC_EINVAL, "snapshots are a 2D feature");
   if (!bytes) return fail(ctx, PIC_EINVAL, "null size");
   const size_t need = snapshot_bytes(ctx);
   if (!host) {
@@ -1520,6 +1573,7 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
 
 pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (!ctx || !host) return PIC_EINVAL;
+  if (ctx->c3) return fail(ctx, PIC_EINVAL, "snapshots are a 2D feature");
   SnapHeader h;
   if (bytes < sizeof h) return fail(ctx, PIC_EINVAL, "snapshot too small");
   memcpy(&h, host, sizeof h);
@@ -1619,6 +1673,7 @@ pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n) {
     for (int q = 0; q < r; ++q)
       if (runs[q] == c) return bfail(b, PIC_EINVAL, "a run appears twice");
     if (c->sticky != PIC_OK) return bfail(b, PIC_ESTATE, "a run holds a device fault");
+    if (c->c3) return bfail(b, PIC_EINVAL, "3D runs are not batched");
     if (!c->cap) return bfail(b, PIC_ESTATE, "a run has no particles loaded");
     if (c->cfg.device != b->device) return bfail(b, PIC_EINVAL, "a run lives on another device");
     if (c->fp32 != runs[0]->fp32) return bfail(b, PIC_EINVAL, "runs of one batch share a precision");

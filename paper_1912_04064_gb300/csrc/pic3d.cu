@@ -1,0 +1,1979 @@
+// 3D3V path: the same SDMD step as the 2D path (Section 2.2 steps (i) and
+// (ii), Section 3.2 operators) on a Yee lattice with E and J on cell edges
+// and B on cell faces.
+//
+// Per step (context stream, optionally one CUDA graph per step parity):
+//   k3_plan          work items (patch slot, first particle), heaviest first
+//   k3_particle_step persistent blocks over the items: gather E, Bm at x^n
+//                    (27-point quadratic stencils read through the L1 /
+//                    read-only path: a 16^3 patch's E and Bm tile would need
+//                    208 KB of shared memory in FP32, so only the current
+//                    tile is staged on chip), Boris push, move, Esirkepov
+//                    current on the 4-node window per axis into the
+//                    shared-memory current tile (halo 2: 144 atomics per
+//                    particle, exact zeros skipped), boundary conditions,
+//                    compaction of stayers and 26 direction buckets for
+//                    leavers; SDMD step (i): the tile is added into the
+//                    region current with global atomics
+//   k3_update_E      E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2})
+//   k3_update_B      B^{n+3/2}, Bm^{n+1} = average, next J set cleared
+//   k3_silver_mueller ghost B of every open face (laser at x_min)
+//   moving-window shift when due (row shift of every stored value, ring of
+//   slot columns, in-flight migration, plasma injection)
+//
+// Esirkepov in 3D with DS = S1 - S0 per axis:
+//   W_x = DSx (S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3)
+// and cyclically; J_a = -q w (d_a / dt) x prefix sum of W_a along axis a.
+// The prefix sums along the 4-node window are DS0, DS0 + DS1 and -DS3 (the
+// sum of DS is zero).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pic3d.h"
+#include "shape.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int G3 = 4;   // ghost cells per side of every axis
+constexpr int NB3 = 26; // direction buckets per slot
+
+struct Geom3 {
+  int n[3];              // cells
+  int p[3];              // patch size
+  int np[3];             // patches per axis
+  int nslots;
+  int sx, sy, sz;        // stored extents (sx: row stride, multiple of 32)
+  long long cs;          // elements per component
+  double d[3], dt;
+  int fbc[3];
+  int pbc[3][2];
+  double q, m;
+};
+
+__host__ __device__ __forceinline__ long long fidx3(const Geom3 &g, int i, int j, int k) {
+  return ((long long)(k + G3) * g.sy + (j + G3)) * g.sx + (i + G3);
+}
+
+template <typename R>
+struct SoA7 {
+  R *x, *y, *z, *ux, *uy, *uz, *w;
+};
+
+struct Buckets26 {
+  int cap[NB3];
+  int off[NB3];
+  int stride;
+};
+
+__host__ __device__ __forceinline__ int dir26(int dx, int dy, int dz) {
+  const int i = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+  return i < 13 ? i : i - 1;
+}
+__host__ __device__ __forceinline__ void delta26(int d, int &dx, int &dy, int &dz) {
+  const int i = d < 13 ? d : d + 1;
+  dx = i % 3 - 1;
+  dy = (i / 3) % 3 - 1;
+  dz = i / 9 - 1;
+}
+
+// Physical patch coordinates of a slot (slot columns form a ring along x,
+// rotated by the moving window: slot column (col0 + px) mod npx holds
+// physical column px).
+__host__ __device__ __forceinline__ void slot_patch(const Geom3 &g, int col0, int s, int &px,
+                                                    int &py, int &pz) {
+  const int sc = s % g.np[0], rest = s / g.np[0];
+  px = sc - col0;
+  if (px < 0) px += g.np[0];
+  py = rest % g.np[1];
+  pz = rest / g.np[1];
+}
+__host__ __device__ __forceinline__ int slot_of(const Geom3 &g, int col0, int px, int py,
+                                                int pz) {
+  return (pz * g.np[1] + py) * g.np[0] + (px + col0) % g.np[0];
+}
+// Neighbour of slot s in direction (dx, dy, dz); -1 outside a non-periodic
+// face.
+__host__ __device__ __forceinline__ int neighbour3(const Geom3 &g, int col0, int s, int dx, int dy,
+                                                   int dz) {
+  int p[3];
+  slot_patch(g, col0, s, p[0], p[1], p[2]);
+  const int dd[3] = {dx, dy, dz};
+  for (int a = 0; a < 3; ++a) {
+    p[a] += dd[a];
+    if (p[a] < 0 || p[a] >= g.np[a]) {
+      if (g.fbc[a] != FBC_PERIODIC) return -1;
+      p[a] = (p[a] + g.np[a]) % g.np[a];
+    }
+  }
+  return slot_of(g, col0, p[0], p[1], p[2]);
+}
+
+// Store v at the periodic ghost images of cell (i, j, k) in the stored range
+// (one image per periodic axis: every periodic axis has n >= 2 G3 cells).
+template <typename R>
+__device__ __forceinline__ void mirror3(const Geom3 &g, R *a, int i, int j, int k, R v) {
+  int m[3] = {0, 0, 0};
+  const int c[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax)
+    if (g.fbc[ax] == FBC_PERIODIC)
+      m[ax] = c[ax] < G3 ? g.n[ax] : (c[ax] >= g.n[ax] - G3 ? -g.n[ax] : 0);
+  for (int cz = 0; cz < 2; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        if (!(cx | cy | cz)) continue;
+        if ((cx && !m[0]) || (cy && !m[1]) || (cz && !m[2])) continue;
+        a[fidx3(g, i + cx * m[0], j + cy * m[1], k + cz * m[2])] = v;
+      }
+}
+
+// ------------------------------------------------------------ step args --
+
+template <typename R>
+struct Step3 {
+  Geom3 g;
+  const R *F;
+  R *Jdst;
+  SoA7<R> pin, pout, bin, bout;
+  const int *cnt_in, *bcnt_in;
+  int *cnt_out, *bcnt_out;
+  int cap;
+  Buckets26 bk;
+  int parity;
+  DevState *st;
+  R rd[3];   // dt / d (cells per unit velocity)
+  R eps;     // q dt / (2 m)
+  R cj[3];   // -q d / dt
+  R RP[3];   // patch size as reals
+  Plan plan;
+};
+
+template <typename R>
+struct Field3 {
+  Geom3 g;
+  R *F;
+  int parity;
+  DevState *st;
+  R dt, id[3];                          // dt, 1 / d
+  R inv1pr[3], omr[3], dtd[3];          // 1/(1+r), 1-r, dt/d per axis (r = dt/d)
+  int laser_on;
+  const double *laser_g;                // [nz + 1][ny]: a0 exp(-r^2 / w^2) at Ey's nodes
+  double tau, t_peak;
+};
+
+// --------------------------------------------------------------- plan ----
+
+constexpr int PLAN3_CLASSES = 64;
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k3_plan(const Step3<R> a) {
+  __shared__ int hist[PLAN3_CLASSES], off[PLAN3_CLASSES];
+  const Geom3 &g = a.g;
+  const Plan &plan = a.plan;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int col0 = a.st->col0;
+  for (int c = tid; c < PLAN3_CLASSES; c += nth) hist[c] = 0;
+  __syncthreads();
+  for (int s = tid; s < g.nslots; s += nth) {
+    int units = min(a.cnt_in[s], a.cap);
+    for (int d = 0; d < NB3; ++d) {
+      int dx, dy, dz;
+      delta26(d, dx, dy, dz);
+      const int src = neighbour3(g, col0, s, -dx, -dy, -dz);
+      if (src >= 0) units += min(a.bcnt_in[(long long)src * NB3 + d], a.bk.cap[d]);
+    }
+    plan.units[s] = units;
+    a.cnt_out[s] = 0;
+    for (int d = 0; d < NB3; ++d) a.bcnt_out[(long long)s * NB3 + d] = 0;
+    const int items = (units + plan.chunk - 1) / plan.chunk;
+    if (items) atomicAdd(&hist[min(items, PLAN3_CLASSES) - 1], items);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int c = PLAN3_CLASSES - 1; c >= 0; --c) {
+      off[c] = run;
+      run += hist[c];
+    }
+    *plan.n_items = min(run, plan.max_items);
+    *plan.next = 0;
+  }
+  __syncthreads();
+  for (int s = tid; s < g.nslots; s += nth) {
+    const int items = (plan.units[s] + plan.chunk - 1) / plan.chunk;
+    if (!items) continue;
+    const int base = atomicAdd(&off[min(items, PLAN3_CLASSES) - 1], items);
+    for (int k = 0; k < items && base + k < plan.max_items; ++k) {
+      plan.item_slot[base + k] = s;
+      plan.item_first[base + k] = k * plan.chunk;
+    }
+  }
+}
+
+// ------------------------------------------------------ particle step ----
+
+// 27-point interpolation from the region array F (component base) with the
+// stencil starting at global node (i0, j0, k0).
+template <typename R>
+__device__ __forceinline__ R gather27(const R *__restrict__ F, const Geom3 &g, int i0, int j0,
+                                      int k0, const R Sx[3], const R Sy[3], const R Sz[3]) {
+  const R *p = F + fidx3(g, i0, j0, k0);
+  R acc = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R pl = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R *r = p + ((long long)c * g.sy + b) * g.sx;
+      pl += Sy[b] * (Sx[0] * __ldg(r) + Sx[1] * __ldg(r + 1) + Sx[2] * __ldg(r + 2));
+    }
+    acc += Sz[c] * pl;
+  }
+  return acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_step(const Step3<R> a) {
+  extern __shared__ unsigned char dsm3[];
+  __shared__ int s_qoff[NB3 + 2];
+  __shared__ int s_cnt[NB3 + 1];
+  __shared__ long long s_base[NB3 + 1];
+  __shared__ int s_item;
+  const Geom3 &g = a.g;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
+  const int P = g.p[0], Q = g.p[1], Rz = g.p[2];
+  const int JW = P + 5, JH = Q + 5, JD = Rz + 5, JT = JW * JH * JD;
+  const uint32_t pad = (128u - (smem_u32(dsm3) & 127u)) & 127u;
+  R *Jt = reinterpret_cast<R *>(dsm3 + pad);
+  const int n_items = *a.plan.n_items;
+  const R eps = a.eps;
+  unsigned err = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int s = a.plan.item_slot[item];
+    const int ufirst = a.plan.item_first[item];
+    const int col0 = a.st->col0;
+    int pc[3];
+    slot_patch(g, col0, s, pc[0], pc[1], pc[2]);
+    const int X0 = pc[0] * P, Y0 = pc[1] * Q, Z0 = pc[2] * Rz;
+    for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
+    if (tid < NB3 + 1) {
+      int cnt = 0;
+      long long base = 0;
+      if (tid == 0) {
+        cnt = min(a.cnt_in[s], a.cap);
+        base = (long long)s * a.cap;
+      } else {
+        const int d = tid - 1;
+        int dx, dy, dz;
+        delta26(d, dx, dy, dz);
+        const int src = neighbour3(g, col0, s, -dx, -dy, -dz);
+        if (src >= 0) {
+          cnt = min(a.bcnt_in[(long long)src * NB3 + d], a.bk.cap[d]);
+          base = (long long)src * a.bk.stride + a.bk.off[d];
+        }
+      }
+      s_cnt[tid] = cnt;
+      s_base[tid] = base;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      s_qoff[0] = 0;
+      for (int i = 0; i <= NB3; ++i) s_qoff[i + 1] = s_qoff[i] + s_cnt[i];
+    }
+    __syncthreads();
+    const int total = min(ufirst + a.plan.chunk, s_qoff[NB3 + 1]);
+    for (int qb = ufirst; qb < total; qb += nth) {
+      const int qi = qb + tid;
+      int dir = -2;  // -1 stay, -2 none, 0..25 bucket
+      R x1[3] = {R(0), R(0), R(0)}, nu[3] = {R(0), R(0), R(0)}, w = R(0);
+      if (qi < total) {
+        int lo = 0, hi = NB3 + 1;  // source: last i with s_qoff[i] <= qi
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_qoff[mid] <= qi) lo = mid; else hi = mid;
+        }
+        const SoA7<R> &A = lo == 0 ? a.pin : a.bin;
+        const long long b = s_base[lo] + (qi - s_qoff[lo]);
+        const R x0[3] = {A.x[b], A.y[b], A.z[b]};
+        R u[3] = {A.ux[b], A.uy[b], A.uz[b]};
+        w = A.w[b];
+        // interpolation: primal and dual stencils per axis
+        int ip[3], id[3];
+        R Sp[3][3], Sd[3][3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) shapes(x0[ax], ip[ax], Sp[ax], id[ax], Sd[ax]);
+        const int gp[3] = {X0 + ip[0] - 1, Y0 + ip[1] - 1, Z0 + ip[2] - 1};
+        const int gd[3] = {X0 + id[0] - 1, Y0 + id[1] - 1, Z0 + id[2] - 1};
+        const R *F = a.F;
+        const long long cs = g.cs;
+        const R Ex = gather27(F + C_EX * cs, g, gd[0], gp[1], gp[2], Sd[0], Sp[1], Sp[2]);
+        const R Ey = gather27(F + C_EY * cs, g, gp[0], gd[1], gp[2], Sp[0], Sd[1], Sp[2]);
+        const R Ez = gather27(F + C_EZ * cs, g, gp[0], gp[1], gd[2], Sp[0], Sp[1], Sd[2]);
+        const R Bx = gather27(F + C_BMX * cs, g, gp[0], gd[1], gd[2], Sp[0], Sd[1], Sd[2]);
+        const R By = gather27(F + C_BMY * cs, g, gd[0], gp[1], gd[2], Sd[0], Sp[1], Sd[2]);
+        const R Bz = gather27(F + C_BMZ * cs, g, gd[0], gd[1], gp[2], Sd[0], Sd[1], Sp[2]);
+        // Boris push u^{n-1/2} -> u^{n+1/2}
+        const R umx = u[0] + eps * Ex, umy = u[1] + eps * Ey, umz = u[2] + eps * Ez;
+        const R ig = eps * rsq(R(1) + umx * umx + umy * umy + umz * umz);
+        const R tx = ig * Bx, ty = ig * By, tz = ig * Bz;
+        const R f = quot(R(2), R(1) + tx * tx + ty * ty + tz * tz);
+        const R upx = umx + (umy * tz - umz * ty);
+        const R upy = umy + (umz * tx - umx * tz);
+        const R upz = umz + (umx * ty - umy * tx);
+        nu[0] = umx + f * (upy * tz - upz * ty) + eps * Ex;
+        nu[1] = umy + f * (upz * tx - upx * tz) + eps * Ey;
+        nu[2] = umz + f * (upx * ty - upy * tx) + eps * Ez;
+        const R inv = rsq(R(1) + nu[0] * nu[0] + nu[1] * nu[1] + nu[2] * nu[2]);
+        bool finite = true, slow = true;
+        R S0[3][4], DS[3][4];
+        int org[3];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          x1[ax] = x0[ax] + a.rd[ax] * nu[ax] * inv;
+          R S13[3];
+          const int i1 = shape_primal(x1[ax], S13);
+          const int di = i1 - ip[ax];
+          finite = finite && isfinite(x1[ax]) && isfinite(nu[ax]);
+          slow = slow && di >= -1 && di <= 1;
+          const bool sh = di < 0;
+          R S1[4];
+          window4(Sp[ax], sh, S0[ax]);
+          window4(S13, di + (sh ? 1 : 0) != 0, S1);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) DS[ax][c] = S1[c] - S0[ax][c];
+          org[ax] = ip[ax] - 1 - (sh ? 1 : 0) + 2;  // window origin in the tile
+        }
+        if (!finite) err |= ERR_NONFINITE;
+        else if (!slow) err |= ERR_FAST;
+        if (finite && slow) {
+          // Esirkepov: component c, prefix along c, A over the other two
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
+            const R cw = a.cj[c] * w;
+            const R Pf[3] = {cw * DS[c][0], cw * (DS[c][0] + DS[c][1]), -cw * DS[c][3]};
+            R *J = Jt + c * JT;
+#pragma unroll
+            for (int m2 = 0; m2 < 4; ++m2)
+#pragma unroll
+              for (int m1 = 0; m1 < 4; ++m1) {
+                const R A = S0[b1][m1] * (S0[b2][m2] + R(0.5) * DS[b2][m2]) +
+                            DS[b1][m1] * (R(0.5) * S0[b2][m2] + R(1.0 / 3.0) * DS[b2][m2]);
+                if (A == R(0)) continue;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  const R v = Pf[q] * A;
+                  if (v == R(0)) continue;
+                  int t[3];
+                  t[c] = org[c] + q;
+                  t[b1] = org[b1] + m1;
+                  t[b2] = org[b2] + m2;
+                  atomicAdd(&J[(t[2] * JH + t[1]) * JW + t[0]], v);
+                }
+              }
+          }
+          // boundary conditions, destination patch
+          int dd[3];
+          bool gone = false;
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            dd[ax] = x1[ax] < R(0) ? -1 : (x1[ax] >= a.RP[ax] ? 1 : 0);
+            if (dd[ax] != 0 && (pc[ax] + dd[ax] < 0 || pc[ax] + dd[ax] >= g.np[ax])) {
+              const int bc = g.pbc[ax][dd[ax] > 0];
+              if (bc == PBC_REFLECT) {
+                x1[ax] = dd[ax] < 0 ? -x1[ax] : R(2 * g.p[ax]) - x1[ax];
+                if (x1[ax] >= a.RP[ax]) x1[ax] = below(a.RP[ax]);
+                nu[ax] = -nu[ax];
+                dd[ax] = 0;
+              } else if (bc == PBC_REMOVE) {
+                gone = true;
+              }
+            }
+          }
+          if (!gone) {
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+              if (dd[ax] < 0) {
+                x1[ax] += a.RP[ax];
+                if (x1[ax] >= a.RP[ax]) x1[ax] = below(a.RP[ax]);
+              } else if (dd[ax] > 0) {
+                x1[ax] -= a.RP[ax];
+              }
+            }
+            dir = (dd[0] == 0 && dd[1] == 0 && dd[2] == 0) ? -1 : dir26(dd[0], dd[1], dd[2]);
+          }
+        }
+      }
+      const bool stay = dir == -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, stay);
+      int wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(&a.cnt_out[s], __popc(bal));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (stay) {
+        const int pos = wbase + __popc(bal & ((1u << lane) - 1u));
+        if (pos < a.cap) {
+          const long long i = (long long)s * a.cap + pos;
+          a.pout.x[i] = x1[0]; a.pout.y[i] = x1[1]; a.pout.z[i] = x1[2];
+          a.pout.ux[i] = nu[0]; a.pout.uy[i] = nu[1]; a.pout.uz[i] = nu[2];
+          a.pout.w[i] = w;
+        } else {
+          err |= ERR_OVERFLOW_SEG;
+        }
+      } else if (dir >= 0) {
+        const int bp = atomicAdd(&a.bcnt_out[(long long)s * NB3 + dir], 1);
+        if (bp < a.bk.cap[dir]) {
+          const long long i = (long long)s * a.bk.stride + a.bk.off[dir] + bp;
+          a.bout.x[i] = x1[0]; a.bout.y[i] = x1[1]; a.bout.z[i] = x1[2];
+          a.bout.ux[i] = nu[0]; a.bout.uy[i] = nu[1]; a.bout.uz[i] = nu[2];
+          a.bout.w[i] = w;
+        } else {
+          err |= ERR_OVERFLOW_BKT;
+        }
+      }
+    }
+    __syncthreads();
+    // SDMD step (i): patch current tile -> region current
+    for (int e = tid; e < 3 * JT; e += nth) {
+      const R v = Jt[e];
+      if (v == R(0)) continue;
+      const int c = e / JT, r = e - c * JT;
+      const int l = r / (JW * JH), r2 = r - l * (JW * JH), m = r2 / JW, q = r2 - m * JW;
+      int gi = X0 - 2 + q, gj = Y0 - 2 + m, gk = Z0 - 2 + l;
+      if (g.fbc[0] == FBC_PERIODIC) gi = gi < 0 ? gi + g.n[0] : (gi >= g.n[0] ? gi - g.n[0] : gi);
+      if (g.fbc[1] == FBC_PERIODIC) gj = gj < 0 ? gj + g.n[1] : (gj >= g.n[1] ? gj - g.n[1] : gj);
+      if (g.fbc[2] == FBC_PERIODIC) gk = gk < 0 ? gk + g.n[2] : (gk >= g.n[2] ? gk - g.n[2] : gk);
+      atomicAdd(&a.Jdst[c * g.cs + fidx3(g, gi, gj, gk)], v);
+    }
+    if (tid == 0) atomicMax(&a.st->maxcnt[a.parity], atomicAdd(&a.cnt_out[s], 0));
+  }
+  if (err) atomicOr(&a.st->err, err);
+}
+
+// -------------------------------------------------------------- fields ----
+
+// E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}): one cell per thread;
+// periodic axes update [0, n), open axes primal nodes [0, n], dual [0, n).
+template <typename R>
+__global__ void __launch_bounds__(256) k3_update_E(const Field3<R> a) {
+  const Geom3 &g = a.g;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  int np_[3];
+  for (int ax = 0; ax < 3; ++ax) np_[ax] = g.n[ax] + (g.fbc[ax] == FBC_SM);
+  if (i >= np_[0] || j >= np_[1] || k >= np_[2]) return;
+  const long long cs = g.cs, o = fidx3(g, i, j, k);
+  const long long sy = g.sx, sz = (long long)g.sx * g.sy;
+  R *F = a.F;
+  R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
+  const R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
+  const R *J = F + (C_JA + 3 * a.parity) * cs;
+  const R dt = a.dt, idx = a.id[0], idy = a.id[1], idz = a.id[2];
+  const R bx = Bx[o], by = By[o], bz = Bz[o];
+  if (i < g.n[0]) {
+    const R v = Ex[o] + dt * ((bz - Bz[o - sy]) * idy - (by - By[o - sz]) * idz - J[o]);
+    Ex[o] = v;
+    mirror3(g, Ex, i, j, k, v);
+  }
+  if (j < g.n[1]) {
+    const R v = Ey[o] + dt * ((bx - Bx[o - sz]) * idz - (bz - Bz[o - 1]) * idx - J[cs + o]);
+    Ey[o] = v;
+    mirror3(g, Ey, i, j, k, v);
+  }
+  if (k < g.n[2]) {
+    const R v = Ez[o] + dt * ((by - By[o - 1]) * idx - (bx - Bx[o - sy]) * idy - J[2 * cs + o]);
+    Ez[o] = v;
+    mirror3(g, Ez, i, j, k, v);
+  }
+}
+
+// B^{n+3/2} = B^{n+1/2} - dt curl_h E^{n+1}, Bm^{n+1} = (B^{n+1/2} +
+// B^{n+3/2}) / 2 (= B where not updated), next J set cleared; covers every
+// stored cell.
+template <typename R>
+__global__ void __launch_bounds__(256) k3_update_B(const Field3<R> a) {
+  const Geom3 &g = a.g;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0) {
+    const int p = a.parity;
+    a.st->t[1 - p] = a.st->t[p] + g.dt;
+    a.st->step[1 - p] = a.st->step[p] + 1;
+    a.st->maxcnt[1 - p] = 0;
+  }
+  const int i = (int)(blockIdx.x * 32 + threadIdx.x) - G3;
+  const int j = (int)(blockIdx.y * 8 + threadIdx.y) - G3;
+  const int k = (int)blockIdx.z - G3;
+  if (i >= g.n[0] + G3 || j >= g.n[1] + G3 || k >= g.n[2] + G3) return;
+  const long long cs = g.cs, o = fidx3(g, i, j, k);
+  const long long sy = g.sx, sz = (long long)g.sx * g.sy;
+  R *F = a.F;
+  R *Jn = F + (C_JA + 3 * (1 - a.parity)) * cs;
+  Jn[o] = R(0);
+  Jn[cs + o] = R(0);
+  Jn[2 * cs + o] = R(0);
+  const int c[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax)
+    if (g.fbc[ax] == FBC_PERIODIC && (c[ax] < 0 || c[ax] >= g.n[ax])) return;  // mirror cell
+  const R *Ex = F + C_EX * cs, *Ey = F + C_EY * cs, *Ez = F + C_EZ * cs;
+  R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
+  R *Bmx = F + C_BMX * cs, *Bmy = F + C_BMY * cs, *Bmz = F + C_BMZ * cs;
+  const R dt = a.dt, idx = a.id[0], idy = a.id[1], idz = a.id[2];
+  bool in = i >= 0 && j >= 0 && k >= 0;
+  bool pr[3], du[3];  // inside the primal / dual update range per axis
+  for (int ax = 0; ax < 3; ++ax) {
+    pr[ax] = c[ax] < g.n[ax] + (g.fbc[ax] == FBC_SM);
+    du[ax] = c[ax] < g.n[ax];
+  }
+  const bool ux = in && pr[0] && du[1] && du[2];
+  const bool uy = in && du[0] && pr[1] && du[2];
+  const bool uz = in && du[0] && du[1] && pr[2];
+  const R bx0 = Bx[o], by0 = By[o], bz0 = Bz[o];
+  R bx1 = bx0, by1 = by0, bz1 = bz0;
+  if (ux) bx1 = bx0 - dt * ((Ez[o + sy] - Ez[o]) * idy - (Ey[o + sz] - Ey[o]) * idz);
+  if (uy) by1 = by0 - dt * ((Ex[o + sz] - Ex[o]) * idz - (Ez[o + 1] - Ez[o]) * idx);
+  if (uz) bz1 = bz0 - dt * ((Ey[o + 1] - Ey[o]) * idx - (Ex[o + sy] - Ex[o]) * idy);
+  if (ux) { Bx[o] = bx1; mirror3(g, Bx, i, j, k, bx1); }
+  if (uy) { By[o] = by1; mirror3(g, By, i, j, k, by1); }
+  if (uz) { Bz[o] = bz1; mirror3(g, Bz, i, j, k, bz1); }
+  const R mx = R(0.5) * (bx0 + bx1), my = R(0.5) * (by0 + by1), mz = R(0.5) * (bz0 + bz1);
+  Bmx[o] = mx;
+  Bmy[o] = my;
+  Bmz[o] = mz;
+  mirror3(g, Bmx, i, j, k, mx);
+  mirror3(g, Bmy, i, j, k, my);
+  mirror3(g, Bmz, i, j, k, mz);
+}
+
+template <typename R>
+__device__ __forceinline__ void set_ghost3(const Geom3 &g, R *B, R *Bm, int i, int j, int k, R v) {
+  const long long o = fidx3(g, i, j, k);
+  const R old = Bm[o];  // = B^{n+1/2} at this ghost after k3_update_B
+  B[o] = v;
+  mirror3(g, B, i, j, k, v);
+  const R m = R(0.5) * (old + v);
+  Bm[o] = m;
+  mirror3(g, Bm, i, j, k, m);
+}
+
+// Ghost B of the open faces from the first-order Silver-Mueller condition
+// taken half a step ahead of E^{n+1} with Ampere's law on the boundary node.
+// Face of axis a, pair (E_c, B_d) with d the third axis; s = +1 when
+// (curl B)_c holds +d_a B_d, -1 when it holds -d_a B_d; T = -s d_d B_a the
+// transverse part (zero where it needs a ghost of another open axis):
+//   lower: G = [2 e + dt T - s (1 - r) I - 4 e_inc] / (s (1 + r))
+//   upper: G = -[2 e + dt T + s (1 - r) I] / (s (1 + r))
+// blockIdx.y = face (2 axis + upper); threads over the face's points.
+template <typename R>
+__global__ void k3_silver_mueller(const Field3<R> a) {
+  const Geom3 &g = a.g;
+  const int face = blockIdx.y, ax = face >> 1, upper = face & 1;
+  if (g.fbc[ax] != FBC_SM) return;
+  __shared__ double s_h;
+  if (threadIdx.x == 0) {
+    double h = 0.0;
+    if (a.laser_on && ax == 0 && !upper) {
+      const double t = a.st->t[a.parity] + 1.5 * g.dt;
+      const double tr = t - (double)(a.st->nshift * g.p[0]) * g.d[0] - a.t_peak;
+      h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
+    }
+    s_h = h;
+  }
+  __syncthreads();
+  const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;  // transverse axes, increasing
+  const int n1 = g.n[b1] + 1, n2 = g.n[b2] + 1;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n1 * n2) return;
+  const int u1 = t % n1, u2 = t / n1;
+  R *F = a.F;
+  const long long cs = g.cs;
+  const R r1 = a.omr[ax], ia = a.inv1pr[ax];
+  for (int c = 0; c < 3; ++c) {
+    if (c == ax) continue;
+    int s, d;
+    if ((c + 1) % 3 == ax) { s = 1; d = (c + 2) % 3; }
+    else { s = -1; d = (c + 1) % 3; }
+    // transverse range of the ghost B_d: primal along d, dual elsewhere
+    const int lim1 = (b1 == d && g.fbc[b1] == FBC_SM) ? g.n[b1] + 1 : g.n[b1];
+    const int lim2 = (b2 == d && g.fbc[b2] == FBC_SM) ? g.n[b2] + 1 : g.n[b2];
+    if (u1 >= lim1 || u2 >= lim2) continue;
+    int node[3];
+    node[ax] = upper ? g.n[ax] : 0;
+    node[b1] = u1;
+    node[b2] = u2;
+    int gh[3] = {node[0], node[1], node[2]}, in[3] = {node[0], node[1], node[2]};
+    gh[ax] = upper ? g.n[ax] : -1;
+    in[ax] = upper ? g.n[ax] - 1 : 0;
+    const R *E = F + (C_EX + c) * cs;
+    R *Bd = F + (C_BX + d) * cs, *Bmd = F + (C_BMX + d) * cs;
+    const R *Ba = F + (C_BX + ax) * cs;
+    R T = R(0);
+    const int nd = node[d];
+    if (g.fbc[d] == FBC_PERIODIC || (nd >= 1 && nd <= g.n[d] - 1)) {
+      int m[3] = {node[0], node[1], node[2]};
+      m[d] -= 1;
+      const R diff = Ba[fidx3(g, node[0], node[1], node[2])] - Ba[fidx3(g, m[0], m[1], m[2])];
+      T = (s > 0 ? -diff : diff);  // times dt / d_d below
+    }
+    const R dtT = a.dtd[d] * T;
+    const R e = E[fidx3(g, node[0], node[1], node[2])];
+    const R I = Bd[fidx3(g, in[0], in[1], in[2])];
+    R v;
+    if (!upper) {
+      R einc = R(0);
+      if (a.laser_on && ax == 0 && c == 1) einc = R(a.laser_g[(long long)node[2] * g.n[1] + node[1]] * s_h);
+      v = s > 0 ? (R(2) * e + dtT - r1 * I - R(4) * einc) * ia
+                : -(R(2) * e + dtT + r1 * I - R(4) * einc) * ia;
+    } else {
+      v = s > 0 ? -(R(2) * e + dtT + r1 * I) * ia : (R(2) * e + dtT - r1 * I) * ia;
+    }
+    set_ghost3(g, Bd, Bmd, gh[0], gh[1], gh[2], v);
+  }
+}
+
+// ------------------------------------------------------ field transfer ----
+
+__host__ __device__ inline void out_dims3(const Geom3 &g, int lo[3], int cnt[3]) {
+  for (int ax = 0; ax < 3; ++ax) {
+    lo[ax] = g.fbc[ax] == FBC_PERIODIC ? 0 : -1;
+    cnt[ax] = g.fbc[ax] == FBC_PERIODIC ? g.n[ax] : g.n[ax] + 2;
+  }
+}
+
+template <typename R, typename S>
+__global__ void k3_set_field(const Geom3 g, R *arr, const S *src, int mirror) {
+  int lo[3], cnt[3];
+  out_dims3(g, lo, cnt);
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % cnt[0]), j = (int)((e / cnt[0]) % cnt[1]), k = (int)(e / ((long long)cnt[0] * cnt[1]));
+    const R v = R(src[e]);
+    arr[fidx3(g, lo[0] + i, lo[1] + j, lo[2] + k)] = v;
+    if (mirror) mirror3(g, arr, lo[0] + i, lo[1] + j, lo[2] + k, v);
+  }
+}
+
+template <typename R>
+__global__ void k3_get_field(const Geom3 g, const R *arr, double *dst) {
+  int lo[3], cnt[3];
+  out_dims3(g, lo, cnt);
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % cnt[0]), j = (int)((e / cnt[0]) % cnt[1]), k = (int)(e / ((long long)cnt[0] * cnt[1]));
+    dst[e] = (double)arr[fidx3(g, lo[0] + i, lo[1] + j, lo[2] + k)];
+  }
+}
+
+// Moving window: every stored row (along x) of `ncomp` components moves P
+// cells down; indices with no source become vacuum.
+template <typename R>
+__global__ void k3_shift_rows(const Geom3 g, R *base, long long comp_stride) {
+  extern __shared__ unsigned char row3_raw[];
+  R *row = reinterpret_cast<R *>(row3_raw);
+  R *a = base + blockIdx.y * comp_stride + (long long)blockIdx.x * g.sx;
+  const int n = g.n[0] + 2 * G3, P = g.p[0];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) row[e] = a[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int i = e - G3;
+    a[e] = (i + P < g.n[0] + G3) ? row[e + P] : R(0);
+  }
+}
+
+// ----------------------------------------------------------- particles ----
+
+__device__ __forceinline__ bool locate3(const Geom3 &g, int col0, const double *x, int &slot,
+                                        int pc[3]) {
+  for (int ax = 0; ax < 3; ++ax) {
+    const double c = x[ax] / g.d[ax];
+    if (!(c >= 0.0 && c < (double)g.n[ax])) return false;
+    pc[ax] = min((int)floor(c) / g.p[ax], g.np[ax] - 1);
+  }
+  slot = slot_of(g, col0, pc[0], pc[1], pc[2]);
+  return true;
+}
+
+template <typename R>
+__device__ __forceinline__ R rel3(double c, int origin, int P) {
+  R r = R(c - (double)origin);
+  if (r < R(0)) r = R(0);
+  if (r >= R(P)) r = nextafter(R(P), R(0));
+  return r;
+}
+
+__global__ void k3_bin_count(const Geom3 g, int col0, const double *x, const double *y,
+                             const double *z, size_t n, int *counts, unsigned *err) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int slot, pc[3];
+    const double p[3] = {x[k], y[k], z[k]};
+    if (!locate3(g, col0, p, slot, pc)) {
+      atomicOr(err, ERR_LOAD_RANGE);
+      continue;
+    }
+    atomicAdd(&counts[slot], 1);
+  }
+}
+
+template <typename R>
+__global__ void k3_bin_place(const Geom3 g, int col0, const double *x, const double *y,
+                             const double *z, const double *ux, const double *uy,
+                             const double *uz, const double *w, size_t n, SoA7<R> seg,
+                             int *counts, int cap, unsigned *err) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    int slot, pc[3];
+    const double p[3] = {x[k], y[k], z[k]};
+    if (!locate3(g, col0, p, slot, pc)) continue;
+    const int pos = atomicAdd(&counts[slot], 1);
+    if (pos >= cap) {
+      atomicOr(err, ERR_OVERFLOW_LOAD);
+      continue;
+    }
+    const long long i = (long long)slot * cap + pos;
+    seg.x[i] = rel3<R>(x[k] / g.d[0], pc[0] * g.p[0], g.p[0]);
+    seg.y[i] = rel3<R>(y[k] / g.d[1], pc[1] * g.p[1], g.p[1]);
+    seg.z[i] = rel3<R>(z[k] / g.d[2], pc[2] * g.p[2], g.p[2]);
+    seg.ux[i] = R(ux[k]);
+    seg.uy[i] = R(uy[k]);
+    seg.uz[i] = R(uz[k]);
+    seg.w[i] = R(w[k]);
+  }
+}
+
+// Live particles of a view: segments of one set plus the buckets of the
+// other, bucket particles in the frame of their destination patch.
+template <typename R>
+struct View3 {
+  SoA7<R> seg, bkt;
+  const int *cnt, *bcnt;
+  int cap;
+  Buckets26 bk;
+};
+
+template <typename R, typename Fn>
+__device__ void for_each3(const Geom3 &g, int col0, const View3<R> &v, Fn fn) {
+  for (int slot = blockIdx.x; slot < g.nslots; slot += gridDim.x) {
+    int pc[3];
+    slot_patch(g, col0, slot, pc[0], pc[1], pc[2]);
+    const int n = min(v.cnt[slot], v.cap);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const long long i = (long long)slot * v.cap + k;
+      fn(pc, v.seg, i);
+    }
+    for (int d = 0; d < NB3; ++d) {
+      const int nb = min(v.bcnt[(long long)slot * NB3 + d], v.bk.cap[d]);
+      if (nb == 0) continue;
+      int dx, dy, dz;
+      delta26(d, dx, dy, dz);
+      const int dest = neighbour3(g, col0, slot, dx, dy, dz);
+      if (dest < 0) continue;
+      int qc[3];
+      slot_patch(g, col0, dest, qc[0], qc[1], qc[2]);
+      for (int k = threadIdx.x; k < nb; k += blockDim.x)
+        fn(qc, v.bkt, (long long)slot * v.bk.stride + v.bk.off[d] + k);
+    }
+  }
+}
+
+__device__ __forceinline__ void shape_d3(double xi, int &i0, double S[3]) {
+  const double fl = floor(xi + 0.5);
+  const double d = xi - fl;
+  S[0] = 0.5 * (0.5 - d) * (0.5 - d);
+  S[1] = 0.75 - d * d;
+  S[2] = 0.5 * (0.5 + d) * (0.5 + d);
+  i0 = (int)fl;
+}
+
+// rho += qw S(x) S(y) S(z) at nodes (periodic axes wrapped to canonical
+// nodes); position in cells relative to the patch origin O.
+__device__ __forceinline__ void deposit_node3(const Geom3 &g, double *rho, const int O[3],
+                                              const double xr[3], double qw) {
+  int i0[3];
+  double S[3][3];
+  for (int ax = 0; ax < 3; ++ax) shape_d3(xr[ax], i0[ax], S[ax]);
+  for (int c = 0; c < 3; ++c)
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) {
+        int gi = O[0] + i0[0] - 1 + a, gj = O[1] + i0[1] - 1 + b, gk = O[2] + i0[2] - 1 + c;
+        if (g.fbc[0] == FBC_PERIODIC) gi = (gi + g.n[0]) % g.n[0];
+        if (g.fbc[1] == FBC_PERIODIC) gj = (gj + g.n[1]) % g.n[1];
+        if (g.fbc[2] == FBC_PERIODIC) gk = (gk + g.n[2]) % g.n[2];
+        atomicAdd(&rho[fidx3(g, gi, gj, gk)], qw * S[0][a] * S[1][b] * S[2][c]);
+      }
+}
+
+template <typename R>
+__global__ void k3_deposit_rho(const Geom3 g, int col0, const View3<R> v, double *rho, double sign) {
+  const double qs = sign * g.q;
+  for_each3<R>(g, col0, v, [&](const int pc[3], const SoA7<R> &A, long long i) {
+    const int O[3] = {pc[0] * g.p[0], pc[1] * g.p[1], pc[2] * g.p[2]};
+    const double xr[3] = {(double)A.x[i], (double)A.y[i], (double)A.z[i]};
+    deposit_node3(g, rho, O, xr, qs * (double)A.w[i]);
+  });
+}
+
+template <typename R>
+__global__ void k3_particle_diag(const Geom3 g, int col0, const View3<R> v, double *partials) {
+  __shared__ double sh[3][256];
+  double ek = 0.0, ws = 0.0, cnt = 0.0;
+  for_each3<R>(g, col0, v, [&](const int *, const SoA7<R> &A, long long i) {
+    const double a = A.ux[i], b = A.uy[i], c = A.uz[i];
+    ek += (double)A.w[i] * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    ws += (double)A.w[i];
+    cnt += 1.0;
+  });
+  sh[0][threadIdx.x] = ek;
+  sh[1][threadIdx.x] = ws;
+  sh[2][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = sh[q][0];
+}
+
+// offsets: [physical-order segment offsets (nslots)] [bucket offsets
+// (nslots * 26)]; rows x, y, z, ux, uy, uz, w of length `stride`.
+template <typename R>
+__global__ void k3_get_particles(const Geom3 g, int col0, const View3<R> v,
+                                 const long long *offsets, double *out, size_t stride) {
+  const int pp = blockIdx.x;  // physical patch index (x fastest)
+  if (pp >= g.nslots) return;
+  const int ppx = pp % g.np[0], ppy = (pp / g.np[0]) % g.np[1], ppz = pp / (g.np[0] * g.np[1]);
+  const int slot = slot_of(g, col0, ppx, ppy, ppz);
+  auto emit = [&](long long o, const int pc[3], const SoA7<R> &A, long long i) {
+    out[o] = ((double)(pc[0] * g.p[0]) + (double)A.x[i]) * g.d[0];
+    out[stride + o] = ((double)(pc[1] * g.p[1]) + (double)A.y[i]) * g.d[1];
+    out[2 * stride + o] = ((double)(pc[2] * g.p[2]) + (double)A.z[i]) * g.d[2];
+    out[3 * stride + o] = (double)A.ux[i];
+    out[4 * stride + o] = (double)A.uy[i];
+    out[5 * stride + o] = (double)A.uz[i];
+    out[6 * stride + o] = (double)A.w[i];
+  };
+  const int pc[3] = {ppx, ppy, ppz};
+  const int n = min(v.cnt[slot], v.cap);
+  const long long base = offsets[pp];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) emit(base + k, pc, v.seg, (long long)slot * v.cap + k);
+  for (int d = 0; d < NB3; ++d) {
+    int dx, dy, dz;
+    delta26(d, dx, dy, dz);
+    const int dest = neighbour3(g, col0, slot, dx, dy, dz);
+    if (dest < 0) continue;
+    const int nb = min(v.bcnt[(long long)slot * NB3 + d], v.bk.cap[d]);
+    int qc[3];
+    slot_patch(g, col0, dest, qc[0], qc[1], qc[2]);
+    const long long b = offsets[g.nslots + (long long)pp * NB3 + d];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+      emit(b + k, qc, v.bkt, (long long)slot * v.bk.stride + v.bk.off[d] + k);
+  }
+}
+
+// Moving window, part 1 (old ring): particles that crossed from the leaving
+// column during the last step are in the leaving slots' +x buckets; append
+// them to their destination segments, then clear every bucket that points
+// into or out of the leaving column.  One block per (py, pz).
+template <typename R>
+__global__ void k3_window_migrate(const Geom3 g, int col0, SoA7<R> seg, int *cnt, SoA7<R> bkt,
+                                  int *bcnt, int cap, Buckets26 bk, unsigned *err) {
+  const int py = blockIdx.x % g.np[1], pz = blockIdx.x / g.np[1];
+  const int sdrop = slot_of(g, col0, 0, py, pz);
+  const int snext = slot_of(g, col0, 1, py, pz);
+  __shared__ int base;
+  for (int e = 0; e < 9; ++e) {
+    const int dy = e % 3 - 1, dz = e / 3 - 1;
+    const int d = dir26(1, dy, dz);
+    const int dest = neighbour3(g, col0, sdrop, 1, dy, dz);
+    const int nb = min(bcnt[(long long)sdrop * NB3 + d], bk.cap[d]);
+    if (dest < 0 || nb == 0) continue;
+    if (threadIdx.x == 0) base = atomicAdd(&cnt[dest], nb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      const int pos = base + k;
+      if (pos >= cap) {
+        atomicOr(err, ERR_OVERFLOW_SEG);
+        continue;
+      }
+      const long long i = (long long)sdrop * bk.stride + bk.off[d] + k;
+      const long long o = (long long)dest * cap + pos;
+      seg.x[o] = bkt.x[i]; seg.y[o] = bkt.y[i]; seg.z[o] = bkt.z[i];
+      seg.ux[o] = bkt.ux[i]; seg.uy[o] = bkt.uy[i]; seg.uz[o] = bkt.uz[i];
+      seg.w[o] = bkt.w[i];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < NB3) {
+    bcnt[(long long)sdrop * NB3 + threadIdx.x] = 0;
+    int dx, dy, dz;
+    delta26(threadIdx.x, dx, dy, dz);
+    if (dx == -1) bcnt[(long long)snext * NB3 + threadIdx.x] = 0;
+  }
+}
+
+// Plasma at rest, regularly placed (ppc per axis), weight = density(x_lab)
+// / ppc, in the cells of the patch whose centre has y >= ymin, with the
+// co-located immobile ions added to the background charge.  Block
+// (py + npy pz, c) fills physical column phys0 + c, held by slot column
+// (slot_col0 + c) mod npx.
+template <typename R>
+__global__ void k3_inject(const Geom3 g, int slot_col0, int phys0, int nshift, SoA7<R> seg,
+                          int *cnt, int cap, double n0, double x0, double ramp, double ymin,
+                          int ppcx, int ppcy, int ppcz, double *rho_bg, unsigned *err) {
+  const int py = blockIdx.x % g.np[1], pz = blockIdx.x / g.np[1];
+  const int phys = phys0 + (int)blockIdx.y;
+  const int slot = (pz * g.np[1] + py) * g.np[0] + (slot_col0 + (int)blockIdx.y) % g.np[0];
+  const int P = g.p[0], Q = g.p[1], Rz = g.p[2];
+  const int X0 = phys * P, Y0 = py * Q, Z0 = pz * Rz;
+  int jf = 0;  // first row of the patch with plasma (rows above it are all in)
+  while (jf < Q && !(((double)(Y0 + jf) + 0.5) * g.d[1] >= ymin)) ++jf;
+  const int rows = Q - jf;
+  const int ppc = ppcx * ppcy * ppcz;
+  const int total = P * rows * Rz * ppc;
+  if (total > cap) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW_SEG);
+    return;
+  }
+  const double shift = __dmul_rn((double)nshift * P, g.d[0]);
+  const int O[3] = {X0, Y0, Z0};
+  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+    const int a = k % ppcx, b = (k / ppcx) % ppcy, c = (k / (ppcx * ppcy)) % ppcz;
+    const int cell = k / ppc;
+    const int ci = cell % P, cj = jf + (cell / P) % rows, ck = cell / (P * rows);
+    const double fx = (a + 0.5) / ppcx, fy = (b + 0.5) / ppcy, fz = (c + 0.5) / ppcz;
+    const double xl = ((double)(X0 + ci) + fx) * g.d[0];
+    const double xphys = __dadd_rn(xl, shift);
+    double n;
+    if (ramp <= 0.0) {
+      n = xphys >= x0 ? n0 : 0.0;
+    } else {
+      double f = (xphys - x0) / ramp;
+      f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+      n = n0 * f;
+    }
+    const double w = n / ppc;
+    const long long o = (long long)slot * cap + k;
+    seg.x[o] = R((double)ci + fx);
+    seg.y[o] = R((double)cj + fy);
+    seg.z[o] = R((double)ck + fz);
+    seg.ux[o] = R(0);
+    seg.uy[o] = R(0);
+    seg.uz[o] = R(0);
+    seg.w[o] = R(w);
+    if (rho_bg) {
+      const double xr[3] = {(double)ci + fx, (double)cj + fy, (double)ck + fz};
+      deposit_node3(g, rho_bg, O, xr, -g.q * (double)R(w));
+    }
+  }
+  if (threadIdx.x == 0) cnt[slot] = total;
+}
+
+// ---------------------------------------------------------- diagnostics ----
+
+template <typename R>
+__global__ void k3_field_energy(const Geom3 g, const R *F, double *partials) {
+  __shared__ double sh[2][256];
+  double ue = 0.0, ub = 0.0;
+  const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nc;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]), k = (int)(e / ((long long)g.n[0] * g.n[1]));
+    const long long o = fidx3(g, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+      const double ev = (double)F[(C_EX + c) * g.cs + o], bv = (double)F[(C_BMX + c) * g.cs + o];
+      ue += ev * ev;
+      ub += bv * bv;
+    }
+  }
+  sh[0][threadIdx.x] = ue;
+  sh[1][threadIdx.x] = ub;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sh[0][0];
+    partials[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+// max |div_h E - rho - rho_bg| and the continuity residual max |(rho -
+// rho_prev)/dt + div_h J| over the cells 3 or more away from open faces.
+template <typename R>
+__global__ void k3_gauss(const Geom3 g, const R *F, int jset, const double *rho,
+                         const double *rho_prev, const double *rho_bg, double *partials) {
+  __shared__ double sh[2][256];
+  int lo[3], w[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    lo[ax] = g.fbc[ax] == FBC_PERIODIC ? 0 : 3;
+    w[ax] = (g.fbc[ax] == FBC_PERIODIC ? g.n[ax] : g.n[ax] - 3) - lo[ax];
+  }
+  double gm = 0.0, cm = 0.0;
+  const R *Ex = F + C_EX * g.cs, *Ey = F + C_EY * g.cs, *Ez = F + C_EZ * g.cs;
+  const R *J = F + (C_JA + 3 * jset) * g.cs;
+  const long long tot = (long long)max(w[0], 0) * max(w[1], 0) * max(w[2], 0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = lo[0] + (int)(e % w[0]), j = lo[1] + (int)((e / w[0]) % w[1]),
+              k = lo[2] + (int)(e / ((long long)w[0] * w[1]));
+    const long long o = fidx3(g, i, j, k);
+    const double divE = ((double)Ex[o] - (double)Ex[fidx3(g, i - 1, j, k)]) / g.d[0] +
+                        ((double)Ey[o] - (double)Ey[fidx3(g, i, j - 1, k)]) / g.d[1] +
+                        ((double)Ez[o] - (double)Ez[fidx3(g, i, j, k - 1)]) / g.d[2];
+    gm = fmax(gm, fabs(divE - rho[o] - rho_bg[o]));
+    if (rho_prev) {
+      // the current lives on canonical nodes: wrap the -1 neighbours
+      const int im = (g.fbc[0] == FBC_PERIODIC && i == 0) ? g.n[0] - 1 : i - 1;
+      const int jm = (g.fbc[1] == FBC_PERIODIC && j == 0) ? g.n[1] - 1 : j - 1;
+      const int km = (g.fbc[2] == FBC_PERIODIC && k == 0) ? g.n[2] - 1 : k - 1;
+      const double divJ = ((double)J[o] - (double)J[fidx3(g, im, j, k)]) / g.d[0] +
+                          ((double)J[g.cs + o] - (double)J[g.cs + fidx3(g, i, jm, k)]) / g.d[1] +
+                          ((double)J[2 * g.cs + o] - (double)J[2 * g.cs + fidx3(g, i, j, km)]) / g.d[2];
+      cm = fmax(cm, fabs((rho[o] - rho_prev[o]) / g.dt + divJ));
+    }
+  }
+  sh[0][threadIdx.x] = gm;
+  sh[1][threadIdx.x] = cm;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + st]);
+      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + st]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sh[0][0];
+    partials[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+__global__ void k3_window_state(DevState *st, int col0, int nshift) {
+  st->col0 = col0;
+  st->nshift = nshift;
+}
+
+}  // namespace
+
+// ================================================================ host ====
+
+struct Ctx3 {
+  pic_config cfg;
+  Geom3 g;
+  bool fp32;
+  size_t rs;
+  cudaStream_t stream;
+  void *F = nullptr;
+  double *rho_bg = nullptr, *rho_a = nullptr, *rho_b = nullptr, *laser_g = nullptr;
+  void *seg[2][7] = {}, *bkt[2][7] = {};
+  int *cnt[2] = {}, *bcnt[2] = {};
+  int cap = 0;
+  Buckets26 bk{};
+  Plan plan{};
+  int ps_grid = 0;
+  size_t ps_smem = 0;
+  DevState *st = nullptr;
+  double *partials = nullptr;
+  int npartials = 1024;
+  long long *offsets = nullptr;
+  double *staging = nullptr;
+  size_t staging_n = 0;
+  long long step = 0;
+  double t = 0.0;
+  int nshift = 0, col0 = 0;
+  bool prev_valid = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  double ms_particles = 0, ms_fields = 0, ms_window = 0;
+  long long launches = 0, ps_launches = 0;
+  int sticky = PIC_OK;
+  std::string err;
+};
+
+namespace {
+
+pic_status fail3(Ctx3 *c, pic_status s, const std::string &m) {
+  if (c) c->err = m;
+  return s;
+}
+
+#define CK3(call)                                                                        \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail3(c, PIC_ECUDA, std::string(#call ": ") + cudaGetErrorString(e_));      \
+  } while (0)
+
+Geom3 make_geom3(const pic_config *cf) {
+  Geom3 g{};
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = cf->n[a];
+    g.p[a] = cf->patch[a];
+    g.np[a] = g.n[a] / g.p[a];
+    g.d[a] = cf->d[a];
+    g.fbc[a] = cf->bc_field[a];
+    g.pbc[a][0] = cf->bc_part[a][0];
+    g.pbc[a][1] = cf->bc_part[a][1];
+  }
+  g.nslots = g.np[0] * g.np[1] * g.np[2];
+  g.sx = (g.n[0] + 2 * G3 + 31) / 32 * 32;
+  g.sy = g.n[1] + 2 * G3;
+  g.sz = g.n[2] + 2 * G3;
+  g.cs = (long long)g.sx * g.sy * g.sz;
+  g.dt = cf->dt;
+  g.q = cf->q;
+  g.m = cf->m;
+  return g;
+}
+
+size_t tile_bytes(const pic_config *cf, size_t rs) {
+  return (size_t)3 * (cf->patch[0] + 5) * (cf->patch[1] + 5) * (cf->patch[2] + 5) * rs + 128;
+}
+
+Buckets26 layout26(int cap) {
+  Buckets26 b{};
+  int off = 0;
+  for (int d = 0; d < NB3; ++d) {
+    int dx, dy, dz;
+    delta26(d, dx, dy, dz);
+    // a step crosses one face of a patch (at most one cell deep) far more
+    // often than an edge or a corner; x faces take the laser-driven sheets
+    const int m = (dx != 0) + (dy != 0) + (dz != 0);
+    const int div = m == 1 ? (dx != 0 ? 2 : 4) : (m == 2 ? 16 : 32);
+    b.cap[d] = std::max(32, (cap / div + 31) / 32 * 32);
+    b.off[d] = off;
+    off += b.cap[d];
+  }
+  b.stride = off;
+  return b;
+}
+
+size_t particle_bytes3(const Geom3 &g, int cap, size_t rs) {
+  const Buckets26 b = layout26(cap);
+  return 2 * (7 * rs * ((size_t)g.nslots * cap + (size_t)g.nslots * b.stride) +
+              sizeof(int) * ((size_t)g.nslots * (1 + NB3)));
+}
+
+template <typename R>
+SoA7<R> soa7(void *const a[7]) {
+  return SoA7<R>{(R *)a[0], (R *)a[1], (R *)a[2], (R *)a[3], (R *)a[4], (R *)a[5], (R *)a[6]};
+}
+
+template <typename R>
+View3<R> view3(Ctx3 *c, int segset, int bktset) {
+  View3<R> v;
+  v.seg = soa7<R>(c->seg[segset]);
+  v.bkt = soa7<R>(c->bkt[bktset]);
+  v.cnt = c->cnt[segset];
+  v.bcnt = c->bcnt[bktset];
+  v.cap = c->cap;
+  v.bk = c->bk;
+  return v;
+}
+
+pic_status poll3(Ctx3 *c) {
+  CK3(cudaStreamSynchronize(c->stream));
+  DevState h;
+  CK3(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost));
+  if (h.err) {
+    pic_status s = PIC_ENONFINITE;
+    std::string m = "device fault:";
+    if (h.err & ERR_TIMEOUT) { s = PIC_ETIMEOUT; m += " wait ran out;"; }
+    if (h.err & (ERR_OVERFLOW_SEG | ERR_OVERFLOW_BKT | ERR_OVERFLOW_LOAD)) {
+      if (s != PIC_ETIMEOUT) s = PIC_EOVERFLOW;
+      m += " patch capacity exceeded (raise capacity_factor);";
+    }
+    if (h.err & ERR_NONFINITE) m += " non-finite particle;";
+    if (h.err & ERR_FAST) m += " particle moved more than one cell;";
+    if (h.err & ERR_LOAD_RANGE) { s = PIC_EINVAL; m += " particle outside the domain;"; }
+    c->sticky = s;
+    return fail3(c, s, m);
+  }
+  return PIC_OK;
+}
+
+void free_graphs3(Ctx3 *c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->gexec[p]) {
+      cudaGraphExecDestroy(c->gexec[p]);
+      c->gexec[p] = nullptr;
+    }
+}
+
+template <typename R>
+pic_status alloc3(Ctx3 *c, int cap) {
+  c->cap = cap;
+  c->bk = layout26(cap);
+  const Geom3 &g = c->g;
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 7; ++a) {
+      CK3(cudaMalloc(&c->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
+      CK3(cudaMalloc(&c->bkt[s][a], sizeof(R) * (size_t)g.nslots * c->bk.stride));
+    }
+    CK3(cudaMalloc(&c->cnt[s], sizeof(int) * g.nslots));
+    CK3(cudaMalloc(&c->bcnt[s], sizeof(int) * (size_t)g.nslots * NB3));
+    CK3(cudaMemsetAsync(c->cnt[s], 0, sizeof(int) * g.nslots, c->stream));
+    CK3(cudaMemsetAsync(c->bcnt[s], 0, sizeof(int) * (size_t)g.nslots * NB3, c->stream));
+  }
+  CK3(cudaMalloc(&c->offsets, sizeof(long long) * ((size_t)g.nslots * (1 + NB3) + 1)));
+  Plan &pl = c->plan;
+  pl.unit = 1;
+  pl.chunk = c->cfg.task_chunk > 0 ? c->cfg.task_chunk : 2048;
+  const long long units_max = (long long)cap + c->bk.stride;
+  pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
+                                          1ll << 30);
+  CK3(cudaMalloc(&pl.item_slot, sizeof(int) * pl.max_items));
+  CK3(cudaMalloc(&pl.item_first, sizeof(int) * pl.max_items));
+  CK3(cudaMalloc(&pl.n_items, sizeof(int) * 2));
+  pl.next = pl.n_items + 1;
+  CK3(cudaMalloc(&pl.units, sizeof(int) * g.nslots));
+  return PIC_OK;
+}
+
+void free_particles3(Ctx3 *c) {
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < 7; ++a) {
+      cudaFree(c->seg[s][a]);
+      cudaFree(c->bkt[s][a]);
+      c->seg[s][a] = c->bkt[s][a] = nullptr;
+    }
+    cudaFree(c->cnt[s]);
+    cudaFree(c->bcnt[s]);
+    c->cnt[s] = c->bcnt[s] = nullptr;
+  }
+  cudaFree(c->offsets);
+  cudaFree(c->plan.item_slot);
+  cudaFree(c->plan.item_first);
+  cudaFree(c->plan.n_items);
+  cudaFree(c->plan.units);
+  c->offsets = nullptr;
+  c->plan = Plan{};
+}
+
+template <typename R>
+Step3<R> step_args3(Ctx3 *c, int p) {
+  const Geom3 &g = c->g;
+  Step3<R> a;
+  a.g = g;
+  a.F = (const R *)c->F;
+  a.Jdst = (R *)c->F + (C_JA + 3 * p) * g.cs;
+  a.pin = soa7<R>(c->seg[p]);
+  a.pout = soa7<R>(c->seg[1 - p]);
+  a.bin = soa7<R>(c->bkt[1 - p]);
+  a.bout = soa7<R>(c->bkt[p]);
+  a.cnt_in = c->cnt[p];
+  a.cnt_out = c->cnt[1 - p];
+  a.bcnt_in = c->bcnt[1 - p];
+  a.bcnt_out = c->bcnt[p];
+  a.cap = c->cap;
+  a.bk = c->bk;
+  a.parity = p;
+  a.st = c->st;
+  for (int ax = 0; ax < 3; ++ax) {
+    a.rd[ax] = R(g.dt / g.d[ax]);
+    a.cj[ax] = R(-g.q * g.d[ax] / g.dt);
+    a.RP[ax] = R(g.p[ax]);
+  }
+  a.eps = R(g.q * g.dt / (2.0 * g.m));
+  a.plan = c->plan;
+  return a;
+}
+
+template <typename R>
+Field3<R> field_args3(Ctx3 *c, int p) {
+  const Geom3 &g = c->g;
+  Field3<R> f;
+  f.g = g;
+  f.F = (R *)c->F;
+  f.parity = p;
+  f.st = c->st;
+  f.dt = R(g.dt);
+  for (int ax = 0; ax < 3; ++ax) {
+    const double r = g.dt / g.d[ax];
+    f.id[ax] = R(1.0 / g.d[ax]);
+    f.inv1pr[ax] = R(1.0 / (1.0 + r));
+    f.omr[ax] = R(1.0 - r);
+    f.dtd[ax] = R(g.dt / g.d[ax]);
+  }
+  f.laser_on = c->cfg.laser_on;
+  f.laser_g = c->laser_g;
+  f.tau = c->cfg.laser_tau;
+  f.t_peak = c->cfg.laser_t_peak;
+  return f;
+}
+
+template <typename R>
+pic_status enqueue_step3(Ctx3 *c, int p, cudaEvent_t mid = nullptr) {
+  const Geom3 &g = c->g;
+  const Step3<R> a = step_args3<R>(c, p);
+  k3_plan<R><<<1, 1024, 0, c->stream>>>(a);
+  k3_particle_step<R><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(a);
+  CK3(cudaGetLastError());
+  if (mid) CK3(cudaEventRecord(mid, c->stream));
+  const Field3<R> f = field_args3<R>(c, p);
+  int npn[3];
+  for (int ax = 0; ax < 3; ++ax) npn[ax] = g.n[ax] + (g.fbc[ax] == FBC_SM);
+  k3_update_E<R><<<dim3((npn[0] + 31) / 32, (npn[1] + 7) / 8, npn[2]), dim3(32, 8), 0, c->stream>>>(f);
+  k3_update_B<R><<<dim3((g.n[0] + 2 * G3 + 31) / 32, (g.n[1] + 2 * G3 + 7) / 8, g.n[2] + 2 * G3),
+                   dim3(32, 8), 0, c->stream>>>(f);
+  if (g.fbc[0] == FBC_SM || g.fbc[1] == FBC_SM || g.fbc[2] == FBC_SM) {
+    int mx = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+      mx = std::max(mx, (g.n[b1] + 1) * (g.n[b2] + 1));
+    }
+    k3_silver_mueller<R><<<dim3((mx + 255) / 256, 6), 256, 0, c->stream>>>(f);
+  }
+  CK3(cudaGetLastError());
+  return PIC_OK;
+}
+
+int kernels_per_step3(const Ctx3 *c) {
+  const Geom3 &g = c->g;
+  return 4 + ((g.fbc[0] == FBC_SM || g.fbc[1] == FBC_SM || g.fbc[2] == FBC_SM) ? 1 : 0);
+}
+
+template <typename R>
+pic_status window_shift3(Ctx3 *c) {
+  const Geom3 &g = c->g;
+  const int q = (int)(c->step & 1), bset = 1 - q, last_j = 1 - q;
+  R *F = (R *)c->F;
+  const size_t smem = sizeof(R) * (g.n[0] + 2 * G3 + g.p[0]);
+  k3_shift_rows<R><<<dim3(g.sy * g.sz, 9), 256, smem, c->stream>>>(g, F, g.cs);
+  k3_shift_rows<R><<<dim3(g.sy * g.sz, 3), 256, smem, c->stream>>>(g, F + (C_JA + 3 * last_j) * g.cs, g.cs);
+  k3_shift_rows<double><<<dim3(g.sy * g.sz, 1), 256, sizeof(double) * (g.n[0] + 2 * G3 + g.p[0]),
+                          c->stream>>>(g, c->rho_bg, g.cs);
+  const int old_col0 = c->col0;
+  c->nshift += 1;
+  c->col0 = (old_col0 + 1) % g.np[0];
+  k3_window_migrate<R><<<g.np[1] * g.np[2], 256, 0, c->stream>>>(
+      g, old_col0, soa7<R>(c->seg[q]), c->cnt[q], soa7<R>(c->bkt[bset]), c->bcnt[bset], c->cap, c->bk,
+      &c->st->err);
+  k3_inject<R><<<dim3(g.np[1] * g.np[2], 1), 256, 0, c->stream>>>(
+      g, old_col0, g.np[0] - 1, c->nshift, soa7<R>(c->seg[q]), c->cnt[q], c->cap, c->cfg.inj_n0,
+      c->cfg.inj_x0, c->cfg.inj_ramp, c->cfg.inj_ymin, c->cfg.inj_ppc[0], c->cfg.inj_ppc[1],
+      c->cfg.inj_ppc[2], c->rho_bg, &c->st->err);
+  k3_window_state<<<1, 1, 0, c->stream>>>(c->st, c->col0, c->nshift);
+  CK3(cudaGetLastError());
+  c->launches += 6;
+  c->prev_valid = false;
+  return PIC_OK;
+}
+
+bool window_due3(const Ctx3 *c) {
+  return c->cfg.moving_window && c->t > c->cfg.mw_t0 &&
+         c->t - c->cfg.mw_t0 >= (c->nshift + 1) * (double)c->g.p[0] * c->g.d[0];
+}
+
+template <typename R>
+pic_status prepare3(Ctx3 *c) {
+  if (c->ps_grid) return PIC_OK;
+  c->ps_smem = tile_bytes(&c->cfg, sizeof(R));
+  CK3(cudaFuncSetAttribute(k3_particle_step<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)c->ps_smem));
+  int per_sm = 0, dev = 0, nsm = 0;
+  CK3(cudaGetDevice(&dev));
+  CK3(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_particle_step<R>, 256, c->ps_smem));
+  if (per_sm <= 0) return fail3(c, PIC_EINVAL, "the patch current tile does not fit in shared memory");
+  c->ps_grid = per_sm * nsm;
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status capture3(Ctx3 *c) {
+  for (int p = 0; p < 2; ++p) {
+    cudaGraph_t gr;
+    CK3(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    pic_status s = enqueue_step3<R>(c, p);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &gr);
+    if (s != PIC_OK) return s;
+    CK3(e);
+    e = cudaGraphInstantiate(&c->gexec[p], gr, 0);
+    cudaGraphDestroy(gr);
+    CK3(e);
+  }
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status run3(Ctx3 *c, int nsteps) {
+  pic_status s = prepare3<R>(c);
+  if (s) return s;
+  const bool timing = c->cfg.timing != 0;
+  const bool use_graph = c->cfg.use_graph && !timing;
+  if (use_graph && !c->gexec[0]) {
+    s = capture3<R>(c);
+    if (s) return s;
+  }
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  pic_status rs = PIC_OK;
+  for (int n = 0; n < nsteps && rs == PIC_OK; ++n) {
+    const int p = (int)(c->step & 1);
+    if (use_graph) {
+      CK3(cudaGraphLaunch(c->gexec[p], c->stream));
+    } else if (timing) {
+      cudaEvent_t e[3];
+      for (int k = 0; k < 3; ++k) CK3(cudaEventCreate(&e[k]));
+      CK3(cudaEventRecord(e[0], c->stream));
+      rs = enqueue_step3<R>(c, p, e[1]);
+      CK3(cudaEventRecord(e[2], c->stream));
+      for (int k = 0; k < 3; ++k) ev.push_back(e[k]);
+      kind.push_back(0);
+    } else {
+      rs = enqueue_step3<R>(c, p);
+    }
+    c->launches += kernels_per_step3(c);
+    c->ps_launches += 1;
+    c->step += 1;
+    c->t += c->g.dt;
+    c->prev_valid = true;
+    if (rs == PIC_OK && window_due3(c)) {
+      cudaEvent_t e[2];
+      if (timing) {
+        for (int k = 0; k < 2; ++k) CK3(cudaEventCreate(&e[k]));
+        CK3(cudaEventRecord(e[0], c->stream));
+      }
+      rs = window_shift3<R>(c);
+      if (timing) {
+        CK3(cudaEventRecord(e[1], c->stream));
+        ev.push_back(e[0]);
+        ev.push_back(e[1]);
+        kind.push_back(1);
+      }
+    }
+  }
+  if (!ev.empty()) {
+    CK3(cudaStreamSynchronize(c->stream));
+    size_t k = 0;
+    for (int t : kind) {
+      float a = 0, b = 0;
+      if (t == 0) {
+        CK3(cudaEventElapsedTime(&a, ev[k], ev[k + 1]));
+        CK3(cudaEventElapsedTime(&b, ev[k + 1], ev[k + 2]));
+        c->ms_particles += a;
+        c->ms_fields += b;
+        k += 3;
+      } else {
+        CK3(cudaEventElapsedTime(&a, ev[k], ev[k + 1]));
+        c->ms_window += a;
+        k += 2;
+      }
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  if (rs) return rs;
+  return poll3(c);
+}
+
+int capacity_for(const Ctx3 *c, int fullest) {
+  const double cf = c->cfg.capacity_factor > 0 ? c->cfg.capacity_factor : 2.0;
+  const int cmin = c->cfg.capacity_min > 0 ? c->cfg.capacity_min : 256;
+  int cap = std::max(cmin, (int)std::ceil(cf * fullest));
+  return (cap + 31) / 32 * 32;
+}
+
+template <typename R>
+pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
+  const Geom3 &g = c->g;
+  const double *d[7];
+  double *tmp = nullptr;
+  if (where == PIC_HOST) {
+    CK3(cudaMalloc(&tmp, sizeof(double) * 7 * std::max<size_t>(n, 1)));
+    for (int a = 0; a < 7; ++a) {
+      CK3(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+      d[a] = tmp + a * n;
+    }
+  } else {
+    for (int a = 0; a < 7; ++a) d[a] = src[a];
+  }
+  int *cnt = nullptr;
+  CK3(cudaMalloc(&cnt, sizeof(int) * g.nslots));
+  CK3(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, c->stream));
+  const int blocks = (int)std::min<size_t>((n + 255) / 256 + 1, 4096);
+  k3_bin_count<<<blocks, 256, 0, c->stream>>>(g, c->col0, d[0], d[1], d[2], n, cnt, &c->st->err);
+  std::vector<int> h(g.nslots);
+  CK3(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, c->stream));
+  DevState hs;
+  CK3(cudaMemcpyAsync(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaStreamSynchronize(c->stream));
+  cudaFree(cnt);
+  c->launches += 1;
+  if (hs.err & ERR_LOAD_RANGE) {
+    const unsigned keep = hs.err & ~ERR_LOAD_RANGE;
+    CK3(cudaMemcpy(&c->st->err, &keep, sizeof keep, cudaMemcpyHostToDevice));
+    if (tmp) cudaFree(tmp);
+    return fail3(c, PIC_EINVAL, "particle position outside the domain");
+  }
+  if (!c->cap) {
+    int mx = *std::max_element(h.begin(), h.end());
+    if (c->cfg.moving_window)
+      mx = std::max(mx, g.p[0] * g.p[1] * g.p[2] * c->cfg.inj_ppc[0] * c->cfg.inj_ppc[1] * c->cfg.inj_ppc[2]);
+    pic_status s = alloc3<R>(c, capacity_for(c, mx));
+    if (s) return s;
+  }
+  const int q = (int)(c->step & 1);
+  k3_bin_place<R><<<blocks, 256, 0, c->stream>>>(g, c->col0, d[0], d[1], d[2], d[3], d[4], d[5],
+                                                 d[6], n, soa7<R>(c->seg[q]), c->cnt[q], c->cap,
+                                                 &c->st->err);
+  CK3(cudaGetLastError());
+  CK3(launch_clamp_counts(c->cnt[q], g.nslots, c->cap, c->stream));
+  c->launches += 2;
+  if (tmp) {
+    CK3(cudaStreamSynchronize(c->stream));
+    cudaFree(tmp);
+  }
+  c->prev_valid = false;
+  free_graphs3(c);
+  return poll3(c);
+}
+
+template <typename R>
+pic_status fill3(Ctx3 *c) {
+  const Geom3 &g = c->g;
+  const pic_config &cf = c->cfg;
+  const int full = g.p[0] * g.p[1] * g.p[2] * cf.inj_ppc[0] * cf.inj_ppc[1] * cf.inj_ppc[2];
+  pic_status s = alloc3<R>(c, capacity_for(c, full));
+  if (s) return s;
+  const int q = (int)(c->step & 1);
+  k3_inject<R><<<dim3(g.np[1] * g.np[2], g.np[0]), 256, 0, c->stream>>>(
+      g, c->col0, 0, c->nshift, soa7<R>(c->seg[q]), c->cnt[q], c->cap, cf.inj_n0, cf.inj_x0,
+      cf.inj_ramp, cf.inj_ymin, cf.inj_ppc[0], cf.inj_ppc[1], cf.inj_ppc[2], c->rho_bg,
+      &c->st->err);
+  CK3(cudaGetLastError());
+  c->launches += 1;
+  c->prev_valid = false;
+  free_graphs3(c);
+  return poll3(c);
+}
+
+pic_status ensure_staging3(Ctx3 *c, size_t n) {
+  if (c->staging_n >= n) return PIC_OK;
+  cudaFree(c->staging);
+  c->staging = nullptr;
+  CK3(cudaMalloc(&c->staging, sizeof(double) * n));
+  c->staging_n = n;
+  return PIC_OK;
+}
+
+size_t out_count3(const Geom3 &g) {
+  int lo[3], cnt[3];
+  out_dims3(g, lo, cnt);
+  return (size_t)cnt[0] * cnt[1] * cnt[2];
+}
+
+int comp_of3(int which) {
+  switch (which) {
+    case PIC_EX: return C_EX;
+    case PIC_EY: return C_EY;
+    case PIC_EZ: return C_EZ;
+    case PIC_BX: return C_BX;
+    case PIC_BY: return C_BY;
+    case PIC_BZ: return C_BZ;
+    case PIC_BMX: return C_BMX;
+    case PIC_BMY: return C_BMY;
+    case PIC_BMZ: return C_BMZ;
+    default: return -1;
+  }
+}
+
+template <typename R>
+pic_status deposit_rho3(Ctx3 *c, double *rho, bool previous) {
+  const Geom3 &g = c->g;
+  CK3(cudaMemsetAsync(rho, 0, sizeof(double) * g.cs, c->stream));
+  if (!c->cap) return PIC_OK;
+  const int q = (int)(c->step & 1);
+  const int segset = previous ? 1 - q : q, bktset = previous ? q : 1 - q;
+  k3_deposit_rho<R><<<g.nslots, 256, 0, c->stream>>>(g, c->col0, view3<R>(c, segset, bktset), rho, 1.0);
+  CK3(cudaGetLastError());
+  c->launches += 1;
+  return PIC_OK;
+}
+
+template <typename R>
+pic_status get_field3(Ctx3 *c, int which, double *dst, int where) {
+  const Geom3 &g = c->g;
+  const size_t n = out_count3(g);
+  double *d = dst;
+  if (where == PIC_HOST) {
+    pic_status s = ensure_staging3(c, n);
+    if (s) return s;
+    d = c->staging;
+  }
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
+  if (which == PIC_RHO || which == PIC_RHO_BG) {
+    const double *src = c->rho_bg;
+    if (which == PIC_RHO) {
+      pic_status s = deposit_rho3<R>(c, c->rho_a, false);
+      if (s) return s;
+      src = c->rho_a;
+    }
+    k3_get_field<double><<<blocks, 256, 0, c->stream>>>(g, src, d);
+  } else {
+    int comp = comp_of3(which);
+    if (which >= PIC_JX && which <= PIC_JZ)
+      comp = C_JA + 3 * (int)((c->step + 1) & 1) + (which - PIC_JX);
+    if (comp < 0) return fail3(c, PIC_EINVAL, "bad field id");
+    k3_get_field<R><<<blocks, 256, 0, c->stream>>>(g, (const R *)c->F + comp * g.cs, d);
+  }
+  CK3(cudaGetLastError());
+  c->launches += 1;
+  if (where == PIC_HOST)
+    CK3(cudaMemcpyAsync(dst, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  return poll3(c);
+}
+
+template <typename R>
+pic_status set_field3(Ctx3 *c, int which, const double *src, int where) {
+  const Geom3 &g = c->g;
+  const size_t n = out_count3(g);
+  const double *d = src;
+  if (where == PIC_HOST) {
+    pic_status s = ensure_staging3(c, n);
+    if (s) return s;
+    CK3(cudaMemcpyAsync(c->staging, src, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    d = c->staging;
+  }
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
+  if (which == PIC_RHO_BG) {
+    k3_set_field<double, double><<<blocks, 256, 0, c->stream>>>(g, c->rho_bg, d, 0);
+  } else {
+    const int comp = comp_of3(which);
+    if (comp < 0) return fail3(c, PIC_EINVAL, "field not settable");
+    k3_set_field<R, double><<<blocks, 256, 0, c->stream>>>(g, (R *)c->F + comp * g.cs, d, 1);
+  }
+  CK3(cudaGetLastError());
+  c->launches += 1;
+  c->prev_valid = false;
+  return poll3(c);
+}
+
+template <typename R>
+pic_status get_particles3(Ctx3 *c, double *out, size_t cap, size_t *n, int where) {
+  const Geom3 &g = c->g;
+  if (!c->cap) {
+    *n = 0;
+    return PIC_OK;
+  }
+  const int q = (int)(c->step & 1);
+  std::vector<int> cn(g.nslots), b((size_t)g.nslots * NB3);
+  CK3(cudaMemcpyAsync(cn.data(), c->cnt[q], sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaMemcpyAsync(b.data(), c->bcnt[1 - q], sizeof(int) * b.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaStreamSynchronize(c->stream));
+  std::vector<long long> off((size_t)g.nslots * (1 + NB3) + 1, 0);
+  long long tot = 0;
+  for (int pp = 0; pp < g.nslots; ++pp) {
+    const int px = pp % g.np[0], py = (pp / g.np[0]) % g.np[1], pz = pp / (g.np[0] * g.np[1]);
+    const int slot = slot_of(g, c->col0, px, py, pz);
+    off[pp] = tot;
+    tot += std::min(cn[slot], c->cap);
+  }
+  for (int pp = 0; pp < g.nslots; ++pp) {
+    const int px = pp % g.np[0], py = (pp / g.np[0]) % g.np[1], pz = pp / (g.np[0] * g.np[1]);
+    const int slot = slot_of(g, c->col0, px, py, pz);
+    for (int d = 0; d < NB3; ++d) {
+      int dx, dy, dz;
+      delta26(d, dx, dy, dz);
+      off[g.nslots + (size_t)pp * NB3 + d] = tot;
+      if (neighbour3(g, c->col0, slot, dx, dy, dz) >= 0)
+        tot += std::min(b[(size_t)slot * NB3 + d], c->bk.cap[d]);
+    }
+  }
+  *n = (size_t)tot;
+  if (!out) return PIC_OK;
+  if ((size_t)tot > cap) return fail3(c, PIC_EINVAL, "output capacity too small");
+  CK3(cudaMemcpyAsync(c->offsets, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
+                      c->stream));
+  double *dst = out, *tmp = nullptr;
+  if (where == PIC_HOST) {
+    CK3(cudaMalloc(&tmp, sizeof(double) * 7 * std::max<size_t>(cap, 1)));
+    dst = tmp;
+  }
+  k3_get_particles<R><<<g.nslots, 256, 0, c->stream>>>(g, c->col0, view3<R>(c, q, 1 - q), c->offsets,
+                                                       dst, cap);
+  CK3(cudaGetLastError());
+  c->launches += 1;
+  if (tmp) {
+    CK3(cudaMemcpyAsync(out, tmp, sizeof(double) * 7 * cap, cudaMemcpyDeviceToHost, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    cudaFree(tmp);
+  }
+  return poll3(c);
+}
+
+template <typename R>
+pic_status diag3(Ctx3 *c, pic_diag_t *out) {
+  const Geom3 &g = c->g;
+  memset(out, 0, sizeof *out);
+  const int nb = c->npartials;
+  std::vector<double> h(3 * nb);
+  const double dV = g.d[0] * g.d[1] * g.d[2];
+  k3_field_energy<R><<<nb, 256, 0, c->stream>>>(g, (const R *)c->F, c->partials);
+  CK3(cudaGetLastError());
+  CK3(cudaMemcpyAsync(h.data(), c->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaStreamSynchronize(c->stream));
+  double ue = 0, ub = 0;
+  for (int b = 0; b < nb; ++b) {
+    ue += h[2 * b];
+    ub += h[2 * b + 1];
+  }
+  out->U_E = 0.5 * ue * dV;
+  out->U_B = 0.5 * ub * dV;
+  double ek = 0, ws = 0, cnt = 0;
+  if (c->cap) {
+    const int q = (int)(c->step & 1);
+    k3_particle_diag<R><<<nb, 256, 0, c->stream>>>(g, c->col0, view3<R>(c, q, 1 - q), c->partials);
+    CK3(cudaGetLastError());
+    CK3(cudaMemcpyAsync(h.data(), c->partials, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nb; ++b) {
+      ek += h[3 * b];
+      ws += h[3 * b + 1];
+      cnt += h[3 * b + 2];
+    }
+  }
+  out->U_K = ek * g.m * dV;
+  out->charge = g.q * ws * dV;
+  out->np = (long long)llround(cnt);
+  pic_status s = deposit_rho3<R>(c, c->rho_a, false);
+  if (s) return s;
+  const bool cont = c->prev_valid && c->cap;
+  if (cont) {
+    s = deposit_rho3<R>(c, c->rho_b, true);
+    if (s) return s;
+  }
+  const int jset = (int)((c->step + 1) & 1);
+  k3_gauss<R><<<nb, 256, 0, c->stream>>>(g, (const R *)c->F, jset, c->rho_a, cont ? c->rho_b : nullptr,
+                                         c->rho_bg, c->partials);
+  CK3(cudaGetLastError());
+  CK3(cudaMemcpyAsync(h.data(), c->partials, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c->stream));
+  DevState hs;
+  CK3(cudaMemcpyAsync(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaStreamSynchronize(c->stream));
+  double gm = 0, cm = 0;
+  for (int b = 0; b < nb; ++b) {
+    gm = std::max(gm, h[2 * b]);
+    cm = std::max(cm, h[2 * b + 1]);
+  }
+  out->gauss = gm;
+  out->continuity = cont ? cm : NAN;
+  out->step = c->step;
+  out->t = c->t;
+  out->shifts = c->nshift;
+  out->max_patch_count = hs.maxcnt[(c->step + 1) & 1];
+  out->capacity = c->cap;
+  out->ms_particles = c->ms_particles;
+  out->ms_fields = c->ms_fields;
+  out->ms_window = c->ms_window;
+  c->launches += 5 + (cont ? 1 : 0);
+  out->launches = c->launches;
+  out->particle_step_launches = c->ps_launches;
+  return poll3(c);
+}
+
+}  // namespace
+
+// --------------------------------------------------------- entry points ----
+
+bool valid_config3(const pic_config *cf, std::string &why) {
+  for (int a = 0; a < 3; ++a) {
+    if (cf->n[a] <= 0 || cf->patch[a] <= 0) { why = "cells and patch sizes must be positive"; return false; }
+    if (cf->patch[a] % 4 || cf->patch[a] > 32) { why = "3D patch sizes must be multiples of 4 up to 32"; return false; }
+    if (cf->n[a] % cf->patch[a]) { why = "cells must be a multiple of the patch size"; return false; }
+    if (!(cf->d[a] > 0)) { why = "cell sizes must be positive"; return false; }
+    if (cf->bc_field[a] != PIC_BC_PERIODIC && cf->bc_field[a] != PIC_BC_SILVER_MULLER) { why = "bad field boundary"; return false; }
+    if (cf->bc_field[a] == PIC_BC_PERIODIC && cf->n[a] < 2 * G3) { why = "periodic axes need at least 8 cells"; return false; }
+    for (int f = 0; f < 2; ++f) {
+      const int b = cf->bc_part[a][f];
+      if (b < 0 || b > 2) { why = "bad particle boundary"; return false; }
+      if ((b == PIC_PBC_PERIODIC) != (cf->bc_field[a] == PIC_BC_PERIODIC)) { why = "periodic particle and field boundaries must pair"; return false; }
+    }
+  }
+  double s = 0.0;
+  for (int a = 0; a < 3; ++a) s += 1.0 / (cf->d[a] * cf->d[a]);
+  if (!(cf->dt > 0) || !(cf->dt * std::sqrt(s) < 1.0)) { why = "dt must satisfy the 3D Courant condition"; return false; }
+  if (cf->filter_passes != 0) { why = "the current filter is a 2D option"; return false; }
+  if (cf->moving_window && cf->inj_ppc[2] < 1) { why = "injected particles per cell must be >= 1"; return false; }
+  const size_t rs = cf->prec == PIC_FP32 ? 4 : 8;
+  if (tile_bytes(cf, rs) > 227 * 1024) { why = "patch current tile exceeds shared memory"; return false; }
+  return true;
+}
+
+size_t footprint3(const pic_config *cf, size_t np_max) {
+  const Geom3 g = make_geom3(cf);
+  const size_t rs = cf->prec == PIC_FP32 ? 4 : 8;
+  const double cfac = cf->capacity_factor > 0 ? cf->capacity_factor : 2.0;
+  const int cmin = cf->capacity_min > 0 ? cf->capacity_min : 256;
+  size_t per = (np_max + g.nslots - 1) / g.nslots;
+  if (cf->moving_window)
+    per = std::max(per, (size_t)g.p[0] * g.p[1] * g.p[2] * cf->inj_ppc[0] * cf->inj_ppc[1] * cf->inj_ppc[2]);
+  int cap = std::max(cmin, (int)std::ceil(cfac * (double)per));
+  cap = (cap + 31) / 32 * 32;
+  return (size_t)NCOMP * g.cs * rs + 3 * sizeof(double) * g.cs + particle_bytes3(g, cap, rs) +
+         sizeof(long long) * ((size_t)g.nslots * (1 + NB3) + 1) + sizeof(double) * 3 * 1024 +
+         sizeof(DevState);
+}
+
+pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std::string &err) {
+  *out = nullptr;
+  Ctx3 *c = new (std::nothrow) Ctx3();
+  if (!c) return PIC_ENOMEM;
+  c->cfg = *cfg;
+  c->g = make_geom3(cfg);
+  c->fp32 = cfg->prec == PIC_FP32;
+  c->rs = c->fp32 ? 4 : 8;
+  c->stream = stream;
+  const Geom3 &g = c->g;
+  auto bail = [&](pic_status s) {
+    err = c->err.empty() ? "device allocation failed" : c->err;
+    c3_destroy(c);
+    return s;
+  };
+  if (cudaMalloc(&c->F, (size_t)NCOMP * g.cs * c->rs) != cudaSuccess) return bail(PIC_ENOMEM);
+  for (double **p : {&c->rho_bg, &c->rho_a, &c->rho_b})
+    if (cudaMalloc(p, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&c->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&c->partials, sizeof(double) * 3 * c->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cfg->laser_on) {
+    std::vector<double> prof((size_t)(g.n[2] + 1) * g.n[1]);
+    for (int k = 0; k <= g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j) {
+        const double ry = ((j + 0.5) * g.d[1] - cfg->laser_y_center) / cfg->laser_waist;
+        const double rz = (k * g.d[2] - cfg->laser_z_center) / cfg->laser_waist;
+        prof[(size_t)k * g.n[1] + j] = cfg->laser_a0 * std::exp(-(ry * ry + rz * rz));
+      }
+    if (cudaMalloc(&c->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cudaMemcpy(c->laser_g, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return bail(PIC_ECUDA);
+  }
+  if (cudaMemsetAsync(c->F, 0, (size_t)NCOMP * g.cs * c->rs, stream) != cudaSuccess ||
+      cudaMemsetAsync(c->rho_bg, 0, sizeof(double) * g.cs, stream) != cudaSuccess ||
+      cudaMemsetAsync(c->st, 0, sizeof(DevState), stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return bail(PIC_ECUDA);
+  *out = c;
+  return PIC_OK;
+}
+
+void c3_destroy(Ctx3 *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_graphs3(c);
+  cudaFree(c->F);
+  cudaFree(c->rho_bg);
+  cudaFree(c->rho_a);
+  cudaFree(c->rho_b);
+  cudaFree(c->laser_g);
+  cudaFree(c->st);
+  cudaFree(c->partials);
+  cudaFree(c->staging);
+  free_particles3(c);
+  delete c;
+}
+
+const char *c3_error(const Ctx3 *c) { return c ? c->err.c_str() : "no context"; }
+
+static pic_status usable3(Ctx3 *c) {
+  if (c->sticky != PIC_OK) return fail3(c, PIC_ESTATE, "context holds a device fault");
+  return PIC_OK;
+}
+
+pic_status c3_load(Ctx3 *c, const double *x, const double *y, const double *z, const double *ux,
+                   const double *uy, const double *uz, const double *w, size_t n, int where) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  const double *src[7] = {x, y, z, ux, uy, uz, w};
+  return c->fp32 ? load3<float>(c, src, n, where) : load3<double>(c, src, n, where);
+}
+
+pic_status c3_fill_plasma(Ctx3 *c) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  if (c->cap) return fail3(c, PIC_ESTATE, "particles are already loaded");
+  for (int a = 0; a < 3; ++a)
+    if (c->cfg.inj_ppc[a] < 1) return fail3(c, PIC_EINVAL, "plasma needs inj_ppc >= 1 on every axis");
+  return c->fp32 ? fill3<float>(c) : fill3<double>(c);
+}
+
+pic_status c3_set_field(Ctx3 *c, int which, const double *src, int where) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  return c->fp32 ? set_field3<float>(c, which, src, where) : set_field3<double>(c, which, src, where);
+}
+
+pic_status c3_get_field(Ctx3 *c, int which, double *dst, int where) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  return c->fp32 ? get_field3<float>(c, which, dst, where) : get_field3<double>(c, which, dst, where);
+}
+
+pic_status c3_set_background(Ctx3 *c, int mode, double value) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  const Geom3 &g = c->g;
+  if (mode == PIC_BG_NONE) {
+    CK3(cudaMemsetAsync(c->rho_bg, 0, sizeof(double) * g.cs, c->stream));
+  } else if (mode == PIC_BG_UNIFORM) {
+    std::vector<double> h((size_t)g.cs, value);
+    CK3(cudaMemcpyAsync(c->rho_bg, h.data(), sizeof(double) * g.cs, cudaMemcpyHostToDevice, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+  } else if (mode == PIC_BG_NEUTRALISING) {
+    CK3(cudaMemsetAsync(c->rho_bg, 0, sizeof(double) * g.cs, c->stream));
+    if (c->cap) {
+      const int q = (int)(c->step & 1);
+      if (c->fp32)
+        k3_deposit_rho<float><<<g.nslots, 256, 0, c->stream>>>(g, c->col0, view3<float>(c, q, 1 - q), c->rho_bg, -1.0);
+      else
+        k3_deposit_rho<double><<<g.nslots, 256, 0, c->stream>>>(g, c->col0, view3<double>(c, q, 1 - q), c->rho_bg, -1.0);
+      CK3(cudaGetLastError());
+      c->launches += 1;
+    }
+  } else {
+    return fail3(c, PIC_EINVAL, "bad background mode");
+  }
+  return poll3(c);
+}
+
+pic_status c3_step(Ctx3 *c, int nsteps) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  if (!c->cap) return fail3(c, PIC_ESTATE, "no particles loaded");
+  return c->fp32 ? run3<float>(c, nsteps) : run3<double>(c, nsteps);
+}
+
+pic_status c3_get_particles(Ctx3 *c, double *out, size_t cap, size_t *n, int where) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  return c->fp32 ? get_particles3<float>(c, out, cap, n, where)
+                 : get_particles3<double>(c, out, cap, n, where);
+}
+
+pic_status c3_diag(Ctx3 *c, pic_diag_t *out) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  return c->fp32 ? diag3<float>(c, out) : diag3<double>(c, out);
+}
+
+pic_status c3_sync(Ctx3 *c) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  return poll3(c);
+}
+
+}  // namespace pic

@@ -78,6 +78,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
                         pic_tune_t *out) {
   if (!cfg || !tuned || !out || steps <= 0 || (where != PIC_HOST && where != PIC_DEVICE))
     return PIC_EINVAL;
+  if (cfg->dims != 2) return PIC_EINVAL;  // tunes the 2D path
   if (n && (!x || !y || !ux || !uy || !uz || !w)) return PIC_EINVAL;
   if (pic_footprint(cfg, n) == 0) return PIC_EINVAL;  // configuration rejected
   const TuneKey key = tune_key(cfg, n);
@@ -269,6 +270,7 @@ pic_status pic_server_create(const pic_server_config *cfg, pic_server **out) {
 pic_status pic_server_submit(pic_server *s, const pic_config *cfg, long long nsteps, int keep,
                              long long *id) {
   if (!s || !cfg || !id || nsteps <= 0) return PIC_EINVAL;
+  if (cfg->dims != 2) return PIC_EINVAL;  // batches hold 2D runs
   if (cfg->inj_ppc[0] < 1 || cfg->inj_ppc[1] < 1) return PIC_EINVAL;
   Request r;
   r.cfg = *cfg;

@@ -27,6 +27,8 @@ FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz", "Jx", "Jy", "
 FBC = {"periodic": 0, "sm": 1}
 PBC = {"periodic": 0, "reflect": 1, "remove": 2}
 BG = {"none": 0, "uniform": 1, "neutralising": 2}
+KEYS2 = ("x", "y", "ux", "uy", "uz", "w")
+KEYS3 = ("x", "y", "z", "ux", "uy", "uz", "w")
 
 
 class pic_config(C.Structure):
@@ -42,6 +44,7 @@ class pic_config(C.Structure):
         ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
         ("sort_every", C.c_int), ("task_chunk", C.c_int), ("filter_passes", C.c_int),
+        ("inj_ymin", C.c_double), ("laser_z_center", C.c_double),
     ]
 
 
@@ -114,7 +117,7 @@ EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_backgro
            "pic_batch_size", "pic_batch_get_diag", "pic_batch_last_error", "pic_batch_destroy",
            "pic_load_plasma", "pic_autotune", "pic_autotune_clear_cache", "pic_server_create",
            "pic_server_submit", "pic_server_tick", "pic_server_info", "pic_server_take",
-           "pic_server_get_stats", "pic_server_clock", "pic_server_destroy"]
+           "pic_server_get_stats", "pic_server_clock", "pic_server_destroy", "pic_load_particles3"]
 
 _lib = None
 
@@ -148,6 +151,8 @@ def lib():
         L.pic_field_energy_noalloc.argtypes = [vp] * 6 + [C.c_int, C.c_int, C.c_double, vp, vp]
         L.pic_field_energy_noalloc.restype = C.c_int
         L.pic_load_plasma.argtypes = [vp]
+        L.pic_load_particles3.argtypes = [vp] + [dp] * 7 + [sz, C.c_int]
+        L.pic_load_particles3.restype = C.c_int
         L.pic_autotune.argtypes = ([C.POINTER(pic_config)] + [dp] * 6 +
                                    [sz, C.c_int, C.c_int, C.POINTER(pic_config), C.POINTER(pic_tune_t)])
         L.pic_autotune_clear_cache.restype = None
@@ -195,14 +200,16 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     task_chunk: int = 0) -> pic_config:
     """pic_config of a run dictionary (see ``workloads``)."""
     c = pic_config()
-    c.dims = 2
-    c.n[0], c.n[1], c.n[2] = run["n"][0], run["n"][1], 1
-    c.d[0], c.d[1], c.d[2] = run["d"][0], run["d"][1], 1.0
+    dims = len(run["n"])
+    c.dims = dims
+    for a in range(3):
+        c.n[a] = run["n"][a] if a < dims else 1
+        c.d[a] = run["d"][a] if a < dims else 1.0
+        c.patch[a] = run["patch"][a] if a < dims else 1
     c.dt = run["dt"]
-    c.patch[0], c.patch[1], c.patch[2] = run["patch"][0], run["patch"][1], 1
     c.prec = PIC_FP32 if prec in ("fp32", PIC_FP32) else PIC_FP64
-    c.bc_field[0], c.bc_field[1] = (FBC[b] for b in run["field_bc"])
-    for a in range(2):
+    for a in range(dims):
+        c.bc_field[a] = FBC[run["field_bc"][a]]
         for f in range(2):
             c.bc_part[a][f] = PBC[run["part_bc"][a][f]]
     c.q = run.get("q", -1.0)
@@ -212,6 +219,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
         c.laser_on = 1
         c.laser_a0, c.laser_waist, c.laser_tau = las["a0"], las["waist"], las["tau"]
         c.laser_t_peak, c.laser_y_center = las["t_peak"], las["y_center"]
+        c.laser_z_center = las.get("z_center", 0.0)
     mw = run.get("moving_window")
     if mw:
         c.moving_window = 1
@@ -219,7 +227,9 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     inj = run.get("injection")
     if inj:
         c.inj_n0, c.inj_x0, c.inj_ramp = inj["n0"], inj["x0"], inj["ramp"]
-        c.inj_ppc[0], c.inj_ppc[1], c.inj_ppc[2] = inj["ppc"][0], inj["ppc"][1], 1
+        ppc = tuple(inj["ppc"]) + (1,) * (3 - len(inj["ppc"]))
+        c.inj_ppc[0], c.inj_ppc[1], c.inj_ppc[2] = ppc
+        c.inj_ymin = inj.get("ymin", 0.0)
     else:
         c.inj_ppc[0] = c.inj_ppc[1] = c.inj_ppc[2] = 1
     c.capacity_factor = capacity_factor
@@ -255,6 +265,11 @@ def _ptr(a):
     raise TypeError(type(a))
 
 
+def _field_shape(cfg: pic_config):
+    dims = 3 if cfg.dims == 3 else 2
+    return tuple(cfg.n[a] + (0 if cfg.bc_field[a] == 0 else 2) for a in reversed(range(dims)))
+
+
 class Pic:
     """One libpic context (C-ABI calls with argument marshalling)."""
 
@@ -262,8 +277,7 @@ class Pic:
         self.cfg = cfg
         self.h = C.c_void_p()
         self._check(lib().pic_create(C.byref(cfg), C.byref(self.h)), create=True)
-        nx, ny = cfg.n[0], cfg.n[1]
-        self.shape = (ny if cfg.bc_field[1] == 0 else ny + 2, nx if cfg.bc_field[0] == 0 else nx + 2)
+        self.shape = _field_shape(cfg)
 
     @classmethod
     def adopt(cls, h, cfg: pic_config) -> "Pic":
@@ -271,8 +285,7 @@ class Pic:
         self = cls.__new__(cls)
         self.cfg = cfg
         self.h = h
-        nx, ny = cfg.n[0], cfg.n[1]
-        self.shape = (ny if cfg.bc_field[1] == 0 else ny + 2, nx if cfg.bc_field[0] == 0 else nx + 2)
+        self.shape = _field_shape(cfg)
         return self
 
     def _check(self, rc, create=False):
@@ -293,9 +306,11 @@ class Pic:
 
     # -- C-ABI calls
     def pic_load_particles(self, p: dict):
-        """Particles as a dict of float64 arrays (numpy: host, torch CUDA: device)."""
+        """Particles as a dict of float64 arrays (numpy: host, torch CUDA:
+        device); 3D contexts take "z" too (pic_load_particles3)."""
+        keys = KEYS3 if self.cfg.dims == 3 else KEYS2
         arrs = []
-        for k in ("x", "y", "ux", "uy", "uz", "w"):
+        for k in keys:
             a = p[k]
             if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
                 a = np.ascontiguousarray(a, dtype=np.float64)
@@ -303,7 +318,8 @@ class Pic:
         ptrs = [_ptr(a) for a in arrs]
         where = ptrs[0][1]
         n = int(arrs[0].shape[0])
-        self._check(lib().pic_load_particles(self.h, *[q for q, _ in ptrs], n, where))
+        fn = lib().pic_load_particles3 if self.cfg.dims == 3 else lib().pic_load_particles
+        self._check(fn(self.h, *[q for q, _ in ptrs], n, where))
 
     def pic_load_plasma(self):
         """Fill the domain with the configuration's plasma profile on the device."""
@@ -334,10 +350,11 @@ class Pic:
         n = C.c_size_t()
         self._check(lib().pic_get_particles(self.h, None, 0, C.byref(n), PIC_HOST))
         cap = max(n.value, 1)
-        out = np.empty((6, cap), dtype=np.float64)
+        keys = KEYS3 if self.cfg.dims == 3 else KEYS2
+        out = np.empty((len(keys), cap), dtype=np.float64)
         self._check(lib().pic_get_particles(self.h, out.ctypes.data, cap, C.byref(n), PIC_HOST))
         m = n.value
-        return {k: out[i, :m].copy() for i, k in enumerate(("x", "y", "ux", "uy", "uz", "w"))}
+        return {k: out[i, :m].copy() for i, k in enumerate(keys)}
 
     def pic_diag(self) -> dict:
         d = pic_diag_t()

@@ -97,6 +97,36 @@ def test_invalid_configs_rejected_before_cuda(libpic, mutate):
     assert pic.pic_footprint(cfg, 1000) == 0
 
 
+@pytest.mark.parametrize("mutate", [
+    lambda c: c.patch.__setitem__(2, 64),            # 3D patches up to 32
+    lambda c: setattr(c, "filter_passes", 1),        # the filter is 2D only
+    lambda c: setattr(c, "dt", 0.3),                 # 3D Courant condition
+    lambda c: c.n.__setitem__(2, 4),                 # periodic axis below 8 cells
+    lambda c: setattr(c, "dims", 4),
+])
+def test_invalid_3d_configs_rejected_before_cuda(libpic, mutate):
+    run = W.periodic_run3((32, 16, 16), (0.1, 0.1, 0.1), (8, 8, 8))
+    cfg = pic.config_from_run(run, "fp64")
+    assert pic.pic_footprint(cfg, 1000) > 0
+    if mutate is not None:
+        mutate(cfg)
+        if cfg.n[2] == 4:
+            cfg.patch[2] = 4
+    h = C.c_void_p()
+    assert libpic.pic_create(C.byref(cfg), C.byref(h)) == pic.PIC_EINVAL
+    assert not h.value
+
+
+def test_footprint_3d_counts_26_buckets(libpic):
+    """The config-3 grid: footprint grows with the particle count and the
+    precision, and fits the device (the FP32 run with capacity factor 2)."""
+    run = W.lwfa_3d()
+    f32 = pic.pic_footprint(pic.config_from_run(run, "fp32", capacity_factor=2.0), 1 << 26)
+    f64 = pic.pic_footprint(pic.config_from_run(run, "fp64", capacity_factor=2.0), 1 << 26)
+    assert 0 < f32 < f64 < 2 * f32 + 1
+    assert f32 < 100e9
+
+
 def test_laser_and_window_need_open_x(libpic):
     run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
     cfg = pic.config_from_run(run, "fp64")
