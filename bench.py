@@ -18,6 +18,7 @@ One JSON line is printed on rank 0:
   e2e          the same metric through the C-ABI from host buffers:
                H2D of the initial particles, K steps, D2H of fields and
                particles inside the timed region
+  lwfa3d       the 3D3V config (1024x256x256, 67 M electrons, FP32)
   serving      the served ensemble (FP32 runs of four grid sizes, Poisson
                arrivals at 70% of the measured capacity, continuous
                batching): p50/p99 latency from arrival, throughput
@@ -223,6 +224,55 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     }
 
 
+def run_gpu3(prec, steps, warmup, spinup, device, cf=2.0):
+    """Config 3 (3D3V LWFA-shaped): 1024 x 256 x 256 cells, 16^3 patches,
+    plasma of 0.005 n_c filling the upper half of the transverse box (2 ppc,
+    67 108 864 electrons, filled on the device), laser a0 = 3 waist 15,
+    moving window; `spinup` untimed steps, `warmup`, then `steps` timed
+    steps (graph replay, CUDA events on the library's stream), then the same
+    steps replayed from a fresh run with per-phase timers."""
+    import torch
+
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    run = W.lwfa_3d()
+    ncell = run["n"][0] * run["n"][1] * run["n"][2]
+    rs = 4 if prec == "fp32" else 8
+    stream = torch.cuda.Stream(device=device)
+    g = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
+                                    capacity_factor=cf))
+    g.pic_load_plasma()
+    g.pic_step(spinup + warmup)
+    d0 = g.pic_diag()
+    torch.cuda.synchronize(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.pic_step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    d1 = g.pic_diag()
+    g.close()
+    gt = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
+                                     capacity_factor=cf, timing=True))
+    gt.pic_load_plasma()
+    gt.pic_step(spinup + warmup)
+    t0 = gt.pic_diag()
+    gt.pic_step(steps)
+    t1 = gt.pic_diag()
+    gt.close()
+    np_mean = 0.5 * (d0["np"] + d1["np"])
+    step_bytes = np_mean * 13 * rs + ncell * 27 * rs
+    ps_ms = (t1["ms_particles"] - t0["ms_particles"]) / steps
+    return {"value": np_mean * steps / (ms / 1e3), "ms_per_step": ms / steps, "np": np_mean,
+            "cells": ncell, "step_bytes": step_bytes, "particle_step_ms": ps_ms,
+            "fields_ms": (t1["ms_fields"] - t0["ms_fields"]) / steps,
+            "kernel_bytes": np_mean * 13 * rs + ncell * 9 * rs,
+            "launches": d1["launches"] - d0["launches"] - 5, "t": d1["t"]}
+
+
 def run_e2e(prec, steps, device):
     """Through the public C-ABI from host buffers: initial particles H2D,
     `steps` steps, fields and particles D2H, all inside the timed region."""
@@ -377,6 +427,8 @@ def main():
                     help="patch capacity / fullest initial patch")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="arrival window of the served-ensemble measurement (0: skip)")
+    ap.add_argument("--steps3d", type=int, default=40,
+                    help="timed steps of the 3D3V config-3 leg (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -425,6 +477,7 @@ def main():
                       world, dist, args.capacity_factor, -1, args.sort_every, args.task_chunk)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
     serving = run_serving(local, args.serve_seconds) if args.serve_seconds > 0 else None
+    r3 = run_gpu3("fp32", args.steps3d, 3, 20, local) if args.steps3d > 0 else None
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
         dist.barrier()
@@ -473,6 +526,22 @@ def main():
                                f"{e2e['steps']} steps from t=0, D2H of E, B and all particles")
     if serving:
         line["serving"] = serving
+    if r3:
+        line["lwfa3d"] = {
+            "workload": ("3D3V LWFA-shaped: 1024x256x256 cells, dx=0.125, dy=dz=0.5 c/w0, "
+                         "dt=0.95 CFL, 16^3-cell patches, 0.005 n_c in the upper half of the "
+                         "transverse box, 2 ppc (67108864 electrons), immobile ions, laser a0=3 "
+                         "waist 15, moving window at c"),
+            "dtype": "f32", "value": r3["value"], "unit": "particle-steps/s",
+            "ms_per_step": r3["ms_per_step"], "steps": args.steps3d,
+            "spinup_steps": 20, "warmup": 3, "t_end": r3["t"],
+            "particle_step_ms": r3["particle_step_ms"], "fields_ms": r3["fields_ms"],
+            "roofline": {"bound": "hbm", "peak": hbm, "unit": "GB/s",
+                         "achieved_whole_step": r3["step_bytes"] / (r3["ms_per_step"] * 1e-3) / 1e9,
+                         "frac_whole_step": r3["step_bytes"] / (r3["ms_per_step"] * 1e-3) / 1e9 / hbm,
+                         "achieved_particle_step": r3["kernel_bytes"] / (r3["particle_step_ms"] * 1e-3) / 1e9,
+                         "frac_particle_step": r3["kernel_bytes"] / (r3["particle_step_ms"] * 1e-3) / 1e9 / hbm,
+                         "bytes_per_step": r3["step_bytes"]}}
     if cpu:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
