@@ -70,6 +70,10 @@ struct pic_ctx {
   long long sorts = 0;
   long long since_sort = 0;
   Ctx3 *c3 = nullptr;  // dims = 3: the 3D context (pic3d.cu)
+  // the next step's work plan is built beside the field update on `aux`
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool plan_ready = false;  // the plan for the current parity is built
 };
 
 namespace {
@@ -359,10 +363,13 @@ FieldArgs<R> field_args(const pic_ctx *ctx, int p) {
   return f;
 }
 
-// One step on the context's stream: the patch particle step, then the region
-// field update.  `mid` (optional) is recorded between the two phases.
+// One step on the context's stream: the patch particle step (its work plan
+// first when with_plan), then the region field update, beside which the
+// next step's work plan is built on the auxiliary stream (it reads only the
+// particle counts the step just wrote).  `mid` (optional) is recorded
+// between the two phases.
 template <typename R>
-pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
+pic_status enqueue_step(pic_ctx *ctx, int parity, bool with_plan, cudaEvent_t mid = nullptr) {
   const Geom &g = ctx->g;
   const StepArgs<R> a = step_args<R>(ctx, parity);
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
@@ -372,9 +379,14 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, cudaEvent_t mid = nullptr) {
     if (ctx->ps_grid <= 0) return fail(ctx, PIC_ECUDA, "particle step occupancy query failed");
   }
   CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,
-                             ctx->stream));
+                             with_plan, ctx->stream));
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
+  CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  CK(launch_plan<R>(step_args<R>(ctx, 1 - parity), ctx->aux));
+  CK(cudaEventRecord(ctx->ev_join, ctx->aux));
   CK(launch_fields<R>(field_args<R>(ctx, parity), ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
   return PIC_OK;
 }
 
@@ -410,6 +422,7 @@ pic_status window_shift(pic_ctx *ctx) {
   CK(cudaGetLastError());
   ctx->launches += 7;
   ctx->prev_valid = false;
+  ctx->plan_ready = false;  // particle counts changed
   return PIC_OK;
 }
 
@@ -423,7 +436,7 @@ pic_status capture_graphs(pic_ctx *ctx) {
   for (int p = 0; p < 2; ++p) {
     cudaGraph_t gr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    pic_status s = enqueue_step<R>(ctx, p);
+    pic_status s = enqueue_step<R>(ctx, p, false);  // replays follow a built plan
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
     if (s != PIC_OK) return s;
     CK(e);
@@ -537,6 +550,7 @@ pic_status restore_backup(pic_ctx *ctx, int new_cap) {
   ctx->nshift = b.nshift;
   ctx->col0 = b.col0;
   ctx->prev_valid = false;
+  ctx->plan_ready = false;
   ctx->sticky = PIC_OK;
   ctx->launches += 1;
   return PIC_OK;
@@ -554,6 +568,7 @@ pic_status sort_particles(pic_ctx *ctx) {
   ctx->launches += 2;
   ctx->sorts += 1;
   ctx->prev_valid = false;
+  ctx->plan_ready = false;
   return PIC_OK;
 }
 
@@ -622,18 +637,25 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
     }
     ctx->since_sort += 1;
     if (use_graph) {
+      if (!ctx->plan_ready) {
+        CK(launch_plan<R>(step_args<R>(ctx, p), ctx->stream));
+        ctx->launches += 1;
+      }
       CK(cudaGraphLaunch(ctx->gexec[p], ctx->stream));
     } else if (timing) {
       cudaEvent_t e[3];
       for (int k = 0; k < 3; ++k) CK(new_event(&e[k]));
       CK(cudaEventRecord(e[0], ctx->stream));
-      rs = enqueue_step<R>(ctx, p, e[1]);
+      rs = enqueue_step<R>(ctx, p, !ctx->plan_ready, e[1]);
       CK(cudaEventRecord(e[2], ctx->stream));
       for (int k = 0; k < 3; ++k) ev.push_back(e[k]);
       kind.push_back(0);
+      if (!ctx->plan_ready) ctx->launches += 1;
     } else {
-      rs = enqueue_step<R>(ctx, p);
+      rs = enqueue_step<R>(ctx, p, !ctx->plan_ready);
+      if (!ctx->plan_ready) ctx->launches += 1;
     }
+    ctx->plan_ready = true;
     ctx->launches += kernels_per_step(ctx);
     ctx->ps_launches += 1;
     ctx->step += 1;
@@ -743,6 +765,7 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
     cudaFree(tmp);
   }
   ctx->prev_valid = false;
+  ctx->plan_ready = false;
   free_graphs(ctx);  // capacity and buffers are baked into captured graphs
   return poll_device(ctx);
 }
@@ -771,6 +794,7 @@ pic_status do_fill(pic_ctx *ctx) {
     ctx->since_sort = 0;
   }
   ctx->prev_valid = false;
+  ctx->plan_ready = false;
   free_graphs(ctx);
   return poll_device(ctx);
 }
@@ -1260,6 +1284,7 @@ pic_status batch_step(pic_batch *b, int nsteps) {
       c->step += 1;
       c->t += c->g.dt;
       c->prev_valid = true;
+      c->plan_ready = false;
       c->ps_launches += 1;
       if (rs == PIC_OK && window_due(c)) {
         // the shift runs on the batch's stream, between batched steps
@@ -1352,6 +1377,10 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
     *out = ctx;
     return PIC_OK;
   }
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(PIC_ECUDA);
   if (cudaMalloc(&ctx->F, field_bytes(g, ctx->rs)) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&ctx->rho_bg, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&ctx->rho_a, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
@@ -1384,6 +1413,12 @@ void pic_destroy(pic_ctx *ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   c3_destroy(ctx->c3);
   ctx->c3 = nullptr;
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   free_graphs(ctx);
   cudaFree(ctx->F);
   cudaFree(ctx->rho_bg);
@@ -1621,6 +1656,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   ctx->nshift = h.nshift;
   ctx->col0 = h.col0;
   ctx->prev_valid = h.prev_valid != 0;
+  ctx->plan_ready = false;
   ctx->sticky = PIC_OK;
   ctx->err.clear();
   return PIC_OK;

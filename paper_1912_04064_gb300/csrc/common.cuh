@@ -237,11 +237,15 @@ struct StepArgs {
   Plan plan;
 };
 
-// Build the plan (and clear the output counts), then run the persistent
-// particle step with `grid` blocks.
+// Clear the output counts and run the persistent particle step with `grid`
+// blocks; plan = true builds the step's work plan first (otherwise the plan
+// was built ahead, by launch_plan, beside the previous field update).
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 bool merge, int block, int grid, cudaStream_t s);
+                                 bool merge, int block, int grid, bool plan, cudaStream_t s);
+// The work plan of the step described by a (reads its input counts only).
+template <typename R>
+cudaError_t launch_plan(const StepArgs<R> &a, cudaStream_t s);
 // Blocks of the particle step resident on the device at once.
 template <typename R>
 int particle_step_grid(int P, int Q, bool tma, bool merge, int block);
@@ -318,7 +322,7 @@ cudaError_t launch_filter(const FieldArgs<R> &a, int src, int dst, cudaStream_t 
 template <typename R>
 cudaError_t launch_fields_batch(const FieldArgs<R> *fa, const BatchGrid grid[4], cudaStream_t s);
 // Blocks per run of the batched field kernels (gx, gy for k = 0..2; the
-// Silver-Mueller kernel is 1D: gx blocks, gy = 1).
+// Silver-Mueller kernel: gx blocks per face, gy = 4 faces).
 void field_batch_blocks(const Geom &g, int filter_passes, int gx[4], int gy[4]);
 
 // Field I/O and utilities.

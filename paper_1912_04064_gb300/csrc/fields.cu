@@ -159,28 +159,23 @@ __device__ __forceinline__ void update_B(const FieldArgs<R> &a, int blk_x, int b
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void set_ghost(const Geom &g, R *B, R *Bm, int i, int j, R v) {
-  const long long o = fidx(g, i, j);
-  const R old = Bm[o];  // = B^{n+1/2} at this ghost after k_update_B
-  B[o] = v;
-  mirror(g, B, o, i, j, v);
-  const R m = R(0.5) * (old + v);
-  Bm[o] = m;
-  mirror(g, Bm, o, i, j, m);
-}
-
 // Ghost B on open faces from the discrete Silver-Mueller condition; the
 // coefficients 1/(1+r), 1-r and the transverse dt/d are precomputed.  The
 // laser Ey_inc(y, t) = profile(y) * envelope(t) carrier(t): the transverse
 // profile is a precomputed array, the temporal factor is evaluated once per
-// block at t_{n+3/2} (retarded by the window's displacement).
+// block at t_{n+3/2} (retarded by the window's displacement).  One thread
+// per face point, faces in parallel (face = 0 x_min, 1 x_max, 2 y_min,
+// 3 y_max): no face reads a value another face writes, and every load is
+// issued before the ghost stores.
 template <typename R>
-__device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, double &s_h) {
+__device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, int face,
+                                               double &s_h) {
   const Geom &g = a.g;
+  const bool xface = face < 2, upper = (face & 1) != 0;
+  if (xface ? g.fbc_x != FBC_SM : g.fbc_y != FBC_SM) return;  // uniform per block
   if (threadIdx.x == 0) {
     double h = 0.0;
-    if (a.laser_on) {
+    if (a.laser_on && face == 0) {
       const double t = a.st->t[a.parity] + 1.5 * g.dt;
       const double tr = t - (double)(a.st->nshift * g.P) * g.dx - a.t_peak;
       h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
@@ -195,45 +190,70 @@ __device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, do
   R *Bx = F + C_BX * cs, *By = F + C_BY * cs, *Bz = F + C_BZ * cs;
   R *Bmx = F + C_BMX * cs, *Bmy = F + C_BMY * cs, *Bmz = F + C_BMZ * cs;
   const Ranges rg = ranges(g);
-  if (g.fbc_x == FBC_SM && t < rg.nyp) {
+  if (xface) {
+    if (t >= rg.nyp) return;
     const int j = t, nx = g.nx;
+    const int ib = upper ? nx : 0, in = upper ? nx - 1 : 0, gh = upper ? nx : -1;
     const R ia = a.smx_inv1pr, b = a.smx_1mr, c = a.smx_dtt;
     const bool inter = g.fbc_y == FBC_PERIODIC || (j >= 1 && j <= g.ny - 1);
-    R dBx0 = R(0), dBxn = R(0);
-    if (inter) {
-      dBx0 = Bx[fidx(g, 0, j)] - Bx[fidx(g, 0, j - 1)];
-      dBxn = Bx[fidx(g, nx, j)] - Bx[fidx(g, nx, j - 1)];
+    const bool hasz = j < rg.nyd;
+    const R dBx = inter ? Bx[fidx(g, ib, j)] - Bx[fidx(g, ib, j - 1)] : R(0);
+    const R ez = Ez[fidx(g, ib, j)], byi = By[fidx(g, in, j)];
+    const R ey = hasz ? Ey[fidx(g, ib, j)] : R(0), bzi = hasz ? Bz[fidx(g, in, j)] : R(0);
+    const long long og = fidx(g, gh, j);
+    const R by_old = Bmy[og], bz_old = hasz ? Bmz[og] : R(0);
+    R by, bz;
+    if (!upper) {
+      const R eyinc = (a.laser_on && hasz) ? R(a.laser_g[j] * s_h) : R(0);
+      by = (R(2) * ez - b * byi - c * dBx) * ia;
+      bz = (R(4) * eyinc - R(2) * ey - b * bzi) * ia;
+    } else {
+      by = (R(-2) * ez - b * byi + c * dBx) * ia;
+      bz = (R(2) * ey - b * bzi) * ia;
     }
-    const R by_lo = (R(2) * Ez[fidx(g, 0, j)] - b * By[fidx(g, 0, j)] - c * dBx0) * ia;
-    const R by_hi = (R(-2) * Ez[fidx(g, nx, j)] - b * By[fidx(g, nx - 1, j)] + c * dBxn) * ia;
-    set_ghost(g, By, Bmy, -1, j, by_lo);
-    set_ghost(g, By, Bmy, nx, j, by_hi);
-    if (j < rg.nyd) {
-      const R eyinc = a.laser_on ? R(a.laser_g[j] * s_h) : R(0);
-      const R bz_lo = (R(4) * eyinc - R(2) * Ey[fidx(g, 0, j)] - b * Bz[fidx(g, 0, j)]) * ia;
-      const R bz_hi = (R(2) * Ey[fidx(g, nx, j)] - b * Bz[fidx(g, nx - 1, j)]) * ia;
-      set_ghost(g, Bz, Bmz, -1, j, bz_lo);
-      set_ghost(g, Bz, Bmz, nx, j, bz_hi);
+    By[og] = by;
+    mirror(g, By, og, gh, j, by);
+    const R mby = R(0.5) * (by_old + by);
+    Bmy[og] = mby;
+    mirror(g, Bmy, og, gh, j, mby);
+    if (hasz) {
+      Bz[og] = bz;
+      mirror(g, Bz, og, gh, j, bz);
+      const R mbz = R(0.5) * (bz_old + bz);
+      Bmz[og] = mbz;
+      mirror(g, Bmz, og, gh, j, mbz);
     }
-  }
-  if (g.fbc_y == FBC_SM && t < rg.nxp) {
+  } else {
+    if (t >= rg.nxp) return;
     const int i = t, ny = g.ny;
+    const int jb = upper ? ny : 0, jn = upper ? ny - 1 : 0, gh = upper ? ny : -1;
     const R ia = a.smy_inv1pr, b = a.smy_1mr, c = a.smy_dtt;
     const bool inter = g.fbc_x == FBC_PERIODIC || (i >= 1 && i <= g.nx - 1);
-    R dBy0 = R(0), dByn = R(0);
-    if (inter) {
-      dBy0 = By[fidx(g, i, 0)] - By[fidx(g, i - 1, 0)];
-      dByn = By[fidx(g, i, ny)] - By[fidx(g, i - 1, ny)];
+    const bool hasz = i < rg.nxd;
+    const R dBy = inter ? By[fidx(g, i, jb)] - By[fidx(g, i - 1, jb)] : R(0);
+    const R ez = Ez[fidx(g, i, jb)], bxi = Bx[fidx(g, i, jn)];
+    const R ex = hasz ? Ex[fidx(g, i, jb)] : R(0), bzi = hasz ? Bz[fidx(g, i, jn)] : R(0);
+    const long long og = fidx(g, i, gh);
+    const R bx_old = Bmx[og], bz_old = hasz ? Bmz[og] : R(0);
+    R bx, bz;
+    if (!upper) {
+      bx = (R(-2) * ez - b * bxi - c * dBy) * ia;
+      bz = (R(2) * ex - b * bzi) * ia;
+    } else {
+      bx = (R(2) * ez - b * bxi + c * dBy) * ia;
+      bz = (R(-2) * ex - b * bzi) * ia;
     }
-    const R bx_lo = (R(-2) * Ez[fidx(g, i, 0)] - b * Bx[fidx(g, i, 0)] - c * dBy0) * ia;
-    const R bx_hi = (R(2) * Ez[fidx(g, i, ny)] - b * Bx[fidx(g, i, ny - 1)] + c * dByn) * ia;
-    set_ghost(g, Bx, Bmx, i, -1, bx_lo);
-    set_ghost(g, Bx, Bmx, i, ny, bx_hi);
-    if (i < rg.nxd) {
-      const R bz_lo = (R(2) * Ex[fidx(g, i, 0)] - b * Bz[fidx(g, i, 0)]) * ia;
-      const R bz_hi = (R(-2) * Ex[fidx(g, i, ny)] - b * Bz[fidx(g, i, ny - 1)]) * ia;
-      set_ghost(g, Bz, Bmz, i, -1, bz_lo);
-      set_ghost(g, Bz, Bmz, i, ny, bz_hi);
+    Bx[og] = bx;
+    mirror(g, Bx, og, i, gh, bx);
+    const R mbx = R(0.5) * (bx_old + bx);
+    Bmx[og] = mbx;
+    mirror(g, Bmx, og, i, gh, mbx);
+    if (hasz) {
+      Bz[og] = bz;
+      mirror(g, Bz, og, i, gh, bz);
+      const R mbz = R(0.5) * (bz_old + bz);
+      Bmz[og] = mbz;
+      mirror(g, Bmz, og, i, gh, mbz);
     }
   }
 }
@@ -301,7 +321,7 @@ __global__ void __launch_bounds__(YBX * YBY) k_update_B(const FieldArgs<R> a) {
 template <typename R>
 __global__ void k_silver_mueller(const FieldArgs<R> a) {
   __shared__ double s_h;
-  silver_mueller(a, blockIdx.x, s_h);
+  silver_mueller(a, blockIdx.x, blockIdx.y, s_h);
 }
 template <typename R, int NP>
 __global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R> a, int src,
@@ -339,7 +359,7 @@ __global__ void k_silver_mueller_batch(const FieldArgs<R> *fa, const BatchGrid b
   __shared__ double s_h;
   int bx, by;
   const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
-  silver_mueller(a, bx, s_h);
+  silver_mueller(a, bx, by, s_h);
 }
 template <typename R>
 __global__ void __launch_bounds__(YBX * YBY) k_filter_current_batch(const FieldArgs<R> *fa,
@@ -503,7 +523,7 @@ cudaError_t launch_fields(const FieldArgs<R> &a, cudaStream_t s) {
   k_update_B<R><<<dim3((ncol + YBX - 1) / YBX, (nrow + YBY - 1) / YBY), blk, 0, s>>>(a);
   if (g.fbc_x == FBC_SM || g.fbc_y == FBC_SM) {
     const int n = (g.nx > g.ny ? g.nx : g.ny) + 1;
-    k_silver_mueller<R><<<(n + 63) / 64, 64, 0, s>>>(a);
+    k_silver_mueller<R><<<dim3((n + 63) / 64, 4), 64, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -524,7 +544,7 @@ void field_batch_blocks(const Geom &g, int filter_passes, int gx[4], int gy[4]) 
   gx[3] = gy[3] = 0;
   if (g.fbc_x == FBC_SM || g.fbc_y == FBC_SM) {
     gx[3] = ((g.nx > g.ny ? g.nx : g.ny) + 1 + 63) / 64;
-    gy[3] = 1;
+    gy[3] = 4;  // one row of blocks per face
   }
 }
 

@@ -210,6 +210,13 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     __syncthreads();
     if (!s_ok) break;
     const int totalq = min(ufirst + plan.chunk, s_qoff[9]);
+    // A patch whose staged E and Bm are exactly zero (plasma the laser has
+    // not reached yet): a particle at rest there stays at rest, in place,
+    // and deposits nothing (exactly what the full step computes), so it is
+    // copied through without the interpolation, push and deposit.
+    int nonzero = 0;
+    for (int e = tid; e < 6 * FT; e += nth) nonzero |= Ft[e] != R(0);
+    const bool quiet = __syncthreads_or(nonzero) == 0;
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -259,7 +266,11 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     for (int m = 0; m < M; ++m) {
       int dir = -2;  // -1 stay, -2 gone / invalid, 0..7 bucket
       R x1 = R(0), y1 = R(0), nux = R(0), nuy = R(0), nuz = R(0);
-      if (m < nval) {
+      if (m < nval && quiet && ux[m] == R(0) && uy[m] == R(0) && uz[m] == R(0)) {
+        x1 = x[m];
+        y1 = y[m];
+        dir = -1;
+      } else if (m < nval) {
         // interpolation at x^n with the shape of each component's stagger
         int ip, id, jp, jd;
         R Sxp[3], Sxd[3], Syp[3], Syd[3];
@@ -454,7 +465,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 constexpr int PLAN_CLASSES = 64;
 
 template <typename R, bool BATCH>
-__global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const BatchRef<R> br) {
+__global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const BatchRef<R> br,
+                                               bool zero_out) {
   __shared__ int hist[PLAN_CLASSES], off[PLAN_CLASSES];
   const int tid = threadIdx.x, nth = blockDim.x;
   const Plan &plan = BATCH ? br.plan : a0.plan;
@@ -475,8 +487,10 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
       if (src >= 0) units += (min(a.bcnt_in[(long long)src * 8 + d], a.bk.cap[d]) + u - 1) / u;
     }
     plan.units[f] = units;
-    a.cnt_out[s] = 0;
-    for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
+    if (zero_out) {
+      a.cnt_out[s] = 0;
+      for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
+    }
     const int items = (units + plan.chunk - 1) / plan.chunk;
     if (items) atomicAdd(&hist[min(items, PLAN_CLASSES) - 1], items);
   }
@@ -580,10 +594,23 @@ int particle_step_batch_grid(int P, int Q, bool tma, int block, size_t smem) {
 }
 
 template <typename R>
-cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
-                                 bool merge, int block, int grid, cudaStream_t s) {
+cudaError_t launch_plan(const StepArgs<R> &a, cudaStream_t s) {
   BatchRef<R> none{};
-  k_plan<R, false><<<1, 1024, 0, s>>>(a, none);
+  k_plan<R, false><<<1, 1024, 0, s>>>(a, none, false);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
+                                 bool merge, int block, int grid, bool plan, cudaStream_t s) {
+  if (plan) {
+    const cudaError_t e = launch_plan<R>(a, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemsetAsync(a.cnt_out, 0, sizeof(int) * a.g.nslots, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.bcnt_out, 0, sizeof(int) * 8 * a.g.nslots, s);
+  if (e != cudaSuccess) return e;
+  BatchRef<R> none{};
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
   const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge);
   TmapSet<1> tm;
@@ -599,7 +626,7 @@ cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatc
                                        int P, int Q, bool tma, int block, int grid,
                                        size_t smem, cudaStream_t s) {
   StepArgs<R> none{};
-  k_plan<R, true><<<1, 1024, 0, s>>>(none, b);
+  k_plan<R, true><<<1, 1024, 0, s>>>(none, b, true);
   const void *k = pick_kernel<R>(P, Q, tma, false, true);
   void *args[] = {(void *)tm, (void *)&none, (void *)&b};
   return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
@@ -614,10 +641,12 @@ template cudaError_t prepare_particle_step<double>(int, int);
 template cudaError_t prepare_particle_step_batch<float>(int, int, size_t);
 template cudaError_t prepare_particle_step_batch<double>(int, int, size_t);
 template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const CUtensorMap *,
-                                                 bool, bool, int, int, cudaStream_t);
+                                                 bool, bool, int, int, bool, cudaStream_t);
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
-                                                  const CUtensorMap *, bool, bool, int, int,
+                                                  const CUtensorMap *, bool, bool, int, int, bool,
                                                   cudaStream_t);
+template cudaError_t launch_plan<float>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_plan<double>(const StepArgs<double> &, cudaStream_t);
 template cudaError_t launch_particle_step_batch<float>(const BatchRef<float> &,
                                                        const TmapSet<kBatchMax> *, int, int,
                                                        bool, int, int, size_t, cudaStream_t);
