@@ -151,6 +151,7 @@ struct Step3 {
   R cj[3];   // -q d / dt
   R RP[3];   // patch size as reals
   Plan plan;
+  const int *active;  // per physical patch: E or Bm nonzero on one of its cells
 };
 
 template <typename R>
@@ -164,7 +165,34 @@ struct Field3 {
   int laser_on;
   const double *laser_g;                // [nz + 1][ny]: a0 exp(-r^2 / w^2) at Ey's nodes
   double tau, t_peak;
+  int *active;                          // per physical patch, set by k3_update_B
 };
+
+// Mark the physical patch of cell (i, j, k) (inside the domain) active when
+// v is nonzero; one flag read per cell, an atomic only for the first mark.
+__device__ __forceinline__ void mark_active(const Geom3 &g, int *active, int i, int j, int k,
+                                            bool v) {
+  if (!v || i < 0 || j < 0 || k < 0 || i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  const int p = ((k / g.p[2]) * g.np[1] + j / g.p[1]) * g.np[0] + i / g.p[0];
+  if (!*(volatile int *)&active[p]) atomicOr(&active[p], 1);
+}
+
+// A patch is quiet when neither it nor any of its 26 neighbours holds a
+// nonzero E or Bm on its cells and it touches no open face (whose ghost
+// values its stencils also read): every interpolation stencil of the patch
+// then reads only zeros.
+__device__ __forceinline__ bool patch_quiet(const Geom3 &g, const int *active, const int pc[3]) {
+  for (int ax = 0; ax < 3; ++ax)
+    if (g.fbc[ax] != FBC_PERIODIC && (pc[ax] == 0 || pc[ax] == g.np[ax] - 1)) return false;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int q[3] = {(pc[0] + dx + g.np[0]) % g.np[0], (pc[1] + dy + g.np[1]) % g.np[1],
+                          (pc[2] + dz + g.np[2]) % g.np[2]};
+        if (active[(q[2] * g.np[1] + q[1]) * g.np[0] + q[0]]) return false;
+      }
+  return true;
+}
 
 // --------------------------------------------------------------- plan ----
 
@@ -292,6 +320,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
     }
     __syncthreads();
     const int total = min(ufirst + a.plan.chunk, s_qoff[NB3 + 1]);
+    // particles at rest in a quiet patch stay at rest, in place, and deposit
+    // nothing: exactly what the full step computes
+    const bool quiet = patch_quiet(g, a.active, pc);
     for (int qb = ufirst; qb < total; qb += nth) {
       const int qi = qb + tid;
       int dir = -2;  // -1 stay, -2 none, 0..25 bucket
@@ -307,6 +338,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
         const R x0[3] = {A.x[b], A.y[b], A.z[b]};
         R u[3] = {A.ux[b], A.uy[b], A.uz[b]};
         w = A.w[b];
+        if (quiet && u[0] == R(0) && u[1] == R(0) && u[2] == R(0)) {
+          x1[0] = x0[0];
+          x1[1] = x0[1];
+          x1[2] = x0[2];
+          dir = -1;
+        } else {
         // interpolation: primal and dual stencils per axis
         int ip[3], id[3];
         R Sp[3][3], Sd[3][3];
@@ -337,6 +374,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
         bool finite = true, slow = true;
         R S0[3][4], DS[3][4];
         int org[3];
+        bool x4[3];  // the window spans all four nodes along the axis
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
           x1[ax] = x0[ax] + a.rd[ax] * nu[ax] * inv;
@@ -352,35 +390,41 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
 #pragma unroll
           for (int c = 0; c < 4; ++c) DS[ax][c] = S1[c] - S0[ax][c];
           org[ax] = ip[ax] - 1 - (sh ? 1 : 0) + 2;  // window origin in the tile
+          x4[ax] = di != 0;
         }
         if (!finite) err |= ERR_NONFINITE;
         else if (!slow) err |= ERR_FAST;
         if (finite && slow) {
-          // Esirkepov: component c, prefix along c, A over the other two
+          // Esirkepov: component c, prefix along c, A over the other two.
+          // Along an axis where the particle kept its nearest node the
+          // window's node 3 carries no shape (S0 = DS = 0 there) and the
+          // prefix -DS[3] vanishes: those entries are skipped, as is a
+          // whole component when the particle did not move along it.
+          const int st3[3] = {1, JW, JW * JH};
+          const int base = (org[2] * JH + org[1]) * JW + org[0];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
             const R cw = a.cj[c] * w;
-            const R Pf[3] = {cw * DS[c][0], cw * (DS[c][0] + DS[c][1]), -cw * DS[c][3]};
-            R *J = Jt + c * JT;
+            const R P0 = cw * DS[c][0], P1 = cw * (DS[c][0] + DS[c][1]), P2 = -cw * DS[c][3];
+            if (P0 == R(0) && P1 == R(0) && P2 == R(0)) continue;
+            R *J = Jt + c * JT + base;
+            const int sc = st3[c], s1 = st3[b1], s2 = st3[b2];
+            const bool w1 = x4[b1], w2 = x4[b2], wc = x4[c];
 #pragma unroll
-            for (int m2 = 0; m2 < 4; ++m2)
+            for (int m2 = 0; m2 < 4; ++m2) {
+              if (m2 == 3 && !w2) continue;
 #pragma unroll
               for (int m1 = 0; m1 < 4; ++m1) {
+                if (m1 == 3 && !w1) continue;
                 const R A = S0[b1][m1] * (S0[b2][m2] + R(0.5) * DS[b2][m2]) +
                             DS[b1][m1] * (R(0.5) * S0[b2][m2] + R(1.0 / 3.0) * DS[b2][m2]);
-                if (A == R(0)) continue;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                  const R v = Pf[q] * A;
-                  if (v == R(0)) continue;
-                  int t[3];
-                  t[c] = org[c] + q;
-                  t[b1] = org[b1] + m1;
-                  t[b2] = org[b2] + m2;
-                  atomicAdd(&J[(t[2] * JH + t[1]) * JW + t[0]], v);
-                }
+                R *row = J + m1 * s1 + m2 * s2;
+                atomicAdd(row, P0 * A);
+                atomicAdd(row + sc, P1 * A);
+                if (wc) atomicAdd(row + 2 * sc, P2 * A);
               }
+            }
           }
           // boundary conditions, destination patch
           int dd[3];
@@ -412,6 +456,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
             }
             dir = (dd[0] == 0 && dd[1] == 0 && dd[2] == 0) ? -1 : dir26(dd[0], dd[1], dd[2]);
           }
+        }
         }
       }
       const bool stay = dir == -1;
@@ -550,6 +595,25 @@ __global__ void __launch_bounds__(256) k3_update_B(const Field3<R> a) {
   mirror3(g, Bmx, i, j, k, mx);
   mirror3(g, Bmy, i, j, k, my);
   mirror3(g, Bmz, i, j, k, mz);
+  mark_active(g, a.active, i, j, k,
+              mx != R(0) || my != R(0) || mz != R(0) || Ex[o] != R(0) || Ey[o] != R(0) ||
+                  Ez[o] != R(0));
+}
+
+// Active flags from the stored fields (after any change outside a step:
+// loading, setting fields, a window shift).
+template <typename R>
+__global__ void k3_scan_active(const Geom3 g, const R *F, int *active) {
+  const long long nc = (long long)g.n[0] * g.n[1] * g.n[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nc;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.n[0]), j = (int)((e / g.n[0]) % g.n[1]);
+    const int k = (int)(e / ((long long)g.n[0] * g.n[1]));
+    const long long o = fidx3(g, i, j, k);
+    bool nz = false;
+    for (int c = 0; c < 6; ++c) nz = nz || F[(long long)c * g.cs + o] != R(0);
+    mark_active(g, active, i, j, k, nz);
+  }
 }
 
 template <typename R>
@@ -1088,6 +1152,8 @@ struct Ctx3 {
   int ps_grid = 0;
   size_t ps_smem = 0;
   DevState *st = nullptr;
+  int *active = nullptr;       // per physical patch: nonzero E or Bm on its cells
+  bool active_valid = false;   // the flags describe the stored fields
   double *partials = nullptr;
   int npartials = 1024;
   long long *offsets = nullptr;
@@ -1290,6 +1356,7 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   }
   a.eps = R(g.q * g.dt / (2.0 * g.m));
   a.plan = c->plan;
+  a.active = c->active;
   return a;
 }
 
@@ -1313,6 +1380,7 @@ Field3<R> field_args3(Ctx3 *c, int p) {
   f.laser_g = c->laser_g;
   f.tau = c->cfg.laser_tau;
   f.t_peak = c->cfg.laser_t_peak;
+  f.active = c->active;
   return f;
 }
 
@@ -1328,6 +1396,7 @@ pic_status enqueue_step3(Ctx3 *c, int p, cudaEvent_t mid = nullptr) {
   int npn[3];
   for (int ax = 0; ax < 3; ++ax) npn[ax] = g.n[ax] + (g.fbc[ax] == FBC_SM);
   k3_update_E<R><<<dim3((npn[0] + 31) / 32, (npn[1] + 7) / 8, npn[2]), dim3(32, 8), 0, c->stream>>>(f);
+  CK3(cudaMemsetAsync(c->active, 0, sizeof(int) * g.nslots, c->stream));  // marked again by B
   k3_update_B<R><<<dim3((g.n[0] + 2 * G3 + 31) / 32, (g.n[1] + 2 * G3 + 7) / 8, g.n[2] + 2 * G3),
                    dim3(32, 8), 0, c->stream>>>(f);
   if (g.fbc[0] == FBC_SM || g.fbc[1] == FBC_SM || g.fbc[2] == FBC_SM) {
@@ -1371,6 +1440,7 @@ pic_status window_shift3(Ctx3 *c) {
   CK3(cudaGetLastError());
   c->launches += 6;
   c->prev_valid = false;
+  c->active_valid = false;  // the fields moved
   return PIC_OK;
 }
 
@@ -1425,6 +1495,13 @@ pic_status run3(Ctx3 *c, int nsteps) {
   pic_status rs = PIC_OK;
   for (int n = 0; n < nsteps && rs == PIC_OK; ++n) {
     const int p = (int)(c->step & 1);
+    if (!c->active_valid) {
+      CK3(cudaMemsetAsync(c->active, 0, sizeof(int) * c->g.nslots, c->stream));
+      k3_scan_active<R><<<1024, 256, 0, c->stream>>>(c->g, (const R *)c->F, c->active);
+      CK3(cudaGetLastError());
+      c->launches += 1;
+      c->active_valid = true;
+    }
     if (use_graph) {
       CK3(cudaGraphLaunch(c->gexec[p], c->stream));
     } else if (timing) {
@@ -1660,6 +1737,7 @@ pic_status set_field3(Ctx3 *c, int which, const double *src, int where) {
   CK3(cudaGetLastError());
   c->launches += 1;
   c->prev_valid = false;
+  c->active_valid = false;
   return poll3(c);
 }
 
@@ -1848,6 +1926,7 @@ pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std
   for (double **p : {&c->rho_bg, &c->rho_a, &c->rho_b})
     if (cudaMalloc(p, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&c->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&c->active, sizeof(int) * g.nslots) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&c->partials, sizeof(double) * 3 * c->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cfg->laser_on) {
     std::vector<double> prof((size_t)(g.n[2] + 1) * g.n[1]);
@@ -1881,6 +1960,7 @@ void c3_destroy(Ctx3 *c) {
   cudaFree(c->rho_b);
   cudaFree(c->laser_g);
   cudaFree(c->st);
+  cudaFree(c->active);
   cudaFree(c->partials);
   cudaFree(c->staging);
   free_particles3(c);
