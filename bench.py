@@ -240,8 +240,12 @@ def run_gpu3(prec, steps, warmup, spinup, device, cf=2.0):
     ncell = run["n"][0] * run["n"][1] * run["n"][2]
     rs = 4 if prec == "fp32" else 8
     stream = torch.cuda.Stream(device=device)
+    # the config's 16^3 SDMD patches set the window step (16 cells); the GPU
+    # stores particles in 16 x 8 x 8 sub-patches so that a patch's E and Bm
+    # tile (70 KB) and current tile (43 KB) fit in shared memory
+    sub = (16, 8, 8)
     g = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                                    capacity_factor=cf))
+                                    capacity_factor=cf, patch=sub))
     g.pic_load_plasma()
     g.pic_step(spinup + warmup)
     d0 = g.pic_diag()
@@ -256,7 +260,7 @@ def run_gpu3(prec, steps, warmup, spinup, device, cf=2.0):
     d1 = g.pic_diag()
     g.close()
     gt = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                                     capacity_factor=cf, timing=True))
+                                     capacity_factor=cf, timing=True, patch=sub))
     gt.pic_load_plasma()
     gt.pic_step(spinup + warmup)
     t0 = gt.pic_diag()
@@ -530,7 +534,8 @@ def main():
     if r3:
         line["lwfa3d"] = {
             "workload": ("3D3V LWFA-shaped: 1024x256x256 cells, dx=0.125, dy=dz=0.5 c/w0, "
-                         "dt=0.95 CFL, 16^3-cell patches, 0.005 n_c in the upper half of the "
+                         "dt=0.95 CFL, 16^3-cell patches (window step 16 cells; stored as "
+                         "16x8x8 GPU sub-patches), 0.005 n_c in the upper half of the "
                          "transverse box, 2 ppc (67108864 electrons), immobile ions, laser a0=3 "
                          "waist 15, moving window at c"),
             "dtype": "f32", "value": r3["value"], "unit": "particle-steps/s",

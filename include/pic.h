@@ -137,6 +137,12 @@ typedef struct pic_config {
                              J before the field update (2D only) */
   double inj_ymin;        /* 3D plasma: lower y bound of the filled cells */
   double laser_z_center;  /* 3D laser: z of the beam axis */
+  int window_cells;       /* moving-window step in cells, a multiple of
+                             patch[0] (0 = patch[0]): the window advances
+                             window_cells / patch[0] patch columns at once,
+                             so the patch size (a performance choice) and
+                             the window step (part of the run) are set
+                             apart; pic_diag's shifts counts window steps */
 } pic_config;
 
 typedef struct pic_diag_t {

@@ -108,6 +108,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool valid_config(const pic_config *c, std::string &why) {
   if (!c) { why = "null config"; return false; }
   if (c->dims != 2 && c->dims != 3) { why = "dims must be 2 (2D3V) or 3 (3D3V)"; return false; }
+  if (c->window_cells < 0 || (c->window_cells > 0 && c->window_cells % c->patch[0])) {
+    why = "window_cells must be a multiple of patch[0]";
+    return false;
+  }
   if (c->dims == 3) {
     if (!valid_config3(c, why)) return false;
     if (c->prec != PIC_FP64 && c->prec != PIC_FP32) { why = "bad precision"; return false; }
@@ -426,9 +430,15 @@ pic_status window_shift(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+// Patch columns per window step.
+int window_columns(const pic_config &c) {
+  return c.window_cells > 0 ? c.window_cells / c.patch[0] : 1;
+}
+
 bool window_due(const pic_ctx *c) {
+  const int m = window_columns(c->cfg);
   return c->cfg.moving_window && c->t > c->cfg.mw_t0 &&
-         c->t - c->cfg.mw_t0 >= (c->nshift + 1) * (double)c->g.P * c->g.dx;
+         c->t - c->cfg.mw_t0 >= (c->nshift / m + 1) * (double)m * c->g.P * c->g.dx;
 }
 
 template <typename R>
@@ -667,7 +677,7 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
         for (int k = 0; k < 2; ++k) CK(new_event(&e[k]));
         CK(cudaEventRecord(e[0], ctx->stream));
       }
-      rs = window_shift<R>(ctx);
+      for (int k = 0; k < window_columns(ctx->cfg) && rs == PIC_OK; ++k) rs = window_shift<R>(ctx);
       if (timing) {
         CK(cudaEventRecord(e[1], ctx->stream));
         ev.push_back(e[0]);
@@ -1022,7 +1032,7 @@ pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
   out->continuity = cont ? cm : NAN;
   out->step = ctx->step;
   out->t = ctx->t;
-  out->shifts = ctx->nshift;
+  out->shifts = ctx->nshift / window_columns(ctx->cfg);
   out->max_patch_count = hs.maxcnt[(ctx->step + 1) & 1];
   out->capacity = ctx->cap;
   out->grows = ctx->grows;
@@ -1290,7 +1300,7 @@ pic_status batch_step(pic_batch *b, int nsteps) {
         // the shift runs on the batch's stream, between batched steps
         cudaStream_t own = c->stream;
         c->stream = b->stream;
-        rs = window_shift<R>(c);
+        for (int k = 0; k < window_columns(c->cfg) && rs == PIC_OK; ++k) rs = window_shift<R>(c);
         c->stream = own;
         if (rs) rs = bfail(b, rs, c->err);
         b->launches += 7;

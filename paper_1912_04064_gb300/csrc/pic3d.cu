@@ -26,6 +26,8 @@
 // and cyclically; J_a = -q w (d_a / dt) x prefix sum of W_a along axis a.
 // The prefix sums along the 4-node window are DS0, DS0 + DS1 and -DS3 (the
 // sum of DS is zero).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -198,16 +200,20 @@ __device__ __forceinline__ bool patch_quiet(const Geom3 &g, const int *active, c
 
 constexpr int PLAN3_CLASSES = 64;
 
+// Work plan in two grid-wide passes (a 3D grid has up to 10^5 patch slots).
+// Pass 1: units per slot (segment plus the 26 incoming buckets, clamped to
+// the capacities), items per slot, a histogram of item counts per class;
+// the step's output counts are cleared.
 template <typename R>
-__global__ void __launch_bounds__(1024) k3_plan(const Step3<R> a) {
-  __shared__ int hist[PLAN3_CLASSES], off[PLAN3_CLASSES];
+__global__ void __launch_bounds__(256) k3_plan_count(const Step3<R> a, int *hist) {
+  __shared__ int h[PLAN3_CLASSES];
   const Geom3 &g = a.g;
   const Plan &plan = a.plan;
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x;
   const int col0 = a.st->col0;
-  for (int c = tid; c < PLAN3_CLASSES; c += nth) hist[c] = 0;
+  for (int c = tid; c < PLAN3_CLASSES; c += blockDim.x) h[c] = 0;
   __syncthreads();
-  for (int s = tid; s < g.nslots; s += nth) {
+  for (int s = blockIdx.x * blockDim.x + tid; s < g.nslots; s += gridDim.x * blockDim.x) {
     int units = min(a.cnt_in[s], a.cap);
     for (int d = 0; d < NB3; ++d) {
       int dx, dy, dz;
@@ -219,23 +225,39 @@ __global__ void __launch_bounds__(1024) k3_plan(const Step3<R> a) {
     a.cnt_out[s] = 0;
     for (int d = 0; d < NB3; ++d) a.bcnt_out[(long long)s * NB3 + d] = 0;
     const int items = (units + plan.chunk - 1) / plan.chunk;
-    if (items) atomicAdd(&hist[min(items, PLAN3_CLASSES) - 1], items);
+    if (items) atomicAdd(&h[min(items, PLAN3_CLASSES) - 1], items);
   }
   __syncthreads();
+  for (int c = tid; c < PLAN3_CLASSES; c += blockDim.x)
+    if (h[c]) atomicAdd(&hist[c], h[c]);
+}
+
+// Pass 2: items laid out by class, heaviest first (class offsets from the
+// histogram, positions within a class from a per-class cursor).
+template <typename R>
+__global__ void __launch_bounds__(256) k3_plan_place(const Step3<R> a, const int *hist,
+                                                     int *cursor) {
+  __shared__ int off[PLAN3_CLASSES];
+  const Geom3 &g = a.g;
+  const Plan &plan = a.plan;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     int run = 0;
     for (int c = PLAN3_CLASSES - 1; c >= 0; --c) {
       off[c] = run;
       run += hist[c];
     }
-    *plan.n_items = min(run, plan.max_items);
-    *plan.next = 0;
+    if (blockIdx.x == 0) {
+      *plan.n_items = min(run, plan.max_items);
+      *plan.next = 0;
+    }
   }
   __syncthreads();
-  for (int s = tid; s < g.nslots; s += nth) {
+  for (int s = blockIdx.x * blockDim.x + tid; s < g.nslots; s += gridDim.x * blockDim.x) {
     const int items = (plan.units[s] + plan.chunk - 1) / plan.chunk;
     if (!items) continue;
-    const int base = atomicAdd(&off[min(items, PLAN3_CLASSES) - 1], items);
+    const int c = min(items, PLAN3_CLASSES) - 1;
+    const int base = off[c] + atomicAdd(&cursor[c], items);
     for (int k = 0; k < items && base + k < plan.max_items; ++k) {
       plan.item_slot[base + k] = s;
       plan.item_first[base + k] = k * plan.chunk;
@@ -265,22 +287,55 @@ __device__ __forceinline__ R gather27(const R *__restrict__ F, const Geom3 &g, i
   return acc;
 }
 
+// 27-point interpolation from a staged tile (row stride BX, plane stride
+// BX * BY); (i0, j0, k0) is the stencil's first node in tile indices.
 template <typename R>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_step(const Step3<R> a) {
+__device__ __forceinline__ R gather27t(const R *T, int BX, int BY, int i0, int j0, int k0,
+                                       const R Sx[3], const R Sy[3], const R Sz[3]) {
+  const R *p = T + (k0 * BY + j0) * BX + i0;
+  R acc = R(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R pl = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const R *r = p + (c * BY + b) * BX;
+      pl += Sy[b] * (Sx[0] * r[0] + Sx[1] * r[1] + Sx[2] * r[2]);
+    }
+    acc += Sz[c] * pl;
+  }
+  return acc;
+}
+
+template <typename R, bool STAGED>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
+    k3_particle_step(const __grid_constant__ CUtensorMap tmap, const Step3<R> a) {
+  // STAGED: the patch's E and Bm (nodes -4..P+3 along x, -1..Q+1, -1..R+1)
+  // are staged into shared memory by one 4D TMA box (SDMD step (ii)) and
+  // gathered there; otherwise gathered from the region in HBM.
   extern __shared__ unsigned char dsm3[];
+  __shared__ uint64_t mbar;
   __shared__ int s_qoff[NB3 + 2];
   __shared__ int s_cnt[NB3 + 1];
   __shared__ long long s_base[NB3 + 1];
   __shared__ int s_item;
+  __shared__ int s_ok;
   const Geom3 &g = a.g;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
   const int P = g.p[0], Q = g.p[1], Rz = g.p[2];
   const int JW = P + 5, JH = Q + 5, JD = Rz + 5, JT = JW * JH * JD;
+  const int BX = P + 8, BY = Q + 3, BZ = Rz + 3, FT = BX * BY * BZ;
   const uint32_t pad = (128u - (smem_u32(dsm3) & 127u)) & 127u;
-  R *Jt = reinterpret_cast<R *>(dsm3 + pad);
+  R *Ft = reinterpret_cast<R *>(dsm3 + pad);
+  R *Jt = STAGED ? Ft + 6 * FT : Ft;
   const int n_items = *a.plan.n_items;
   const R eps = a.eps;
   unsigned err = 0;
+  uint32_t phase = 0;
+  if (STAGED && tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
   for (;;) {
     __syncthreads();
     if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
@@ -293,6 +348,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
     int pc[3];
     slot_patch(g, col0, s, pc[0], pc[1], pc[2]);
     const int X0 = pc[0] * P, Y0 = pc[1] * Q, Z0 = pc[2] * Rz;
+    if (STAGED && tid == 0) {
+      mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
+      tma_load_4d(Ft, &tmap, &mbar, X0 - 4 + G3, Y0 - 1 + G3, Z0 - 1 + G3, 0);
+    }
     for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
     if (tid < NB3 + 1) {
       int cnt = 0;
@@ -317,8 +376,22 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
     if (tid == 0) {
       s_qoff[0] = 0;
       for (int i = 0; i <= NB3; ++i) s_qoff[i + 1] = s_qoff[i] + s_cnt[i];
+      int ok = 1;
+      if (STAGED) {
+        ok = 0;
+        for (long long it = 0; it < WAIT_POLLS; ++it)
+          if (mbar_try_wait(&mbar, phase)) { ok = 1; break; }
+        if (!ok) {
+          atomicOr(&a.st->err, ERR_TIMEOUT);
+          for (long long it = 0; it < DRAIN_POLLS; ++it)
+            if (mbar_try_wait(&mbar, phase)) break;
+        }
+      }
+      s_ok = ok;
     }
+    phase ^= 1u;
     __syncthreads();
+    if (!s_ok) break;
     const int total = min(ufirst + a.plan.chunk, s_qoff[NB3 + 1]);
     // particles at rest in a quiet patch stay at rest, in place, and deposit
     // nothing: exactly what the full step computes
@@ -351,14 +424,26 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1)) k3_particle_ste
         for (int ax = 0; ax < 3; ++ax) shapes(x0[ax], ip[ax], Sp[ax], id[ax], Sd[ax]);
         const int gp[3] = {X0 + ip[0] - 1, Y0 + ip[1] - 1, Z0 + ip[2] - 1};
         const int gd[3] = {X0 + id[0] - 1, Y0 + id[1] - 1, Z0 + id[2] - 1};
-        const R *F = a.F;
-        const long long cs = g.cs;
-        const R Ex = gather27(F + C_EX * cs, g, gd[0], gp[1], gp[2], Sd[0], Sp[1], Sp[2]);
-        const R Ey = gather27(F + C_EY * cs, g, gp[0], gd[1], gp[2], Sp[0], Sd[1], Sp[2]);
-        const R Ez = gather27(F + C_EZ * cs, g, gp[0], gp[1], gd[2], Sp[0], Sp[1], Sd[2]);
-        const R Bx = gather27(F + C_BMX * cs, g, gp[0], gd[1], gd[2], Sp[0], Sd[1], Sd[2]);
-        const R By = gather27(F + C_BMY * cs, g, gd[0], gp[1], gd[2], Sd[0], Sp[1], Sd[2]);
-        const R Bz = gather27(F + C_BMZ * cs, g, gd[0], gd[1], gp[2], Sd[0], Sd[1], Sp[2]);
+        R Ex, Ey, Ez, Bx, By, Bz;
+        if (STAGED) {
+          // tile index of patch-relative node (x, y, z): x + 4, y + 1, z + 1
+          const int tp[3] = {ip[0] + 3, ip[1], ip[2]}, td[3] = {id[0] + 3, id[1], id[2]};
+          Ex = gather27t(Ft, BX, BY, td[0], tp[1], tp[2], Sd[0], Sp[1], Sp[2]);
+          Ey = gather27t(Ft + FT, BX, BY, tp[0], td[1], tp[2], Sp[0], Sd[1], Sp[2]);
+          Ez = gather27t(Ft + 2 * FT, BX, BY, tp[0], tp[1], td[2], Sp[0], Sp[1], Sd[2]);
+          Bx = gather27t(Ft + 3 * FT, BX, BY, tp[0], td[1], td[2], Sp[0], Sd[1], Sd[2]);
+          By = gather27t(Ft + 4 * FT, BX, BY, td[0], tp[1], td[2], Sd[0], Sp[1], Sd[2]);
+          Bz = gather27t(Ft + 5 * FT, BX, BY, td[0], td[1], tp[2], Sd[0], Sd[1], Sp[2]);
+        } else {
+          const R *F = a.F;
+          const long long cs = g.cs;
+          Ex = gather27(F + C_EX * cs, g, gd[0], gp[1], gp[2], Sd[0], Sp[1], Sp[2]);
+          Ey = gather27(F + C_EY * cs, g, gp[0], gd[1], gp[2], Sp[0], Sd[1], Sp[2]);
+          Ez = gather27(F + C_EZ * cs, g, gp[0], gp[1], gd[2], Sp[0], Sp[1], Sd[2]);
+          Bx = gather27(F + C_BMX * cs, g, gp[0], gd[1], gd[2], Sp[0], Sd[1], Sd[2]);
+          By = gather27(F + C_BMY * cs, g, gd[0], gp[1], gd[2], Sd[0], Sp[1], Sd[2]);
+          Bz = gather27(F + C_BMZ * cs, g, gd[0], gd[1], gp[2], Sd[0], Sd[1], Sp[2]);
+        }
         // Boris push u^{n-1/2} -> u^{n+1/2}
         const R umx = u[0] + eps * Ex, umy = u[1] + eps * Ey, umz = u[2] + eps * Ez;
         const R ig = eps * rsq(R(1) + umx * umx + umy * umy + umz * umz);
@@ -1151,8 +1236,11 @@ struct Ctx3 {
   Plan plan{};
   int ps_grid = 0;
   size_t ps_smem = 0;
+  bool staged = false;   // E and Bm tiles staged into shared memory by TMA
+  CUtensorMap tmap{};
   DevState *st = nullptr;
   int *active = nullptr;       // per physical patch: nonzero E or Bm on its cells
+  int *plan_hist = nullptr;    // class histogram and cursors of the work plan
   bool active_valid = false;   // the flags describe the stored fields
   double *partials = nullptr;
   int npartials = 1024;
@@ -1388,8 +1476,14 @@ template <typename R>
 pic_status enqueue_step3(Ctx3 *c, int p, cudaEvent_t mid = nullptr) {
   const Geom3 &g = c->g;
   const Step3<R> a = step_args3<R>(c, p);
-  k3_plan<R><<<1, 1024, 0, c->stream>>>(a);
-  k3_particle_step<R><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(a);
+  CK3(cudaMemsetAsync(c->plan_hist, 0, sizeof(int) * 2 * PLAN3_CLASSES, c->stream));
+  const int pb = std::min(1024, (g.nslots + 255) / 256);
+  k3_plan_count<R><<<pb, 256, 0, c->stream>>>(a, c->plan_hist);
+  k3_plan_place<R><<<pb, 256, 0, c->stream>>>(a, c->plan_hist, c->plan_hist + PLAN3_CLASSES);
+  if (c->staged)
+    k3_particle_step<R, true><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(c->tmap, a);
+  else
+    k3_particle_step<R, false><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(c->tmap, a);
   CK3(cudaGetLastError());
   if (mid) CK3(cudaEventRecord(mid, c->stream));
   const Field3<R> f = field_args3<R>(c, p);
@@ -1413,7 +1507,7 @@ pic_status enqueue_step3(Ctx3 *c, int p, cudaEvent_t mid = nullptr) {
 
 int kernels_per_step3(const Ctx3 *c) {
   const Geom3 &g = c->g;
-  return 4 + ((g.fbc[0] == FBC_SM || g.fbc[1] == FBC_SM || g.fbc[2] == FBC_SM) ? 1 : 0);
+  return 5 + ((g.fbc[0] == FBC_SM || g.fbc[1] == FBC_SM || g.fbc[2] == FBC_SM) ? 1 : 0);
 }
 
 template <typename R>
@@ -1444,21 +1538,61 @@ pic_status window_shift3(Ctx3 *c) {
   return PIC_OK;
 }
 
+int window_columns3(const pic_config &c) {
+  return c.window_cells > 0 ? c.window_cells / c.patch[0] : 1;
+}
+
 bool window_due3(const Ctx3 *c) {
+  const int m = window_columns3(c->cfg);
   return c->cfg.moving_window && c->t > c->cfg.mw_t0 &&
-         c->t - c->cfg.mw_t0 >= (c->nshift + 1) * (double)c->g.p[0] * c->g.d[0];
+         c->t - c->cfg.mw_t0 >= (c->nshift / m + 1) * (double)m * c->g.p[0] * c->g.d[0];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode3() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
 }
 
 template <typename R>
 pic_status prepare3(Ctx3 *c) {
   if (c->ps_grid) return PIC_OK;
-  c->ps_smem = tile_bytes(&c->cfg, sizeof(R));
-  CK3(cudaFuncSetAttribute(k3_particle_step<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)c->ps_smem));
+  const Geom3 &g = c->g;
+  const size_t field_tile = (size_t)6 * (g.p[0] + 8) * (g.p[1] + 3) * (g.p[2] + 3) * sizeof(R);
+  const size_t staged_smem = field_tile + tile_bytes(&c->cfg, sizeof(R));
+  auto enc = encode3();
+  c->staged = c->cfg.tma != 0 && enc && staged_smem <= 227 * 1024;
+  if (c->staged) {
+    // 4D box (x, y, z, component) over E and Bm, components 0..5
+    cuuint64_t dims[4] = {(cuuint64_t)g.sx, (cuuint64_t)g.sy, (cuuint64_t)g.sz, 6};
+    cuuint64_t strides[3] = {(cuuint64_t)g.sx * sizeof(R), (cuuint64_t)g.sx * g.sy * sizeof(R),
+                             (cuuint64_t)g.cs * sizeof(R)};
+    cuuint32_t box[4] = {(cuuint32_t)(g.p[0] + 8), (cuuint32_t)(g.p[1] + 3),
+                         (cuuint32_t)(g.p[2] + 3), 6};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = enc(&c->tmap,
+                           sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           4, c->F, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) c->staged = false;
+  }
+  c->ps_smem = c->staged ? staged_smem : tile_bytes(&c->cfg, sizeof(R));
+  const void *k = c->staged ? (const void *)k3_particle_step<R, true>
+                            : (const void *)k3_particle_step<R, false>;
+  CK3(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->ps_smem));
   int per_sm = 0, dev = 0, nsm = 0;
   CK3(cudaGetDevice(&dev));
   CK3(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_particle_step<R>, 256, c->ps_smem));
+  CK3(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, c->ps_smem));
   if (per_sm <= 0) return fail3(c, PIC_EINVAL, "the patch current tile does not fit in shared memory");
   c->ps_grid = per_sm * nsm;
   return PIC_OK;
@@ -1526,7 +1660,7 @@ pic_status run3(Ctx3 *c, int nsteps) {
         for (int k = 0; k < 2; ++k) CK3(cudaEventCreate(&e[k]));
         CK3(cudaEventRecord(e[0], c->stream));
       }
-      rs = window_shift3<R>(c);
+      for (int k = 0; k < window_columns3(c->cfg) && rs == PIC_OK; ++k) rs = window_shift3<R>(c);
       if (timing) {
         CK3(cudaEventRecord(e[1], c->stream));
         ev.push_back(e[0]);
@@ -1852,7 +1986,7 @@ pic_status diag3(Ctx3 *c, pic_diag_t *out) {
   out->continuity = cont ? cm : NAN;
   out->step = c->step;
   out->t = c->t;
-  out->shifts = c->nshift;
+  out->shifts = c->nshift / window_columns3(c->cfg);
   out->max_patch_count = hs.maxcnt[(c->step + 1) & 1];
   out->capacity = c->cap;
   out->ms_particles = c->ms_particles;
@@ -1927,6 +2061,7 @@ pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std
     if (cudaMalloc(p, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&c->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&c->active, sizeof(int) * g.nslots) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cudaMalloc(&c->plan_hist, sizeof(int) * 2 * PLAN3_CLASSES) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cudaMalloc(&c->partials, sizeof(double) * 3 * c->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cfg->laser_on) {
     std::vector<double> prof((size_t)(g.n[2] + 1) * g.n[1]);
@@ -1961,6 +2096,7 @@ void c3_destroy(Ctx3 *c) {
   cudaFree(c->laser_g);
   cudaFree(c->st);
   cudaFree(c->active);
+  cudaFree(c->plan_hist);
   cudaFree(c->partials);
   cudaFree(c->staging);
   free_particles3(c);

@@ -44,7 +44,7 @@ class pic_config(C.Structure):
         ("stream", C.c_void_p), ("device", C.c_int), ("use_graph", C.c_int), ("timing", C.c_int),
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
         ("sort_every", C.c_int), ("task_chunk", C.c_int), ("filter_passes", C.c_int),
-        ("inj_ymin", C.c_double), ("laser_z_center", C.c_double),
+        ("inj_ymin", C.c_double), ("laser_z_center", C.c_double), ("window_cells", C.c_int),
     ]
 
 
@@ -197,15 +197,17 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     use_graph: bool = True, timing: bool = False, tma: bool = True,
                     capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0,
                     merge: int = -1, auto_grow: bool = True, sort_every: int = 0,
-                    task_chunk: int = 0) -> pic_config:
-    """pic_config of a run dictionary (see ``workloads``)."""
+                    task_chunk: int = 0, patch=None) -> pic_config:
+    """pic_config of a run dictionary (see ``workloads``); `patch` overrides
+    the run's patch size (the window step stays the run's patch width
+    unless the run names its own ``moving_window["cells"]``)."""
     c = pic_config()
     dims = len(run["n"])
     c.dims = dims
     for a in range(3):
         c.n[a] = run["n"][a] if a < dims else 1
         c.d[a] = run["d"][a] if a < dims else 1.0
-        c.patch[a] = run["patch"][a] if a < dims else 1
+        c.patch[a] = (patch or run["patch"])[a] if a < dims else 1
     c.dt = run["dt"]
     c.prec = PIC_FP32 if prec in ("fp32", PIC_FP32) else PIC_FP64
     for a in range(dims):
@@ -224,6 +226,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     if mw:
         c.moving_window = 1
         c.mw_t0 = mw["t0"]
+        c.window_cells = int(mw.get("cells", run["patch"][0] if patch else 0))
     inj = run.get("injection")
     if inj:
         c.inj_n0, c.inj_x0, c.inj_ramp = inj["n0"], inj["x0"], inj["ramp"]

@@ -78,8 +78,10 @@ def _assert(errs, tol):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("patch", [(8, 8, 8), (16, 8, 4), (4, 8, 16)])
+@pytest.mark.parametrize("patch", [(8, 8, 8), (16, 8, 4), (4, 8, 16), (16, 16, 16)])
 def test_single_step_fp64_periodic(patch):
+    """Patches whose E and Bm tile fits in shared memory stage it by TMA;
+    16^3 (a 208 KB FP32 tile) gathers from HBM through L1."""
     run = W.periodic_run3((32, 16, 16), (0.1, 0.12, 0.15), patch)
     parts = W.small_random_particles3(run, 30000, seed=1, uth=0.5)
     fields = W.random_fields(W.field_shape3(run), seed=2, amp=0.1)
@@ -163,6 +165,27 @@ def test_moving_window_upper_half_plasma_fp64():
     _assert(field_errs(o, g, EB), 1e-9)
     _assert(particle_errs(o, g), 1e-9)
     assert dg["gauss"] <= 1e-9 + 1e-9 * do["gauss"]
+
+
+def test_window_step_decoupled_from_patch_size():
+    """GPU patches of 8^3 with a 16-cell window step equal the oracle run
+    with 16^3 patches (whose window steps one 16-cell patch column)."""
+    run = W.lwfa_3d(n=(64, 32, 16), d=(0.125, 0.5, 0.5), patch=(16, 16, 16), ppc=(2, 1, 1),
+                    n0=0.01, ramp=3.0, a0=1.0, waist=4.0, tau=3.0, t_mw=0.5)
+    run["laser"]["t_peak"] = 4.0
+    o = Oracle3(run, track_continuity=True)
+    o.fill_plasma()
+    g = pic.Pic(pic.config_from_run(run, "fp64", patch=(8, 8, 8)))
+    assert g.cfg.window_cells == 16
+    g.pic_load_plasma()
+    nsteps = 2 * math.ceil(16 * 0.125 / run["dt"]) + 6
+    for _ in range(nsteps):
+        o.step(1)
+        g.pic_step(1)
+    do, dg = o.diag(), g.pic_diag()
+    assert do["shifts"] >= 2 and dg["shifts"] == do["shifts"] and dg["np"] == do["np"]
+    _assert(field_errs(o, g, EB), 1e-9)
+    _assert(particle_errs(o, g), 1e-9)
 
 
 def test_fp32_single_step_bounds():

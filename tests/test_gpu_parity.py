@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.oracle import poisson_periodic
+from oracle.oracle import Oracle, poisson_periodic
 from paper_1912_04064_gb300 import pic
 from paper_1912_04064_gb300 import workloads as W
 
@@ -149,6 +149,32 @@ def test_moving_window_fp64():
     perr = particle_errors(o, g)
     assert max(perr.values()) <= 1e-9, perr
     assert abs(dg["gauss"] - do["gauss"]) <= 1e-9 * max(do["gauss"], 1e-12) + 1e-12
+
+
+def test_window_step_decoupled_from_patch_size_2d():
+    """GPU patches of 8 x 16 cells with a 16-cell window step equal the
+    oracle run with 16 x 16 patches."""
+    run, parts = W.lwfa_2d(n=(128, 64), d=(0.125, 0.5), patch=(16, 16), ppc=(2, 2),
+                           ramp=6.0, t_mw=1.0, a0=1.0, waist=5.0, tau=3.0)
+    run["laser"]["t_peak"] = 6.0
+    rng = np.random.default_rng(19)
+    parts["ux"] = rng.normal(0, 0.3, parts["x"].size)
+    o = Oracle(run)
+    o.load(parts)
+    o.set_background("neutralising")
+    g = pic.Pic(pic.config_from_run(run, "fp64", patch=(8, 16)))
+    assert g.cfg.window_cells == 16
+    g.pic_load_particles(parts)
+    g.pic_set_background("neutralising")
+    nsteps = 2 * math.ceil(16 * 0.125 / run["dt"]) + 12
+    for _ in range(nsteps):
+        o.step(1)
+        g.pic_step(1)
+    do, dg = o.diag(), g.pic_diag()
+    assert do["shifts"] >= 2 and dg["shifts"] == do["shifts"] and dg["np"] == do["np"]
+    errs = field_errors(o, g, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Bmx", "Bmy", "Bmz"))
+    _assert_fields(errs, 1e-9)
+    assert max(particle_errors(o, g).values()) <= 1e-9
 
 
 @pytest.mark.parametrize("case", ["empty_patches", "one_full_patch", "corners", "seam"])
