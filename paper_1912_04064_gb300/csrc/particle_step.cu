@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
               acc = cur;
               key = o;
             }
-          } else {
+          } else if (x1 != x[m] || y1 != y[m] || nuz != R(0)) {
+            // (a particle that did not move deposits nothing)
             flush<R, JWc>(Jt, JW, JT, o, cur);
           }
           // boundary conditions at domain faces, then destination patch
