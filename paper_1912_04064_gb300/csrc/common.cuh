@@ -53,6 +53,7 @@ struct DevState {
   int col0;       // slot column holding physical patch column 0
   unsigned err;
   int maxcnt[2];  // fullest patch written by the particle step of parity p
+  double laser_h; // laser temporal factor at t_{n+3/2}, set by the E update
 };
 
 struct Geom {

@@ -39,9 +39,25 @@ __device__ __forceinline__ bool block_mirrors(const Geom &g, int i0, int i1, int
 
 // E^{n+1} = E^n + dt (curl_h B^{n+1/2} - J^{n+1/2}); one cell per thread so
 // that every thread issues its loads at once.
+// Laser temporal factor envelope(t) carrier(t) at t_{n+3/2}, retarded by the
+// window's displacement; evaluated once per step by one thread of the E
+// update (FP64, off the Silver-Mueller kernel's path) into the device state.
+template <typename R>
+__device__ __forceinline__ void laser_factor(const FieldArgs<R> &a) {
+  const Geom &g = a.g;
+  double h = 0.0;
+  if (a.laser_on) {
+    const double t = a.st->t[a.parity] + 1.5 * g.dt;
+    const double tr = t - (double)(a.st->nshift * g.P) * g.dx - a.t_peak;
+    h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
+  }
+  a.st->laser_h = h;
+}
+
 template <typename R>
 __device__ __forceinline__ void update_E(const FieldArgs<R> &a, int blk_x, int blk_y) {
   const Geom &g = a.g;
+  if (blk_x == 0 && blk_y == 0 && threadIdx.x == 0 && threadIdx.y == 0) laser_factor(a);
   const Ranges rg = ranges(g);
   const int i0 = blk_x * YBX, j0 = blk_y * YBY;
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
@@ -162,27 +178,17 @@ __device__ __forceinline__ void update_B(const FieldArgs<R> &a, int blk_x, int b
 // Ghost B on open faces from the discrete Silver-Mueller condition; the
 // coefficients 1/(1+r), 1-r and the transverse dt/d are precomputed.  The
 // laser Ey_inc(y, t) = profile(y) * envelope(t) carrier(t): the transverse
-// profile is a precomputed array, the temporal factor is evaluated once per
-// block at t_{n+3/2} (retarded by the window's displacement).  One thread
+// profile is a precomputed array, the temporal factor comes from the device
+// state (set by the E update of this step).  One thread
 // per face point, faces in parallel (face = 0 x_min, 1 x_max, 2 y_min,
 // 3 y_max): no face reads a value another face writes, and every load is
 // issued before the ghost stores.
 template <typename R>
-__device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, int face,
-                                               double &s_h) {
+__device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, int face) {
   const Geom &g = a.g;
   const bool xface = face < 2, upper = (face & 1) != 0;
-  if (xface ? g.fbc_x != FBC_SM : g.fbc_y != FBC_SM) return;  // uniform per block
-  if (threadIdx.x == 0) {
-    double h = 0.0;
-    if (a.laser_on && face == 0) {
-      const double t = a.st->t[a.parity] + 1.5 * g.dt;
-      const double tr = t - (double)(a.st->nshift * g.P) * g.dx - a.t_peak;
-      h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
-    }
-    s_h = h;
-  }
-  __syncthreads();
+  if (xface ? g.fbc_x != FBC_SM : g.fbc_y != FBC_SM) return;
+  const double s_h = face == 0 ? a.st->laser_h : 0.0;
   const int t = bx * blockDim.x + threadIdx.x;
   R *F = a.F;
   const long long cs = g.cs;
@@ -320,8 +326,7 @@ __global__ void __launch_bounds__(YBX * YBY) k_update_B(const FieldArgs<R> a) {
 }
 template <typename R>
 __global__ void k_silver_mueller(const FieldArgs<R> a) {
-  __shared__ double s_h;
-  silver_mueller(a, blockIdx.x, blockIdx.y, s_h);
+  silver_mueller(a, blockIdx.x, blockIdx.y);
 }
 template <typename R, int NP>
 __global__ void __launch_bounds__(YBX * YBY) k_filter_current(const FieldArgs<R> a, int src,
@@ -356,10 +361,9 @@ __global__ void __launch_bounds__(YBX * YBY) k_update_B_batch(const FieldArgs<R>
 }
 template <typename R>
 __global__ void k_silver_mueller_batch(const FieldArgs<R> *fa, const BatchGrid bg) {
-  __shared__ double s_h;
   int bx, by;
   const FieldArgs<R> a = fa[batch_block(bg, bx, by)];
-  silver_mueller(a, bx, by, s_h);
+  silver_mueller(a, bx, by);
 }
 template <typename R>
 __global__ void __launch_bounds__(YBX * YBY) k_filter_current_batch(const FieldArgs<R> *fa,

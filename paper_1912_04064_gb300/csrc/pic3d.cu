@@ -596,6 +596,17 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
 template <typename R>
 __global__ void __launch_bounds__(256) k3_update_E(const Field3<R> a) {
   const Geom3 &g = a.g;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0) {
+    // laser temporal factor at t_{n+3/2} for the Silver-Mueller kernel
+    double h = 0.0;
+    if (a.laser_on) {
+      const double t = a.st->t[a.parity] + 1.5 * g.dt;
+      const double tr = t - (double)(a.st->nshift * g.p[0]) * g.d[0] - a.t_peak;
+      h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
+    }
+    a.st->laser_h = h;
+  }
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   int np_[3];
   for (int ax = 0; ax < 3; ++ax) np_[ax] = g.n[ax] + (g.fbc[ax] == FBC_SM);
@@ -725,17 +736,7 @@ __global__ void k3_silver_mueller(const Field3<R> a) {
   const Geom3 &g = a.g;
   const int face = blockIdx.y, ax = face >> 1, upper = face & 1;
   if (g.fbc[ax] != FBC_SM) return;
-  __shared__ double s_h;
-  if (threadIdx.x == 0) {
-    double h = 0.0;
-    if (a.laser_on && ax == 0 && !upper) {
-      const double t = a.st->t[a.parity] + 1.5 * g.dt;
-      const double tr = t - (double)(a.st->nshift * g.p[0]) * g.d[0] - a.t_peak;
-      h = exp(-2.0 * log(2.0) * tr * tr / (a.tau * a.tau)) * sin(tr);
-    }
-    s_h = h;
-  }
-  __syncthreads();
+  const double s_h = (ax == 0 && !upper) ? a.st->laser_h : 0.0;  // set by k3_update_E
   const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;  // transverse axes, increasing
   const int n1 = g.n[b1] + 1, n2 = g.n[b2] + 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
