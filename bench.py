@@ -19,6 +19,8 @@ One JSON line is printed on rank 0:
                H2D of the initial particles, K steps, D2H of fields and
                particles inside the timed region
   lwfa3d       the 3D3V config (1024x256x256, 67 M electrons, FP32)
+  batching     64 small runs batched (one launch per kernel per step) vs
+               the same runs stepped one after the other
   serving      the served ensemble (FP32 runs of four grid sizes, Poisson
                arrivals at 70% of the measured capacity, continuous
                batching): p50/p99 latency from arrival, throughput
@@ -389,6 +391,69 @@ def run_serving(device, seconds, seed=5, probe=16, load=0.7, cf=4.0, steps_per_t
     }
 
 
+def run_batching(device, nruns=64, steps=100):
+    """Many small runs (64 LWFA-shaped runs of 256 x 128 cells, 32 x 32
+    patches, 4 ppc, laser, FP32; 131 072 electrons each, plasma filled on
+    the device) advanced `steps` steps: one batch (one launch per kernel per
+    step for all runs) against the same runs stepped one after the other.
+    Device time with CUDA events on the batch / run streams."""
+    import torch
+
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    def runs_for(stream):
+        out = []
+        for k in range(nruns):
+            run = W.lwfa_run(n=(256, 128), patch=(32, 32), ppc=(2, 2), n0=0.005 + 0.0002 * k,
+                             ramp=20.0, a0=1.0 + 0.02 * k, waist=8.0, tau=10.0)
+            g = pic.Pic(pic.config_from_run(run, "fp32", stream=stream.cuda_stream,
+                                            device=device, capacity_factor=4.0))
+            g.pic_load_plasma()
+            out.append(g)
+        return out
+
+    stream = torch.cuda.Stream(device=device)
+    alone = runs_for(stream)
+    for g in alone:
+        g.pic_step(3)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for g in alone:
+        g.pic_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms_alone = e0.elapsed_time(e1)
+    np_total = sum(g.pic_diag()["np"] for g in alone)
+    launches_alone = sum(g.pic_diag()["launches"] for g in alone)
+    for g in alone:
+        g.close()
+    batched = runs_for(stream)
+    b = pic.Batch(stream=stream.cuda_stream, device=device)
+    b.pic_batch_set(batched)
+    b.pic_batch_step(3)
+    d0 = b.pic_batch_get_diag()
+    torch.cuda.synchronize(device)
+    e0.record(stream)
+    b.pic_batch_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    ms_batch = e0.elapsed_time(e1)
+    d1 = b.pic_batch_get_diag()
+    b.close()
+    for g in batched:
+        g.close()
+    return {"workload": f"{nruns} LWFA-shaped runs of 256x128 cells (32x32 patches, 4 ppc, laser, "
+                        f"FP32), {steps} steps each, plasma filled on the device",
+            "particles": np_total, "steps": steps,
+            "batched_particle_steps_per_s": np_total * steps / (ms_batch * 1e-3),
+            "alone_particle_steps_per_s": np_total * steps / (ms_alone * 1e-3),
+            "speedup": ms_alone / ms_batch,
+            "launches_per_batched_step": (d1["launches"] - d0["launches"]) / steps,
+            "grid": d1["grid"]}
+
+
 def cpu_oracle(steps, threads=0):
     """The FP64 CPU oracle on the same workload from its initial state."""
     from oracle.oracle import Oracle
@@ -433,6 +498,8 @@ def main():
                     help="arrival window of the served-ensemble measurement (0: skip)")
     ap.add_argument("--steps3d", type=int, default=40,
                     help="timed steps of the 3D3V config-3 leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=100,
+                    help="steps of the batching comparison (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -483,6 +550,7 @@ def main():
     serving = run_serving(local, args.serve_seconds) if args.serve_seconds > 0 else None
     r3 = (run_gpu3("fp32", args.steps3d, 3, max(0, 500 - args.steps3d - 3), local)
           if args.steps3d > 0 else None)
+    batching = run_batching(local, steps=args.batch_steps) if args.batch_steps > 0 else None
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
         dist.barrier()
@@ -531,6 +599,8 @@ def main():
                                f"{e2e['steps']} steps from t=0, D2H of E, B and all particles")
     if serving:
         line["serving"] = serving
+    if batching:
+        line["batching"] = batching
     if r3:
         line["lwfa3d"] = {
             "workload": ("3D3V LWFA-shaped: 1024x256x256 cells, dx=0.125, dy=dz=0.5 c/w0, "

@@ -296,8 +296,8 @@ void pic_batch_destroy(pic_batch *b);
 
 /* ---- Autotuner ---------------------------------------------------------
  * Chooses the launch shape of a workload by timing: square patch sizes
- * {8, 16, 32} (only the configured patch size when the moving window is on,
- * since the window advances by one patch column), particle-step blocks of
+ * {8, 16, 32} (with the moving window, only those dividing its step, which
+ * is kept: window_cells of the result names it), particle-step blocks of
  * {128, 256} threads and work items of {1024, 2048, 4096} particles, plus the
  * configuration as given.  Each candidate is a fresh context loaded with the
  * caller's particles (float64, PIC_HOST or PIC_DEVICE), stepped 2 steps to
@@ -306,7 +306,8 @@ void pic_batch_destroy(pic_batch *b);
  * order of the current sums, never the method.  Results are cached per
  * process by (grid, boundaries, laser, window, filter, precision, particles
  * per cell); a cached key returns without timing (candidates = 0).
- * On success *tuned is cfg with patch, block and task_chunk replaced. */
+ * On success *tuned is cfg with patch, block, task_chunk (and, with the
+ * moving window, window_cells) replaced. */
 typedef struct pic_tune_t {
   int patch[3];        /* chosen patch size */
   int block;           /* chosen particle-step block size */

@@ -26,16 +26,16 @@ using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int, int
 TuneKey tune_key(const pic_config *c, size_t n) {
   const double cells = (double)c->n[0] * c->n[1];
   const long long ppc = std::llround((double)n / std::max(cells, 1.0));
+  const int wstep = c->moving_window ? (c->window_cells > 0 ? c->window_cells : c->patch[0]) : 0;
   return TuneKey(c->dims, c->n[0], c->n[1], c->prec, c->bc_field[0], c->bc_field[1],
-                 c->laser_on, c->moving_window, c->filter_passes,
-                 c->moving_window ? c->patch[0] : 0, c->moving_window ? c->patch[1] : 0,
-                 c->tma, ppc);
+                 c->laser_on, c->moving_window, c->filter_passes, wstep, 0, c->tma, ppc);
 }
 
 struct TuneEntry {
   int patch[2];
   int block, chunk;
   double ms, ms_given;
+  int window_cells;
 };
 
 std::mutex g_tune_mutex;
@@ -88,6 +88,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
     tuned->patch[1] = e.patch[1];
     tuned->block = e.block;
     tuned->task_chunk = e.chunk;
+    tuned->window_cells = e.window_cells;
     out->patch[0] = e.patch[0];
     out->patch[1] = e.patch[1];
     out->patch[2] = cfg->patch[2];
@@ -117,17 +118,21 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
   TuneEntry best{{cfg->patch[0], cfg->patch[1]},
                  base.block > 0 ? base.block : 256,
                  base.task_chunk > 0 ? base.task_chunk : 2048,
-                 ms_given, ms_given};
+                 ms_given, ms_given, cfg->window_cells};
   int timed = 1;
-  std::vector<int> sizes;
-  if (cfg->moving_window) sizes.push_back(-1);  // keep the configured patch
-  else sizes = {8, 16, 32};
-  for (int P : sizes)
+  // the moving window's step (cells) is part of the run: patch widths that
+  // divide it keep it, the window then advancing several columns at once
+  const int wstep = cfg->window_cells > 0 ? cfg->window_cells : cfg->patch[0];
+  for (int P : {8, 16, 32})
     for (int block : {128, 256})
       for (int chunk : {1024, 2048, 4096}) {
         pic_config c = base;
-        if (P > 0) c.patch[0] = c.patch[1] = P;
+        c.patch[0] = c.patch[1] = P;
         if (c.n[0] % c.patch[0] || c.n[1] % c.patch[1]) continue;
+        if (cfg->moving_window) {
+          if (wstep % P) continue;
+          c.window_cells = wstep;
+        }
         c.block = block;
         c.task_chunk = chunk;
         const double ms = time_candidate(c, p, n, where, steps);
@@ -137,6 +142,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
           best.patch[1] = c.patch[1];
           best.block = block;
           best.chunk = chunk;
+          best.window_cells = c.window_cells;
           best.ms = ms;
         }
       }
