@@ -140,6 +140,27 @@ def profiled_traffic(name):
         return None
 
 
+def profiled_value(name, key):
+    """An integer recorded as `key` in the committed ncu summary
+    profiles/<name>, if its kernel sources still hash to the recorded
+    value; else None."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
+        h = hashlib.sha256()
+        for f in re.findall(r"`([^`]+)`", m.group(2)):
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if not h.hexdigest().startswith(m.group(1)):
+            return None
+        v = re.search(r"`" + key + r"` (\d+)", text)
+        return int(v.group(1)) if v else None
+    except Exception:
+        return None
+
+
 def algorithmic_bytes(npart, ncell, rsize):
     """Bytes the method must move once per step: per particle read
     x, y, ux, uy, uz, w and write x, y, ux, uy, uz (11 words); per cell gather
@@ -476,6 +497,39 @@ def cpu_oracle(steps, threads=0):
                       f"(after 1 warm-up step), FP64, OpenMP over patches"}
 
 
+def issue_roofline(launch_ms):
+    """Secondary ceiling of the FP32 particle step, which is bound by
+    instruction issue: warp instructions of one launch (ncu, step 1005)
+    over the mean launch time, against 152 SMs x 4 schedulers x the
+    measured maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = json.load(f)["sm_max_mhz"]
+    except Exception:
+        mhz = 2070.0
+    n = profiled_value("particle_step_instruction_mix_lwfa2048.md", "warp_instructions_fp32")
+    peak = 152 * 4 * mhz * 1e6
+    if n is None or not launch_ms:
+        return {"bound": "issue", "achieved": None, "peak": peak, "unit": "warp instructions/s"}
+    ach = n / (launch_ms * 1e-3)
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp instructions/s",
+            "frac": ach / peak, "warp_instructions_per_launch": n,
+            "source": "profiles/particle_step_instruction_mix_lwfa2048.md (one launch, step 1005)"}
+
+
+def alu_roofline_fp64(launch_ms):
+    """The FP64 particle step is bound by GB300's FP64 unit: FP64 flops of
+    one launch (2 FMA + add + mul thread instructions, ncu, step 1005)
+    over the mean launch time, against the nominal 1.25 TFLOP/s."""
+    n = profiled_value("particle_step_instruction_mix_lwfa2048.md", "fp64_flops")
+    peak = 1250.0
+    if n is None or not launch_ms:
+        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "GFLOP/s"}
+    ach = n / (launch_ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s", "frac": ach / peak,
+            "peak_source": "nominal FP64 rate (profiling recipe)", "flops_per_launch": n}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,14 +636,16 @@ def main():
                                        "the kernel sources changed since",
                      "bytes_per_launch": r32["kernel_bytes"], "launch_ms": r32["particle_step_ms"],
                      "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
-                                    "bytes_per_step": r32["step_bytes"]}},
+                                    "bytes_per_step": r32["step_bytes"]},
+                     "issue": issue_roofline(r32["particle_step_ms"])},
         "phases_ms": {"particle_step": r32["particle_step_ms"], "fields": r32["fields_ms"],
                       "window": r32["window_ms"], "sort": r32["sort_ms"]},
         "fp64": None if r64 is None else {
             "value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": args.fp64_steps,
             "particle_step_ms": r64["particle_step_ms"], "fields_ms": r64["fields_ms"],
             "speedup_fp32_over_fp64": r32["value"] / r64["value"],
-            "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm},
+            "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm,
+            "roofline": alu_roofline_fp64(r64["particle_step_ms"])},
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }
