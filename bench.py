@@ -606,6 +606,7 @@ def main():
           if args.steps3d > 0 else None)
     batching = run_batching(local, steps=args.batch_steps) if args.batch_steps > 0 else None
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
+    cpu1 = cpu_oracle(1, threads=1) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
         dist.barrier()
     if rank != 0:
@@ -677,6 +678,8 @@ def main():
                          "bytes_per_step": r3["step_bytes"]}}
     if cpu:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        if cpu1:
+            line["cpu_baseline"]["one_thread"] = {k: cpu1[k] for k in ("value", "cores", "sample")}
     print(json.dumps(line), flush=True)
 
 

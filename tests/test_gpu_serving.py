@@ -143,6 +143,36 @@ def test_served_runs_equal_runs_alone(prec):
     srv.close()
 
 
+def test_mixed_precision_requests_share_a_server():
+    """FP32 and FP64 requests in one server: one batch per precision, both
+    stepped every tick; each result equals its run alone."""
+    reqs = [(_lwfa(n=(128, 64), patch=(16, 16)), "fp64", 30),
+            (_lwfa(n=(64, 64), patch=(8, 8), window=False), "fp32", 20),
+            (_lwfa(n=(96, 64), patch=(16, 16), n0=0.02), "fp32", 25),
+            (_lwfa(n=(64, 32), patch=(16, 16), laser=False, window=False), "fp64", 15)]
+    srv = pic.Server(steps_per_tick=5)
+    ids = []
+    for run, prec, n in reqs:
+        cfg = pic.config_from_run(run, prec)
+        ids.append((srv.pic_server_submit(cfg, n, keep=True), cfg))
+    for _ in range(200):
+        srv.pic_server_tick()
+        st = srv.pic_server_get_stats()
+        if st["done"] + st["failed"] == len(reqs):
+            break
+    assert st["done"] == len(reqs), st
+    for (rid, cfg), (run, prec, n) in zip(ids, reqs):
+        served = srv.pic_server_take(rid, cfg)
+        alone = _alone(run, prec, n)
+        for k in ("Ex", "Ey", "Bz"):
+            a, b = served.pic_get_field(k), alone.pic_get_field(k)
+            rel = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+            assert rel <= TOL_MIX[prec], (prec, k, rel)
+        served.close()
+        alone.close()
+    srv.close()
+
+
 def test_admission_by_memory_budget_and_late_arrivals():
     """Budget for two runs: a third waits until one finishes, then joins
     while the second is still running (continuous batching)."""
