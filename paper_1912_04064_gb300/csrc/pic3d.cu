@@ -677,10 +677,11 @@ __global__ void __launch_bounds__(256) k3_update_B(const Field3<R> a) {
   const bool uy = in && du[0] && pr[1] && du[2];
   const bool uz = in && du[0] && du[1] && pr[2];
   const R bx0 = Bx[o], by0 = By[o], bz0 = Bz[o];
+  const R ex = Ex[o], ey = Ey[o], ez = Ez[o];
   R bx1 = bx0, by1 = by0, bz1 = bz0;
-  if (ux) bx1 = bx0 - dt * ((Ez[o + sy] - Ez[o]) * idy - (Ey[o + sz] - Ey[o]) * idz);
-  if (uy) by1 = by0 - dt * ((Ex[o + sz] - Ex[o]) * idz - (Ez[o + 1] - Ez[o]) * idx);
-  if (uz) bz1 = bz0 - dt * ((Ey[o + 1] - Ey[o]) * idx - (Ex[o + sy] - Ex[o]) * idy);
+  if (ux) bx1 = bx0 - dt * ((Ez[o + sy] - ez) * idy - (Ey[o + sz] - ey) * idz);
+  if (uy) by1 = by0 - dt * ((Ex[o + sz] - ex) * idz - (Ez[o + 1] - ez) * idx);
+  if (uz) bz1 = bz0 - dt * ((Ey[o + 1] - ey) * idx - (Ex[o + sy] - ex) * idy);
   if (ux) { Bx[o] = bx1; mirror3(g, Bx, i, j, k, bx1); }
   if (uy) { By[o] = by1; mirror3(g, By, i, j, k, by1); }
   if (uz) { Bz[o] = bz1; mirror3(g, Bz, i, j, k, bz1); }
@@ -691,9 +692,9 @@ __global__ void __launch_bounds__(256) k3_update_B(const Field3<R> a) {
   mirror3(g, Bmx, i, j, k, mx);
   mirror3(g, Bmy, i, j, k, my);
   mirror3(g, Bmz, i, j, k, mz);
-  mark_active(g, a.active, i, j, k,
-              mx != R(0) || my != R(0) || mz != R(0) || Ex[o] != R(0) || Ey[o] != R(0) ||
-                  Ez[o] != R(0));
+  const bool nz = mx != R(0) || my != R(0) || mz != R(0) || ex != R(0) || ey != R(0) ||
+                  ez != R(0);
+  if (__any_sync(__activemask(), nz)) mark_active(g, a.active, i, j, k, nz);
 }
 
 // Active flags from the stored fields (after any change outside a step:
