@@ -208,6 +208,14 @@ pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where);
  * the particles currently loaded. */
 pic_status pic_set_background(pic_ctx *ctx, int mode, double value);
 
+/* Initial fields.  PIC_INIT_ZERO: E, B and Bm zero.  PIC_INIT_POISSON (every
+ * axis periodic): E from Gauss's law for the loaded particles and the
+ * background, div_h E = rho - <rho>, E = -grad_h phi on the Yee lattice,
+ * solved in FP64 with a spectral (FFT) Poisson solve; B = Bm = 0.  Other
+ * boundaries give PIC_EINVAL. */
+enum { PIC_INIT_ZERO = 0, PIC_INIT_POISSON = 1 };
+pic_status pic_init_fields(pic_ctx *ctx, int mode);
+
 /* Advance nsteps steps.  Synchronises with the device at the end and reports
  * device-side faults. */
 pic_status pic_step(pic_ctx *ctx, int nsteps);

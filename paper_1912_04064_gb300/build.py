@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpic.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["api", "particle_step", "fields", "particles", "noalloc", "runtime", "pic3d"]
+UNITS = ["api", "particle_step", "fields", "particles", "noalloc", "runtime", "pic3d", "poisson"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]
@@ -40,8 +40,9 @@ def build(force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(_compile, UNITS))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.run(["nvcc"] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs,
-                   check=True)
+    # cuFFT (shared, from the CUDA toolkit) serves the initial Poisson solve
+    subprocess.run(["nvcc"] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs +
+                   ["-lcufft"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

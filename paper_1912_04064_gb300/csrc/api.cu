@@ -13,6 +13,7 @@
 #include "../../include/pic.h"
 #include "common.cuh"
 #include "pic3d.h"
+#include "poisson.h"
 
 using namespace pic;
 
@@ -1523,6 +1524,46 @@ pic_status pic_set_background(pic_ctx *ctx, int mode, double value) {
   } else {
     return fail(ctx, PIC_EINVAL, "bad background mode");
   }
+  return poll_device(ctx);
+}
+
+pic_status pic_init_fields(pic_ctx *ctx, int mode) {
+  pic_status s = check_usable(ctx);
+  if (s) return s;
+  if (mode != PIC_INIT_ZERO && mode != PIC_INIT_POISSON) return fail(ctx, PIC_EINVAL, "bad init mode");
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_init_fields(ctx->c3, mode);
+  const Geom &g = ctx->g;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemsetAsync(ctx->F, 0, 9 * g.cs * ctx->rs, ctx->stream));  // E, Bm, B
+  ctx->prev_valid = false;
+  if (mode == PIC_INIT_ZERO) return poll_device(ctx);
+  if (g.fbc_x != FBC_PERIODIC || g.fbc_y != FBC_PERIODIC)
+    return fail(ctx, PIC_EINVAL, "the Poisson start needs periodic axes");
+  const size_t n = (size_t)g.nx * g.ny;
+  double *buf = nullptr;
+  CK(cudaMalloc(&buf, sizeof(double) * 5 * n));
+  double *rho = buf, *bg = buf + n, *ex = buf + 2 * n, *ey = buf + 3 * n, *ez = buf + 4 * n;
+  s = ctx->fp32 ? deposit_current_rho<float>(ctx, ctx->rho_a, false)
+                : deposit_current_rho<double>(ctx, ctx->rho_a, false);
+  if (s) { cudaFree(buf); return s; }
+  CK(launch_get_field_f64(g, ctx->rho_a, rho, ctx->stream));
+  CK(launch_get_field_f64(g, ctx->rho_bg, bg, ctx->stream));
+  CK(launch_axpy_f64(rho, bg, n, ctx->stream));
+  CK(cudaMemsetAsync(ez, 0, sizeof(double) * n, ctx->stream));
+  const int nn[3] = {g.nx, g.ny, 1};
+  const double dd[3] = {g.dx, g.dy, 1.0};
+  s = poisson_fields(2, nn, dd, rho, ex, ey, nullptr, ctx->stream, ctx->err);
+  if (!s) {
+    const double *src[3] = {ex, ey, ez};
+    for (int c = 0; c < 3 && !s; ++c)
+      s = ctx->fp32 ? do_set_field<float>(ctx, PIC_EX + c, src[c], PIC_DEVICE)
+                    : do_set_field<double>(ctx, PIC_EX + c, src[c], PIC_DEVICE);
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(buf);
+  ctx->launches += 6;
+  if (s) return s;
   return poll_device(ctx);
 }
 

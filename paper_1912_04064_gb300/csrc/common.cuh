@@ -342,6 +342,8 @@ template <typename R>
 cudaError_t launch_get_field(const Geom &g, const R *arr, double *dst, cudaStream_t s);
 cudaError_t launch_get_field_f64(const Geom &g, const double *arr, double *dst, cudaStream_t s);
 cudaError_t launch_set_field_f64(const Geom &g, double *arr, const double *src, cudaStream_t s);
+// y[i] += x[i], i < n (float64).
+cudaError_t launch_axpy_f64(double *y, const double *x, size_t n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_shift_fields(const Geom &g, R *F, int ncomp, cudaStream_t s);
 cudaError_t launch_shift_f64(const Geom &g, double *a, cudaStream_t s);

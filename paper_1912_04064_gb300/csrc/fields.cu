@@ -585,6 +585,20 @@ cudaError_t launch_get_field(const Geom &g, const R *arr, double *dst, cudaStrea
 cudaError_t launch_get_field_f64(const Geom &g, const double *arr, double *dst, cudaStream_t s) {
   return launch_get_field<double>(g, arr, dst, s);
 }
+namespace {
+__global__ void k_axpy_f64(double *y, const double *x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+}  // namespace
+
+cudaError_t launch_axpy_f64(double *y, const double *x, size_t n, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_axpy_f64<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(y, x, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_field_f64(const Geom &g, double *arr, const double *src, cudaStream_t s) {
   return launch_set_field<double>(g, arr, src, s);
 }

@@ -36,6 +36,7 @@
 
 #include "common.cuh"
 #include "pic3d.h"
+#include "poisson.h"
 #include "shape.cuh"
 
 namespace pic {
@@ -2165,6 +2166,43 @@ pic_status c3_set_background(Ctx3 *c, int mode, double value) {
   } else {
     return fail3(c, PIC_EINVAL, "bad background mode");
   }
+  return poll3(c);
+}
+
+pic_status c3_init_fields(Ctx3 *c, int mode) {
+  pic_status s = usable3(c);
+  if (s) return s;
+  const Geom3 &g = c->g;
+  CK3(cudaStreamSynchronize(c->stream));
+  CK3(cudaMemsetAsync(c->F, 0, 9 * g.cs * c->rs, c->stream));  // E, Bm, B
+  c->prev_valid = false;
+  c->active_valid = false;
+  if (mode == PIC_INIT_ZERO) return poll3(c);
+  for (int a = 0; a < 3; ++a)
+    if (g.fbc[a] != FBC_PERIODIC) return fail3(c, PIC_EINVAL, "the Poisson start needs periodic axes");
+  const size_t n = (size_t)g.n[0] * g.n[1] * g.n[2];
+  double *buf = nullptr;
+  CK3(cudaMalloc(&buf, sizeof(double) * 5 * n));
+  double *rho = buf, *bg = buf + n, *ex = buf + 2 * n, *ey = buf + 3 * n, *ez = buf + 4 * n;
+  s = c->fp32 ? deposit_rho3<float>(c, c->rho_a, false) : deposit_rho3<double>(c, c->rho_a, false);
+  if (s) { cudaFree(buf); return s; }
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
+  k3_get_field<double><<<blocks, 256, 0, c->stream>>>(g, c->rho_a, rho);
+  k3_get_field<double><<<blocks, 256, 0, c->stream>>>(g, c->rho_bg, bg);
+  CK3(cudaGetLastError());
+  CK3(launch_axpy_f64(rho, bg, n, c->stream));
+  const double dd[3] = {g.d[0], g.d[1], g.d[2]};
+  s = poisson_fields(3, g.n, dd, rho, ex, ey, ez, c->stream, c->err);
+  if (!s) {
+    const double *src[3] = {ex, ey, ez};
+    for (int k = 0; k < 3 && !s; ++k)
+      s = c->fp32 ? set_field3<float>(c, PIC_EX + k, src[k], PIC_DEVICE)
+                  : set_field3<double>(c, PIC_EX + k, src[k], PIC_DEVICE);
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  c->launches += 6;
+  if (s) return s;
   return poll3(c);
 }
 

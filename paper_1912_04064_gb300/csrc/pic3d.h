@@ -24,6 +24,7 @@ pic_status c3_fill_plasma(Ctx3 *c);
 pic_status c3_set_field(Ctx3 *c, int which, const double *src, int where);
 pic_status c3_get_field(Ctx3 *c, int which, double *dst, int where);
 pic_status c3_set_background(Ctx3 *c, int mode, double value);
+pic_status c3_init_fields(Ctx3 *c, int mode);
 pic_status c3_step(Ctx3 *c, int nsteps);
 pic_status c3_get_particles(Ctx3 *c, double *out, size_t cap, size_t *n, int where);
 pic_status c3_diag(Ctx3 *c, pic_diag_t *out);

@@ -117,7 +117,8 @@ EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_backgro
            "pic_batch_size", "pic_batch_get_diag", "pic_batch_last_error", "pic_batch_destroy",
            "pic_load_plasma", "pic_autotune", "pic_autotune_clear_cache", "pic_server_create",
            "pic_server_submit", "pic_server_tick", "pic_server_info", "pic_server_take",
-           "pic_server_get_stats", "pic_server_clock", "pic_server_destroy", "pic_load_particles3"]
+           "pic_server_get_stats", "pic_server_clock", "pic_server_destroy", "pic_load_particles3",
+           "pic_init_fields"]
 
 _lib = None
 
@@ -151,6 +152,8 @@ def lib():
         L.pic_field_energy_noalloc.argtypes = [vp] * 6 + [C.c_int, C.c_int, C.c_double, vp, vp]
         L.pic_field_energy_noalloc.restype = C.c_int
         L.pic_load_plasma.argtypes = [vp]
+        L.pic_init_fields.argtypes = [vp, C.c_int]
+        L.pic_init_fields.restype = C.c_int
         L.pic_load_particles3.argtypes = [vp] + [dp] * 7 + [sz, C.c_int]
         L.pic_load_particles3.restype = C.c_int
         L.pic_autotune.argtypes = ([C.POINTER(pic_config)] + [dp] * 6 +
@@ -335,6 +338,10 @@ class Pic:
             raise ValueError(f"{name}: shape {tuple(a.shape)} != {self.shape}")
         q, where = _ptr(a)
         self._check(lib().pic_set_field(self.h, FIELDS.index(name), q, where))
+
+    def pic_init_fields(self, mode: str = "poisson"):
+        """Initial fields: "zero", or "poisson" (E from Gauss's law, periodic axes)."""
+        self._check(lib().pic_init_fields(self.h, {"zero": 0, "poisson": 1}[mode]))
 
     def pic_set_background(self, mode: str, value: float = 0.0):
         self._check(lib().pic_set_background(self.h, BG[mode], value))
