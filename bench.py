@@ -24,6 +24,9 @@ One JSON line is printed on rank 0:
   serving      the served ensemble (FP32 runs of four grid sizes, Poisson
                arrivals at 70% of the measured capacity, continuous
                batching): p50/p99 latency from arrival, throughput
+  precision_study  FP32 against FP64 from identical inputs over the
+               workload's 2000 steps: field and energy differences, both
+               paths' continuity and Gauss residuals
   cpu_baseline the FP64 CPU oracle on a bounded sample of the workload
 `--impl reference` times the oracle alone (the reference arm).
 
@@ -264,9 +267,9 @@ def run_gpu3(prec, steps, warmup, spinup, device, cf=2.0):
     rs = 4 if prec == "fp32" else 8
     stream = torch.cuda.Stream(device=device)
     # the config's 16^3 SDMD patches set the window step (16 cells); the GPU
-    # stores particles in 16 x 8 x 8 sub-patches so that a patch's E and Bm
-    # tile (70 KB) and current tile (43 KB) fit in shared memory
-    sub = (16, 8, 8)
+    # stores particles in 8 x 8 x 8 sub-patches: a patch's E and Bm tile
+    # (46 KB) and current tile (26 KB) fit three blocks per SM
+    sub = (8, 8, 8)
     g = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                                     capacity_factor=cf, patch=sub))
     g.pic_load_plasma()
@@ -475,6 +478,81 @@ def run_batching(device, nruns=64, steps=100):
             "grid": d1["grid"]}
 
 
+def run_precision(device, steps=2000, every=50):
+    """The precision study on the LWFA workload: the FP32 and FP64 paths
+    advanced side by side from identical inputs (same particles, t = 0) for
+    `steps` steps.  Every `every` steps (and after steps 1 and 10) the FP32
+    fields are compared with the FP64 ones (||a - b||_inf / ||b||_inf per
+    component; worst of the E, B and J components), with the particle count,
+    both paths' FP64 continuity and Gauss residuals and their energies.
+    Accumulated differences, not single-step errors: the FP32 run is never
+    reset to the FP64 state."""
+    import torch
+
+    from paper_1912_04064_gb300 import pic
+    from paper_1912_04064_gb300 import workloads as W
+
+    run, parts = W.lwfa_2d()
+    stream = torch.cuda.Stream(device=device)
+    ctx = {}
+    for prec in ("fp64", "fp32"):
+        g = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
+                                        use_graph=True, capacity_factor=4.0))
+        g.pic_load_particles(parts)
+        g.pic_set_background("neutralising")
+        ctx[prec] = g
+    shape = ctx["fp64"].shape
+    bufs = {p: torch.empty(shape, dtype=torch.float64, device=f"cuda:{device}") for p in ctx}
+    groups = {"E": ("Ex", "Ey", "Ez"), "B": ("Bx", "By", "Bz"), "J": ("Jx", "Jy", "Jz")}
+    marks = sorted({1, 10, *range(every, steps + 1, every)})
+    hist, done = [], 0
+    for m in marks:
+        for g in ctx.values():
+            g.pic_step(m - done)
+        done = m
+        rec = {"step": m}
+        for grp, names in groups.items():
+            worst = 0.0
+            for k in names:
+                for p, g in ctx.items():
+                    g.pic_get_field(k, out=bufs[p])
+                torch.cuda.synchronize(device)
+                ref = bufs["fp64"].abs().max().item()
+                diff = (bufs["fp32"] - bufs["fp64"]).abs().max().item()
+                worst = max(worst, diff / ref if ref > 0 else diff)
+            rec[grp] = worst
+        d64, d32 = ctx["fp64"].pic_diag(), ctx["fp32"].pic_diag()
+        for k in ("U_E", "U_B", "U_K"):
+            rec[k] = abs(d32[k] - d64[k]) / max(abs(d64[k]), 1e-300)
+        rec["np"] = (d32["np"], d64["np"])
+        # residuals not available at this step (e.g. right after a window
+        # shift) are reported as null
+        fin = lambda v: v if math.isfinite(v) else None  # noqa: E731
+        rec["continuity"] = (fin(d32["continuity"]), fin(d64["continuity"]))
+        rec["gauss"] = (fin(d32["gauss"]), fin(d64["gauss"]))
+        hist.append(rec)
+    for g in ctx.values():
+        g.close()
+
+    def at(step):
+        r = next(h for h in hist if h["step"] == step)
+        return {k: r[k] for k in ("E", "B", "J", "U_E", "U_B", "U_K")}
+
+    pick = [m for m in (1, 10, 100, 500, 1000, 2000) if m in marks]
+    last = hist[-1]
+    return {"workload": "the LWFA workload above, FP32 and FP64 from identical inputs at t = 0, "
+                        f"{steps} steps, recorded every {every}",
+            "metric": "||fp32 - fp64||_inf / ||fp64||_inf per field component (worst of each "
+                      "group); relative energy difference",
+            "at_step": {str(m): at(m) for m in pick},
+            "max_over_run": {k: max(h[k] for h in hist) for k in ("E", "B", "J", "U_E", "U_B", "U_K")},
+            "particles_at_end": {"fp32": last["np"][0], "fp64": last["np"][1]},
+            "continuity_at_end": {"fp32": last["continuity"][0], "fp64": last["continuity"][1]},
+            "gauss_at_end": {"fp32": last["gauss"][0], "fp64": last["gauss"][1]},
+            "gauss_max_over_run": {p: max((h["gauss"][i] for h in hist if h["gauss"][i] is not None),
+                                          default=None) for i, p in enumerate(("fp32", "fp64"))}}
+
+
 def cpu_oracle(steps, threads=0):
     """The FP64 CPU oracle on the same workload from its initial state."""
     from oracle.oracle import Oracle
@@ -552,6 +630,8 @@ def main():
                     help="arrival window of the served-ensemble measurement (0: skip)")
     ap.add_argument("--steps3d", type=int, default=40,
                     help="timed steps of the 3D3V config-3 leg (0: skip)")
+    ap.add_argument("--precision-steps", type=int, default=2000,
+                    help="steps of the FP32-vs-FP64 precision study (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="steps of the batching comparison (0: skip)")
     args = ap.parse_args()
@@ -605,6 +685,8 @@ def main():
     r3 = (run_gpu3("fp32", args.steps3d, 3, max(0, 500 - args.steps3d - 3), local)
           if args.steps3d > 0 else None)
     batching = run_batching(local, steps=args.batch_steps) if args.batch_steps > 0 else None
+    precision = (run_precision(local, args.precision_steps)
+                 if rank == 0 and args.precision_steps > 0 else None)
     cpu = cpu_oracle(args.cpu_steps) if rank == 0 and args.cpu_steps > 0 else None
     cpu1 = cpu_oracle(1, threads=1) if rank == 0 and args.cpu_steps > 0 else None
     if dist:
@@ -658,11 +740,13 @@ def main():
         line["serving"] = serving
     if batching:
         line["batching"] = batching
+    if precision:
+        line["precision_study"] = precision
     if r3:
         line["lwfa3d"] = {
             "workload": ("3D3V LWFA-shaped: 1024x256x256 cells, dx=0.125, dy=dz=0.5 c/w0, "
                          "dt=0.95 CFL, 16^3-cell patches (window step 16 cells; stored as "
-                         "16x8x8 GPU sub-patches), 0.005 n_c in the upper half of the "
+                         "8x8x8 GPU sub-patches), 0.005 n_c in the upper half of the "
                          "transverse box, 2 ppc (67108864 electrons), immobile ions, laser a0=3 "
                          "waist 15, moving window at c"),
             "dtype": "f32", "value": r3["value"], "unit": "particle-steps/s",

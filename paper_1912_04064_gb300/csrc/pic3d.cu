@@ -50,6 +50,7 @@ struct Geom3 {
   int n[3];              // cells
   int p[3];              // patch size
   int np[3];             // patches per axis
+  int pshift[3];         // log2 of the patch size when a power of two, else -1
   int nslots;
   int sx, sy, sz;        // stored extents (sx: row stride, multiple of 32)
   long long cs;          // elements per component
@@ -126,6 +127,7 @@ __device__ __forceinline__ void mirror3(const Geom3 &g, R *a, int i, int j, int 
   for (int ax = 0; ax < 3; ++ax)
     if (g.fbc[ax] == FBC_PERIODIC)
       m[ax] = c[ax] < G3 ? g.n[ax] : (c[ax] >= g.n[ax] - G3 ? -g.n[ax] : 0);
+  if (!(m[0] | m[1] | m[2])) return;  // no image: interior cell or no periodic axis
   for (int cz = 0; cz < 2; ++cz)
     for (int cy = 0; cy < 2; ++cy)
       for (int cx = 0; cx < 2; ++cx) {
@@ -171,12 +173,25 @@ struct Field3 {
   int *active;                          // per physical patch, set by k3_update_B
 };
 
+__device__ __forceinline__ int patch_coord(const Geom3 &g, int ax, int c) {
+  return g.pshift[ax] >= 0 ? c >> g.pshift[ax] : c / g.p[ax];
+}
+
 // Mark the physical patch of cell (i, j, k) (inside the domain) active when
-// v is nonzero; one flag read per cell, an atomic only for the first mark.
+// v is nonzero.  Called by every lane of the active mask; the lanes that
+// mark the same patch elect one, which reads the flag and sets it with an
+// atomic only if it is still clear.
 __device__ __forceinline__ void mark_active(const Geom3 &g, int *active, int i, int j, int k,
                                             bool v) {
-  if (!v || i < 0 || j < 0 || k < 0 || i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
-  const int p = ((k / g.p[2]) * g.np[1] + j / g.p[1]) * g.np[0] + i / g.p[0];
+  const bool in = v && i >= 0 && j >= 0 && k >= 0 && i < g.n[0] && j < g.n[1] && k < g.n[2];
+  const unsigned mask = __ballot_sync(__activemask(), in);
+  if (!in) return;
+  const int p = (patch_coord(g, 2, k) * g.np[1] + patch_coord(g, 1, j)) * g.np[0] +
+                patch_coord(g, 0, i);
+  const unsigned same = __match_any_sync(mask, p);
+  unsigned lane;
+  asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+  if ((unsigned)(__ffs(same) - 1) != lane) return;
   if (!*(volatile int *)&active[p]) atomicOr(&active[p], 1);
 }
 
@@ -308,8 +323,22 @@ __device__ __forceinline__ R gather27t(const R *T, int BX, int BY, int i0, int j
   return acc;
 }
 
-template <typename R, bool STAGED>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
+// Blocks per SM that the shared memory of a patch shape allows (at most 3),
+// used as the launch bound of the compile-time-shaped kernels: it caps the
+// registers so that the occupancy shared memory permits is also reached.
+template <typename R, bool STAGED, int PX, int PY, int PZ>
+constexpr int k3_min_blocks() {
+  if (PX == 0) return sizeof(R) == 4 ? 2 : 1;
+  const int smem = (STAGED ? 6 * (PX + 8) * (PY + 3) * (PZ + 3) * (int)sizeof(R) : 0) +
+                   3 * (PX + 5) * (PY + 5) * (PZ + 5) * (int)sizeof(R) + 1024 + 128;
+  const int n = (228 * 1024) / smem;
+  return n >= 3 ? 3 : (n >= 1 ? n : 1);
+}
+
+// PX, PY, PZ: the patch shape when fixed at compile time (0: read from the
+// geometry), so that tile strides become immediates.
+template <typename R, bool STAGED, int PX = 0, int PY = 0, int PZ = 0>
+__global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     k3_particle_step(const __grid_constant__ CUtensorMap tmap, const Step3<R> a) {
   // STAGED: the patch's E and Bm (nodes -4..P+3 along x, -1..Q+1, -1..R+1)
   // are staged into shared memory by one 4D TMA box (SDMD step (ii)) and
@@ -323,7 +352,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
   __shared__ int s_ok;
   const Geom3 &g = a.g;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
-  const int P = g.p[0], Q = g.p[1], Rz = g.p[2];
+  const int P = PX ? PX : g.p[0], Q = PY ? PY : g.p[1], Rz = PZ ? PZ : g.p[2];
   const int JW = P + 5, JH = Q + 5, JD = Rz + 5, JT = JW * JH * JD;
   const int BX = P + 8, BY = Q + 3, BZ = Rz + 3, FT = BX * BY * BZ;
   const uint32_t pad = (128u - (smem_u32(dsm3) & 127u)) & 127u;
@@ -1239,6 +1268,7 @@ struct Ctx3 {
   Plan plan{};
   int ps_grid = 0;
   size_t ps_smem = 0;
+  const void *ps_kernel = nullptr;  // the particle-step instance for this patch shape
   bool staged = false;   // E and Bm tiles staged into shared memory by TMA
   CUtensorMap tmap{};
   DevState *st = nullptr;
@@ -1285,6 +1315,11 @@ Geom3 make_geom3(const pic_config *cf) {
     g.fbc[a] = cf->bc_field[a];
     g.pbc[a][0] = cf->bc_part[a][0];
     g.pbc[a][1] = cf->bc_part[a][1];
+  }
+  for (int a = 0; a < 3; ++a) {
+    g.pshift[a] = -1;
+    for (int b = 0; b < 16; ++b)
+      if (g.p[a] == (1 << b)) g.pshift[a] = b;
   }
   g.nslots = g.np[0] * g.np[1] * g.np[2];
   g.sx = (g.n[0] + 2 * G3 + 31) / 32 * 32;
@@ -1483,10 +1518,11 @@ pic_status enqueue_step3(Ctx3 *c, int p, cudaEvent_t mid = nullptr) {
   const int pb = std::min(1024, (g.nslots + 255) / 256);
   k3_plan_count<R><<<pb, 256, 0, c->stream>>>(a, c->plan_hist);
   k3_plan_place<R><<<pb, 256, 0, c->stream>>>(a, c->plan_hist, c->plan_hist + PLAN3_CLASSES);
-  if (c->staged)
-    k3_particle_step<R, true><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(c->tmap, a);
-  else
-    k3_particle_step<R, false><<<c->ps_grid, 256, c->ps_smem, c->stream>>>(c->tmap, a);
+  {
+    using K = void (*)(CUtensorMap, Step3<R>);
+    const K k = reinterpret_cast<K>(const_cast<void *>(c->ps_kernel));
+    k<<<c->ps_grid, 256, c->ps_smem, c->stream>>>(c->tmap, a);
+  }
   CK3(cudaGetLastError());
   if (mid) CK3(cudaEventRecord(mid, c->stream));
   const Field3<R> f = field_args3<R>(c, p);
@@ -1564,6 +1600,24 @@ PFN_cuTensorMapEncodeTiled_v12000 encode3() {
   return fn;
 }
 
+// The particle-step instance for a patch shape: FP32 patches of 16x8x8,
+// 8x8x8 and 16x16x16 cells get compile-time-shaped kernels, every other
+// shape (and FP64, bound by its FP64 rate) the runtime-shaped one.
+template <typename R>
+const void *pick_particle_step3(const int p[3], bool staged) {
+  if constexpr (sizeof(R) == 4) {
+    if (p[0] == 16 && p[1] == 8 && p[2] == 8)
+      return staged ? (const void *)k3_particle_step<R, true, 16, 8, 8>
+                    : (const void *)k3_particle_step<R, false, 16, 8, 8>;
+    if (p[0] == 8 && p[1] == 8 && p[2] == 8)
+      return staged ? (const void *)k3_particle_step<R, true, 8, 8, 8>
+                    : (const void *)k3_particle_step<R, false, 8, 8, 8>;
+    if (p[0] == 16 && p[1] == 16 && p[2] == 16 && !staged)
+      return (const void *)k3_particle_step<R, false, 16, 16, 16>;
+  }
+  return staged ? (const void *)k3_particle_step<R, true> : (const void *)k3_particle_step<R, false>;
+}
+
 template <typename R>
 pic_status prepare3(Ctx3 *c) {
   if (c->ps_grid) return PIC_OK;
@@ -1589,8 +1643,8 @@ pic_status prepare3(Ctx3 *c) {
     if (r != CUDA_SUCCESS) c->staged = false;
   }
   c->ps_smem = c->staged ? staged_smem : tile_bytes(&c->cfg, sizeof(R));
-  const void *k = c->staged ? (const void *)k3_particle_step<R, true>
-                            : (const void *)k3_particle_step<R, false>;
+  const void *k = pick_particle_step3<R>(g.p, c->staged);
+  c->ps_kernel = k;
   CK3(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->ps_smem));
   int per_sm = 0, dev = 0, nsm = 0;
   CK3(cudaGetDevice(&dev));

@@ -188,13 +188,18 @@ def test_window_step_decoupled_from_patch_size():
     _assert(particle_errs(o, g), 1e-9)
 
 
-def test_fp32_single_step_bounds():
+@pytest.mark.parametrize("patch,tma", [((16, 8, 8), True), ((8, 8, 8), True), ((16, 8, 8), False),
+                                       ((16, 16, 16), False), ((8, 16, 8), True)])
+def test_fp32_single_step_bounds(patch, tma):
+    """FP32 step from an FP64 state, for the compile-time patch shapes
+    (16x8x8, 8x8x8 staged or gathered from HBM, 16^3 gathered) and a
+    runtime-shaped one (8x16x8)."""
     run = _open3()
     parts = W.small_random_particles3(run, 40000, seed=9, uth=0.6)
     fields = W.random_fields(W.field_shape3(run), seed=10, amp=0.1)
     o = Oracle3(run)
     o.load(parts)
-    g = pic.Pic(pic.config_from_run(run, "fp32"))
+    g = pic.Pic(pic.config_from_run(run, "fp32", patch=patch, tma=tma))
     g.pic_load_particles(parts)
     for k, v in fields.items():
         o.set_field(k, v)
@@ -253,7 +258,8 @@ def test_full_size_config3_invariants_fp32():
     moving window: a few steps in the benchmark's launch configuration;
     particle count, charge and the discrete continuity residual checked."""
     run = W.lwfa_3d()
-    g = pic.Pic(pic.config_from_run(run, "fp32", capacity_factor=2.0))
+    # the benchmark stores the 16^3 patches' particles in 8^3 sub-patches
+    g = pic.Pic(pic.config_from_run(run, "fp32", capacity_factor=2.0, patch=(8, 8, 8)))
     g.pic_load_plasma()
     d0 = g.pic_diag()
     assert d0["np"] == 1024 * 128 * 256 * 2
