@@ -60,6 +60,52 @@ struct Win {
   R x[4][3], y[4][3], z[4][4];
 };
 
+// Shared-memory reduction v into *p when c holds, as one predicated
+// instruction (no branch around it).  Volatile, without a memory clobber:
+// the tile is read only after the block barrier that follows the particle
+// loop, which the compiler does not move these statements across, and the
+// particles' other shared-memory accesses (field gathers) need not be
+// ordered against them.
+__device__ __forceinline__ void red_if(float *p, float v, bool c) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f32 [%0], %1;\n\t}" ::"r"(
+          smem_u32(p)),
+      "f"(v), "r"((int)c));
+}
+__device__ __forceinline__ void red_if(double *p, double v, bool c) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f64 [%0], %1;\n\t}" ::"r"(
+          smem_u32(p)),
+      "d"(v), "r"((int)c));
+}
+
+// The contributions of one particle's window, skipping those that are zero
+// by construction: the window's last column (row) when the particle kept its
+// nearest node along x (y) (x4, y4 false: S0 and S1 vanish there and the
+// prefix sum of DS ends at zero one node earlier), and a whole component
+// whose weight is zero (jx, jy: no displacement along it; jz: u_z = 0).
+template <typename R, int JWc>
+__device__ __forceinline__ void deposit(R *Jt, int JWr, int JHW, int o, const Win<R> &w, bool x4,
+                                        bool y4, bool jx, bool jy, bool jz) {
+  const int JW = JWc ? JWc : JWr;
+  R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      red_if(&Jx[l * JW + q], w.x[l][q], jx && (q < 2 || x4) && (l < 3 || y4));
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      red_if(&Jy[l * JW + q], w.y[q][l], jy && (l < 2 || y4) && (q < 3 || x4));
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      red_if(&Jz[l * JW + q], w.z[l][q], jz && (q < 3 || x4) && (l < 3 || y4));
+}
+
 template <typename R, int JWc>
 __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<R> &w) {
   const int JW = JWc ? JWc : JWr;
@@ -170,7 +216,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
         Ft[e] = a.F[c * g.cs + fidx(g, X0 - 4 + xx, Y0 - 1 + yy)];
       }
     }
-    for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
+    {
+      // current tile cleared with 16-byte stores (it starts 16-byte aligned:
+      // 6 FT s bytes after the aligned field tile)
+      uint4 *J4 = reinterpret_cast<uint4 *>(Jt);
+      const int n4 = (int)(3 * JT * sizeof(R) / 16);
+      for (int e = tid; e < n4; e += nth) J4[e] = make_uint4(0u, 0u, 0u, 0u);
+      for (int e = n4 * (int)(16 / sizeof(R)) + tid; e < 3 * JT; e += nth) Jt[e] = R(0);
+    }
     if (tid < 9) {
       int cnt = 0;
       long long base = 0;
@@ -214,9 +267,19 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     // not reached yet): a particle at rest there stays at rest, in place,
     // and deposits nothing (exactly what the full step computes), so it is
     // copied through without the interpolation, push and deposit.
-    int nonzero = 0;
-    for (int e = tid; e < 6 * FT; e += nth) nonzero |= Ft[e] != R(0);
-    const bool quiet = __syncthreads_or(nonzero) == 0;
+    // (16-byte words of the tile, sign bits masked: -0 counts as zero; the
+    // tile holds a multiple of 16 bytes since P is a multiple of 16 / s)
+    unsigned nonzero = 0;
+    {
+      const uint4 *F4 = reinterpret_cast<const uint4 *>(Ft);
+      const int n4 = (int)(6 * FT * sizeof(R) / 16);
+      for (int e = tid; e < n4; e += nth) {
+        const uint4 v = F4[e];
+        nonzero |= sizeof(R) == 4 ? ((v.x | v.y | v.z | v.w) & 0x7fffffffu)
+                                  : (v.x | v.z | ((v.y | v.w) & 0x7fffffffu));
+      }
+    }
+    const bool quiet = __syncthreads_or(nonzero != 0u) == 0;
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -367,8 +430,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
               key = o;
             }
           } else if (x1 != x[m] || y1 != y[m] || nuz != R(0)) {
-            // (a particle that did not move deposits nothing)
-            flush<R, JWc>(Jt, JW, JT, o, cur);
+            // (a particle that did not move deposits nothing).  FP64 skips
+            // the structural zeros by integer flags (an FP64 compare per
+            // entry costs FP64-pipe slots, the path's bound); FP32 tests
+            // each entry, which measured faster there.
+            if constexpr (sizeof(R) == 8)
+              deposit<R, JWc>(Jt, JW, JT, o, cur, di != 0, dj != 0, wx != R(0) && x1 != x[m],
+                              wy != R(0) && y1 != y[m], wz != R(0));
+            else
+              flush<R, JWc>(Jt, JW, JT, o, cur);
           }
           // boundary conditions at domain faces, then destination patch
           int ddx = 0, ddy = 0;
