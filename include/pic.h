@@ -143,6 +143,18 @@ typedef struct pic_config {
                              so the patch size (a performance choice) and
                              the window step (part of the run) are set
                              apart; pic_diag's shifts counts window steps */
+  /* Device memory of the context (fields, particles, buffers, and the
+   * Poisson start's scratch and FFT work area): when dev_alloc is set, taken
+   * with dev_alloc(bytes, alloc_user) and given back with dev_free(ptr,
+   * alloc_user), else cudaMalloc / cudaFree.  Set both or neither
+   * (PIC_EINVAL otherwise).  dev_alloc returns memory of cfg.device aligned
+   * to at least 256 bytes, or NULL (the call then fails with PIC_ENOMEM).
+   * Both are called on the thread of the API call that needs them; the
+   * context's stream is synchronised before each dev_free.  Batches and
+   * servers keep their own small argument arrays with cudaMalloc. */
+  void *(*dev_alloc)(size_t bytes, void *user);
+  void (*dev_free)(void *ptr, void *user);
+  void *alloc_user;
 } pic_config;
 
 typedef struct pic_diag_t {

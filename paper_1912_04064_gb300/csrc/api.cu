@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "alloc.h"
 #include "common.cuh"
 #include "pic3d.h"
 #include "poisson.h"
@@ -78,6 +79,15 @@ struct pic_ctx {
 };
 
 namespace {
+// Device memory of a 2D context (the caller's allocator when configured).
+template <typename T>
+cudaError_t cmalloc(pic_ctx *c, T **p, size_t bytes) {
+  return dev_malloc(c->cfg, p, bytes);
+}
+void cfree(pic_ctx *c, void *p) { dev_free(c->cfg, c->stream, p); }
+}  // namespace
+
+namespace {
 
 const char *kVersion = "libpic 0.1 (sm_103a, 2D3V SDMD patch PIC)";
 
@@ -109,6 +119,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool valid_config(const pic_config *c, std::string &why) {
   if (!c) { why = "null config"; return false; }
   if (c->dims != 2 && c->dims != 3) { why = "dims must be 2 (2D3V) or 3 (3D3V)"; return false; }
+  if (!c->dev_alloc != !c->dev_free) { why = "dev_alloc and dev_free are set together"; return false; }
   if (c->window_cells < 0 || (c->window_cells > 0 && c->window_cells % c->patch[0])) {
     why = "window_cells must be a multiple of patch[0]";
     return false;
@@ -253,15 +264,15 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
   const Geom &g = ctx->g;
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < 6; ++a) {
-      CK(cudaMalloc(&ctx->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
-      CK(cudaMalloc(&ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * ctx->bk.stride));
+      CK(cmalloc(ctx, &ctx->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
+      CK(cmalloc(ctx, &ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * ctx->bk.stride));
     }
-    CK(cudaMalloc(&ctx->cnt[s], sizeof(int) * g.nslots));
-    CK(cudaMalloc(&ctx->bcnt[s], sizeof(int) * g.nslots * 8));
+    CK(cmalloc(ctx, &ctx->cnt[s], sizeof(int) * g.nslots));
+    CK(cmalloc(ctx, &ctx->bcnt[s], sizeof(int) * g.nslots * 8));
     CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
     CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
   }
-  CK(cudaMalloc(&ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
+  CK(cmalloc(ctx, &ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
   // work plan: a slot holds at most cap + bucket stride particles per step
   const bool merge = ctx->cfg.merge > 0;
   Plan &pl = ctx->plan;
@@ -271,11 +282,11 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
   const long long units_max = (long long)(cap + ctx->bk.stride) / pl.unit + 9;
   pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
                                           1ll << 30);
-  CK(cudaMalloc(&pl.item_slot, sizeof(int) * pl.max_items));
-  CK(cudaMalloc(&pl.item_first, sizeof(int) * pl.max_items));
-  CK(cudaMalloc(&pl.n_items, sizeof(int) * 2));
+  CK(cmalloc(ctx, &pl.item_slot, sizeof(int) * pl.max_items));
+  CK(cmalloc(ctx, &pl.item_first, sizeof(int) * pl.max_items));
+  CK(cmalloc(ctx, &pl.n_items, sizeof(int) * 2));
   pl.next = pl.n_items + 1;
-  CK(cudaMalloc(&pl.units, sizeof(int) * g.nslots));
+  CK(cmalloc(ctx, &pl.units, sizeof(int) * g.nslots));
   return PIC_OK;
 }
 
@@ -460,35 +471,35 @@ pic_status capture_graphs(pic_ctx *ctx) {
 
 void free_backup(pic_ctx *c) {
   auto &b = c->bak;
-  cudaFree(b.F);
-  cudaFree(b.rho_bg);
+  cfree(c, b.F);
+  cfree(c, b.rho_bg);
   for (int a = 0; a < 6; ++a) {
-    cudaFree(b.seg[a]);
-    cudaFree(b.bkt[a]);
+    cfree(c, b.seg[a]);
+    cfree(c, b.bkt[a]);
   }
-  cudaFree(b.cnt);
-  cudaFree(b.bcnt);
-  cudaFree(b.st);
+  cfree(c, b.cnt);
+  cfree(c, b.bcnt);
+  cfree(c, b.st);
   b = pic_ctx::Backup{};
 }
 
 void free_particles(pic_ctx *c) {
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < 6; ++a) {
-      cudaFree(c->seg[s][a]);
-      cudaFree(c->bkt[s][a]);
+      cfree(c, c->seg[s][a]);
+      cfree(c, c->bkt[s][a]);
       c->seg[s][a] = c->bkt[s][a] = nullptr;
     }
-    cudaFree(c->cnt[s]);
-    cudaFree(c->bcnt[s]);
+    cfree(c, c->cnt[s]);
+    cfree(c, c->bcnt[s]);
     c->cnt[s] = c->bcnt[s] = nullptr;
   }
-  cudaFree(c->offsets);
+  cfree(c, c->offsets);
   c->offsets = nullptr;
-  cudaFree(c->plan.item_slot);
-  cudaFree(c->plan.item_first);
-  cudaFree(c->plan.n_items);
-  cudaFree(c->plan.units);
+  cfree(c, c->plan.item_slot);
+  cfree(c, c->plan.item_first);
+  cfree(c, c->plan.n_items);
+  cfree(c, c->plan.units);
   c->plan = Plan{};
 }
 
@@ -502,15 +513,15 @@ pic_status take_backup(pic_ctx *ctx) {
   if (!b.F) {
     b.cap = ctx->cap;
     b.bk = ctx->bk;
-    CK(cudaMalloc(&b.F, 9 * g.cs * sizeof(R)));
-    CK(cudaMalloc(&b.rho_bg, g.cs * sizeof(double)));
+    CK(cmalloc(ctx, &b.F, 9 * g.cs * sizeof(R)));
+    CK(cmalloc(ctx, &b.rho_bg, g.cs * sizeof(double)));
     for (int a = 0; a < 6; ++a) {
-      CK(cudaMalloc(&b.seg[a], sizeof(R) * (size_t)g.nslots * b.cap));
-      CK(cudaMalloc(&b.bkt[a], sizeof(R) * (size_t)g.nslots * b.bk.stride));
+      CK(cmalloc(ctx, &b.seg[a], sizeof(R) * (size_t)g.nslots * b.cap));
+      CK(cmalloc(ctx, &b.bkt[a], sizeof(R) * (size_t)g.nslots * b.bk.stride));
     }
-    CK(cudaMalloc(&b.cnt, sizeof(int) * g.nslots));
-    CK(cudaMalloc(&b.bcnt, sizeof(int) * g.nslots * 8));
-    CK(cudaMalloc(&b.st, sizeof(DevState)));
+    CK(cmalloc(ctx, &b.cnt, sizeof(int) * g.nslots));
+    CK(cmalloc(ctx, &b.bcnt, sizeof(int) * g.nslots * 8));
+    CK(cmalloc(ctx, &b.st, sizeof(DevState)));
   }
   const int q = (int)(ctx->step & 1);
   CK(cudaMemcpyAsync(b.F, ctx->F, 9 * g.cs * sizeof(R), cudaMemcpyDeviceToDevice, ctx->stream));
@@ -718,7 +729,7 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   const double *d[6];
   double *tmp = nullptr;
   if (where == PIC_HOST) {
-    CK(cudaMalloc(&tmp, sizeof(double) * 6 * std::max<size_t>(n, 1)));
+    CK(cmalloc(ctx, &tmp, sizeof(double) * 6 * std::max<size_t>(n, 1)));
     for (int a = 0; a < 6; ++a) {
       CK(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
                          ctx->stream));
@@ -732,7 +743,7 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   // validation / counting pass: particles outside the domain reject the
   // whole call without touching the stored particles
   int *cnt = nullptr;
-  CK(cudaMalloc(&cnt, sizeof(int) * g.nslots));
+  CK(cmalloc(ctx, &cnt, sizeof(int) * g.nslots));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, ctx->stream));
   CK(launch_bin_count<R>(g, ctx->col0, d[0], d[1], n, cnt, &ctx->st->err, ctx->stream));
   std::vector<int> h(g.nslots);
@@ -740,12 +751,12 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   DevState hs;
   CK(cudaMemcpyAsync(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  cudaFree(cnt);
+  cfree(ctx, cnt);
   ctx->launches += 1;
   if (hs.err & ERR_LOAD_RANGE) {
     unsigned zero = hs.err & ~ERR_LOAD_RANGE;
     CK(cudaMemcpy(&ctx->st->err, &zero, sizeof zero, cudaMemcpyHostToDevice));
-    if (tmp) cudaFree(tmp);
+    if (tmp) cfree(ctx, tmp);
     return fail(ctx, PIC_EINVAL, "particle position outside the domain");
   }
   if (!ctx->cap) {
@@ -773,7 +784,7 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   // clamp counts of overflowing slots happens via the error word
   if (tmp) {
     CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(tmp);
+    cfree(ctx, tmp);
   }
   ctx->prev_valid = false;
   ctx->plan_ready = false;
@@ -848,7 +859,7 @@ pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, in
   double *dst = out;
   double *tmp = nullptr;
   if (where == PIC_HOST) {
-    CK(cudaMalloc(&tmp, sizeof(double) * 6 * std::max<size_t>(cap, 1)));
+    CK(cmalloc(ctx, &tmp, sizeof(double) * 6 * std::max<size_t>(cap, 1)));
     dst = tmp;
   }
   CK(launch_get_particles<R>(g, ctx->col0, view<R>(ctx, q, 1 - q), ctx->offsets, dst, cap,
@@ -857,16 +868,16 @@ pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, in
   if (tmp) {
     CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(tmp);
+    cfree(ctx, tmp);
   }
   return poll_device(ctx);
 }
 
 pic_status ensure_staging(pic_ctx *ctx, size_t n) {
   if (ctx->staging_n >= n) return PIC_OK;
-  if (ctx->staging) cudaFree(ctx->staging);
+  if (ctx->staging) cfree(ctx, ctx->staging);
   ctx->staging = nullptr;
-  CK(cudaMalloc(&ctx->staging, sizeof(double) * n));
+  CK(cmalloc(ctx, &ctx->staging, sizeof(double) * n));
   ctx->staging_n = n;
   return PIC_OK;
 }
@@ -1392,20 +1403,20 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(PIC_ECUDA);
-  if (cudaMalloc(&ctx->F, field_bytes(g, ctx->rs)) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&ctx->rho_bg, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&ctx->rho_a, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&ctx->rho_b, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&ctx->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->F, field_bytes(g, ctx->rs)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->rho_bg, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->rho_a, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->rho_b, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
   ctx->npartials = 1024;
-  if (cudaMalloc(&ctx->partials, sizeof(double) * 3 * ctx->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc(ctx, &ctx->partials, sizeof(double) * 3 * ctx->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cfg->laser_on) {
     std::vector<double> prof(g.ny + 1);
     for (int j = 0; j <= g.ny; ++j) {
       const double r = ((j + 0.5) * g.dy - cfg->laser_y_center) / cfg->laser_waist;
       prof[j] = cfg->laser_a0 * std::exp(-r * r);
     }
-    if (cudaMalloc(&ctx->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cmalloc(ctx, &ctx->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
     if (cudaMemcpy(ctx->laser_g, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return bail(PIC_ECUDA);
@@ -1431,14 +1442,14 @@ void pic_destroy(pic_ctx *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   free_graphs(ctx);
-  cudaFree(ctx->F);
-  cudaFree(ctx->rho_bg);
-  cudaFree(ctx->rho_a);
-  cudaFree(ctx->rho_b);
-  cudaFree(ctx->laser_g);
-  cudaFree(ctx->st);
-  cudaFree(ctx->partials);
-  cudaFree(ctx->staging);
+  cfree(ctx, ctx->F);
+  cfree(ctx, ctx->rho_bg);
+  cfree(ctx, ctx->rho_a);
+  cfree(ctx, ctx->rho_b);
+  cfree(ctx, ctx->laser_g);
+  cfree(ctx, ctx->st);
+  cfree(ctx, ctx->partials);
+  cfree(ctx, ctx->staging);
   free_particles(ctx);
   free_backup(ctx);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1542,18 +1553,18 @@ pic_status pic_init_fields(pic_ctx *ctx, int mode) {
     return fail(ctx, PIC_EINVAL, "the Poisson start needs periodic axes");
   const size_t n = (size_t)g.nx * g.ny;
   double *buf = nullptr;
-  CK(cudaMalloc(&buf, sizeof(double) * 5 * n));
+  CK(cmalloc(ctx, &buf, sizeof(double) * 5 * n));
   double *rho = buf, *bg = buf + n, *ex = buf + 2 * n, *ey = buf + 3 * n, *ez = buf + 4 * n;
   s = ctx->fp32 ? deposit_current_rho<float>(ctx, ctx->rho_a, false)
                 : deposit_current_rho<double>(ctx, ctx->rho_a, false);
-  if (s) { cudaFree(buf); return s; }
+  if (s) { cfree(ctx, buf); return s; }
   CK(launch_get_field_f64(g, ctx->rho_a, rho, ctx->stream));
   CK(launch_get_field_f64(g, ctx->rho_bg, bg, ctx->stream));
   CK(launch_axpy_f64(rho, bg, n, ctx->stream));
   CK(cudaMemsetAsync(ez, 0, sizeof(double) * n, ctx->stream));
   const int nn[3] = {g.nx, g.ny, 1};
   const double dd[3] = {g.dx, g.dy, 1.0};
-  s = poisson_fields(2, nn, dd, rho, ex, ey, nullptr, ctx->stream, ctx->err);
+  s = poisson_fields(ctx->cfg, 2, nn, dd, rho, ex, ey, nullptr, ctx->stream, ctx->err);
   if (!s) {
     const double *src[3] = {ex, ey, ez};
     for (int c = 0; c < 3 && !s; ++c)
@@ -1561,7 +1572,7 @@ pic_status pic_init_fields(pic_ctx *ctx, int mode) {
                     : do_set_field<double>(ctx, PIC_EX + c, src[c], PIC_DEVICE);
   }
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(buf);
+  cfree(ctx, buf);
   ctx->launches += 6;
   if (s) return s;
   return poll_device(ctx);

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "alloc.h"
 #include "pic3d.h"
 #include "poisson.h"
 #include "shape.cuh"
@@ -1291,6 +1292,13 @@ struct Ctx3 {
   std::string err;
 };
 
+// Device memory of a 3D context (the caller's allocator when configured).
+template <typename T>
+cudaError_t cmalloc3(Ctx3 *c, T **p, size_t bytes) {
+  return dev_malloc(c->cfg, p, bytes);
+}
+void cfree3(Ctx3 *c, void *p) { dev_free(c->cfg, c->stream, p); }
+
 namespace {
 
 pic_status fail3(Ctx3 *c, pic_status s, const std::string &m) {
@@ -1413,45 +1421,45 @@ pic_status alloc3(Ctx3 *c, int cap) {
   const Geom3 &g = c->g;
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < 7; ++a) {
-      CK3(cudaMalloc(&c->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
-      CK3(cudaMalloc(&c->bkt[s][a], sizeof(R) * (size_t)g.nslots * c->bk.stride));
+      CK3(cmalloc3(c, &c->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
+      CK3(cmalloc3(c, &c->bkt[s][a], sizeof(R) * (size_t)g.nslots * c->bk.stride));
     }
-    CK3(cudaMalloc(&c->cnt[s], sizeof(int) * g.nslots));
-    CK3(cudaMalloc(&c->bcnt[s], sizeof(int) * (size_t)g.nslots * NB3));
+    CK3(cmalloc3(c, &c->cnt[s], sizeof(int) * g.nslots));
+    CK3(cmalloc3(c, &c->bcnt[s], sizeof(int) * (size_t)g.nslots * NB3));
     CK3(cudaMemsetAsync(c->cnt[s], 0, sizeof(int) * g.nslots, c->stream));
     CK3(cudaMemsetAsync(c->bcnt[s], 0, sizeof(int) * (size_t)g.nslots * NB3, c->stream));
   }
-  CK3(cudaMalloc(&c->offsets, sizeof(long long) * ((size_t)g.nslots * (1 + NB3) + 1)));
+  CK3(cmalloc3(c, &c->offsets, sizeof(long long) * ((size_t)g.nslots * (1 + NB3) + 1)));
   Plan &pl = c->plan;
   pl.unit = 1;
   pl.chunk = c->cfg.task_chunk > 0 ? c->cfg.task_chunk : 2048;
   const long long units_max = (long long)cap + c->bk.stride;
   pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
                                           1ll << 30);
-  CK3(cudaMalloc(&pl.item_slot, sizeof(int) * pl.max_items));
-  CK3(cudaMalloc(&pl.item_first, sizeof(int) * pl.max_items));
-  CK3(cudaMalloc(&pl.n_items, sizeof(int) * 2));
+  CK3(cmalloc3(c, &pl.item_slot, sizeof(int) * pl.max_items));
+  CK3(cmalloc3(c, &pl.item_first, sizeof(int) * pl.max_items));
+  CK3(cmalloc3(c, &pl.n_items, sizeof(int) * 2));
   pl.next = pl.n_items + 1;
-  CK3(cudaMalloc(&pl.units, sizeof(int) * g.nslots));
+  CK3(cmalloc3(c, &pl.units, sizeof(int) * g.nslots));
   return PIC_OK;
 }
 
 void free_particles3(Ctx3 *c) {
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < 7; ++a) {
-      cudaFree(c->seg[s][a]);
-      cudaFree(c->bkt[s][a]);
+      cfree3(c, c->seg[s][a]);
+      cfree3(c, c->bkt[s][a]);
       c->seg[s][a] = c->bkt[s][a] = nullptr;
     }
-    cudaFree(c->cnt[s]);
-    cudaFree(c->bcnt[s]);
+    cfree3(c, c->cnt[s]);
+    cfree3(c, c->bcnt[s]);
     c->cnt[s] = c->bcnt[s] = nullptr;
   }
-  cudaFree(c->offsets);
-  cudaFree(c->plan.item_slot);
-  cudaFree(c->plan.item_first);
-  cudaFree(c->plan.n_items);
-  cudaFree(c->plan.units);
+  cfree3(c, c->offsets);
+  cfree3(c, c->plan.item_slot);
+  cfree3(c, c->plan.item_first);
+  cfree3(c, c->plan.n_items);
+  cfree3(c, c->plan.units);
   c->offsets = nullptr;
   c->plan = Plan{};
 }
@@ -1762,7 +1770,7 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
   const double *d[7];
   double *tmp = nullptr;
   if (where == PIC_HOST) {
-    CK3(cudaMalloc(&tmp, sizeof(double) * 7 * std::max<size_t>(n, 1)));
+    CK3(cmalloc3(c, &tmp, sizeof(double) * 7 * std::max<size_t>(n, 1)));
     for (int a = 0; a < 7; ++a) {
       CK3(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
       d[a] = tmp + a * n;
@@ -1771,7 +1779,7 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
     for (int a = 0; a < 7; ++a) d[a] = src[a];
   }
   int *cnt = nullptr;
-  CK3(cudaMalloc(&cnt, sizeof(int) * g.nslots));
+  CK3(cmalloc3(c, &cnt, sizeof(int) * g.nslots));
   CK3(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, c->stream));
   const int blocks = (int)std::min<size_t>((n + 255) / 256 + 1, 4096);
   k3_bin_count<<<blocks, 256, 0, c->stream>>>(g, c->col0, d[0], d[1], d[2], n, cnt, &c->st->err);
@@ -1780,12 +1788,12 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
   DevState hs;
   CK3(cudaMemcpyAsync(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost, c->stream));
   CK3(cudaStreamSynchronize(c->stream));
-  cudaFree(cnt);
+  cfree3(c, cnt);
   c->launches += 1;
   if (hs.err & ERR_LOAD_RANGE) {
     const unsigned keep = hs.err & ~ERR_LOAD_RANGE;
     CK3(cudaMemcpy(&c->st->err, &keep, sizeof keep, cudaMemcpyHostToDevice));
-    if (tmp) cudaFree(tmp);
+    if (tmp) cfree3(c, tmp);
     return fail3(c, PIC_EINVAL, "particle position outside the domain");
   }
   if (!c->cap) {
@@ -1804,7 +1812,7 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
   c->launches += 2;
   if (tmp) {
     CK3(cudaStreamSynchronize(c->stream));
-    cudaFree(tmp);
+    cfree3(c, tmp);
   }
   c->prev_valid = false;
   free_graphs3(c);
@@ -1832,9 +1840,9 @@ pic_status fill3(Ctx3 *c) {
 
 pic_status ensure_staging3(Ctx3 *c, size_t n) {
   if (c->staging_n >= n) return PIC_OK;
-  cudaFree(c->staging);
+  cfree3(c, c->staging);
   c->staging = nullptr;
-  CK3(cudaMalloc(&c->staging, sizeof(double) * n));
+  CK3(cmalloc3(c, &c->staging, sizeof(double) * n));
   c->staging_n = n;
   return PIC_OK;
 }
@@ -1970,7 +1978,7 @@ pic_status get_particles3(Ctx3 *c, double *out, size_t cap, size_t *n, int where
                       c->stream));
   double *dst = out, *tmp = nullptr;
   if (where == PIC_HOST) {
-    CK3(cudaMalloc(&tmp, sizeof(double) * 7 * std::max<size_t>(cap, 1)));
+    CK3(cmalloc3(c, &tmp, sizeof(double) * 7 * std::max<size_t>(cap, 1)));
     dst = tmp;
   }
   k3_get_particles<R><<<g.nslots, 256, 0, c->stream>>>(g, c->col0, view3<R>(c, q, 1 - q), c->offsets,
@@ -1980,7 +1988,7 @@ pic_status get_particles3(Ctx3 *c, double *out, size_t cap, size_t *n, int where
   if (tmp) {
     CK3(cudaMemcpyAsync(out, tmp, sizeof(double) * 7 * cap, cudaMemcpyDeviceToHost, c->stream));
     CK3(cudaStreamSynchronize(c->stream));
-    cudaFree(tmp);
+    cfree3(c, tmp);
   }
   return poll3(c);
 }
@@ -2113,13 +2121,13 @@ pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std
     c3_destroy(c);
     return s;
   };
-  if (cudaMalloc(&c->F, (size_t)NCOMP * g.cs * c->rs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc3(c, &c->F, (size_t)NCOMP * g.cs * c->rs) != cudaSuccess) return bail(PIC_ENOMEM);
   for (double **p : {&c->rho_bg, &c->rho_a, &c->rho_b})
-    if (cudaMalloc(p, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&c->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&c->active, sizeof(int) * g.nslots) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&c->plan_hist, sizeof(int) * 2 * PLAN3_CLASSES) != cudaSuccess) return bail(PIC_ENOMEM);
-  if (cudaMalloc(&c->partials, sizeof(double) * 3 * c->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cmalloc3(c, p, sizeof(double) * g.cs) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc3(c, &c->st, sizeof(DevState)) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc3(c, &c->active, sizeof(int) * g.nslots) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc3(c, &c->plan_hist, sizeof(int) * 2 * PLAN3_CLASSES) != cudaSuccess) return bail(PIC_ENOMEM);
+  if (cmalloc3(c, &c->partials, sizeof(double) * 3 * c->npartials) != cudaSuccess) return bail(PIC_ENOMEM);
   if (cfg->laser_on) {
     std::vector<double> prof((size_t)(g.n[2] + 1) * g.n[1]);
     for (int k = 0; k <= g.n[2]; ++k)
@@ -2128,7 +2136,7 @@ pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std
         const double rz = (k * g.d[2] - cfg->laser_z_center) / cfg->laser_waist;
         prof[(size_t)k * g.n[1] + j] = cfg->laser_a0 * std::exp(-(ry * ry + rz * rz));
       }
-    if (cudaMalloc(&c->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
+    if (cmalloc3(c, &c->laser_g, sizeof(double) * prof.size()) != cudaSuccess) return bail(PIC_ENOMEM);
     if (cudaMemcpy(c->laser_g, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return bail(PIC_ECUDA);
@@ -2146,16 +2154,16 @@ void c3_destroy(Ctx3 *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_graphs3(c);
-  cudaFree(c->F);
-  cudaFree(c->rho_bg);
-  cudaFree(c->rho_a);
-  cudaFree(c->rho_b);
-  cudaFree(c->laser_g);
-  cudaFree(c->st);
-  cudaFree(c->active);
-  cudaFree(c->plan_hist);
-  cudaFree(c->partials);
-  cudaFree(c->staging);
+  cfree3(c, c->F);
+  cfree3(c, c->rho_bg);
+  cfree3(c, c->rho_a);
+  cfree3(c, c->rho_b);
+  cfree3(c, c->laser_g);
+  cfree3(c, c->st);
+  cfree3(c, c->active);
+  cfree3(c, c->plan_hist);
+  cfree3(c, c->partials);
+  cfree3(c, c->staging);
   free_particles3(c);
   delete c;
 }
@@ -2236,17 +2244,17 @@ pic_status c3_init_fields(Ctx3 *c, int mode) {
     if (g.fbc[a] != FBC_PERIODIC) return fail3(c, PIC_EINVAL, "the Poisson start needs periodic axes");
   const size_t n = (size_t)g.n[0] * g.n[1] * g.n[2];
   double *buf = nullptr;
-  CK3(cudaMalloc(&buf, sizeof(double) * 5 * n));
+  CK3(cmalloc3(c, &buf, sizeof(double) * 5 * n));
   double *rho = buf, *bg = buf + n, *ex = buf + 2 * n, *ey = buf + 3 * n, *ez = buf + 4 * n;
   s = c->fp32 ? deposit_rho3<float>(c, c->rho_a, false) : deposit_rho3<double>(c, c->rho_a, false);
-  if (s) { cudaFree(buf); return s; }
+  if (s) { cfree3(c, buf); return s; }
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
   k3_get_field<double><<<blocks, 256, 0, c->stream>>>(g, c->rho_a, rho);
   k3_get_field<double><<<blocks, 256, 0, c->stream>>>(g, c->rho_bg, bg);
   CK3(cudaGetLastError());
   CK3(launch_axpy_f64(rho, bg, n, c->stream));
   const double dd[3] = {g.d[0], g.d[1], g.d[2]};
-  s = poisson_fields(3, g.n, dd, rho, ex, ey, ez, c->stream, c->err);
+  s = poisson_fields(c->cfg, 3, g.n, dd, rho, ex, ey, ez, c->stream, c->err);
   if (!s) {
     const double *src[3] = {ex, ey, ez};
     for (int k = 0; k < 3 && !s; ++k)
@@ -2254,7 +2262,7 @@ pic_status c3_init_fields(Ctx3 *c, int mode) {
                   : set_field3<double>(c, PIC_EX + k, src[k], PIC_DEVICE);
   }
   cudaStreamSynchronize(c->stream);
-  cudaFree(buf);
+  cfree3(c, buf);
   c->launches += 6;
   if (s) return s;
   return poll3(c);

@@ -9,6 +9,7 @@
 
 #include <string>
 
+#include "alloc.h"
 #include "common.cuh"
 #include "poisson.h"
 
@@ -67,24 +68,35 @@ __global__ void k_poisson_gradient(const double *phi, int dims, int n0, int n1, 
 
 }  // namespace
 
-pic_status poisson_fields(int dims, const int n[3], const double d[3], double *rho, double *Ex,
-                          double *Ey, double *Ez, cudaStream_t s, std::string &err) {
+pic_status poisson_fields(const pic_config &cf, int dims, const int n[3], const double d[3],
+                          double *rho, double *Ex, double *Ey, double *Ez, cudaStream_t s,
+                          std::string &err) {
   const long long cells = (long long)n[0] * n[1] * (dims == 3 ? n[2] : 1);
   const long long half = (long long)(n[0] / 2 + 1) * n[1] * (dims == 3 ? n[2] : 1);
   cufftDoubleComplex *h = nullptr;
-  if (cudaMalloc(&h, sizeof(cufftDoubleComplex) * half) != cudaSuccess) {
+  if (dev_malloc(cf, &h, sizeof(cufftDoubleComplex) * half) != cudaSuccess) {
     err = "cannot allocate the Poisson spectrum";
     return PIC_ENOMEM;
   }
+  // plans without their own work areas: one shared area from the context's
+  // allocator
   cufftHandle fwd = 0, inv = 0;
-  bool ok = true;
-  if (dims == 3) {
-    ok = cufftPlan3d(&fwd, n[2], n[1], n[0], CUFFT_D2Z) == CUFFT_SUCCESS &&
-         cufftPlan3d(&inv, n[2], n[1], n[0], CUFFT_Z2D) == CUFFT_SUCCESS;
-  } else {
-    ok = cufftPlan2d(&fwd, n[1], n[0], CUFFT_D2Z) == CUFFT_SUCCESS &&
-         cufftPlan2d(&inv, n[1], n[0], CUFFT_Z2D) == CUFFT_SUCCESS;
+  size_t ws_f = 0, ws_i = 0;
+  void *work = nullptr;
+  bool ok = cufftCreate(&fwd) == CUFFT_SUCCESS && cufftCreate(&inv) == CUFFT_SUCCESS &&
+            cufftSetAutoAllocation(fwd, 0) == CUFFT_SUCCESS &&
+            cufftSetAutoAllocation(inv, 0) == CUFFT_SUCCESS;
+  if (ok && dims == 3) {
+    ok = cufftMakePlan3d(fwd, n[2], n[1], n[0], CUFFT_D2Z, &ws_f) == CUFFT_SUCCESS &&
+         cufftMakePlan3d(inv, n[2], n[1], n[0], CUFFT_Z2D, &ws_i) == CUFFT_SUCCESS;
+  } else if (ok) {
+    ok = cufftMakePlan2d(fwd, n[1], n[0], CUFFT_D2Z, &ws_f) == CUFFT_SUCCESS &&
+         cufftMakePlan2d(inv, n[1], n[0], CUFFT_Z2D, &ws_i) == CUFFT_SUCCESS;
   }
+  const size_t ws = ws_f > ws_i ? ws_f : ws_i;
+  ok = ok && (ws == 0 || dev_malloc(cf, &work, ws) == cudaSuccess);
+  ok = ok && cufftSetWorkArea(fwd, work) == CUFFT_SUCCESS &&
+       cufftSetWorkArea(inv, work) == CUFFT_SUCCESS;
   ok = ok && cufftSetStream(fwd, s) == CUFFT_SUCCESS && cufftSetStream(inv, s) == CUFFT_SUCCESS;
   ok = ok && cufftExecD2Z(fwd, rho, h) == CUFFT_SUCCESS;
   if (ok) {
@@ -103,7 +115,8 @@ pic_status poisson_fields(int dims, const int n[3], const double d[3], double *r
   ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
   if (fwd) cufftDestroy(fwd);
   if (inv) cufftDestroy(inv);
-  cudaFree(h);
+  dev_free(cf, s, work);
+  dev_free(cf, s, h);
   if (!ok) {
     err = "the Poisson solve failed";
     return PIC_ECUDA;

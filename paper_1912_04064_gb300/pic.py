@@ -45,7 +45,31 @@ class pic_config(C.Structure):
         ("tma", C.c_int), ("block", C.c_int), ("merge", C.c_int), ("auto_grow", C.c_int),
         ("sort_every", C.c_int), ("task_chunk", C.c_int), ("filter_passes", C.c_int),
         ("inj_ymin", C.c_double), ("laser_z_center", C.c_double), ("window_cells", C.c_int),
+        ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_user", C.c_void_p),
     ]
+
+
+# the caller's device allocator (pic_config.dev_alloc / dev_free)
+DEV_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def torch_allocator(device: int = 0):
+    """dev_alloc / dev_free callbacks that take the context's device memory
+    from PyTorch's caching allocator; returns (alloc, free), to be kept alive
+    as long as the context (``Pic(cfg, allocator=...)`` does)."""
+    import torch
+
+    def alloc(nbytes, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device)
+        except Exception:
+            return None
+
+    def free(ptr, _user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return DEV_ALLOC(alloc), DEV_FREE(free)
 
 
 class pic_diag_t(C.Structure):
@@ -279,8 +303,15 @@ def _field_shape(cfg: pic_config):
 class Pic:
     """One libpic context (C-ABI calls with argument marshalling)."""
 
-    def __init__(self, cfg: pic_config):
+    def __init__(self, cfg: pic_config, allocator=None):
+        """allocator: optional (dev_alloc, dev_free) ctypes callbacks (e.g.
+        ``torch_allocator()``) for all device memory of the context; kept
+        alive with it."""
         self.cfg = cfg
+        self._allocator = allocator
+        if allocator is not None:
+            cfg.dev_alloc = C.cast(allocator[0], C.c_void_p)
+            cfg.dev_free = C.cast(allocator[1], C.c_void_p)
         self.h = C.c_void_p()
         self._check(lib().pic_create(C.byref(cfg), C.byref(self.h)), create=True)
         self.shape = _field_shape(cfg)

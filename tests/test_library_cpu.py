@@ -86,6 +86,8 @@ def test_version(libpic):
     lambda c: c.bc_part[0].__setitem__(0, 0),     # periodic particles, open fields
     lambda c: setattr(c, "block", 100),
     lambda c: setattr(c, "m", 0.0),
+    lambda c: setattr(c, "dev_alloc", 4096),       # allocator without its free
+    lambda c: setattr(c, "dev_free", 4096),        # free without its allocator
 ])
 def test_invalid_configs_rejected_before_cuda(libpic, mutate):
     run, _ = W.lwfa_2d(n=(256, 128), patch=(32, 32))
