@@ -164,6 +164,25 @@ def profiled_value(name, key):
         return None
 
 
+def over_ranks(v, dist, device, op="max"):
+    """v reduced over all ranks (max or sum); v itself on a single rank.
+    device: where the collective's tensor lives ("cuda:k" under NCCL, "cpu"
+    under gloo)."""
+    if not dist:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_rate(units_this_rank, ms_this_rank, dist, device):
+    """Units processed by all ranks / the slowest rank's time, per second."""
+    units = over_ranks(units_this_rank, dist, device, "sum")
+    ms_max = over_ranks(ms_this_rank, dist, device, "max")
+    return units / (ms_max / 1e3), ms_max
+
+
 def algorithmic_bytes(npart, ncell, rsize):
     """Bytes the method must move once per step: per particle read
     x, y, ux, uy, uz, w and write x, y, ux, uy, uz (11 words); per cell gather
@@ -208,6 +227,8 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
         g.pic_step(steps)
         ev1.record(stream)
         torch.cuda.synchronize(device)
+    if dist:
+        dist.barrier()
     ms = ev0.elapsed_time(ev1)
     d1 = g.pic_diag()
     # per-kernel times over the same steps (replayed from the snapshot taken
@@ -223,17 +244,13 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     gt.pic_step(steps)
     t1 = gt.pic_diag()
     gt.close()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{device}")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     np_mean = 0.5 * (d0["np"] + d1["np"])
-    total_ps = np_mean * steps * world
+    value, ms_max = whole_job_rate(np_mean * steps, ms, dist, f"cuda:{device}")
     step_bytes, k_bytes = algorithmic_bytes(np_mean, ncell, rs)
     ps_ms = (t1["ms_particles"] - t0["ms_particles"]) / steps
     fd_ms = (t1["ms_fields"] - t0["ms_fields"]) / steps
     return {
-        "value": total_ps / (ms_max / 1e3),
+        "value": value,
         "ms_per_step": ms_max / steps,
         "np": np_mean, "np0": npart0, "ncell": ncell, "rs": rs,
         "step_bytes": step_bytes, "kernel_bytes": k_bytes,

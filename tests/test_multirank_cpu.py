@@ -1,0 +1,74 @@
+"""The multi-rank host logic of the benchmark on CPU with gloo (world size
+2): the whole-job rate is the units of all ranks over the slowest rank's
+time, and the reference arm runs on rank 0 only under torchrun."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    units = [100.0, 300.0][rank]
+    ms = [10.0, 20.0][rank]
+    rate, ms_max = bench.whole_job_rate(units, ms, dist, "cpu")
+    q.put((rank, rate, ms_max, bench.over_ranks(rank + 1, dist, "cpu", "sum")))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_whole_job_rate_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, rate, ms_max, total in got:
+        assert ms_max == 20.0            # the slowest rank's time
+        assert rate == pytest.approx(400.0 / 0.020)   # all ranks' units
+        assert total == 3.0
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    rate, ms_max = bench.whole_job_rate(50.0, 5.0, None, "cpu")
+    assert (rate, ms_max) == (50.0 / 0.005, 5.0)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """`bench.py --impl reference` under torchrun with two ranks: one JSON
+    line, from rank 0 (the oracle on a bounded sample); rank 1 exits 0."""
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--cpu-steps", "1"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
