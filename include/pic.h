@@ -131,7 +131,11 @@ typedef struct pic_config {
   int task_chunk;         /* particles per work item of the particle step: a
                              patch holding more is split over several
                              blocks, each with its own current tile
-                             (0 = 2048) */
+                             (0 = 2048; at most 4096: the FP32 tile
+                             accumulates in 32-bit fixed point whose
+                             resolution, 2^(ceil(log2 task_chunk) - 30)
+                             of the largest particle's contribution,
+                             follows from it) */
   int filter_passes;      /* binomial current filter (Section 3.2): 0 off, 1 or
                              2 passes of (1,2,1)/4 along x then y applied to
                              J before the field update (2D only) */
@@ -292,7 +296,7 @@ typedef struct pic_batch_config {
   void *stream;    /* cudaStream_t of the batch; NULL = library-owned */
   int device;      /* CUDA device ordinal (every run's) */
   int use_graph;   /* 1: each step replays a captured CUDA graph */
-  int task_chunk;  /* particles per work item (0 = 2048) */
+  int task_chunk;  /* particles per work item (0 = 2048, at most 4096) */
 } pic_batch_config;
 typedef struct pic_batch_diag_t {
   long long steps;     /* batched steps taken */

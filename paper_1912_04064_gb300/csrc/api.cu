@@ -46,6 +46,9 @@ struct pic_ctx {
   long long step = 0;
   double t = 0.0;
   int nshift = 0, col0 = 0;
+  // largest |w| the context holds or injects (scales the FP32 fixed-point
+  // current tile; weights never change once loaded)
+  double wmax = 0.0;
   bool prev_valid = false;  // previous particle state + last J usable
   CUtensorMap tmap;
   bool tmap_ok = false;
@@ -120,6 +123,7 @@ bool valid_config(const pic_config *c, std::string &why) {
   if (!c) { why = "null config"; return false; }
   if (c->dims != 2 && c->dims != 3) { why = "dims must be 2 (2D3V) or 3 (3D3V)"; return false; }
   if (!c->dev_alloc != !c->dev_free) { why = "dev_alloc and dev_free are set together"; return false; }
+  if (c->task_chunk < 0 || c->task_chunk > 4096) { why = "task_chunk must be in [0, 4096]"; return false; }
   if (c->window_cells < 0 || (c->window_cells > 0 && c->window_cells % c->patch[0])) {
     why = "window_cells must be a multiple of patch[0]";
     return false;
@@ -320,6 +324,32 @@ pic_status build_tmap(pic_ctx *ctx) {
 
 // Arguments of the particle step of parity p: reads segment set p and the
 // bucket set 1 - p, writes segment set 1 - p, bucket set p and current set p.
+// Fixed-point scales of the FP32 current tile for work items of at most
+// per_item particles (see StepArgs::jscale).  Every contribution of a
+// particle of weight w is at most (3/4)^2 |q| w in magnitude, for all three
+// components:
+//   x: (q dx/dt) w P A with P a prefix sum of S1 - S0, |P| <= 3/4 |dx_cells|
+//      (the cumulative quadratic shape has slope at most 3/4) and
+//      |dx_cells| < dt/dx (v < c), A = (S0 + S1)/2 <= 3/4;  y alike;
+//   z: q w v_z W_z with |v_z| < 1 and W_z <= (3/4)^2.
+// So 2^K / ((3/4)^2 |q| w_max) keeps each contribution within 2^K and an
+// item's sums within per_item 2^K <= 2^30.
+template <typename R>
+void set_current_scale(StepArgs<R> &a, const Geom &g, double wmax, int per_item) {
+  int lg = 0;
+  while ((1 << lg) < per_item) ++lg;
+  const double two_k = std::ldexp(1.0, 30 - lg);
+  const double c = 0.5625 * std::fabs(g.q);
+  // a floor on w_max keeps the scale finite in FP32 (tinier weights only
+  // lose resolution)
+  const double wm = c > 0 ? std::max(wmax, two_k / (c * 1e30)) : 0.0;
+  const double sc = c > 0 ? two_k / (c * wm) : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    a.jscale[k] = R(sc);
+    a.junit[k] = sc > 0 ? R(1.0 / sc) : R(0);
+  }
+}
+
 template <typename R>
 StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   const Geom &g = ctx->g;
@@ -348,6 +378,8 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.RP = R(g.P);
   a.RQ = R(g.Q);
   a.plan = ctx->plan;
+  set_current_scale(a, g, ctx->wmax,
+                    ctx->plan.chunk > 0 ? ctx->plan.chunk * ctx->plan.unit : 2048);
   return a;
 }
 
@@ -746,19 +778,32 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   CK(cmalloc(ctx, &cnt, sizeof(int) * g.nslots));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, ctx->stream));
   CK(launch_bin_count<R>(g, ctx->col0, d[0], d[1], n, cnt, &ctx->st->err, ctx->stream));
+  // largest |w| of the call (float64 bits; +inf for a non-finite weight)
+  unsigned long long *wbits = reinterpret_cast<unsigned long long *>(ctx->partials);
+  CK(cudaMemsetAsync(wbits, 0, sizeof *wbits, ctx->stream));
+  CK(launch_absmax_f64(d[5], n, wbits, ctx->stream));
+  unsigned long long hw = 0;
+  CK(cudaMemcpyAsync(&hw, wbits, sizeof hw, cudaMemcpyDeviceToHost, ctx->stream));
   std::vector<int> h(g.nslots);
   CK(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, ctx->stream));
   DevState hs;
   CK(cudaMemcpyAsync(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   cfree(ctx, cnt);
-  ctx->launches += 1;
+  ctx->launches += 2;
   if (hs.err & ERR_LOAD_RANGE) {
     unsigned zero = hs.err & ~ERR_LOAD_RANGE;
     CK(cudaMemcpy(&ctx->st->err, &zero, sizeof zero, cudaMemcpyHostToDevice));
     if (tmp) cfree(ctx, tmp);
     return fail(ctx, PIC_EINVAL, "particle position outside the domain");
   }
+  double wl = 0.0;
+  memcpy(&wl, &hw, sizeof wl);
+  if (!std::isfinite(wl)) {
+    if (tmp) cfree(ctx, tmp);
+    return fail(ctx, PIC_EINVAL, "non-finite particle weight");
+  }
+  ctx->wmax = std::max(ctx->wmax, wl);
   if (!ctx->cap) {
     int mx = *std::max_element(h.begin(), h.end());
     double cf = ctx->cfg.capacity_factor > 0 ? ctx->cfg.capacity_factor : 2.0;
@@ -1067,6 +1112,7 @@ struct SnapHeader {
   long long step;
   double t;
   int prev_valid, sticky_pad;
+  double wmax;
 };
 
 size_t snapshot_bytes(const pic_ctx *c) {
@@ -1101,6 +1147,7 @@ struct pic_batch {
   bool dirty = true;
   std::vector<int> cap_built;
   std::vector<void *> seg_built;
+  std::vector<double> wmax_built;  // the runs' weight bounds the scales were set for
   std::vector<int> parity0;  // run parity at phase 0
   int phase = 0;
   // device arrays: step / field arguments per phase, plan
@@ -1151,7 +1198,9 @@ bool batch_stale(const pic_batch *b) {
   if (b->dirty) return true;
   for (size_t r = 0; r < b->runs.size(); ++r) {
     const pic_ctx *c = b->runs[r];
-    if (c->cap != b->cap_built[r] || c->seg[0][0] != b->seg_built[r]) return true;
+    if (c->cap != b->cap_built[r] || c->seg[0][0] != b->seg_built[r] ||
+        c->wmax != b->wmax_built[r])
+      return true;
     if ((int)(c->step & 1) != (b->parity0[r] ^ b->phase)) return true;
   }
   return false;
@@ -1184,6 +1233,7 @@ pic_status batch_build(pic_batch *b) {
   batch_free_graphs(b);
   b->cap_built.assign(n, 0);
   b->seg_built.assign(n, nullptr);
+  b->wmax_built.assign(n, 0.0);
   b->parity0.assign(n, 0);
   b->phase = 0;
   b->P = b->runs[0]->g.P;
@@ -1208,8 +1258,10 @@ pic_status batch_build(pic_batch *b) {
     b->parity0[r] = p0;
     b->cap_built[r] = c->cap;
     b->seg_built[r] = c->seg[0][0];
+    b->wmax_built[r] = c->wmax;
     for (int k = 0; k < 2; ++k) {
       sa[k].push_back(step_args<R>(c, p0 ^ k));
+      set_current_scale(sa[k].back(), g, c->wmax, chunk);  // the batch plan's items
       fa[k].push_back(field_args<R>(c, p0 ^ k));
     }
     slots.off[r + 1] = slots.off[r] + g.nslots;
@@ -1380,6 +1432,11 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
   if (ctx->cfg.tma < 0) ctx->cfg.tma = 1;
   ctx->g = make_geom(cfg);
   ctx->fp32 = cfg->prec == PIC_FP32;
+  {
+    // weights the injection (window, pic_load_plasma) can create
+    const int ppc = cfg->inj_ppc[0] * cfg->inj_ppc[1];
+    if (ppc > 0 && std::isfinite(cfg->inj_n0)) ctx->wmax = std::fabs(cfg->inj_n0) / ppc;
+  }
   ctx->rs = ctx->fp32 ? 4 : 8;
   const Geom &g = ctx->g;
   auto bail = [&](pic_status s) {
@@ -1642,10 +1699,10 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   const Geom &g = ctx->g;
   char *p = (char *)host;
   SnapHeader h{};
-  memcpy(h.magic, "PICSNAP1", 8);
+  memcpy(h.magic, "PICSNAP2", 8);
   h.nx = g.nx; h.ny = g.ny; h.P = g.P; h.Q = g.Q; h.fp32 = ctx->fp32;
   h.cap = ctx->cap; h.nshift = ctx->nshift; h.col0 = ctx->col0;
-  h.step = ctx->step; h.t = ctx->t; h.prev_valid = ctx->prev_valid;
+  h.step = ctx->step; h.t = ctx->t; h.prev_valid = ctx->prev_valid; h.wmax = ctx->wmax;
   memcpy(p, &h, sizeof h);
   p += sizeof h;
   auto d2h = [&](const void *src, size_t n) -> cudaError_t {
@@ -1675,7 +1732,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (bytes < sizeof h) return fail(ctx, PIC_EINVAL, "snapshot too small");
   memcpy(&h, host, sizeof h);
   const Geom &g = ctx->g;
-  if (memcmp(h.magic, "PICSNAP1", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
+  if (memcmp(h.magic, "PICSNAP2", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
       h.fp32 != (int)ctx->fp32)
     return fail(ctx, PIC_EINVAL, "snapshot does not match this configuration");
   CK(cudaSetDevice(ctx->cfg.device));
@@ -1689,6 +1746,8 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
     }
   }
   ctx->cap = h.cap;
+  if (h.wmax != ctx->wmax) free_graphs(ctx);  // the current scales are baked into the graphs
+  ctx->wmax = h.wmax;
   ctx->bk = bucket_layout(h.cap);
   const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
                       (h.cap ? particle_bytes(g, h.cap, ctx->rs) : 0);
@@ -1729,7 +1788,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
 pic_status pic_batch_create(const pic_batch_config *cfg, pic_batch **out) {
   if (!out || !cfg) return PIC_EINVAL;
   *out = nullptr;
-  if (cfg->task_chunk < 0) return PIC_EINVAL;
+  if (cfg->task_chunk < 0 || cfg->task_chunk > 4096) return PIC_EINVAL;
   pic_batch *b = new (std::nothrow) pic_batch();
   if (!b) return PIC_ENOMEM;
   b->device = cfg->device;

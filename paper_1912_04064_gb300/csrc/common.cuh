@@ -244,6 +244,13 @@ struct StepArgs {
   R eps;               // q dt / (2 m)
   R cjx, cjy, cjz;     // -q dx / dt, -q dy / dt, q
   R RP, RQ;            // patch size as reals
+  // FP32: the shared current tile accumulates in 32-bit fixed point
+  // (integer shared atomics are native; float ones are not): a contribution
+  // v of component c adds round(v jscale[c]); the tile's integer times
+  // junit[c] = 1 / jscale[c] is the current.  jscale[c] = 2^K / ((3/4)^2
+  // |q| w_max) bounds every contribution by 2^K, and K = 30 - ceil(log2(the
+  // particles of a work item)) keeps an item's sums below 2^30.
+  R jscale[3], junit[3];
   Plan plan;
 };
 
@@ -342,6 +349,9 @@ template <typename R>
 cudaError_t launch_get_field(const Geom &g, const R *arr, double *dst, cudaStream_t s);
 cudaError_t launch_get_field_f64(const Geom &g, const double *arr, double *dst, cudaStream_t s);
 cudaError_t launch_set_field_f64(const Geom &g, double *arr, const double *src, cudaStream_t s);
+// *out = max(*out, max |w[i]|) over i < n as float64 bits (out on the
+// device, initialised by the caller; a non-finite w gives +inf).
+cudaError_t launch_absmax_f64(const double *w, size_t n, unsigned long long *out, cudaStream_t s);
 // y[i] += x[i], i < n (float64).
 cudaError_t launch_axpy_f64(double *y, const double *x, size_t n, cudaStream_t s);
 template <typename R>

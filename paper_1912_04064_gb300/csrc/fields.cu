@@ -593,6 +593,31 @@ __global__ void k_axpy_f64(double *y, const double *x, size_t n) {
 }
 }  // namespace
 
+namespace {
+__global__ void k_absmax_f64(const double *w, size_t n, unsigned long long *out) {
+  unsigned long long m = 0ull;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double a = fabs(w[i]);
+    // bits of a non-negative double order as the values; NaN counts as inf
+    const unsigned long long b =
+        isfinite(a) ? (unsigned long long)__double_as_longlong(a) : 0x7ff0000000000000ull;
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_down_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+}  // namespace
+
+cudaError_t launch_absmax_f64(const double *w, size_t n, unsigned long long *out, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+  k_absmax_f64<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(w, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_f64(double *y, const double *x, size_t n, cudaStream_t s) {
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_axpy_f64<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(y, x, n);

@@ -106,25 +106,63 @@ __device__ __forceinline__ void deposit(R *Jt, int JWr, int JHW, int o, const Wi
       red_if(&Jz[l * JW + q], w.z[l][q], jz && (q < 3 || x4) && (l < 3 || y4));
 }
 
-template <typename R, int JWc>
-__device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<R> &w) {
+// FP32 window flush into the 32-bit fixed-point current tile: each
+// contribution becomes round(v scale) (native integer shared atomics; a
+// contribution that rounds to zero is skipped).
+template <int JWc>
+__device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, const Win<float> &w,
+                                            const float sc[3]) {
   const int JW = JWc ? JWc : JWr;
-  R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
+  int *Jx = reinterpret_cast<int *>(Jt) + o, *Jy = Jx + JHW, *Jz = Jx + 2 * JHW;
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      if (w.x[l][q] != R(0)) atomicAdd(&Jx[l * JW + q], w.x[l][q]);
+    for (int q = 0; q < 3; ++q) {
+      const int v = __float2int_rn(w.x[l][q] * sc[0]);
+      if (v != 0) atomicAdd(&Jx[l * JW + q], v);
+    }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-      if (w.y[q][l] != R(0)) atomicAdd(&Jy[l * JW + q], w.y[q][l]);
+    for (int l = 0; l < 3; ++l) {
+      const int v = __float2int_rn(w.y[q][l] * sc[1]);
+      if (v != 0) atomicAdd(&Jy[l * JW + q], v);
+    }
 #pragma unroll
   for (int l = 0; l < 4; ++l)
 #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int v = __float2int_rn(w.z[l][q] * sc[2]);
+      if (v != 0) atomicAdd(&Jz[l * JW + q], v);
+    }
+}
+
+// The window's contributions into the current tile: FP32 in fixed point,
+// FP64 by value-tested float64 atomics (the MERGE path's sums).
+template <typename R, int JWc>
+__device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<R> &w,
+                                      const R sc[3]) {
+  if constexpr (sizeof(R) == 4) {
+    flush_fixed<JWc>(Jt, JWr, JHW, o, w, sc);
+  } else {
+    const int JW = JWc ? JWc : JWr;
+    R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (w.x[l][q] != R(0)) atomicAdd(&Jx[l * JW + q], w.x[l][q]);
+#pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (w.z[l][q] != R(0)) atomicAdd(&Jz[l * JW + q], w.z[l][q]);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        if (w.y[q][l] != R(0)) atomicAdd(&Jy[l * JW + q], w.y[q][l]);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (w.z[l][q] != R(0)) atomicAdd(&Jz[l * JW + q], w.z[l][q]);
+  }
 }
 
 // Particle step kernel.  PT, QT: patch size known at compile time (0 =
@@ -193,6 +231,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     R *Jt = Ft + 6 * FT;
     const R rdx = a.rdx, rdy = a.rdy, eps = a.eps;
     const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
+    const R jsc[3] = {a.jscale[0], a.jscale[1], a.jscale[2]};
+    const R ju0 = a.junit[0], ju1 = a.junit[1], ju2 = a.junit[2];
     const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
     const int col0 = a.st->col0;
     unsigned err = 0;
@@ -425,20 +465,20 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc.z[l][q] += cur.z[l][q];
             } else {
-              if (key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc);
+              if (key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc);
               acc = cur;
               key = o;
             }
           } else if (x1 != x[m] || y1 != y[m] || nuz != R(0)) {
             // (a particle that did not move deposits nothing).  FP64 skips
             // the structural zeros by integer flags (an FP64 compare per
-            // entry costs FP64-pipe slots, the path's bound); FP32 tests
-            // each entry, which measured faster there.
+            // entry costs FP64-pipe slots, the path's bound); FP32 converts
+            // each entry to fixed point and skips the zeros.
             if constexpr (sizeof(R) == 8)
               deposit<R, JWc>(Jt, JW, JT, o, cur, di != 0, dj != 0, wx != R(0) && x1 != x[m],
                               wy != R(0) && y1 != y[m], wz != R(0));
             else
-              flush<R, JWc>(Jt, JW, JT, o, cur);
+              flush<R, JWc>(Jt, JW, JT, o, cur, jsc);
           }
           // boundary conditions at domain faces, then destination patch
           int ddx = 0, ddy = 0;
@@ -503,7 +543,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
         }
       }
     }
-    if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc);
+    if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       x[m] = nx_[m]; y[m] = ny_[m]; ux[m] = nux_[m]; uy[m] = nuy_[m]; uz[m] = nuz_[m];
@@ -514,7 +554,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     __syncthreads();
     // ---- SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
-      const R v = Jt[e];
+      R v;
+      if constexpr (sizeof(R) == 4) {
+        const int iv = reinterpret_cast<const int *>(Jt)[e];
+        const int c = e / JT;
+        v = iv ? R(iv) * (c == 0 ? ju0 : (c == 1 ? ju1 : ju2)) : R(0);
+      } else {
+        v = Jt[e];
+      }
       if (v != R(0)) {
         const int c = e / JT, r = e - c * JT, l = r / JW, q = r - l * JW;
         int gi = X0 - 2 + q, gj = Y0 - 2 + l;

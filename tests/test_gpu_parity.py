@@ -228,6 +228,50 @@ def test_fp32_single_step_error_bounds():
     assert max(perr[k] for k in ("ux", "uy", "uz")) < 1e-5
 
 
+@pytest.mark.parametrize("chunk", [0, 4096])
+def test_fp32_fixed_point_current_at_its_bound(chunk):
+    """The FP32 current tile accumulates in 32-bit fixed point scaled so
+    that a work item's sums stay below 2^30.  The worst case: every particle
+    of the item in one cell with the largest weight and the same fast
+    velocity, so that all contributions to a node add up and their rounding
+    errors align (2048 particles, the default item; then one item of 4096,
+    the largest allowed).  No wrap-around, and J within the FP32 bound of
+    the oracle."""
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    n = 2048 if chunk == 0 else 4096
+    parts = {"x": np.full(n, 20.0 * 0.1 + 0.013), "y": np.full(n, 30.0 * 0.1 + 0.071),
+             "ux": np.full(n, 2.0), "uy": np.full(n, -1.5), "uz": np.full(n, 1.0),
+             "w": np.full(n, 1.0)}
+    o, g = pair(run, parts, prec="fp32", task_chunk=chunk, capacity_factor=1.0)
+    o.step(1)
+    g.pic_step(1)
+    errs = field_errors(o, g, names=("Jx", "Jy", "Jz"))
+    print("fp32 pile-up J errors", errs)
+    _assert_fields(errs, TOL32_J, names=("Jx", "Jy", "Jz"))
+
+
+def test_fp32_current_with_disparate_weights():
+    """Weights spanning six decades (the fixed-point unit follows the
+    largest): J still within the FP32 bound relative to its maximum."""
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    parts = W.small_random_particles(run, 20000, seed=43, uth=0.5)
+    parts["w"] = 10.0 ** np.random.default_rng(44).uniform(-6, 0, parts["w"].size)
+    o, g = pair(run, parts, prec="fp32")
+    o.step(1)
+    g.pic_step(1)
+    _assert_fields(field_errors(o, g, names=("Jx", "Jy", "Jz")), TOL32_J, names=("Jx", "Jy", "Jz"))
+
+
+def test_non_finite_weight_is_rejected_at_load():
+    run = W.periodic_run((64, 64), (0.1, 0.1), (16, 16))
+    parts = W.small_random_particles(run, 100, seed=45)
+    parts["w"][7] = np.inf
+    g = pic.Pic(pic.config_from_run(run, "fp32"))
+    with pytest.raises(pic.PicError) as e:
+        g.pic_load_particles(parts)
+    assert e.value.status == pic.PIC_EINVAL
+
+
 def test_fp32_energy_history_config1():
     run, parts = W.thermal_2d(seed=1)
     o, g = pair(run, parts, prec="fp32", background=("uniform", 1.0))
