@@ -156,6 +156,10 @@ struct Step3 {
   R eps;     // q dt / (2 m)
   R cj[3];   // -q d / dt
   R RP[3];   // patch size as reals
+  // FP32: the shared current tile accumulates in 32-bit fixed point (see
+  // StepArgs::jscale): a contribution v adds round(v jscale), the tile's
+  // integer times junit is the current
+  R jscale, junit;
   Plan plan;
   const int *active;  // per physical patch: E or Bm nonzero on one of its cells
 };
@@ -518,6 +522,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
           // whole component when the particle did not move along it.
           const int st3[3] = {1, JW, JW * JH};
           const int base = (org[2] * JH + org[1]) * JW + org[0];
+          const R jsc = a.jscale;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
@@ -536,9 +541,17 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
                 const R A = S0[b1][m1] * (S0[b2][m2] + R(0.5) * DS[b2][m2]) +
                             DS[b1][m1] * (R(0.5) * S0[b2][m2] + R(1.0 / 3.0) * DS[b2][m2]);
                 R *row = J + m1 * s1 + m2 * s2;
-                atomicAdd(row, P0 * A);
-                atomicAdd(row + sc, P1 * A);
-                if (wc) atomicAdd(row + 2 * sc, P2 * A);
+                if constexpr (sizeof(R) == 4) {
+                  // 32-bit fixed point (native integer shared atomics)
+                  int *ir = reinterpret_cast<int *>(row);
+                  atomicAdd(ir, __float2int_rn(P0 * A * jsc));
+                  atomicAdd(ir + sc, __float2int_rn(P1 * A * jsc));
+                  if (wc) atomicAdd(ir + 2 * sc, __float2int_rn(P2 * A * jsc));
+                } else {
+                  atomicAdd(row, P0 * A);
+                  atomicAdd(row + sc, P1 * A);
+                  if (wc) atomicAdd(row + 2 * sc, P2 * A);
+                }
               }
             }
           }
@@ -605,7 +618,13 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     __syncthreads();
     // SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
-      const R v = Jt[e];
+      R v;
+      if constexpr (sizeof(R) == 4) {
+        const int iv = reinterpret_cast<const int *>(Jt)[e];
+        v = iv ? R(iv) * a.junit : R(0);
+      } else {
+        v = Jt[e];
+      }
       if (v == R(0)) continue;
       const int c = e / JT, r = e - c * JT;
       const int l = r / (JW * JH), r2 = r - l * (JW * JH), m = r2 / JW, q = r2 - m * JW;
@@ -1284,6 +1303,7 @@ struct Ctx3 {
   long long step = 0;
   double t = 0.0;
   int nshift = 0, col0 = 0;
+  double wmax = 0.0;  // largest |w| held or injected (FP32 current scale)
   bool prev_valid = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   double ms_particles = 0, ms_fields = 0, ms_window = 0;
@@ -1491,6 +1511,19 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   a.eps = R(g.q * g.dt / (2.0 * g.m));
   a.plan = c->plan;
   a.active = c->active;
+  // Every contribution is (q d/dt) w P A with |P| <= 3/4 |displacement in
+  // cells| < 3/4 dt/d and the transverse weight A <= (3/4)^2, so at most
+  // (3/4)^3 |q| w_max; 2^K / that keeps it within 2^K and an item's sums
+  // within 2^30 (K = 30 - ceil(log2 of the particles of an item)).
+  const int per_item = c->plan.chunk > 0 ? c->plan.chunk : 2048;
+  int lg = 0;
+  while ((1 << lg) < per_item) ++lg;
+  const double two_k = std::ldexp(1.0, 30 - lg);
+  const double cm = 0.421875 * std::fabs(g.q);
+  const double wm = cm > 0 ? std::max(c->wmax, two_k / (cm * 1e30)) : 0.0;
+  const double sc = cm > 0 ? two_k / (cm * wm) : 0.0;
+  a.jscale = R(sc);
+  a.junit = sc > 0 ? R(1.0 / sc) : R(0);
   return a;
 }
 
@@ -1783,6 +1816,11 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
   CK3(cudaMemsetAsync(cnt, 0, sizeof(int) * g.nslots, c->stream));
   const int blocks = (int)std::min<size_t>((n + 255) / 256 + 1, 4096);
   k3_bin_count<<<blocks, 256, 0, c->stream>>>(g, c->col0, d[0], d[1], d[2], n, cnt, &c->st->err);
+  unsigned long long *wbits = reinterpret_cast<unsigned long long *>(c->partials);
+  CK3(cudaMemsetAsync(wbits, 0, sizeof *wbits, c->stream));
+  CK3(launch_absmax_f64(d[6], n, wbits, c->stream));
+  unsigned long long hw = 0;
+  CK3(cudaMemcpyAsync(&hw, wbits, sizeof hw, cudaMemcpyDeviceToHost, c->stream));
   std::vector<int> h(g.nslots);
   CK3(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * g.nslots, cudaMemcpyDeviceToHost, c->stream));
   DevState hs;
@@ -1795,6 +1833,16 @@ pic_status load3(Ctx3 *c, const double *const src[7], size_t n, int where) {
     CK3(cudaMemcpy(&c->st->err, &keep, sizeof keep, cudaMemcpyHostToDevice));
     if (tmp) cfree3(c, tmp);
     return fail3(c, PIC_EINVAL, "particle position outside the domain");
+  }
+  double wl = 0.0;
+  memcpy(&wl, &hw, sizeof wl);
+  if (!std::isfinite(wl)) {
+    if (tmp) cfree3(c, tmp);
+    return fail3(c, PIC_EINVAL, "non-finite particle weight");
+  }
+  if (wl > c->wmax) {
+    c->wmax = wl;
+    free_graphs3(c);  // the current scale is baked into captured steps
   }
   if (!c->cap) {
     int mx = *std::max_element(h.begin(), h.end());
@@ -2112,6 +2160,11 @@ pic_status c3_create(const pic_config *cfg, cudaStream_t stream, Ctx3 **out, std
   if (!c) return PIC_ENOMEM;
   c->cfg = *cfg;
   c->g = make_geom3(cfg);
+  {
+    // weights the injection (window, pic_load_plasma) can create
+    const int ppc = cfg->inj_ppc[0] * cfg->inj_ppc[1] * cfg->inj_ppc[2];
+    if (ppc > 0 && std::isfinite(cfg->inj_n0)) c->wmax = std::fabs(cfg->inj_n0) / ppc;
+  }
   c->fp32 = cfg->prec == PIC_FP32;
   c->rs = c->fp32 ? 4 : 8;
   c->stream = stream;
