@@ -12,6 +12,8 @@ the defaults (1000 + 10 + 990) cover the workload's 2000 steps.
 One JSON line is printed on rank 0:
   value        particle-steps/s over all ranks (FP32 path, the headline)
   fp64         the same for the FP64 path (its own run)
+  fp32_float_current  the FP32 path with float shared-atomic current
+               accumulation instead of the default 32-bit fixed point
   roofline     dominant kernel (the patch particle step): algorithmic bytes
                per launch / mean launch time (CUDA events on the launching
                stream) against the measured HBM copy bandwidth
@@ -196,7 +198,7 @@ def algorithmic_bytes(npart, ncell, rsize):
 
 
 def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1, sort=0,
-            chunk=0):
+            chunk=0, current_float=False):
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -209,7 +211,8 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     stream = torch.cuda.Stream(device=device)
     cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                               use_graph=True, timing=False, capacity_factor=cf, merge=merge,
-                              sort_every=sort, task_chunk=chunk)
+                              sort_every=sort, task_chunk=chunk,
+                              current_float=current_float)
     g = pic.Pic(cfg)
     g.pic_load_particles(parts)
     g.pic_set_background("neutralising")
@@ -236,7 +239,8 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     # launching stream (no graph replay)
     cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                                 use_graph=False, timing=True, capacity_factor=cf, merge=merge,
-                                sort_every=sort, task_chunk=chunk)
+                                sort_every=sort, task_chunk=chunk,
+                              current_float=current_float)
     g.close()
     gt = pic.Pic(cfg_t)
     gt.pic_restore(blob)
@@ -647,6 +651,8 @@ def main():
                     help="arrival window of the served-ensemble measurement (0: skip)")
     ap.add_argument("--steps3d", type=int, default=40,
                     help="timed steps of the 3D3V config-3 leg (0: skip)")
+    ap.add_argument("--float-current", type=int, default=1,
+                    help="1: also time the FP32 path with float shared-atomic current accumulation")
     ap.add_argument("--precision-steps", type=int, default=2000,
                     help="steps of the FP32-vs-FP64 precision study (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=100,
@@ -693,6 +699,11 @@ def main():
 
     r32 = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist,
                   args.capacity_factor, args.merge, args.sort_every, args.task_chunk)
+    r32f = None
+    if args.float_current:
+        r32f = run_gpu("fp32", args.steps, args.warmup, args.spinup, local, rank, world, dist,
+                       args.capacity_factor, args.merge, args.sort_every, args.task_chunk,
+                       current_float=True)
     r64 = None
     if args.fp64_steps > 0:
         r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
@@ -746,6 +757,11 @@ def main():
             "speedup_fp32_over_fp64": r32["value"] / r64["value"],
             "hbm_frac_whole_step": r64["step_bytes"] / (r64["ms_per_step"] * 1e-3) / 1e9 / hbm,
             "roofline": alu_roofline_fp64(r64["particle_step_ms"])},
+        "fp32_float_current": None if r32f is None else {
+            "value": r32f["value"], "ms_per_step": r32f["ms_per_step"],
+            "particle_step_ms": r32f["particle_step_ms"],
+            "note": "the same FP32 path and steps with the shared current tile accumulated by "
+                    "float atomics (pic_config.current_float = 1) instead of 32-bit fixed point"},
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
     }

@@ -159,6 +159,13 @@ typedef struct pic_config {
   void *(*dev_alloc)(size_t bytes, void *user);
   void (*dev_free)(void *ptr, void *user);
   void *alloc_user;
+  int current_float;      /* FP32 path: 1 = the shared current tile
+                             accumulates with float atomics; 0 (default) =
+                             32-bit fixed point scaled to the largest
+                             particle weight (native integer shared atomics;
+                             contributions below 2^(ceil(log2 task_chunk)
+                             - 31) of the largest possible one are lost).
+                             FP64 always accumulates in float64. */
 } pic_config;
 
 typedef struct pic_diag_t {

@@ -380,6 +380,7 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.plan = ctx->plan;
   set_current_scale(a, g, ctx->wmax,
                     ctx->plan.chunk > 0 ? ctx->plan.chunk * ctx->plan.unit : 2048);
+  a.jfloat = ctx->cfg.current_float != 0;
   return a;
 }
 

@@ -251,6 +251,7 @@ struct StepArgs {
   // |q| w_max) bounds every contribution by 2^K, and K = 30 - ceil(log2(the
   // particles of a work item)) keeps an item's sums below 2^30.
   R jscale[3], junit[3];
+  int jfloat;          // FP32: accumulate the tile with float atomics instead
   Plan plan;
 };
 

@@ -66,12 +66,6 @@ struct Win {
 // loop, which the compiler does not move these statements across, and the
 // particles' other shared-memory accesses (field gathers) need not be
 // ordered against them.
-__device__ __forceinline__ void red_if(float *p, float v, bool c) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f32 [%0], %1;\n\t}" ::"r"(
-          smem_u32(p)),
-      "f"(v), "r"((int)c));
-}
 __device__ __forceinline__ void red_if(double *p, double v, bool c) {
   asm volatile(
       "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f64 [%0], %1;\n\t}" ::"r"(
@@ -137,13 +131,15 @@ __device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, 
     }
 }
 
-// The window's contributions into the current tile: FP32 in fixed point,
-// FP64 by value-tested float64 atomics (the MERGE path's sums).
+// The window's contributions into the current tile: FP32 in fixed point
+// (or, jfloat, by value-tested float atomics), FP64 by value-tested float64
+// atomics (the MERGE path's sums).
 template <typename R, int JWc>
 __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<R> &w,
-                                      const R sc[3]) {
-  if constexpr (sizeof(R) == 4) {
-    flush_fixed<JWc>(Jt, JWr, JHW, o, w, sc);
+                                      const R sc[3], bool jfloat) {
+  if (sizeof(R) == 4 && !jfloat) {
+    flush_fixed<JWc>(reinterpret_cast<float *>(Jt), JWr, JHW, o,
+                     reinterpret_cast<const Win<float> &>(w), reinterpret_cast<const float *>(sc));
   } else {
     const int JW = JWc ? JWc : JWr;
     R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
@@ -233,6 +229,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
     const R jsc[3] = {a.jscale[0], a.jscale[1], a.jscale[2]};
     const R ju0 = a.junit[0], ju1 = a.junit[1], ju2 = a.junit[2];
+    const bool jfloat = a.jfloat != 0;
     const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
     const int col0 = a.st->col0;
     unsigned err = 0;
@@ -465,7 +462,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc.z[l][q] += cur.z[l][q];
             } else {
-              if (key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc);
+              if (key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc, jfloat);
               acc = cur;
               key = o;
             }
@@ -478,7 +475,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
               deposit<R, JWc>(Jt, JW, JT, o, cur, di != 0, dj != 0, wx != R(0) && x1 != x[m],
                               wy != R(0) && y1 != y[m], wz != R(0));
             else
-              flush<R, JWc>(Jt, JW, JT, o, cur, jsc);
+              flush<R, JWc>(Jt, JW, JT, o, cur, jsc, jfloat);
           }
           // boundary conditions at domain faces, then destination patch
           int ddx = 0, ddy = 0;
@@ -543,7 +540,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
         }
       }
     }
-    if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc);
+    if (MERGE && key >= 0) flush<R, JWc>(Jt, JW, JT, key, acc, jsc, jfloat);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       x[m] = nx_[m]; y[m] = ny_[m]; ux[m] = nux_[m]; uy[m] = nuy_[m]; uz[m] = nuz_[m];
@@ -555,7 +552,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     // ---- SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
       R v;
-      if constexpr (sizeof(R) == 4) {
+      if (sizeof(R) == 4 && !jfloat) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
         const int c = e / JT;
         v = iv ? R(iv) * (c == 0 ? ju0 : (c == 1 ? ju1 : ju2)) : R(0);

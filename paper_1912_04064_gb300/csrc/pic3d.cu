@@ -160,6 +160,7 @@ struct Step3 {
   // StepArgs::jscale): a contribution v adds round(v jscale), the tile's
   // integer times junit is the current
   R jscale, junit;
+  int jfloat;  // FP32: accumulate the tile with float atomics instead
   Plan plan;
   const int *active;  // per physical patch: E or Bm nonzero on one of its cells
 };
@@ -523,6 +524,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
           const int st3[3] = {1, JW, JW * JH};
           const int base = (org[2] * JH + org[1]) * JW + org[0];
           const R jsc = a.jscale;
+          const bool fixed = sizeof(R) == 4 && !a.jfloat;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
                 const R A = S0[b1][m1] * (S0[b2][m2] + R(0.5) * DS[b2][m2]) +
                             DS[b1][m1] * (R(0.5) * S0[b2][m2] + R(1.0 / 3.0) * DS[b2][m2]);
                 R *row = J + m1 * s1 + m2 * s2;
-                if constexpr (sizeof(R) == 4) {
+                if (fixed) {
                   // 32-bit fixed point (native integer shared atomics)
                   int *ir = reinterpret_cast<int *>(row);
                   atomicAdd(ir, __float2int_rn(P0 * A * jsc));
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     // SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
       R v;
-      if constexpr (sizeof(R) == 4) {
+      if (sizeof(R) == 4 && !a.jfloat) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
         v = iv ? R(iv) * a.junit : R(0);
       } else {
@@ -1524,6 +1526,7 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   const double sc = cm > 0 ? two_k / (cm * wm) : 0.0;
   a.jscale = R(sc);
   a.junit = sc > 0 ? R(1.0 / sc) : R(0);
+  a.jfloat = c->cfg.current_float != 0;
   return a;
 }
 

@@ -188,18 +188,20 @@ def test_window_step_decoupled_from_patch_size():
     _assert(particle_errs(o, g), 1e-9)
 
 
-@pytest.mark.parametrize("patch,tma", [((16, 8, 8), True), ((8, 8, 8), True), ((16, 8, 8), False),
-                                       ((16, 16, 16), False), ((8, 16, 8), True)])
-def test_fp32_single_step_bounds(patch, tma):
+@pytest.mark.parametrize("patch,tma,cfloat", [((16, 8, 8), True, False), ((8, 8, 8), True, False),
+                                              ((16, 8, 8), False, False), ((16, 16, 16), False, False),
+                                              ((8, 16, 8), True, False), ((8, 8, 8), True, True)])
+def test_fp32_single_step_bounds(patch, tma, cfloat):
     """FP32 step from an FP64 state, for the compile-time patch shapes
     (16x8x8, 8x8x8 staged or gathered from HBM, 16^3 gathered) and a
-    runtime-shaped one (8x16x8)."""
+    runtime-shaped one (8x16x8), the current tile in fixed point; and 8^3
+    with float shared atomics."""
     run = _open3()
     parts = W.small_random_particles3(run, 40000, seed=9, uth=0.6)
     fields = W.random_fields(W.field_shape3(run), seed=10, amp=0.1)
     o = Oracle3(run)
     o.load(parts)
-    g = pic.Pic(pic.config_from_run(run, "fp32", patch=patch, tma=tma))
+    g = pic.Pic(pic.config_from_run(run, "fp32", patch=patch, tma=tma, current_float=cfloat))
     g.pic_load_particles(parts)
     for k, v in fields.items():
         o.set_field(k, v)

@@ -211,11 +211,14 @@ def test_edge_cases_fp64(case):
     assert max(particle_errors(o, g).values()) <= 1e-11
 
 
-def test_fp32_single_step_error_bounds():
+@pytest.mark.parametrize("current_float", [False, True])
+def test_fp32_single_step_error_bounds(current_float):
+    """FP32 step from an FP64 state, with the current tile in 32-bit fixed
+    point (default) and with float shared atomics."""
     run = W.periodic_run((128, 64), (0.1, 0.1), (16, 16))
     parts = W.small_random_particles(run, 40000, seed=41, uth=0.5)
     fields = W.random_fields((64, 128), seed=42, amp=0.1)
-    o, g = pair(run, parts, fields, prec="fp32")
+    o, g = pair(run, parts, fields, prec="fp32", current_float=current_float)
     o.step(1)
     g.pic_step(1)
     errs = field_errors(o, g)
