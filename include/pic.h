@@ -165,7 +165,8 @@ typedef struct pic_config {
                              particle weight (native integer shared atomics;
                              contributions below 2^(ceil(log2 task_chunk)
                              - 31) of the largest possible one are lost).
-                             FP64 always accumulates in float64. */
+                             FP64 always accumulates in float64; batched
+                             steps and merge = 1 always in fixed point. */
 } pic_config;
 
 typedef struct pic_diag_t {

@@ -424,7 +424,8 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, bool with_plan, cudaEvent_t mi
   const int block = ctx->cfg.block ? ctx->cfg.block : 256;
   const bool merge = ctx->cfg.merge > 0;
   if (!ctx->ps_grid) {
-    ctx->ps_grid = particle_step_grid<R>(g.P, g.Q, ctx->cfg.tma != 0, merge, block);
+    ctx->ps_grid = particle_step_grid<R>(g.P, g.Q, ctx->cfg.tma != 0, merge, block,
+                                         ctx->cfg.current_float != 0);
     if (ctx->ps_grid <= 0) return fail(ctx, PIC_ECUDA, "particle step occupancy query failed");
   }
   CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,

@@ -252,6 +252,7 @@ struct StepArgs {
   // particles of a work item)) keeps an item's sums below 2^30.
   R jscale[3], junit[3];
   int jfloat;          // FP32: accumulate the tile with float atomics instead
+                       // (selects the kernel instance; batches ignore it)
   Plan plan;
 };
 
@@ -266,7 +267,7 @@ template <typename R>
 cudaError_t launch_plan(const StepArgs<R> &a, cudaStream_t s);
 // Blocks of the particle step resident on the device at once.
 template <typename R>
-int particle_step_grid(int P, int Q, bool tma, bool merge, int block);
+int particle_step_grid(int P, int Q, bool tma, bool merge, int block, bool jfloat = false);
 
 // ---- batches: several independent runs advanced by one launch per kernel.
 // Runs per batch; the tensor maps of a batch travel as one kernel parameter

@@ -165,8 +165,10 @@ __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<
 // runtime).  MERGE: consecutive particles of a thread that share a window
 // are summed in registers before one set of shared atomics.  BATCH: the
 // work items of several independent runs in one launch; each item names its
-// run, whose arguments and tensor map are read from device arrays.
-template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH>
+// run, whose arguments and tensor map are read from device arrays.  JF
+// (FP32): the current tile accumulates with float atomics instead of 32-bit
+// fixed point.
+template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH, bool JF = false>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     k_particle_step(const __grid_constant__ TmapSet<BATCH ? kBatchMax : 1> tm,
                     const StepArgs<R> a0, const BatchRef<R> br) {
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     const R cjx = a.cjx, cjy = a.cjy, cjz = a.cjz;
     const R jsc[3] = {a.jscale[0], a.jscale[1], a.jscale[2]};
     const R ju0 = a.junit[0], ju1 = a.junit[1], ju2 = a.junit[2];
-    const bool jfloat = a.jfloat != 0;
+    constexpr bool jfloat = JF;
     const R RP = PT ? R(PT) : a.RP, RQ = QT ? R(QT) : a.RQ;
     const int col0 = a.st->col0;
     unsigned err = 0;
@@ -634,28 +636,35 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
   }
 }
 
-template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH>
+template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH, bool JF>
 const void *kernel_ptr() {
-  return (const void *)k_particle_step<R, PT, QT, TMA, MERGE, BATCH>;
+  return (const void *)k_particle_step<R, PT, QT, TMA, MERGE, BATCH, JF>;
 }
 
 // Kernel for a patch shape: compile-time tile sizes for the common square
 // patches, a runtime-size kernel otherwise; plain loads always runtime-size.
 // Batched launches (runs may differ in patch size) use runtime sizes unless
 // every run shares the patch shape.
-template <typename R, bool MERGE, bool BATCH>
+template <typename R, bool MERGE, bool BATCH, bool JF = false>
 const void *pick(int P, int Q, bool tma) {
-  if (!tma) return kernel_ptr<R, 0, 0, false, MERGE, BATCH>();
-  if (P == 32 && Q == 32) return kernel_ptr<R, 32, 32, true, MERGE, BATCH>();
-  if (P == 16 && Q == 16) return kernel_ptr<R, 16, 16, true, MERGE, BATCH>();
-  if (P == 8 && Q == 8) return kernel_ptr<R, 8, 8, true, MERGE, BATCH>();
-  return kernel_ptr<R, 0, 0, true, MERGE, BATCH>();
+  if (!tma) return kernel_ptr<R, 0, 0, false, MERGE, BATCH, JF>();
+  if (P == 32 && Q == 32) return kernel_ptr<R, 32, 32, true, MERGE, BATCH, JF>();
+  if (P == 16 && Q == 16) return kernel_ptr<R, 16, 16, true, MERGE, BATCH, JF>();
+  if (P == 8 && Q == 8) return kernel_ptr<R, 8, 8, true, MERGE, BATCH, JF>();
+  return kernel_ptr<R, 0, 0, true, MERGE, BATCH, JF>();
 }
 
+// jfloat (FP32 float-atomic current tile) has its own single-run kernels;
+// batches and the merge variant accumulate in fixed point.
 template <typename R>
-const void *pick_kernel(int P, int Q, bool tma, bool merge, bool batch = false) {
+const void *pick_kernel(int P, int Q, bool tma, bool merge, bool batch = false,
+                        bool jfloat = false) {
   if (batch) return pick<R, false, true>(P, Q, tma);  // batches: one particle per thread
-  return merge ? pick<R, true, false>(P, Q, tma) : pick<R, false, false>(P, Q, tma);
+  if (merge) return pick<R, true, false>(P, Q, tma);
+  if constexpr (sizeof(R) == 4) {
+    if (jfloat) return pick<R, false, false, true>(P, Q, tma);
+  }
+  return pick<R, false, false>(P, Q, tma);
 }
 
 }  // namespace
@@ -668,8 +677,8 @@ template <typename R>
 cudaError_t prepare_particle_step(int P, int Q) {
   const int smem = (int)particle_step_smem(P, Q, sizeof(R));
   for (int t = 0; t < 2; ++t)
-    for (int mg = 0; mg < 2; ++mg) {
-      cudaError_t e = cudaFuncSetAttribute(pick_kernel<R>(P, Q, t != 0, mg != 0),
+    for (int mg = 0; mg < 3; ++mg) {
+      cudaError_t e = cudaFuncSetAttribute(pick_kernel<R>(P, Q, t != 0, mg == 1, false, mg == 2),
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
     }
@@ -698,8 +707,8 @@ int resident_grid(const void *k, int block, size_t smem) {
 }  // namespace
 
 template <typename R>
-int particle_step_grid(int P, int Q, bool tma, bool merge, int block) {
-  return resident_grid(pick_kernel<R>(P, Q, tma, merge), block,
+int particle_step_grid(int P, int Q, bool tma, bool merge, int block, bool jfloat) {
+  return resident_grid(pick_kernel<R>(P, Q, tma, merge, false, jfloat), block,
                        particle_step_smem(P, Q, sizeof(R)));
 }
 
@@ -727,7 +736,7 @@ cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, 
   if (e != cudaSuccess) return e;
   BatchRef<R> none{};
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
-  const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge);
+  const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge, false, a.jfloat != 0);
   TmapSet<1> tm;
   tm.m[0] = *tmap;
   void *args[] = {(void *)&tm, (void *)&a, (void *)&none};
@@ -747,8 +756,8 @@ cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatc
   return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
 }
 
-template int particle_step_grid<float>(int, int, bool, bool, int);
-template int particle_step_grid<double>(int, int, bool, bool, int);
+template int particle_step_grid<float>(int, int, bool, bool, int, bool);
+template int particle_step_grid<double>(int, int, bool, bool, int, bool);
 template int particle_step_batch_grid<float>(int, int, bool, int, size_t);
 template int particle_step_batch_grid<double>(int, int, bool, int, size_t);
 template cudaError_t prepare_particle_step<float>(int, int);

@@ -342,8 +342,9 @@ constexpr int k3_min_blocks() {
 }
 
 // PX, PY, PZ: the patch shape when fixed at compile time (0: read from the
-// geometry), so that tile strides become immediates.
-template <typename R, bool STAGED, int PX = 0, int PY = 0, int PZ = 0>
+// geometry), so that tile strides become immediates.  JF (FP32): the current
+// tile accumulates with float atomics instead of 32-bit fixed point.
+template <typename R, bool STAGED, int PX = 0, int PY = 0, int PZ = 0, bool JF = false>
 __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     k3_particle_step(const __grid_constant__ CUtensorMap tmap, const Step3<R> a) {
   // STAGED: the patch's E and Bm (nodes -4..P+3 along x, -1..Q+1, -1..R+1)
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
           const int st3[3] = {1, JW, JW * JH};
           const int base = (org[2] * JH + org[1]) * JW + org[0];
           const R jsc = a.jscale;
-          const bool fixed = sizeof(R) == 4 && !a.jfloat;
+          constexpr bool fixed = sizeof(R) == 4 && !JF;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     // SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
       R v;
-      if (sizeof(R) == 4 && !a.jfloat) {
+      if (sizeof(R) == 4 && !JF) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
         v = iv ? R(iv) * a.junit : R(0);
       } else {
@@ -1646,10 +1647,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode3() {
 
 // The particle-step instance for a patch shape: FP32 patches of 16x8x8,
 // 8x8x8 and 16x16x16 cells get compile-time-shaped kernels, every other
-// shape (and FP64, bound by its FP64 rate) the runtime-shaped one.
+// shape (and FP64, bound by its FP64 rate, and the FP32 float-atomic
+// current tile) the runtime-shaped one.
 template <typename R>
-const void *pick_particle_step3(const int p[3], bool staged) {
+const void *pick_particle_step3(const int p[3], bool staged, bool jfloat) {
   if constexpr (sizeof(R) == 4) {
+    // float-atomic current tile: the runtime-shaped instances
+    if (jfloat)
+      return staged ? (const void *)k3_particle_step<R, true, 0, 0, 0, true>
+                    : (const void *)k3_particle_step<R, false, 0, 0, 0, true>;
     if (p[0] == 16 && p[1] == 8 && p[2] == 8)
       return staged ? (const void *)k3_particle_step<R, true, 16, 8, 8>
                     : (const void *)k3_particle_step<R, false, 16, 8, 8>;
@@ -1687,7 +1693,7 @@ pic_status prepare3(Ctx3 *c) {
     if (r != CUDA_SUCCESS) c->staged = false;
   }
   c->ps_smem = c->staged ? staged_smem : tile_bytes(&c->cfg, sizeof(R));
-  const void *k = pick_particle_step3<R>(g.p, c->staged);
+  const void *k = pick_particle_step3<R>(g.p, c->staged, c->cfg.current_float != 0);
   c->ps_kernel = k;
   CK3(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->ps_smem));
   int per_sm = 0, dev = 0, nsm = 0;
