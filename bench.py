@@ -616,6 +616,40 @@ def issue_roofline(launch_ms):
             "source": "profiles/particle_step_instruction_mix_lwfa2048.md (one launch, step 1005)"}
 
 
+def shared_atomic_ceiling(launch_ms):
+    """Shared-atomic throughput of the FP32 deposit: the shared-atomic
+    wavefronts of one particle-step launch (ncu, step 1005) over the mean
+    launch time, against the measured rate of conflict-free 32-bit integer
+    shared reductions on this GPU (0.91 warp operations per clock per SM,
+    one wavefront each) at the maximum SM clock."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = json.load(f)["sm_max_mhz"]
+    except Exception:
+        mhz = 2070.0
+    peak = 0.91 * 152 * mhz * 1e6
+    out = {"achieved": None, "peak": peak, "unit": "shared-atomic wavefronts/s",
+           "peak_source": "integer red.shared probe, 0.91 per clock per SM"}
+    try:
+        text = open(os.path.join(ROOT, "profiles", "particle_step_fp32_lwfa2048.md")).read()
+        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
+        h = hashlib.sha256()
+        for f in re.findall(r"`([^`]+)`", m.group(2)):
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if not h.hexdigest().startswith(m.group(1)) or not launch_ms:
+            return out
+        w = int(re.search(r"mem_shared_op_atom\.sum`\) \| (\d+)", text).group(1))
+    except Exception:
+        return out
+    ach = w / (launch_ms * 1e-3)
+    out.update({"achieved": ach, "frac": ach / peak, "wavefronts_per_launch": w,
+                "source": "profiles/particle_step_fp32_lwfa2048.md (one launch, step 1005)"})
+    return out
+
+
 def alu_roofline_fp64(launch_ms):
     """The FP64 particle step is bound by GB300's FP64 unit: FP64 flops of
     one launch (2 FMA + add + mul thread instructions, ncu, step 1005)
@@ -748,7 +782,8 @@ def main():
                      "bytes_per_launch": r32["kernel_bytes"], "launch_ms": r32["particle_step_ms"],
                      "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
                                     "bytes_per_step": r32["step_bytes"]},
-                     "issue": issue_roofline(r32["particle_step_ms"])},
+                     "issue": issue_roofline(r32["particle_step_ms"]),
+                     "shared_atomics": shared_atomic_ceiling(r32["particle_step_ms"])},
         "phases_ms": {"particle_step": r32["particle_step_ms"], "fields": r32["fields_ms"],
                       "window": r32["window_ms"], "sort": r32["sort_ms"]},
         "fp64": None if r64 is None else {
