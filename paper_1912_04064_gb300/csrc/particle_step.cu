@@ -202,12 +202,37 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     fence_mbar_init();
   }
 
+  // PF: the next item is fetched, and its field tile load issued, as soon
+  // as the particles of the current one are done with the field tile, so
+  // that the load overlaps the current tile's flush to the domain (single
+  // runs; a batch's next item may belong to another run).
+  constexpr bool PF = TMA && !BATCH;
+  auto issue_tile = [&](int it) {
+    const Geom &g0 = a0.g;
+    const int P0 = PT ? PT : g0.P, Q0 = QT ? QT : g0.Q;
+    const int FT0 = (BYc ? BYc : Q0 + 3) * (BXc ? BXc : P0 + 8);
+    const int ss = plan.item_slot[it];
+    int pxx = ss % g0.npx - a0.st->col0;
+    if (pxx < 0) pxx += g0.npx;
+    const int pyy = ss / g0.npx;
+    R *F0 = reinterpret_cast<R *>(dsm_raw + pad);
+    mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT0 * sizeof(R)));
+    tma_load_3d(F0, &tm.m[0], &mbar, pxx * P0 - 4 + GX, pyy * Q0 - 1 + GY, 0);
+  };
+  if (PF && tid == 0) {
+    const int first = atomicAdd(plan.next, 1);
+    s_item = first;
+    if (first < n_items) issue_tile(first);
+  }
+
   // Persistent loop over work items: (run, patch slot, chunk of its
   // particles), heaviest patches first, fetched from a global counter.
   for (;;) {
     __syncthreads();  // the previous item is done with the tiles
-    if (tid == 0) s_item = atomicAdd(plan.next, 1);
-    __syncthreads();
+    if (!PF) {
+      if (tid == 0) s_item = atomicAdd(plan.next, 1);
+      __syncthreads();
+    }
     const int item = s_item;
     if (item >= n_items) break;
     const int run = BATCH ? br.item_run[item] : 0;
@@ -244,12 +269,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     const int X0 = px * P, Y0 = py * Q;
 
     // ---- 1. region -> patch field staging (SDMD step ii)
-    if (TMA) {
+    if (TMA && !PF) {
       if (tid == 0) {
         mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
         tma_load_3d(Ft, tmap, &mbar, X0 - 4 + GX, Y0 - 1 + GY, 0);
       }
-    } else {
+    } else if (!TMA) {
       for (int e = tid; e < 6 * FT; e += nth) {
         int c = e / FT, r = e - c * FT, yy = r / BX, xx = r - yy * BX;
         Ft[e] = a.F[c * g.cs + fidx(g, X0 - 4 + xx, Y0 - 1 + yy)];
@@ -551,6 +576,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     nval = nnval;
   }
     __syncthreads();
+    // the field tile is free: fetch the next item and start its tile load
+    if (PF && tid == 0) {
+      const int nxt = atomicAdd(plan.next, 1);
+      s_item = nxt;
+      if (nxt < n_items) issue_tile(nxt);
+    }
     // ---- SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
       R v;
