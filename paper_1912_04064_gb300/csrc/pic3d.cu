@@ -373,10 +373,26 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     mbar_init(&mbar, 1);
     fence_mbar_init();
   }
+  // STAGED: the next item is fetched, and its field tile load issued, as
+  // soon as the particles of the current one are done with the field tile,
+  // so that the load overlaps the current tile's flush to the domain.
+  auto issue_tile = [&](int it) {
+    int q[3];
+    slot_patch(g, a.st->col0, a.plan.item_slot[it], q[0], q[1], q[2]);
+    mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
+    tma_load_4d(Ft, &tmap, &mbar, q[0] * P - 4 + G3, q[1] * Q - 1 + G3, q[2] * Rz - 1 + G3, 0);
+  };
+  if (STAGED && tid == 0) {
+    const int first = atomicAdd(a.plan.next, 1);
+    s_item = first;
+    if (first < n_items) issue_tile(first);
+  }
   for (;;) {
     __syncthreads();
-    if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
-    __syncthreads();
+    if (!STAGED) {
+      if (tid == 0) s_item = atomicAdd(a.plan.next, 1);
+      __syncthreads();
+    }
     const int item = s_item;
     if (item >= n_items) break;
     const int s = a.plan.item_slot[item];
@@ -385,10 +401,6 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
     int pc[3];
     slot_patch(g, col0, s, pc[0], pc[1], pc[2]);
     const int X0 = pc[0] * P, Y0 = pc[1] * Q, Z0 = pc[2] * Rz;
-    if (STAGED && tid == 0) {
-      mbar_arrive_expect_tx(&mbar, (uint32_t)(6 * FT * sizeof(R)));
-      tma_load_4d(Ft, &tmap, &mbar, X0 - 4 + G3, Y0 - 1 + G3, Z0 - 1 + G3, 0);
-    }
     for (int e = tid; e < 3 * JT; e += nth) Jt[e] = R(0);
     if (tid < NB3 + 1) {
       int cnt = 0;
@@ -619,6 +631,12 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
       }
     }
     __syncthreads();
+    // the field tile is free: fetch the next item and start its tile load
+    if (STAGED && tid == 0) {
+      const int nxt = atomicAdd(a.plan.next, 1);
+      s_item = nxt;
+      if (nxt < n_items) issue_tile(nxt);
+    }
     // SDMD step (i): patch current tile -> region current
     for (int e = tid; e < 3 * JT; e += nth) {
       R v;
