@@ -88,6 +88,7 @@ def test_version(libpic):
     lambda c: setattr(c, "m", 0.0),
     lambda c: setattr(c, "dev_alloc", 4096),       # allocator without its free
     lambda c: setattr(c, "dev_free", 4096),        # free without its allocator
+    lambda c: setattr(c, "task_chunk", 8192),      # above the fixed-point tile's item bound
 ])
 def test_invalid_configs_rejected_before_cuda(libpic, mutate):
     run, _ = W.lwfa_2d(n=(256, 128), patch=(32, 32))
@@ -170,6 +171,7 @@ def test_null_arguments(libpic):
     assert b"no batch" in libpic.pic_batch_last_error(None)
     libpic.pic_batch_destroy(None)
     assert libpic.pic_load_plasma(None) == pic.PIC_EINVAL
+    assert libpic.pic_init_fields(None, 1) == pic.PIC_EINVAL
     assert libpic.pic_autotune(None, None, None, None, None, None, None, 0, 0, 1, None,
                                None) == pic.PIC_EINVAL
     libpic.pic_autotune_clear_cache()
