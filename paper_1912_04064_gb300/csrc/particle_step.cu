@@ -1,8 +1,10 @@
-// Patch particle step: one thread block per patch slot (the fine
-// decomposition of SDMD, Section 2.2).  Per block:
+// Patch particle step (the fine decomposition of SDMD, Section 2.2): a
+// persistent grid whose blocks pull work items (a patch slot, or a chunk of
+// a heavy one) from a per-step plan.  Per item:
 //   1. SDMD step (ii): the patch's E and Bm tile (nodes -4..P+3 in x,
 //      -1..Q+1 in y, six components) is staged into shared memory with one
-//      3D TMA box copy (or plain coalesced loads);
+//      3D TMA box copy (or plain coalesced loads); single runs issue the
+//      next item's copy while the current tile is flushed;
 //   2. every particle of the patch (its segment plus the particles that
 //      entered from the 8 neighbours during the previous step) is
 //      interpolated with the quadratic shape, pushed with the Boris scheme
@@ -10,7 +12,8 @@
 //   3. Esirkepov deposition (second-order shape, Section 3.2) into a shared
 //      memory current tile with a 2-node halo, on the 4-node window that
 //      covers both shapes (at most 40 shared atomics per particle, exact
-//      zeros skipped);
+//      zeros skipped); FP32 accumulates in 32-bit fixed point (integer
+//      shared atomics), FP64 in float64;
 //   4. SDMD step (i): the tile is added into the region current;
 //   5. re-binning: particles that stay are compacted into the output
 //      segment, particles that left are appended to the direction bucket

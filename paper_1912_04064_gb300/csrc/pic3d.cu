@@ -5,13 +5,14 @@
 // Per step (context stream, optionally one CUDA graph per step parity):
 //   k3_plan          work items (patch slot, first particle), heaviest first
 //   k3_particle_step persistent blocks over the items: gather E, Bm at x^n
-//                    (27-point quadratic stencils read through the L1 /
-//                    read-only path: a 16^3 patch's E and Bm tile would need
-//                    208 KB of shared memory in FP32, so only the current
-//                    tile is staged on chip), Boris push, move, Esirkepov
-//                    current on the 4-node window per axis into the
-//                    shared-memory current tile (halo 2: 144 atomics per
-//                    particle, exact zeros skipped), boundary conditions,
+//                    (27-point quadratic stencils from a tile staged by one
+//                    4D TMA box where it fits beside the current tile, e.g.
+//                    8^3 or 16x8x8 patches; otherwise through the L1 /
+//                    read-only path, as for 16^3, whose FP32 tile would need
+//                    208 KB), Boris push, move, Esirkepov current on the
+//                    4-node window per axis into the shared-memory current
+//                    tile (halo 2: at most 144 atomics per particle; FP32 in
+//                    32-bit fixed point), boundary conditions,
 //                    compaction of stayers and 26 direction buckets for
 //                    leavers; SDMD step (i): the tile is added into the
 //                    region current with global atomics
