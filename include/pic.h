@@ -383,7 +383,8 @@ typedef struct pic_server_config {
   int steps_per_tick;    /* batched steps per tick at most (0 = 10) */
   int use_graph;         /* batches replay captured CUDA graphs */
 } pic_server_config;
-enum { PIC_REQ_QUEUED = 0, PIC_REQ_RUNNING = 1, PIC_REQ_DONE = 2, PIC_REQ_FAILED = 3 };
+enum { PIC_REQ_QUEUED = 0, PIC_REQ_RUNNING = 1, PIC_REQ_DONE = 2, PIC_REQ_FAILED = 3,
+       PIC_REQ_CANCELLED = 4 };
 typedef struct pic_request_info {
   int state;             /* PIC_REQ_* */
   int status;            /* pic_status of a failed request */
@@ -400,6 +401,7 @@ typedef struct pic_server_stats {
   double particle_steps; /* sum over runs of particles at admission x steps */
   size_t hbm_in_use;     /* footprint estimates of the runs held */
   double busy_s;         /* time spent inside pic_server_tick */
+  long long cancelled;   /* requests cancelled by pic_server_cancel */
 } pic_server_stats;
 
 pic_status pic_server_create(const pic_server_config *cfg, pic_server **out);
@@ -416,6 +418,12 @@ pic_status pic_server_info(const pic_server *s, long long id, pic_request_info *
 /* Hand a finished, kept run's context to the caller, who destroys it
  * (before the server: the context runs on the server's stream). */
 pic_status pic_server_take(pic_server *s, long long id, pic_ctx **out);
+/* Cancel a queued or running request between ticks: a queued one leaves
+ * the queue; a running one leaves its batch and its context is destroyed
+ * (its memory returns to the budget).  Its state becomes PIC_REQ_CANCELLED
+ * with the steps it had done.  PIC_ESTATE for a request that already
+ * finished, failed or was cancelled; PIC_EINVAL for an unknown id. */
+pic_status pic_server_cancel(pic_server *s, long long id);
 pic_status pic_server_get_stats(const pic_server *s, pic_server_stats *out);
 double pic_server_clock(const pic_server *s);
 void pic_server_destroy(pic_server *s);

@@ -1,8 +1,10 @@
 // Device memory of a context: the caller's allocator when pic_config names
-// one (dev_alloc / dev_free / alloc_user), else cudaMalloc / cudaFree.
+// one (dev_alloc / dev_free / alloc_user), else cudaMalloc / cudaFree; and
+// NVTX ranges for the host API calls.
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pic.h"
 
@@ -33,5 +35,14 @@ inline void dev_free(const pic_config &cf, cudaStream_t s, void *p) {
   cudaStreamSynchronize(s);
   cf.dev_free(p, cf.alloc_user);
 }
+
+// NVTX range around a host API call (visible in a profiler's timeline; no
+// cost without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace pic

@@ -1523,6 +1523,7 @@ const char *pic_last_error(const pic_ctx *ctx) {
 pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y, const double *ux,
                               const double *uy, const double *uz, const double *w, size_t n,
                               int where) {
+  NvtxRange range("pic_load_particles");
   pic_status s = check_usable(ctx);
   if (s) return s;
   if (n && (!x || !y || !ux || !uy || !uz || !w)) return fail(ctx, PIC_EINVAL, "null particle array");
@@ -1598,6 +1599,7 @@ pic_status pic_set_background(pic_ctx *ctx, int mode, double value) {
 }
 
 pic_status pic_init_fields(pic_ctx *ctx, int mode) {
+  NvtxRange range("pic_init_fields");
   pic_status s = check_usable(ctx);
   if (s) return s;
   if (mode != PIC_INIT_ZERO && mode != PIC_INIT_POISSON) return fail(ctx, PIC_EINVAL, "bad init mode");
@@ -1638,6 +1640,7 @@ pic_status pic_init_fields(pic_ctx *ctx, int mode) {
 }
 
 pic_status pic_step(pic_ctx *ctx, int nsteps) {
+  NvtxRange range("pic_step");
   pic_status s = check_usable(ctx);
   if (s) return s;
   if (nsteps < 0) return fail(ctx, PIC_EINVAL, "negative step count");
@@ -1844,6 +1847,7 @@ pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n) {
 }
 
 pic_status pic_batch_step(pic_batch *b, int nsteps) {
+  NvtxRange range("pic_batch_step");
   if (!b) return PIC_EINVAL;
   if (nsteps < 0) return bfail(b, PIC_EINVAL, "negative step count");
   if (nsteps == 0 || b->runs.empty()) return PIC_OK;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "alloc.h"
 
 namespace {
 
@@ -193,7 +194,7 @@ struct pic_server {
   pic_batch *batch[2] = {nullptr, nullptr};  // [0] FP64 runs, [1] FP32 runs
   long long next_id = 1;
   size_t in_use = 0;
-  long long ticks = 0, batched_steps = 0, done = 0, failed = 0, submitted = 0;
+  long long ticks = 0, batched_steps = 0, done = 0, failed = 0, submitted = 0, cancelled = 0;
   double particle_steps = 0, busy_s = 0;
 };
 
@@ -226,6 +227,7 @@ void finish(pic_server *s, Request &r, int state, int status) {
   r.status = status;
   r.t_done = server_now(s);
   if (state == PIC_REQ_DONE) ++s->done;
+  else if (state == PIC_REQ_CANCELLED) ++s->cancelled;
   else ++s->failed;
 }
 
@@ -297,6 +299,7 @@ pic_status pic_server_submit(pic_server *s, const pic_config *cfg, long long nst
 }
 
 pic_status pic_server_tick(pic_server *s, int *running) {
+  pic::NvtxRange range("pic_server_tick");
   if (!s) return PIC_EINVAL;
   const double t_enter = server_now(s);
   if (cudaSetDevice(s->cfg.device) != cudaSuccess) return PIC_ECUDA;
@@ -427,12 +430,33 @@ pic_status pic_server_take(pic_server *s, long long id, pic_ctx **out) {
   return PIC_OK;
 }
 
+pic_status pic_server_cancel(pic_server *s, long long id) {
+  if (!s) return PIC_EINVAL;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return PIC_EINVAL;
+  Request &r = it->second;
+  if (r.state == PIC_REQ_QUEUED) {
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), id));
+    finish(s, r, PIC_REQ_CANCELLED, PIC_OK);
+    return PIC_OK;
+  }
+  if (r.state != PIC_REQ_RUNNING) return PIC_ESTATE;
+  if (cudaSetDevice(s->cfg.device) != cudaSuccess) return PIC_ECUDA;
+  // membership first, then the context goes
+  s->running.erase(std::find(s->running.begin(), s->running.end(), id));
+  const pic_status st = sync_batches(s);
+  finish(s, r, PIC_REQ_CANCELLED, PIC_OK);
+  release(s, r);
+  return st;
+}
+
 pic_status pic_server_get_stats(const pic_server *s, pic_server_stats *out) {
   if (!s || !out) return PIC_EINVAL;
   out->submitted = s->submitted;
   out->done = s->done;
   out->failed = s->failed;
   out->queued = (long long)s->queue.size();
+  out->cancelled = s->cancelled;
   out->running = (long long)s->running.size();
   out->ticks = s->ticks;
   out->batched_steps = s->batched_steps;

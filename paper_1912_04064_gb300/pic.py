@@ -107,7 +107,7 @@ class pic_batch_diag_t(C.Structure):
 
 
 PIC_BATCH_MAX = 64
-PIC_REQ_QUEUED, PIC_REQ_RUNNING, PIC_REQ_DONE, PIC_REQ_FAILED = range(4)
+PIC_REQ_QUEUED, PIC_REQ_RUNNING, PIC_REQ_DONE, PIC_REQ_FAILED, PIC_REQ_CANCELLED = range(5)
 
 
 class pic_server_config(C.Structure):
@@ -130,7 +130,7 @@ class pic_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("done", C.c_longlong), ("failed", C.c_longlong),
                 ("queued", C.c_longlong), ("running", C.c_longlong), ("ticks", C.c_longlong),
                 ("batched_steps", C.c_longlong), ("particle_steps", C.c_double),
-                ("hbm_in_use", C.c_size_t), ("busy_s", C.c_double)]
+                ("hbm_in_use", C.c_size_t), ("busy_s", C.c_double), ("cancelled", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -143,7 +143,7 @@ EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_backgro
            "pic_load_plasma", "pic_autotune", "pic_autotune_clear_cache", "pic_server_create",
            "pic_server_submit", "pic_server_tick", "pic_server_info", "pic_server_take",
            "pic_server_get_stats", "pic_server_clock", "pic_server_destroy", "pic_load_particles3",
-           "pic_init_fields"]
+           "pic_init_fields", "pic_server_cancel"]
 
 _lib = None
 
@@ -190,6 +190,8 @@ def lib():
         L.pic_server_tick.argtypes = [vp, C.POINTER(C.c_int)]
         L.pic_server_info.argtypes = [vp, C.c_longlong, C.POINTER(pic_request_info)]
         L.pic_server_take.argtypes = [vp, C.c_longlong, C.POINTER(C.c_void_p)]
+        L.pic_server_cancel.argtypes = [vp, C.c_longlong]
+        L.pic_server_cancel.restype = C.c_int
         L.pic_server_get_stats.argtypes = [vp, C.POINTER(pic_server_stats)]
         L.pic_server_clock.argtypes = [vp]
         L.pic_server_clock.restype = C.c_double
@@ -522,6 +524,11 @@ class Server:
         if rc != PIC_OK:
             raise PicError(rc, "request not finished or not kept")
         return Pic.adopt(h, cfg)
+
+    def pic_server_cancel(self, rid: int):
+        rc = lib().pic_server_cancel(self.h, rid)
+        if rc != PIC_OK:
+            raise PicError(rc, "cannot cancel request %d" % rid)
 
     def pic_server_get_stats(self) -> dict:
         st = pic_server_stats()

@@ -204,6 +204,46 @@ def test_admission_by_memory_budget_and_late_arrivals():
     srv.close()
 
 
+def test_cancel_queued_and_running_requests():
+    """A queued request leaves the queue; a running one leaves its batch
+    and gives its memory back; the others finish equal to runs alone."""
+    run = _lwfa(n=(128, 64), patch=(16, 16), window=False)
+    cfg = pic.config_from_run(run, "fp64")
+    srv = pic.Server(max_runs=2, steps_per_tick=5)
+    a = srv.pic_server_submit(cfg, 30, keep=True)
+    b = srv.pic_server_submit(cfg, 40)
+    c = srv.pic_server_submit(cfg, 20)      # waits for a slot
+    assert srv.pic_server_tick() == 2
+    srv.pic_server_cancel(c)                # queued
+    srv.pic_server_cancel(b)                # running, 5 steps done
+    st = srv.pic_server_get_stats()
+    assert st["cancelled"] == 2 and st["running"] == 1 and st["queued"] == 0
+    for _ in range(100):
+        srv.pic_server_tick()
+        st = srv.pic_server_get_stats()
+        if st["done"] == 1:
+            break
+    ia, ib, ic = (srv.pic_server_info(r) for r in (a, b, c))
+    assert ia["state"] == pic.PIC_REQ_DONE and ia["steps_done"] == 30
+    assert ib["state"] == pic.PIC_REQ_CANCELLED and ib["steps_done"] == 5
+    assert ic["state"] == pic.PIC_REQ_CANCELLED and ic["steps_done"] == 0
+    with pytest.raises(pic.PicError) as e:
+        srv.pic_server_cancel(a)            # already finished
+    assert e.value.status == pic.PIC_ESTATE
+    with pytest.raises(pic.PicError) as e:
+        srv.pic_server_cancel(12345)
+    assert e.value.status == pic.PIC_EINVAL
+    served = srv.pic_server_take(a, cfg)
+    alone = _alone(run, "fp64", 30)
+    for k in EB:
+        x, y = served.pic_get_field(k), alone.pic_get_field(k)
+        assert float(np.max(np.abs(x - y)) / max(np.max(np.abs(y)), 1e-300)) <= TOL_MIX["fp64"], k
+    served.close()
+    alone.close()
+    assert srv.pic_server_get_stats()["hbm_in_use"] == 0
+    srv.close()
+
+
 def test_autotuner_choice_is_valid_cached_and_exact():
     run = W.periodic_run((128, 64), (0.1, 0.1), (16, 16))
     parts = W.small_random_particles(run, 30000, seed=12, uth=0.3)
