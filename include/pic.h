@@ -352,6 +352,15 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
                         const double *ux, const double *uy, const double *uz,
                         const double *w, size_t n, int where, int steps,
                         pic_config *tuned, pic_tune_t *out);
+/* The autotuner on the configured plasma instead of caller particles (each
+ * candidate filled on the device as by pic_load_plasma; needs inj_ppc >= 1
+ * on every axis), for 2D and 3D contexts.  2D candidates as pic_autotune;
+ * 3D candidates are the patch shapes {8, 16}^3 that divide the grid (and,
+ * with the moving window, whose width divides its step) with work items of
+ * {1024, 2048, 4096} particles, plus the configuration as given.  Cached
+ * per process like pic_autotune, keyed by the full grid and the plasma. */
+pic_status pic_autotune_plasma(const pic_config *cfg, int steps, pic_config *tuned,
+                               pic_tune_t *out);
 void pic_autotune_clear_cache(void);
 
 /* ---- Serving ------------------------------------------------------------

@@ -33,11 +33,22 @@ TuneKey tune_key(const pic_config *c, size_t n) {
 }
 
 struct TuneEntry {
-  int patch[2];
+  int patch[3];
   int block, chunk;
   double ms, ms_given;
   int window_cells;
 };
+
+// Key of a plasma-filled workload: the whole grid, boundaries, sources and
+// the injection profile (ppc slot -1 marks the plasma form).
+TuneKey plasma_key(const pic_config *c) {
+  const int wstep = c->moving_window ? (c->window_cells > 0 ? c->window_cells : c->patch[0]) : 0;
+  const long long prof = std::llround(c->inj_n0 * 1e9) * 1000003ll + std::llround(c->inj_ramp * 1e3) +
+                         7919ll * (c->inj_ppc[0] + 31 * c->inj_ppc[1] + 961 * c->inj_ppc[2]);
+  return TuneKey(c->dims, c->n[0], c->n[1], c->prec, c->bc_field[0], c->bc_field[1],
+                 c->laser_on, c->moving_window, c->filter_passes, wstep, c->dims == 3 ? c->n[2] : 1,
+                 c->tma, -1 - (prof & 0x7fffffffffffll));
+}
 
 std::mutex g_tune_mutex;
 std::map<TuneKey, TuneEntry> g_tune_cache;
@@ -57,6 +68,19 @@ double time_candidate(const pic_config &cfg, const double *const p[6], size_t n,
   double ms = -1.0;
   if (pic_load_particles(ctx, p[0], p[1], p[2], p[3], p[4], p[5], n, where) == PIC_OK &&
       pic_step(ctx, 2) == PIC_OK) {
+    const double t0 = now_ms();
+    if (pic_step(ctx, steps) == PIC_OK) ms = (now_ms() - t0) / steps;
+  }
+  pic_destroy(ctx);
+  return ms;
+}
+
+// As time_candidate, with the configured plasma filled on the device.
+double time_candidate_plasma(const pic_config &cfg, int steps) {
+  pic_ctx *ctx = nullptr;
+  if (pic_create(&cfg, &ctx) != PIC_OK) return -1.0;
+  double ms = -1.0;
+  if (pic_load_plasma(ctx) == PIC_OK && pic_step(ctx, 2) == PIC_OK) {
     const double t0 = now_ms();
     if (pic_step(ctx, steps) == PIC_OK) ms = (now_ms() - t0) / steps;
   }
@@ -92,7 +116,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
     tuned->window_cells = e.window_cells;
     out->patch[0] = e.patch[0];
     out->patch[1] = e.patch[1];
-    out->patch[2] = cfg->patch[2];
+    out->patch[2] = e.patch[2];
     out->block = e.block;
     out->task_chunk = e.chunk;
     out->ms_per_step = e.ms;
@@ -116,7 +140,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
   base.merge = 0;
   // the configuration as given first: the tuner never returns a slower one
   const double ms_given = time_candidate(base, p, n, where, steps);
-  TuneEntry best{{cfg->patch[0], cfg->patch[1]},
+  TuneEntry best{{cfg->patch[0], cfg->patch[1], cfg->patch[2]},
                  base.block > 0 ? base.block : 256,
                  base.task_chunk > 0 ? base.task_chunk : 2048,
                  ms_given, ms_given, cfg->window_cells};
@@ -147,6 +171,100 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
           best.ms = ms;
         }
       }
+  if (!(best.ms > 0)) return PIC_ECUDA;  // no candidate ran
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+  }
+  apply(best, timed);
+  return PIC_OK;
+}
+
+pic_status pic_autotune_plasma(const pic_config *cfg, int steps, pic_config *tuned,
+                               pic_tune_t *out) {
+  if (!cfg || !tuned || !out || steps <= 0) return PIC_EINVAL;
+  const int dims = cfg->dims;
+  if (dims != 2 && dims != 3) return PIC_EINVAL;
+  for (int a = 0; a < dims; ++a)
+    if (cfg->inj_ppc[a] < 1) return PIC_EINVAL;
+  size_t np = 1;
+  for (int a = 0; a < dims; ++a) np *= (size_t)cfg->n[a] * cfg->inj_ppc[a];
+  if (pic_footprint(cfg, np) == 0) return PIC_EINVAL;  // configuration rejected
+  const TuneKey key = plasma_key(cfg);
+  auto apply = [&](const TuneEntry &e, int timed) {
+    *tuned = *cfg;
+    for (int a = 0; a < 3; ++a) tuned->patch[a] = e.patch[a];
+    tuned->block = e.block;
+    tuned->task_chunk = e.chunk;
+    tuned->window_cells = e.window_cells;
+    for (int a = 0; a < 3; ++a) out->patch[a] = e.patch[a];
+    out->block = e.block;
+    out->task_chunk = e.chunk;
+    out->ms_per_step = e.ms;
+    out->ms_given = e.ms_given;
+    out->candidates = timed;
+  };
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply(it->second, 0);
+      return PIC_OK;
+    }
+  }
+  pic_config base = *cfg;
+  base.timing = 0;
+  base.use_graph = 1;
+  base.auto_grow = 0;
+  base.sort_every = 0;
+  base.merge = 0;
+  const double ms_given = time_candidate_plasma(base, steps);
+  TuneEntry best{{cfg->patch[0], cfg->patch[1], cfg->patch[2]},
+                 base.block > 0 ? base.block : 256,
+                 base.task_chunk > 0 ? base.task_chunk : 2048,
+                 ms_given, ms_given, cfg->window_cells};
+  int timed = 1;
+  const int wstep = cfg->window_cells > 0 ? cfg->window_cells : cfg->patch[0];
+  auto consider = [&](pic_config c) {
+    for (int a = 0; a < dims; ++a)
+      if (c.n[a] % c.patch[a]) return;
+    if (cfg->moving_window) {
+      if (wstep % c.patch[0]) return;
+      c.window_cells = wstep;
+    }
+    const double ms = time_candidate_plasma(c, steps);
+    ++timed;
+    if (ms > 0 && (best.ms <= 0 || ms < best.ms)) {
+      for (int a = 0; a < 3; ++a) best.patch[a] = c.patch[a];
+      best.block = c.block > 0 ? c.block : 256;
+      best.chunk = c.task_chunk;
+      best.window_cells = c.window_cells;
+      best.ms = ms;
+    }
+  };
+  for (int chunk : {1024, 2048, 4096}) {
+    if (dims == 2) {
+      for (int P : {8, 16, 32})
+        for (int block : {128, 256}) {
+          pic_config c = base;
+          c.patch[0] = c.patch[1] = P;
+          c.block = block;
+          c.task_chunk = chunk;
+          consider(c);
+        }
+    } else {
+      for (int px : {8, 16})
+        for (int py : {8, 16})
+          for (int pz : {8, 16}) {
+            pic_config c = base;
+            c.patch[0] = px;
+            c.patch[1] = py;
+            c.patch[2] = pz;
+            c.task_chunk = chunk;
+            consider(c);
+          }
+    }
+  }
   if (!(best.ms > 0)) return PIC_ECUDA;  // no candidate ran
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -143,7 +143,7 @@ EXPORTS = ["pic_create", "pic_load_particles", "pic_set_field", "pic_set_backgro
            "pic_load_plasma", "pic_autotune", "pic_autotune_clear_cache", "pic_server_create",
            "pic_server_submit", "pic_server_tick", "pic_server_info", "pic_server_take",
            "pic_server_get_stats", "pic_server_clock", "pic_server_destroy", "pic_load_particles3",
-           "pic_init_fields", "pic_server_cancel"]
+           "pic_init_fields", "pic_server_cancel", "pic_autotune_plasma"]
 
 _lib = None
 
@@ -184,6 +184,9 @@ def lib():
         L.pic_autotune.argtypes = ([C.POINTER(pic_config)] + [dp] * 6 +
                                    [sz, C.c_int, C.c_int, C.POINTER(pic_config), C.POINTER(pic_tune_t)])
         L.pic_autotune_clear_cache.restype = None
+        L.pic_autotune_plasma.argtypes = [C.POINTER(pic_config), C.c_int, C.POINTER(pic_config),
+                                          C.POINTER(pic_tune_t)]
+        L.pic_autotune_plasma.restype = C.c_int
         L.pic_server_create.argtypes = [C.POINTER(pic_server_config), C.POINTER(C.c_void_p)]
         L.pic_server_submit.argtypes = [vp, C.POINTER(pic_config), C.c_longlong, C.c_int,
                                         C.POINTER(C.c_longlong)]
@@ -435,6 +438,19 @@ def pic_autotune(cfg: pic_config, parts: dict, steps: int = 5):
     if rc != PIC_OK:
         raise PicError(rc, "pic_autotune failed")
     info = {"patch": (res.patch[0], res.patch[1]), "block": res.block,
+            "task_chunk": res.task_chunk, "ms_per_step": res.ms_per_step,
+            "ms_given": res.ms_given, "candidates": res.candidates}
+    return tuned, info
+
+
+def pic_autotune_plasma(cfg: pic_config, steps: int = 5):
+    """Time candidate launch shapes on the configured plasma (filled on the
+    device; 2D or 3D); returns (tuned pic_config, dict of the choice)."""
+    tuned, res = pic_config(), pic_tune_t()
+    rc = lib().pic_autotune_plasma(C.byref(cfg), int(steps), C.byref(tuned), C.byref(res))
+    if rc != PIC_OK:
+        raise PicError(rc, "pic_autotune_plasma failed")
+    info = {"patch": tuple(res.patch[a] for a in range(cfg.dims)), "block": res.block,
             "task_chunk": res.task_chunk, "ms_per_step": res.ms_per_step,
             "ms_given": res.ms_given, "candidates": res.candidates}
     return tuned, info

@@ -273,3 +273,31 @@ def test_full_size_config3_invariants_fp32():
     rho_scale = 0.005
     assert d["continuity"] < 1e-3 * rho_scale / run["dt"], d["continuity"]
     assert d["U_E"] > 0  # the laser has entered
+
+
+def test_plasma_autotuner_3d_choice_is_valid_cached_and_exact():
+    """pic_autotune_plasma on a 3D LWFA-shaped run with the moving window:
+    the choice is one of the candidate shapes that divide the grid and the
+    16-cell window step, a second call returns it from the cache, and the
+    tuned context evolves like the given one (FP64: rounding order only)."""
+    run = W.lwfa_3d(n=(64, 32, 32), d=(0.125, 0.5, 0.5), patch=(16, 8, 8), a0=1.0, waist=5.0,
+                    tau=3.0, t_mw=1.0)
+    cfg = pic.config_from_run(run, "fp64")
+    pic.lib().pic_autotune_clear_cache()
+    tuned, info = pic.pic_autotune_plasma(cfg, steps=2)
+    assert info["candidates"] > 1
+    px, py, pz = info["patch"]
+    assert px in (8, 16) and py in (8, 16) and pz in (8, 16, cfg.patch[2])
+    assert 16 % px == 0 and tuned.window_cells in (0, 16)
+    assert info["task_chunk"] in (1024, 2048, 4096)
+    assert info["ms_per_step"] <= info["ms_given"]
+    again, info2 = pic.pic_autotune_plasma(cfg, steps=2)
+    assert info2["candidates"] == 0 and info2["patch"] == info["patch"]
+    a, b = pic.Pic(cfg), pic.Pic(tuned)
+    for g in (a, b):
+        g.pic_load_plasma()
+        g.pic_step(60)
+    da, db = a.pic_diag(), b.pic_diag()
+    assert da["np"] == db["np"] and da["shifts"] == db["shifts"] >= 2
+    for k in EB:
+        assert rel(b.pic_get_field(k), a.pic_get_field(k)) <= 1e-9, k

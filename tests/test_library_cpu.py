@@ -172,6 +172,7 @@ def test_null_arguments(libpic):
     libpic.pic_batch_destroy(None)
     assert libpic.pic_load_plasma(None) == pic.PIC_EINVAL
     assert libpic.pic_init_fields(None, 1) == pic.PIC_EINVAL
+    assert libpic.pic_autotune_plasma(None, 2, None, None) == pic.PIC_EINVAL
     assert libpic.pic_autotune(None, None, None, None, None, None, None, 0, 0, 1, None,
                                None) == pic.PIC_EINVAL
     libpic.pic_autotune_clear_cache()
