@@ -151,6 +151,30 @@ def test_moving_window_fp64():
     assert abs(dg["gauss"] - do["gauss"]) <= 1e-9 * max(do["gauss"], 1e-12) + 1e-12
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-3), ("fp32", 1e-3)])
+def test_energy_history_lwfa_window_2000_steps(prec, tol):
+    """The LWFA workload's shape at a small size (256 x 64 cells, 32 x 32
+    patches, 4 ppc, ramp, laser, moving window, Silver-Mueller faces,
+    removal and reflection) over the workload's 2000 steps: field and kinetic
+    energy histories within 1e-3 of the FP64 oracle at every 100th step,
+    the particle count equal, the same window shifts."""
+    run, parts = W.lwfa_2d(n=(256, 64), d=(0.125, 0.5), patch=(32, 32), ppc=(2, 2),
+                           ramp=8.0, a0=1.0, waist=5.0, tau=4.0)
+    o, g = pair(run, parts, prec=prec, background=("neutralising", 0.0))
+    worst = {}
+    for _ in range(20):
+        o.step(100)
+        g.pic_step(100)
+        do, dg = o.diag(), g.pic_diag()
+        assert dg["np"] == do["np"] and dg["shifts"] == do["shifts"]
+        for k in ("U_E", "U_B", "U_K"):
+            if do[k] > 0:
+                worst[k] = max(worst.get(k, 0.0), abs(dg[k] - do[k]) / do[k])
+    print(prec, "LWFA 2000-step energy history worst rel", worst, "shifts", do["shifts"])
+    assert do["shifts"] >= 5
+    assert all(v <= tol for v in worst.values()), worst
+
+
 def test_window_step_decoupled_from_patch_size_2d():
     """GPU patches of 8 x 16 cells with a 16-cell window step equal the
     oracle run with 16 x 16 patches."""
