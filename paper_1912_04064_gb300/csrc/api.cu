@@ -92,7 +92,7 @@ void cfree(pic_ctx *c, void *p) { dev_free(c->cfg, c->stream, p); }
 
 namespace {
 
-const char *kVersion = "libpic 0.1 (sm_103a, 2D3V SDMD patch PIC)";
+const char *kVersion = "libpic 0.2 (sm_103a, 2D3V and 3D3V SDMD patch PIC; FP64, FP32 with fixed-point current tiles)";
 
 pic_status fail(pic_ctx *c, pic_status s, const std::string &msg) {
   if (c) c->err = msg;
