@@ -123,21 +123,60 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _code_only(text):
+    """Source text without comments, trailing blanks and blank lines: what
+    the compiler sees, so that the digest of a kernel does not change when
+    only its comments do.  String literals are copied as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text[i] == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln)
+
+
+def source_digest(files):
+    """sha256 of the listed kernel sources (repo-relative), comments
+    stripped."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
+    return h.hexdigest()
+
+
+def _summary_matches(text):
+    """True when an ncu summary's recorded digest equals the digest of its
+    kernel sources as they are now."""
+    import re
+    m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
+    if not m:
+        return False
+    return source_digest(re.findall(r"`([^`]+)`", m.group(2))).startswith(m.group(1))
+
+
 def profiled_traffic(name):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     from the committed ncu summary profiles/<name>, if the kernel sources
     it names still hash to the value recorded at capture time; else None."""
-    import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", name)).read()
-        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
-        files = re.findall(r"`([^`]+)`", m.group(2))
-        h = hashlib.sha256()
-        for f in files:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        if not h.hexdigest().startswith(m.group(1)):
+        if not _summary_matches(text):
             return None
         t = re.search(r"traffic = DRAM read \+ write per launch \| (\d+) bytes", text)
         return int(t.group(1)) if t else None
@@ -149,16 +188,10 @@ def profiled_value(name, key):
     """An integer recorded as `key` in the committed ncu summary
     profiles/<name>, if its kernel sources still hash to the recorded
     value; else None."""
-    import hashlib
     import re
     try:
         text = open(os.path.join(ROOT, "profiles", name)).read()
-        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
-        h = hashlib.sha256()
-        for f in re.findall(r"`([^`]+)`", m.group(2)):
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        if not h.hexdigest().startswith(m.group(1)):
+        if not _summary_matches(text):
             return None
         v = re.search(r"`" + key + r"` (\d+)", text)
         return int(v.group(1)) if v else None
@@ -622,7 +655,6 @@ def shared_atomic_ceiling(launch_ms):
     launch time, against the measured rate of conflict-free 32-bit integer
     shared reductions on this GPU (0.91 warp operations per clock per SM,
     one wavefront each) at the maximum SM clock."""
-    import hashlib
     import re
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -634,12 +666,7 @@ def shared_atomic_ceiling(launch_ms):
            "peak_source": "integer red.shared probe, 0.91 per clock per SM"}
     try:
         text = open(os.path.join(ROOT, "profiles", "particle_step_fp32_lwfa2048.md")).read()
-        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
-        h = hashlib.sha256()
-        for f in re.findall(r"`([^`]+)`", m.group(2)):
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        if not h.hexdigest().startswith(m.group(1)) or not launch_ms:
+        if not _summary_matches(text) or not launch_ms:
             return out
         w = int(re.search(r"mem_shared_op_atom\.sum`\) \| (\d+)", text).group(1))
     except Exception:

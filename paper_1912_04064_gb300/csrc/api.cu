@@ -326,14 +326,15 @@ pic_status build_tmap(pic_ctx *ctx) {
 // bucket set 1 - p, writes segment set 1 - p, bucket set p and current set p.
 // Fixed-point scales of the FP32 current tile for work items of at most
 // per_item particles (see StepArgs::jscale).  Every contribution of a
-// particle of weight w is at most (3/4)^2 |q| w in magnitude, for all three
-// components:
-//   x: (q dx/dt) w P A with P a prefix sum of S1 - S0, |P| <= 3/4 |dx_cells|
-//      (the cumulative quadratic shape has slope at most 3/4) and
-//      |dx_cells| < dt/dx (v < c), A = (S0 + S1)/2 <= 3/4;  y alike;
+// particle of weight w is below (3/4) |q| w in magnitude:
+//   x: (q dx/dt) w P A with P a prefix sum of S1 - S0.  The prefix sum of
+//      the quadratic shape weights changes with position at a rate equal to
+//      a linear hat, at most 1, so |P| <= |dx_cells| = |v_x| dt/dx < dt/dx;
+//      A = (S0 + S1)/2 <= 3/4.  y alike;
 //   z: q w v_z W_z with |v_z| < 1 and W_z <= (3/4)^2.
-// So 2^K / ((3/4)^2 |q| w_max) keeps each contribution within 2^K and an
-// item's sums within per_item 2^K <= 2^30.
+// The scale 2^K / ((3/4)^2 |q| w_max) therefore keeps each contribution
+// below (4/3) 2^K and an item's sums below (4/3) per_item 2^K <= (4/3) 2^30,
+// inside the 32-bit range.
 template <typename R>
 void set_current_scale(StepArgs<R> &a, const Geom &g, double wmax, int per_item) {
   int lg = 0;

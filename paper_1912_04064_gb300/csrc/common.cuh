@@ -248,8 +248,9 @@ struct StepArgs {
   // (integer shared atomics are native; float ones are not): a contribution
   // v of component c adds round(v jscale[c]); the tile's integer times
   // junit[c] = 1 / jscale[c] is the current.  jscale[c] = 2^K / ((3/4)^2
-  // |q| w_max) bounds every contribution by 2^K, and K = 30 - ceil(log2(the
-  // particles of a work item)) keeps an item's sums below 2^30.
+  // |q| w_max) with K = 30 - ceil(log2(the particles of a work item)): every
+  // contribution is below (4/3) 2^K (at most (3/4) |q| w), so an item's sums
+  // stay below (4/3) 2^30 < 2^31.
   R jscale[3], junit[3];
   int jfloat;          // FP32: accumulate the tile with float atomics instead
                        // (selects the kernel instance; batches ignore it)

@@ -1533,10 +1533,12 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   a.eps = R(g.q * g.dt / (2.0 * g.m));
   a.plan = c->plan;
   a.active = c->active;
-  // Every contribution is (q d/dt) w P A with |P| <= 3/4 |displacement in
-  // cells| < 3/4 dt/d and the transverse weight A <= (3/4)^2, so at most
-  // (3/4)^3 |q| w_max; 2^K / that keeps it within 2^K and an item's sums
-  // within 2^30 (K = 30 - ceil(log2 of the particles of an item)).
+  // Every contribution is (q d/dt) w P A with |P| <= |displacement in
+  // cells| < dt/d (the prefix sum of the quadratic shape weights changes at
+  // most at rate 1) and the transverse weight A <= (3/4)^2: below (3/4)^2
+  // |q| w_max.  The scale 2^K / ((3/4)^3 |q| w_max) keeps it below (4/3)
+  // 2^K and an item's sums below (4/3) 2^30 < 2^31 (K = 30 - ceil(log2 of
+  // the particles of an item)).
   const int per_item = c->plan.chunk > 0 ? c->plan.chunk : 2048;
   int lg = 0;
   while ((1 << lg) < per_item) ++lg;

@@ -224,6 +224,33 @@ def test_esirkepov3d_continuity_and_zero_motion():
     assert np.all(J == 0.0)
 
 
+def test_esirkepov3d_contribution_bound():
+    """3D: every current contribution of one particle of weight w moving at
+    |v| < c for one step is below (3/4)^2 |q| w (prefix sum of S1 - S0 at
+    most the displacement, below dt/d; transverse weight at most (3/4)^2).
+    The FP32 kernels' fixed-point scale, 2^K / ((3/4)^3 |q| w_max), keeps
+    contributions below (4/3) 2^K on this bound; (3/4)^3 alone is exceeded."""
+    run = W.periodic_run3((16, 16, 16), (0.1, 0.2, 0.15), (4, 4, 4))
+    o = Oracle3(run)
+    d, dt = np.array(run["d"]), run["dt"]
+    rng = np.random.default_rng(19)
+    worst = 0.0
+    for n in range(2000):
+        if n % 2:
+            x0 = rng.uniform(0.5, 1.1, 3) * np.array([1.0, 1.5, 1.2])
+            v = rng.normal(size=3)
+            v *= rng.uniform(0.0, 0.999999) / np.linalg.norm(v)
+        else:   # fast along x, centred between x nodes, on y and z nodes
+            x0 = np.array([(rng.integers(3, 8) + 0.5 + rng.uniform(-0.3, 0.3)) * d[0],
+                           rng.integers(3, 8) * d[1], rng.integers(3, 8) * d[2]])
+            v = np.array([rng.choice([-1, 1]) * rng.uniform(0.99, 0.999999), 0.0, 0.0])
+        w = rng.uniform(0.1, 2.0)
+        J, _ = o.esirkepov(x0, x0 + v * dt, w)
+        worst = max(worst, float(np.max(np.abs(J))) / w)
+    assert worst < 0.5625, worst
+    assert worst > 0.421875, worst
+
+
 def test_esirkepov3d_planar_move_integrates_to_2d():
     """A move with no z displacement: summing the 3D Jx, Jy over the z
     window gives the 2D oracle's Jx, Jy of the same (x, y) move."""

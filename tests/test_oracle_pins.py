@@ -295,6 +295,36 @@ def test_esirkepov_zero_displacement_and_continuity():
         assert np.max(np.abs(res)) / scale < 1e-14
 
 
+def test_esirkepov_contribution_bound():
+    """Every current contribution of one particle of weight w moving at
+    |v| < c for one step is below (3/4) |q| w per window node and component:
+    the prefix sums of S1 - S0 change with position at a rate equal to a
+    linear hat (at most 1), so |P| <= |displacement in cells| < dt/d, and
+    the averaged transverse shape is at most 3/4 (J_z: |v_z| < 1 and
+    W_z <= (3/4)^2).  The FP32 kernels' fixed-point scale, 2^K / ((3/4)^2
+    |q| w_max), keeps contributions below (4/3) 2^K on this bound; the
+    extreme moves below show that (3/4)^2 alone would not bound them."""
+    run = W.periodic_run((16, 16), (0.2, 0.3), (8, 8))
+    o = Oracle(run)
+    dx, dt = run["d"][0], run["dt"]
+    rng = np.random.default_rng(17)
+    worst = 0.0
+    for n in range(3000):
+        if n % 2:
+            x0, y0 = rng.uniform(0.5, 2.5), rng.uniform(0.5, 4.0)
+            v = rng.normal(size=3)
+            v *= rng.uniform(0.0, 0.999999) / np.linalg.norm(v)
+        else:   # fast along x, centred between nodes, on a y node
+            x0 = (rng.integers(3, 10) + 0.5 + rng.uniform(-0.3, 0.3)) * dx
+            y0 = rng.integers(3, 10) * run["d"][1]
+            v = np.array([rng.choice([-1, 1]) * rng.uniform(0.99, 0.999999), 0.0, 0.0])
+        w = rng.uniform(0.1, 2.0)
+        J, _, _ = o.esirkepov(x0, y0, x0 + v[0] * dt, y0 + v[1] * dt, w, v[2])
+        worst = max(worst, float(np.max(np.abs(J))) / w)
+    assert worst < 0.75, worst
+    assert worst > 0.5625, worst
+
+
 def test_gather_bruteforce():
     """Interpolation of every component equals the exact rational sum of the
     piecewise B-spline weights at the component's own stagger."""
