@@ -4,8 +4,9 @@
  * The method is Single Domain Multiple Decompositions (SDMD, Section 2.2 of
  * "Single Domain Multiple Decompositions for Particle-in-Cell simulations"):
  * macro-particles live in small patches, fields live in one large region.
- * Here a patch is one thread block whose field tile and current tile sit in
- * shared memory, and the region is the whole single domain in HBM.  One step
+ * Here a patch (or a chunk of a heavy one) is one work item of a persistent
+ * grid: a thread block stages its field tile and accumulates its current
+ * tile in shared memory; the region is the whole single domain in HBM.  One step
  * is: region -> patch field staging (SDMD step (ii)), interpolation, Boris
  * push, Esirkepov deposition into the patch current tile, patch -> region
  * current reduction (SDMD step (i)), re-binning of particles that left their
