@@ -72,3 +72,32 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_kernel_digest_ignores_comments_only():
+    """The digest that ties an ncu summary to its kernel sources changes
+    with the code, not with comments or blank lines; string literals
+    (inline PTX) count as code."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base = 'int f() {\n  // note\n  return 1; /* x */\n}\nconst char *s = "a // b";\n'
+    same = 'int f() {\n\n  // another note\n  return 1;\n}\n/* block */\nconst char *s = "a // b";\n'
+    code = 'int f() {\n  return 2;\n}\nconst char *s = "a // b";\n'
+    lit = 'int f() {\n  return 1;\n}\nconst char *s = "a // c";\n'
+    d = [bench._code_only(t) for t in (base, same, code, lit)]
+    assert d[0] == d[1]
+    assert d[0] != d[2] and d[0] != d[3]
+    assert '"a // b"' in d[0]
+
+
+def test_committed_summaries_name_existing_sources():
+    """Every ncu summary that records a digest names sources that exist."""
+    import glob
+    import re
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(p).read()
+        m = re.search(r"sha256 `([0-9a-f]+)` of (.*)", text)
+        if not m:
+            continue
+        for f in re.findall(r"`([^`]+)`", m.group(2)):
+            assert os.path.exists(os.path.join(ROOT, f)), (p, f)
