@@ -32,6 +32,11 @@ struct pic_ctx {
   int *cnt[2] = {};
   void *bkt[2][6] = {};
   int *bcnt[2] = {};
+  // per-slot calm flags of the particle step (StepArgs::calm_in/out), and
+  // whether they still describe the particle sets (any change of the
+  // particles outside a step clears them before the next step)
+  unsigned char *calm[2] = {};
+  bool calm_ok = false;
   int cap = 0;
   Buckets bk{};
   Plan plan{};
@@ -275,7 +280,9 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
     CK(cmalloc(ctx, &ctx->bcnt[s], sizeof(int) * g.nslots * 8));
     CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
     CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
+    CK(cmalloc(ctx, &ctx->calm[s], g.nslots));
   }
+  ctx->calm_ok = false;
   CK(cmalloc(ctx, &ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
   // work plan: a slot holds at most cap + bucket stride particles per step
   const bool merge = ctx->cfg.merge > 0;
@@ -334,12 +341,13 @@ pic_status build_tmap(pic_ctx *ctx) {
 //   z: q w v_z W_z with |v_z| < 1 and W_z <= (3/4)^2.
 // The scale 2^K / ((3/4)^2 |q| w_max) therefore keeps each contribution
 // below (4/3) 2^K and an item's sums below (4/3) per_item 2^K <= (4/3) 2^30,
-// inside the 32-bit range.
+// inside the 32-bit range.  K <= 20 keeps every contribution below 2^22,
+// the range in which the 2D kernel rounds it by adding 1.5 * 2^23.
 template <typename R>
 void set_current_scale(StepArgs<R> &a, const Geom &g, double wmax, int per_item) {
   int lg = 0;
   while ((1 << lg) < per_item) ++lg;
-  const double two_k = std::ldexp(1.0, 30 - lg);
+  const double two_k = std::ldexp(1.0, std::min(30 - lg, 20));
   const double c = 0.5625 * std::fabs(g.q);
   // a floor on w_max keeps the scale finite in FP32 (tinier weights only
   // lose resolution)
@@ -366,6 +374,8 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.bout = soa<R>(ctx->bkt[p]);
   a.bcnt_in = ctx->bcnt[1 - p];
   a.bcnt_out = ctx->bcnt[p];
+  a.calm_in = ctx->calm[p];
+  a.calm_out = ctx->calm[1 - p];
   a.cap = ctx->cap;
   a.bk = ctx->bk;
   a.parity = p;
@@ -474,6 +484,7 @@ pic_status window_shift(pic_ctx *ctx) {
   ctx->launches += 7;
   ctx->prev_valid = false;
   ctx->plan_ready = false;  // particle counts changed
+  ctx->calm_ok = false;
   return PIC_OK;
 }
 
@@ -527,7 +538,9 @@ void free_particles(pic_ctx *c) {
     }
     cfree(c, c->cnt[s]);
     cfree(c, c->bcnt[s]);
+    cfree(c, c->calm[s]);
     c->cnt[s] = c->bcnt[s] = nullptr;
+    c->calm[s] = nullptr;
   }
   cfree(c, c->offsets);
   c->offsets = nullptr;
@@ -608,6 +621,7 @@ pic_status restore_backup(pic_ctx *ctx, int new_cap) {
   ctx->col0 = b.col0;
   ctx->prev_valid = false;
   ctx->plan_ready = false;
+  ctx->calm_ok = false;
   ctx->sticky = PIC_OK;
   ctx->launches += 1;
   return PIC_OK;
@@ -626,11 +640,21 @@ pic_status sort_particles(pic_ctx *ctx) {
   ctx->sorts += 1;
   ctx->prev_valid = false;
   ctx->plan_ready = false;
+  ctx->calm_ok = false;
   return PIC_OK;
 }
 
 template <typename R>
 pic_status run_steps(pic_ctx *ctx, int nsteps);
+
+// Clear the calm flags when the particles changed outside a step since
+// they were written (load, restore, window shift, sort, regrow).
+pic_status ensure_calm(pic_ctx *ctx, cudaStream_t s) {
+  if (ctx->calm_ok) return PIC_OK;
+  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(ctx->calm[k], 0, ctx->g.nslots, s));
+  ctx->calm_ok = true;
+  return PIC_OK;
+}
 
 // Advance nsteps; with auto_grow, an overflow of a patch or bucket capacity
 // grows the capacity and replays the steps from the state at entry.
@@ -693,6 +717,10 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
       ctx->since_sort = 0;
     }
     ctx->since_sort += 1;
+    {
+      const pic_status cs = ensure_calm(ctx, ctx->stream);
+      if (cs) return cs;
+    }
     if (use_graph) {
       if (!ctx->plan_ready) {
         CK(launch_plan<R>(step_args<R>(ctx, p), ctx->stream));
@@ -836,6 +864,7 @@ pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double 
   }
   ctx->prev_valid = false;
   ctx->plan_ready = false;
+  ctx->calm_ok = false;
   free_graphs(ctx);  // capacity and buffers are baked into captured graphs
   return poll_device(ctx);
 }
@@ -865,6 +894,7 @@ pic_status do_fill(pic_ctx *ctx) {
   }
   ctx->prev_valid = false;
   ctx->plan_ready = false;
+  ctx->calm_ok = false;
   free_graphs(ctx);
   return poll_device(ctx);
 }
@@ -1352,6 +1382,10 @@ pic_status batch_step(pic_batch *b, int nsteps) {
   pic_status rs = PIC_OK;
   for (int it = 0; it < nsteps && rs == PIC_OK; ++it) {
     const int k = b->phase;
+    for (pic_ctx *c : b->runs) {
+      const pic_status cs = ensure_calm(c, b->stream);
+      if (cs) return bfail(b, cs, c->err);
+    }
     if (b->use_graph) BCK(cudaGraphLaunch(b->gexec[k], b->stream));
     else rs = batch_enqueue<R>(b, k);
     b->launches += batch_kernels_per_step(b);
@@ -1784,6 +1818,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   ctx->col0 = h.col0;
   ctx->prev_valid = h.prev_valid != 0;
   ctx->plan_ready = false;
+  ctx->calm_ok = false;
   ctx->sticky = PIC_OK;
   ctx->err.clear();
   return PIC_OK;

@@ -234,6 +234,13 @@ struct StepArgs {
   SoA<R> bin, bout;    // direction buckets, read / written
   const int *bcnt_in;
   int *bcnt_out;
+  // per slot: 1 when the step that wrote this array found the slot calm
+  // (every particle at rest in an all-zero field tile, nothing arriving),
+  // i.e. both segment sets then hold the same particles; the step reads
+  // calm_in (previous step) and writes calm_out (set to 1 before the step,
+  // cleared by any item of a slot that was not calm)
+  const unsigned char *calm_in;
+  unsigned char *calm_out;
   int cap;
   Buckets bk;
   int parity;

@@ -134,6 +134,48 @@ __device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, 
     }
 }
 
+// FP32 fixed-point deposit with the scale folded into the 1D factors:
+// adding 1.5 * 2^23 to a value |v| < 2^22 leaves round(v) in the low
+// mantissa bits, so one FMA both forms a contribution and rounds it to the
+// tile's integer unit (no conversion instruction); a contribution that
+// rounds to zero is skipped by a predicated shared reduction (no branch).
+constexpr float kRoundMagic = 12582912.0f;
+constexpr int kRoundBits = 0x4B400000;
+__device__ __forceinline__ void red_fixed(uint32_t addr, float t) {
+  const int v = __float_as_int(t) - kRoundBits;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(
+          addr),
+      "r"(v));
+}
+// Jx[l][q] = Px[q] Ay[l], Jy[q][l] = Py[l] Ax[q], Jz[l][q] = zA[q] Ay[l] +
+// zD[q] DSy[l], all already in units of the tile (scale folded into Px, Py,
+// zA, zD).
+template <int JWc>
+__device__ __forceinline__ void deposit_fixed(const float *Jt, int JWr, int JHW, int o,
+                                              const float Px[3], const float Py[3],
+                                              const float Ax[4], const float Ay[4],
+                                              const float zA[4], const float zD[4],
+                                              const float DSy[4]) {
+  const int JW = JWc ? JWc : JWr;
+  const uint32_t bx = smem_u32(Jt + o), by = bx + 4u * JHW, bz = by + 4u * JHW;
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      red_fixed(bx + 4u * (l * JW + q), fmaf(Px[q], Ay[l], kRoundMagic));
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      red_fixed(by + 4u * (l * JW + q), fmaf(Py[l], Ax[q], kRoundMagic));
+#pragma unroll
+  for (int l = 0; l < 4; ++l)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      red_fixed(bz + 4u * (l * JW + q), fmaf(zA[q], Ay[l], zD[q] * DSy[l]) + kRoundMagic);
+}
+
 // The window's contributions into the current tile: FP32 in fixed point
 // (or, jfloat, by value-tested float atomics), FP64 by value-tested float64
 // atomics (the MERGE path's sums).
@@ -191,6 +233,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
   __shared__ long long s_base[9];
   __shared__ int s_item;
   __shared__ int s_ok;
+  __shared__ int s_calm;
   // BATCH: the current item's run arguments, copied from the device array
   __shared__ __align__(16) StepArgs<R> s_args[1];
 
@@ -297,6 +340,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
       if (tid == 0) {
         cnt = min(a.cnt_in[s], a.cap);
         base = (long long)s * a.cap;
+        s_calm = a.calm_in[s];
       } else {
         int k = tid - 1, ddx, ddy;
         dir_delta(k, ddx, ddy);
@@ -347,6 +391,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
       }
     }
     const bool quiet = __syncthreads_or(nonzero != 0u) == 0;
+    // A calm slot (the previous step found its particles at rest in a zero
+    // tile with nothing arriving, so both segment sets hold the same
+    // particles) that is still calm is skipped: its output set already
+    // holds its particles, unchanged.  Only the count is carried over.
+    const bool arrivals = (s_cnt[1] | s_cnt[2] | s_cnt[3] | s_cnt[4] | s_cnt[5] | s_cnt[6] |
+                           s_cnt[7] | s_cnt[8]) != 0;
+    const bool skip = quiet && !arrivals && s_calm;
+    if (skip && tid == 0 && ufirst == 0) a.cnt_out[s] = s_cnt[0];
+    bool moving = false;  // a particle of this item had u != 0
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -385,8 +438,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     return nval;
   };
   R x[M], y[M], ux[M], uy[M], uz[M], w[M];
-  int nval = load(ufirst + tid, x, y, ux, uy, uz, w);
-  for (int qb = ufirst; qb < totalq; qb += nth) {
+  int nval = skip ? 0 : load(ufirst + tid, x, y, ux, uy, uz, w);
+  for (int qb = ufirst; qb < (skip ? ufirst : totalq); qb += nth) {
     // prefetch the next work item so its global loads overlap this one
     R nx_[M], ny_[M], nux_[M], nuy_[M], nuz_[M], nw_[M];
     const int nnval = load(qb + nth + tid, nx_, ny_, nux_, nuy_, nuz_, nw_);
@@ -396,6 +449,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     for (int m = 0; m < M; ++m) {
       int dir = -2;  // -1 stay, -2 gone / invalid, 0..7 bucket
       R x1 = R(0), y1 = R(0), nux = R(0), nuy = R(0), nuz = R(0);
+      moving |= m < nval && (ux[m] != R(0) || uy[m] != R(0) || uz[m] != R(0));
       if (m < nval && quiet && ux[m] == R(0) && uy[m] == R(0) && uz[m] == R(0)) {
         x1 = x[m];
         y1 = y[m];
@@ -454,7 +508,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
             Ax[c] = S0x[c] + R(0.5) * DSx[c];
             Ay[c] = S0y[c] + R(0.5) * DSy[c];
           }
-          const R wx = cjx * w[m], wy = cjy * w[m], wz = cjz * w[m] * nuz * inv;
+          // FP32 fixed point (single particles): the tile scale folded into
+          // the per-particle factors
+          constexpr bool FIX = sizeof(R) == 4 && !JF && !MERGE;
+          const R wx = (FIX ? cjx * jsc[0] : cjx) * w[m];
+          const R wy = (FIX ? cjy * jsc[1] : cjy) * w[m];
+          const R wz = (FIX ? cjz * jsc[2] : cjz) * w[m] * nuz * inv;
           const R Px[3] = {wx * DSx[0], wx * (DSx[0] + DSx[1]), -wx * DSx[3]};
           const R Py[3] = {wy * DSy[0], wy * (DSy[0] + DSy[1]), -wy * DSy[3]};
           R zA[4], zD[4];
@@ -464,18 +523,20 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
             zD[c] = (wz * R(1.0 / 12.0)) * DSx[c];
           }
           Win<R> cur;
+          if constexpr (!FIX) {
 #pragma unroll
-          for (int l = 0; l < 4; ++l)
+            for (int l = 0; l < 4; ++l)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) cur.x[l][q] = Px[q] * Ay[l];
+              for (int q = 0; q < 3; ++q) cur.x[l][q] = Px[q] * Ay[l];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) cur.y[q][l] = Py[l] * Ax[q];
+              for (int l = 0; l < 3; ++l) cur.y[q][l] = Py[l] * Ax[q];
 #pragma unroll
-          for (int l = 0; l < 4; ++l)
+            for (int l = 0; l < 4; ++l)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cur.z[l][q] = zA[q] * Ay[l] + zD[q] * DSy[l];
+              for (int q = 0; q < 4; ++q) cur.z[l][q] = zA[q] * Ay[l] + zD[q] * DSy[l];
+          }
           // window origin in the current tile (tile starts at node -2)
           const int o = (jp - 1 - (shy ? 1 : 0) + 2) * JW + ip - 1 - (shx ? 1 : 0) + 2;
           if (MERGE) {
@@ -504,6 +565,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
             if constexpr (sizeof(R) == 8)
               deposit<R, JWc>(Jt, JW, JT, o, cur, di != 0, dj != 0, wx != R(0) && x1 != x[m],
                               wy != R(0) && y1 != y[m], wz != R(0));
+            else if constexpr (FIX)
+              deposit_fixed<JWc>(reinterpret_cast<const float *>(Jt), JW, JT, o,
+                                 reinterpret_cast<const float *>(Px),
+                                 reinterpret_cast<const float *>(Py),
+                                 reinterpret_cast<const float *>(Ax),
+                                 reinterpret_cast<const float *>(Ay),
+                                 reinterpret_cast<const float *>(zA),
+                                 reinterpret_cast<const float *>(zD),
+                                 reinterpret_cast<const float *>(DSy));
             else
               flush<R, JWc>(Jt, JW, JT, o, cur, jsc, jfloat);
           }
@@ -578,7 +648,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     }
     nval = nnval;
   }
-    __syncthreads();
+    // the slot stays calm only if every item of it was calm (its output is
+    // then a copy of its input)
+    const bool moved = __syncthreads_or(moving) != 0;
+    if (tid == 0 && !skip && (!quiet || arrivals || moved)) a.calm_out[s] = 0;
     // the field tile is free: fetch the next item and start its tile load
     if (PF && tid == 0) {
       const int nxt = atomicAdd(plan.next, 1);
@@ -586,7 +659,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
       if (nxt < n_items) issue_tile(nxt);
     }
     // ---- SDMD step (i): patch current tile -> region current
-    for (int e = tid; e < 3 * JT; e += nth) {
+    for (int e = skip ? 3 * JT : tid; e < 3 * JT; e += nth) {
       R v;
       if (sizeof(R) == 4 && !jfloat) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
@@ -614,6 +687,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 // the output counts of the step are cleared here.  BATCH: the slots of all
 // runs, flattened (run r owns flat slots [br.slots.off[r], off[r + 1])).
 constexpr int PLAN_CLASSES = 64;
+// Class of a slot with `items` work items: slots that were calm at the
+// previous step (likely skipped again, so cheap) form the last class;
+// the others go heaviest first.
+__device__ __forceinline__ int plan_class(int items, unsigned char calm) {
+  return calm ? 0 : min(items, PLAN_CLASSES - 1);
+}
 
 template <typename R, bool BATCH>
 __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const BatchRef<R> br,
@@ -641,9 +720,10 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
     if (zero_out) {
       a.cnt_out[s] = 0;
       for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
+      a.calm_out[s] = 1;
     }
     const int items = (units + plan.chunk - 1) / plan.chunk;
-    if (items) atomicAdd(&hist[min(items, PLAN_CLASSES) - 1], items);
+    if (items) atomicAdd(&hist[plan_class(items, a.calm_in[s])], items);
   }
   __syncthreads();
   if (tid == 0) {
@@ -661,7 +741,8 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
     if (!items) continue;
     const int run = BATCH ? batch_run(br.slots.off, br.slots.n, f) : 0;
     const int s = BATCH ? f - br.slots.off[run] : f;
-    const int base = atomicAdd(&off[min(items, PLAN_CLASSES) - 1], items);
+    const StepArgs<R> &a = BATCH ? br.args[run] : a0;
+    const int base = atomicAdd(&off[plan_class(items, a.calm_in[s])], items);
     for (int k = 0; k < items && base + k < plan.max_items; ++k) {
       plan.item_slot[base + k] = s;
       plan.item_first[base + k] = k * plan.chunk;
@@ -767,6 +848,7 @@ cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, 
   }
   cudaError_t e = cudaMemsetAsync(a.cnt_out, 0, sizeof(int) * a.g.nslots, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.bcnt_out, 0, sizeof(int) * 8 * a.g.nslots, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.calm_out, 1, a.g.nslots, s);
   if (e != cudaSuccess) return e;
   BatchRef<R> none{};
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
