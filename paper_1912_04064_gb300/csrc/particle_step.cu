@@ -137,43 +137,81 @@ __device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, 
 // FP32 fixed-point deposit with the scale folded into the 1D factors:
 // adding 1.5 * 2^23 to a value |v| < 2^22 leaves round(v) in the low
 // mantissa bits, so one FMA both forms a contribution and rounds it to the
-// tile's integer unit (no conversion instruction); a contribution that
-// rounds to zero is skipped by a predicated shared reduction (no branch).
+// tile's integer unit (no conversion instruction).
 constexpr float kRoundMagic = 12582912.0f;
 constexpr int kRoundBits = 0x4B400000;
 __device__ __forceinline__ void red_fixed(uint32_t addr, float t) {
-  const int v = __float_as_int(t) - kRoundBits;
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(
-          addr),
-      "r"(v));
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(__float_as_int(t) - kRoundBits));
 }
 // Jx[l][q] = Px[q] Ay[l], Jy[q][l] = Py[l] Ax[q], Jz[l][q] = zA[q] Ay[l] +
 // zD[q] DSy[l], all already in units of the tile (scale folded into Px, Py,
-// zA, zD).
+// zA, zD).  Entries are issued in groups, skipping those that are zero by
+// construction: the window's last column (row) when the particle kept its
+// nearest node along x (y) (x4, y4 false), and a whole component whose
+// weight is zero (jx, jy: no displacement along it; jz: u_z = 0).  Inside a
+// group every entry is issued unconditionally (no per-entry test, so no
+// branch per entry).
 template <int JWc>
 __device__ __forceinline__ void deposit_fixed(const float *Jt, int JWr, int JHW, int o,
                                               const float Px[3], const float Py[3],
                                               const float Ax[4], const float Ay[4],
                                               const float zA[4], const float zD[4],
-                                              const float DSy[4]) {
+                                              const float DSy[4], bool x4, bool y4, bool jx,
+                                              bool jy, bool jz) {
   const int JW = JWc ? JWc : JWr;
   const uint32_t bx = smem_u32(Jt + o), by = bx + 4u * JHW, bz = by + 4u * JHW;
+  auto ax = [&](int l, int q) { red_fixed(bx + 4u * (l * JW + q), fmaf(Px[q], Ay[l], kRoundMagic)); };
+  auto ay = [&](int q, int l) { red_fixed(by + 4u * (l * JW + q), fmaf(Py[l], Ax[q], kRoundMagic)); };
+  auto az = [&](int l, int q) {
+    red_fixed(bz + 4u * (l * JW + q), fmaf(zA[q], Ay[l], zD[q] * DSy[l]) + kRoundMagic);
+  };
+  if (jx) {
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < 3; ++l) {
+      ax(l, 0);
+      ax(l, 1);
+    }
+    if (x4) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      red_fixed(bx + 4u * (l * JW + q), fmaf(Px[q], Ay[l], kRoundMagic));
+      for (int l = 0; l < 3; ++l) ax(l, 2);
+    }
+    if (y4) {
+      ax(3, 0);
+      ax(3, 1);
+      if (x4) ax(3, 2);
+    }
+  }
+  if (jy) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q) {
+      ay(q, 0);
+      ay(q, 1);
+    }
+    if (y4) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) ay(q, 2);
+    }
+    if (x4) {
+      ay(3, 0);
+      ay(3, 1);
+      if (y4) ay(3, 2);
+    }
+  }
+  if (jz) {
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      red_fixed(by + 4u * (l * JW + q), fmaf(Py[l], Ax[q], kRoundMagic));
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+      for (int q = 0; q < 3; ++q) az(l, q);
+    if (x4) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      red_fixed(bz + 4u * (l * JW + q), fmaf(zA[q], Ay[l], zD[q] * DSy[l]) + kRoundMagic);
+      for (int l = 0; l < 3; ++l) az(l, 3);
+    }
+    if (y4) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) az(3, q);
+      if (x4) az(3, 3);
+    }
+  }
 }
 
 // The window's contributions into the current tile: FP32 in fixed point
@@ -573,7 +611,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
                                  reinterpret_cast<const float *>(Ay),
                                  reinterpret_cast<const float *>(zA),
                                  reinterpret_cast<const float *>(zD),
-                                 reinterpret_cast<const float *>(DSy));
+                                 reinterpret_cast<const float *>(DSy), di != 0, dj != 0,
+                                 x1 != x[m], y1 != y[m], nuz != R(0));
             else
               flush<R, JWc>(Jt, JW, JT, o, cur, jsc, jfloat);
           }
