@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
   __shared__ int s_item;
   __shared__ int s_ok;
   __shared__ int s_calm;
+  __shared__ unsigned s_cmask;  // staged components that hold a nonzero value
   // BATCH: the current item's run arguments, copied from the device array
   __shared__ __align__(16) StepArgs<R> s_args[1];
 
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     }
     __syncthreads();
     if (tid == 0) {
+      s_cmask = 0u;
       s_qoff[0] = 0;
       for (int i = 0; i < 9; ++i) s_qoff[i + 1] = s_qoff[i] + (s_cnt[i] + M - 1) / M;
       int ok = 1;
@@ -418,17 +420,25 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
     // copied through without the interpolation, push and deposit.
     // (16-byte words of the tile, sign bits masked: -0 counts as zero; the
     // tile holds a multiple of 16 bytes since P is a multiple of 16 / s)
-    unsigned nonzero = 0;
+    // (also per component: a component that is zero over the whole tile,
+    // e.g. E_z, B_x, B_y of a field polarised in the plane, is not gathered)
     {
+      unsigned cmask = 0;
       const uint4 *F4 = reinterpret_cast<const uint4 *>(Ft);
-      const int n4 = (int)(6 * FT * sizeof(R) / 16);
+      const int wc = (int)(FT * sizeof(R) / 16);  // 16-byte words per component
+      const int n4 = 6 * wc;
       for (int e = tid; e < n4; e += nth) {
         const uint4 v = F4[e];
-        nonzero |= sizeof(R) == 4 ? ((v.x | v.y | v.z | v.w) & 0x7fffffffu)
-                                  : (v.x | v.z | ((v.y | v.w) & 0x7fffffffu));
+        const unsigned nz = sizeof(R) == 4 ? ((v.x | v.y | v.z | v.w) & 0x7fffffffu)
+                                           : (v.x | v.z | ((v.y | v.w) & 0x7fffffffu));
+        if (nz) cmask |= 1u << (e / wc);
       }
+      cmask = __reduce_or_sync(0xffffffffu, cmask);
+      if (lane == 0 && cmask) atomicOr(&s_cmask, cmask);
     }
-    const bool quiet = __syncthreads_or(nonzero != 0u) == 0;
+    __syncthreads();
+    const unsigned cmask = s_cmask;
+    const bool quiet = cmask == 0u;
     // A calm slot (the previous step found its particles at rest in a zero
     // tile with nothing arriving, so both segment sets hold the same
     // particles) that is still calm is skipped: its output set already
@@ -502,12 +512,12 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
         // stencil at n - 1); row node n -> n (tile starts at node -1)
         const int opp = jp * BX + ip + 3, opd = jd * BX + ip + 3;
         const int odp = jp * BX + id + 3, odd = jd * BX + id + 3;
-        const R Ex = gather<R, BXc>(Ft, BX, odp, Sxd, Syp);
-        const R Ey = gather<R, BXc>(Ft + FT, BX, opd, Sxp, Syd);
-        const R Ez = gather<R, BXc>(Ft + 2 * FT, BX, opp, Sxp, Syp);
-        const R Bx = gather<R, BXc>(Ft + 3 * FT, BX, opd, Sxp, Syd);
-        const R By = gather<R, BXc>(Ft + 4 * FT, BX, odp, Sxd, Syp);
-        const R Bz = gather<R, BXc>(Ft + 5 * FT, BX, odd, Sxd, Syd);
+        const R Ex = (cmask & 1u) ? gather<R, BXc>(Ft, BX, odp, Sxd, Syp) : R(0);
+        const R Ey = (cmask & 2u) ? gather<R, BXc>(Ft + FT, BX, opd, Sxp, Syd) : R(0);
+        const R Ez = (cmask & 4u) ? gather<R, BXc>(Ft + 2 * FT, BX, opp, Sxp, Syp) : R(0);
+        const R Bx = (cmask & 8u) ? gather<R, BXc>(Ft + 3 * FT, BX, opd, Sxp, Syd) : R(0);
+        const R By = (cmask & 16u) ? gather<R, BXc>(Ft + 4 * FT, BX, odp, Sxd, Syp) : R(0);
+        const R Bz = (cmask & 32u) ? gather<R, BXc>(Ft + 5 * FT, BX, odd, Sxd, Syd) : R(0);
         // Boris push u^{n-1/2} -> u^{n+1/2}
         const R umx = ux[m] + eps * Ex, umy = uy[m] + eps * Ey, umz = uz[m] + eps * Ez;
         const R ig = eps * rsq(R(1) + umx * umx + umy * umy + umz * umz);
