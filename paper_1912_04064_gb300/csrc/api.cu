@@ -37,6 +37,9 @@ struct pic_ctx {
   // particles outside a step clears them before the next step)
   unsigned char *calm[2] = {};
   bool calm_ok = false;
+  // counts of the previous state's particle sets (the inputs of the most
+  // recent step), copied aside by the work plan that clears the arrays
+  int *cnt_prev = nullptr, *bcnt_prev = nullptr;
   int cap = 0;
   Buckets bk{};
   Plan plan{};
@@ -58,6 +61,9 @@ struct pic_ctx {
   CUtensorMap tmap;
   bool tmap_ok = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // kGraphSteps consecutive steps from parity p in one graph (used when no
+  // window shift or sort falls inside them)
+  cudaGraphExec_t gexec_n[2] = {nullptr, nullptr};
   double ms_particles = 0, ms_fields = 0, ms_window = 0, ms_sort = 0;
   long long launches = 0, ps_launches = 0;
   int sticky = PIC_OK;
@@ -282,6 +288,10 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
     CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
     CK(cmalloc(ctx, &ctx->calm[s], g.nslots));
   }
+  CK(cmalloc(ctx, &ctx->cnt_prev, sizeof(int) * g.nslots));
+  CK(cmalloc(ctx, &ctx->bcnt_prev, sizeof(int) * g.nslots * 8));
+  CK(cudaMemsetAsync(ctx->cnt_prev, 0, sizeof(int) * g.nslots, ctx->stream));
+  CK(cudaMemsetAsync(ctx->bcnt_prev, 0, sizeof(int) * g.nslots * 8, ctx->stream));
   ctx->calm_ok = false;
   CK(cmalloc(ctx, &ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
   // work plan: a slot holds at most cap + bucket stride particles per step
@@ -302,6 +312,11 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
 }
 
 void free_graphs(pic_ctx *c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->gexec_n[p]) {
+      cudaGraphExecDestroy(c->gexec_n[p]);
+      c->gexec_n[p] = nullptr;
+    }
   for (int p = 0; p < 2; ++p)
     if (c->gexec[p]) {
       cudaGraphExecDestroy(c->gexec[p]);
@@ -376,6 +391,8 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.bcnt_out = ctx->bcnt[p];
   a.calm_in = ctx->calm[p];
   a.calm_out = ctx->calm[1 - p];
+  a.cnt_prev = ctx->cnt_prev;
+  a.bcnt_prev = ctx->bcnt_prev;
   a.cap = ctx->cap;
   a.bk = ctx->bk;
   a.parity = p;
@@ -444,7 +461,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, bool with_plan, cudaEvent_t mi
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
   CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-  CK(launch_plan<R>(step_args<R>(ctx, 1 - parity), ctx->aux));
+  CK(launch_plan<R>(step_args<R>(ctx, 1 - parity), true, ctx->aux));
   CK(cudaEventRecord(ctx->ev_join, ctx->aux));
   CK(launch_fields<R>(field_args<R>(ctx, parity), ctx->stream));
   CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
@@ -493,25 +510,42 @@ int window_columns(const pic_config &c) {
   return c.window_cells > 0 ? c.window_cells / c.patch[0] : 1;
 }
 
-bool window_due(const pic_ctx *c) {
+bool window_due_at(const pic_ctx *c, double t) {
   const int m = window_columns(c->cfg);
-  return c->cfg.moving_window && c->t > c->cfg.mw_t0 &&
-         c->t - c->cfg.mw_t0 >= (c->nshift / m + 1) * (double)m * c->g.P * c->g.dx;
+  return c->cfg.moving_window && t > c->cfg.mw_t0 &&
+         t - c->cfg.mw_t0 >= (c->nshift / m + 1) * (double)m * c->g.P * c->g.dx;
+}
+bool window_due(const pic_ctx *c) { return window_due_at(c, c->t); }
+// Steps of one multi-step graph replay.
+constexpr int kGraphSteps = 8;
+// True when the next kGraphSteps steps may run as one graph: no window shift
+// due after any but the last of them (the time advanced as the steps
+// advance it) and no cell-order sort due before the last.
+bool graph_run_ok(const pic_ctx *c) {
+  double t = c->t;
+  for (int k = 1; k < kGraphSteps; ++k) {
+    t += c->g.dt;
+    if (window_due_at(c, t)) return false;
+  }
+  return !(c->cfg.sort_every > 0 && c->since_sort + kGraphSteps > c->cfg.sort_every);
 }
 
 template <typename R>
 pic_status capture_graphs(pic_ctx *ctx) {
-  for (int p = 0; p < 2; ++p) {
-    cudaGraph_t gr;
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    pic_status s = enqueue_step<R>(ctx, p, false);  // replays follow a built plan
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
-    if (s != PIC_OK) return s;
-    CK(e);
-    e = cudaGraphInstantiate(&ctx->gexec[p], gr, 0);
-    cudaGraphDestroy(gr);
-    CK(e);
-  }
+  for (int n : {1, kGraphSteps})
+    for (int p = 0; p < 2; ++p) {
+      cudaGraph_t gr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      pic_status s = PIC_OK;
+      for (int k = 0; k < n && s == PIC_OK; ++k)
+        s = enqueue_step<R>(ctx, p ^ (k & 1), false);  // replays follow a built plan
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      if (s != PIC_OK) return s;
+      CK(e);
+      e = cudaGraphInstantiate(n == 1 ? &ctx->gexec[p] : &ctx->gexec_n[p], gr, 0);
+      cudaGraphDestroy(gr);
+      CK(e);
+    }
   return PIC_OK;
 }
 
@@ -542,6 +576,9 @@ void free_particles(pic_ctx *c) {
     c->cnt[s] = c->bcnt[s] = nullptr;
     c->calm[s] = nullptr;
   }
+  cfree(c, c->cnt_prev);
+  cfree(c, c->bcnt_prev);
+  c->cnt_prev = c->bcnt_prev = nullptr;
   cfree(c, c->offsets);
   c->offsets = nullptr;
   cfree(c, c->plan.item_slot);
@@ -721,12 +758,18 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
       const pic_status cs = ensure_calm(ctx, ctx->stream);
       if (cs) return cs;
     }
+    int adv = 1;  // steps this iteration advances
     if (use_graph) {
       if (!ctx->plan_ready) {
-        CK(launch_plan<R>(step_args<R>(ctx, p), ctx->stream));
+        CK(launch_plan<R>(step_args<R>(ctx, p), false, ctx->stream));
         ctx->launches += 1;
       }
-      CK(cudaGraphLaunch(ctx->gexec[p], ctx->stream));
+      if (nsteps - n >= kGraphSteps && graph_run_ok(ctx)) {
+        CK(cudaGraphLaunch(ctx->gexec_n[p], ctx->stream));
+        adv = kGraphSteps;
+      } else {
+        CK(cudaGraphLaunch(ctx->gexec[p], ctx->stream));
+      }
     } else if (timing) {
       cudaEvent_t e[3];
       for (int k = 0; k < 3; ++k) CK(new_event(&e[k]));
@@ -741,10 +784,14 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
       if (!ctx->plan_ready) ctx->launches += 1;
     }
     ctx->plan_ready = true;
-    ctx->launches += kernels_per_step(ctx);
-    ctx->ps_launches += 1;
-    ctx->step += 1;
-    ctx->t += ctx->g.dt;
+    for (int k = 0; k < adv; ++k) {
+      ctx->launches += kernels_per_step(ctx);
+      ctx->ps_launches += 1;
+      ctx->step += 1;
+      ctx->t += ctx->g.dt;
+    }
+    ctx->since_sort += adv - 1;
+    n += adv - 1;
     ctx->prev_valid = true;
     if (rs == PIC_OK && window_due(ctx)) {
       cudaEvent_t e[2];
@@ -988,7 +1035,12 @@ pic_status deposit_current_rho(pic_ctx *ctx, double *rho, bool previous) {
   const int q = (int)(ctx->step & 1);
   const int segset = previous ? 1 - q : q;
   const int bktset = previous ? q : 1 - q;
-  CK(launch_deposit_rho<R>(g, ctx->col0, view<R>(ctx, segset, bktset), rho, 1.0, ctx->stream));
+  PartView<R> v = view<R>(ctx, segset, bktset);
+  if (previous) {  // the arrays may have been cleared for the coming step
+    v.cnt = ctx->cnt_prev;
+    v.bcnt = ctx->bcnt_prev;
+  }
+  CK(launch_deposit_rho<R>(g, ctx->col0, v, rho, 1.0, ctx->stream));
   ctx->launches += 1;
   return PIC_OK;
 }
@@ -1753,11 +1805,14 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   CK(d2h(ctx->F, field_bytes(g, ctx->rs)));
   CK(d2h(ctx->rho_bg, sizeof(double) * g.cs));
   if (ctx->cap) {
+    // the previous state's sets (segments 1 - q, buckets q) are saved with
+    // the counts kept aside for them
+    const int q = (int)(ctx->step & 1);
     for (int st = 0; st < 2; ++st) {
       for (int a = 0; a < 6; ++a) CK(d2h(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
       for (int a = 0; a < 6; ++a) CK(d2h(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * ctx->bk.stride));
-      CK(d2h(ctx->cnt[st], sizeof(int) * g.nslots));
-      CK(d2h(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
+      CK(d2h(st == q ? ctx->cnt[st] : ctx->cnt_prev, sizeof(int) * g.nslots));
+      CK(d2h(st == q ? ctx->bcnt_prev : ctx->bcnt[st], sizeof(int) * g.nslots * 8));
     }
   }
   CK(d2h(ctx->st, sizeof(DevState)));
@@ -1807,6 +1862,9 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
       CK(h2d(ctx->cnt[st], sizeof(int) * g.nslots));
       CK(h2d(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
     }
+    const int q = (int)(h.step & 1);
+    CK(cudaMemcpy(ctx->cnt_prev, ctx->cnt[1 - q], sizeof(int) * g.nslots, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(ctx->bcnt_prev, ctx->bcnt[q], sizeof(int) * g.nslots * 8, cudaMemcpyDeviceToDevice));
   }
   DevState ds;
   memcpy(&ds, p, sizeof ds);

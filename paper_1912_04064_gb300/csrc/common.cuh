@@ -241,6 +241,10 @@ struct StepArgs {
   // cleared by any item of a slot that was not calm)
   const unsigned char *calm_in;
   unsigned char *calm_out;
+  // copies of the counts of the previous state's particle sets (the inputs
+  // of the most recent step), kept for the continuity diagnostic: the work
+  // plan clears the step's output counts, which may still hold them
+  int *cnt_prev, *bcnt_prev;
   int cap;
   Buckets bk;
   int parity;
@@ -270,9 +274,11 @@ struct StepArgs {
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
                                  bool merge, int block, int grid, bool plan, cudaStream_t s);
-// The work plan of the step described by a (reads its input counts only).
+// The work plan of the step described by a, which also clears the step's
+// output counts; ahead: built while the step before is the most recent one
+// (its inputs are then the previous state kept aside).
 template <typename R>
-cudaError_t launch_plan(const StepArgs<R> &a, cudaStream_t s);
+cudaError_t launch_plan(const StepArgs<R> &a, bool ahead, cudaStream_t s);
 // Blocks of the particle step resident on the device at once.
 template <typename R>
 int particle_step_grid(int P, int Q, bool tma, bool merge, int block, bool jfloat = false);

@@ -733,7 +733,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
 // Plan of one step: units per slot (segment plus incoming buckets, counts
 // clamped to the capacities), items per slot, items ordered by decreasing
 // item count of their slot (classes of one item count, heaviest first);
-// the output counts of the step are cleared here.  BATCH: the slots of all
+// the output counts of the step are cleared here (zero_out) and its calm
+// flags set, after the previous state's counts are copied aside: those of
+// the step's inputs, or (prev_from_out: a plan built ahead, while the step
+// before is still the most recent one) the ones its outputs hold.  BATCH: the slots of all
 // runs, flattened (run r owns flat slots [br.slots.off[r], off[r + 1])).
 constexpr int PLAN_CLASSES = 64;
 // Class of a slot with `items` work items: slots that were calm at the
@@ -745,7 +748,7 @@ __device__ __forceinline__ int plan_class(int items, unsigned char calm) {
 
 template <typename R, bool BATCH>
 __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const BatchRef<R> br,
-                                               bool zero_out) {
+                                               bool zero_out, bool prev_from_out) {
   __shared__ int hist[PLAN_CLASSES], off[PLAN_CLASSES];
   const int tid = threadIdx.x, nth = blockDim.x;
   const Plan &plan = BATCH ? br.plan : a0.plan;
@@ -766,6 +769,12 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
       if (src >= 0) units += (min(a.bcnt_in[(long long)src * 8 + d], a.bk.cap[d]) + u - 1) / u;
     }
     plan.units[f] = units;
+    if (zero_out && a.cnt_prev) {
+      a.cnt_prev[s] = prev_from_out ? a.cnt_out[s] : a.cnt_in[s];
+      for (int d = 0; d < 8; ++d)
+        a.bcnt_prev[(long long)s * 8 + d] =
+            prev_from_out ? a.bcnt_out[(long long)s * 8 + d] : a.bcnt_in[(long long)s * 8 + d];
+    }
     if (zero_out) {
       a.cnt_out[s] = 0;
       for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
@@ -882,24 +891,21 @@ int particle_step_batch_grid(int P, int Q, bool tma, int block, size_t smem) {
 }
 
 template <typename R>
-cudaError_t launch_plan(const StepArgs<R> &a, cudaStream_t s) {
+cudaError_t launch_plan(const StepArgs<R> &a, bool ahead, cudaStream_t s) {
   BatchRef<R> none{};
-  k_plan<R, false><<<1, 1024, 0, s>>>(a, none, false);
+  k_plan<R, false><<<1, 1024, 0, s>>>(a, none, true, ahead);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, bool tma,
                                  bool merge, int block, int grid, bool plan, cudaStream_t s) {
+  BatchRef<R> none{};
   if (plan) {
-    const cudaError_t e = launch_plan<R>(a, s);
+    k_plan<R, false><<<1, 1024, 0, s>>>(a, none, true, false);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = cudaMemsetAsync(a.cnt_out, 0, sizeof(int) * a.g.nslots, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.bcnt_out, 0, sizeof(int) * 8 * a.g.nslots, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(a.calm_out, 1, a.g.nslots, s);
-  if (e != cudaSuccess) return e;
-  BatchRef<R> none{};
   const size_t smem = particle_step_smem(a.g.P, a.g.Q, sizeof(R));
   const void *k = pick_kernel<R>(a.g.P, a.g.Q, tma, merge, false, a.jfloat != 0);
   TmapSet<1> tm;
@@ -915,7 +921,7 @@ cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatc
                                        int P, int Q, bool tma, int block, int grid,
                                        size_t smem, cudaStream_t s) {
   StepArgs<R> none{};
-  k_plan<R, true><<<1, 1024, 0, s>>>(none, b, true);
+  k_plan<R, true><<<1, 1024, 0, s>>>(none, b, true, false);
   const void *k = pick_kernel<R>(P, Q, tma, false, true);
   void *args[] = {(void *)tm, (void *)&none, (void *)&b};
   return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
@@ -934,8 +940,8 @@ template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const 
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
                                                   const CUtensorMap *, bool, bool, int, int, bool,
                                                   cudaStream_t);
-template cudaError_t launch_plan<float>(const StepArgs<float> &, cudaStream_t);
-template cudaError_t launch_plan<double>(const StepArgs<double> &, cudaStream_t);
+template cudaError_t launch_plan<float>(const StepArgs<float> &, bool, cudaStream_t);
+template cudaError_t launch_plan<double>(const StepArgs<double> &, bool, cudaStream_t);
 template cudaError_t launch_particle_step_batch<float>(const BatchRef<float> &,
                                                        const TmapSet<kBatchMax> *, int, int,
                                                        bool, int, int, size_t, cudaStream_t);
