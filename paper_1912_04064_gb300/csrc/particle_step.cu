@@ -252,7 +252,7 @@ __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<
 // (FP32): the current tile accumulates with float atomics instead of 32-bit
 // fixed point.
 template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH, bool JF = false>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 3) : 1))
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
     k_particle_step(const __grid_constant__ TmapSet<BATCH ? kBatchMax : 1> tm,
                     const StepArgs<R> a0, const BatchRef<R> br) {
   // MERGE: M = 16 / sizeof(R) consecutive particles per thread, one 128-bit
