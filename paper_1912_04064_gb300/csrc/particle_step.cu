@@ -63,44 +63,76 @@ struct Win {
   R x[4][3], y[4][3], z[4][4];
 };
 
-// Shared-memory reduction v into *p when c holds, as one predicated
-// instruction (no branch around it).  Volatile, without a memory clobber:
-// the tile is read only after the block barrier that follows the particle
-// loop, which the compiler does not move these statements across, and the
-// particles' other shared-memory accesses (field gathers) need not be
-// ordered against them.
-__device__ __forceinline__ void red_if(double *p, double v, bool c) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f64 [%0], %1;\n\t}" ::"r"(
-          smem_u32(p)),
-      "d"(v), "r"((int)c));
+// FP64 deposit: the same groups as the fixed-point FP32 deposit below
+// (entries that are zero by construction skipped a group at a time: the
+// window's last column (row) when the particle kept its nearest node along
+// x (y), x4 / y4 false, and a whole component whose weight is zero), each
+// entry an unconditional float64 shared reduction.  Volatile, without a
+// memory clobber: the tile is read only after the block barrier that
+// follows the particle loop, which the compiler does not move these
+// statements across.
+__device__ __forceinline__ void red_f64(uint32_t addr, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(addr), "d"(v));
 }
-
-// The contributions of one particle's window, skipping those that are zero
-// by construction: the window's last column (row) when the particle kept its
-// nearest node along x (y) (x4, y4 false: S0 and S1 vanish there and the
-// prefix sum of DS ends at zero one node earlier), and a whole component
-// whose weight is zero (jx, jy: no displacement along it; jz: u_z = 0).
-template <typename R, int JWc>
-__device__ __forceinline__ void deposit(R *Jt, int JWr, int JHW, int o, const Win<R> &w, bool x4,
-                                        bool y4, bool jx, bool jy, bool jz) {
+template <int JWc>
+__device__ __forceinline__ void deposit_f64(const double *Jt, int JWr, int JHW, int o,
+                                            const double Px[3], const double Py[3],
+                                            const double Ax[4], const double Ay[4],
+                                            const double zA[4], const double zD[4],
+                                            const double DSy[4], bool x4, bool y4, bool jx,
+                                            bool jy, bool jz) {
   const int JW = JWc ? JWc : JWr;
-  R *Jx = Jt + o, *Jy = Jt + JHW + o, *Jz = Jt + 2 * JHW + o;
+  const uint32_t bx = smem_u32(Jt + o), by = bx + 8u * JHW, bz = by + 8u * JHW;
+  auto ax = [&](int l, int q) { red_f64(bx + 8u * (l * JW + q), Px[q] * Ay[l]); };
+  auto ay = [&](int q, int l) { red_f64(by + 8u * (l * JW + q), Py[l] * Ax[q]); };
+  auto az = [&](int l, int q) { red_f64(bz + 8u * (l * JW + q), zA[q] * Ay[l] + zD[q] * DSy[l]); };
+  if (jx) {
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < 3; ++l) {
+      ax(l, 0);
+      ax(l, 1);
+    }
+    if (x4) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-      red_if(&Jx[l * JW + q], w.x[l][q], jx && (q < 2 || x4) && (l < 3 || y4));
+      for (int l = 0; l < 3; ++l) ax(l, 2);
+    }
+    if (y4) {
+      ax(3, 0);
+      ax(3, 1);
+      if (x4) ax(3, 2);
+    }
+  }
+  if (jy) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q) {
+      ay(q, 0);
+      ay(q, 1);
+    }
+    if (y4) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) ay(q, 2);
+    }
+    if (x4) {
+      ay(3, 0);
+      ay(3, 1);
+      if (y4) ay(3, 2);
+    }
+  }
+  if (jz) {
 #pragma unroll
     for (int l = 0; l < 3; ++l)
-      red_if(&Jy[l * JW + q], w.y[q][l], jy && (l < 2 || y4) && (q < 3 || x4));
 #pragma unroll
-  for (int l = 0; l < 4; ++l)
+      for (int q = 0; q < 3; ++q) az(l, q);
+    if (x4) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      red_if(&Jz[l * JW + q], w.z[l][q], jz && (q < 3 || x4) && (l < 3 || y4));
+      for (int l = 0; l < 3; ++l) az(l, 3);
+    }
+    if (y4) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) az(3, q);
+      if (x4) az(3, 3);
+    }
+  }
 }
 
 // FP32 window flush into the 32-bit fixed-point current tile: each
@@ -571,7 +603,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
             zD[c] = (wz * R(1.0 / 12.0)) * DSx[c];
           }
           Win<R> cur;
-          if constexpr (!FIX) {
+          if constexpr (MERGE || (sizeof(R) == 4 && JF)) {
 #pragma unroll
             for (int l = 0; l < 4; ++l)
 #pragma unroll
@@ -611,8 +643,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
             // entry costs FP64-pipe slots, the path's bound); FP32 converts
             // each entry to fixed point and skips the zeros.
             if constexpr (sizeof(R) == 8)
-              deposit<R, JWc>(Jt, JW, JT, o, cur, di != 0, dj != 0, wx != R(0) && x1 != x[m],
-                              wy != R(0) && y1 != y[m], wz != R(0));
+              deposit_f64<JWc>(reinterpret_cast<const double *>(Jt), JW, JT, o,
+                               reinterpret_cast<const double *>(Px),
+                               reinterpret_cast<const double *>(Py),
+                               reinterpret_cast<const double *>(Ax),
+                               reinterpret_cast<const double *>(Ay),
+                               reinterpret_cast<const double *>(zA),
+                               reinterpret_cast<const double *>(zD),
+                               reinterpret_cast<const double *>(DSy), di != 0, dj != 0,
+                               wx != R(0) && x1 != x[m], wy != R(0) && y1 != y[m], wz != R(0));
             else if constexpr (FIX)
               deposit_fixed<JWc>(reinterpret_cast<const float *>(Jt), JW, JT, o,
                                  reinterpret_cast<const float *>(Px),
