@@ -166,15 +166,8 @@ __device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, 
     }
 }
 
-// FP32 fixed-point deposit with the scale folded into the 1D factors:
-// adding 1.5 * 2^23 to a value |v| < 2^22 leaves round(v) in the low
-// mantissa bits, so one FMA both forms a contribution and rounds it to the
-// tile's integer unit (no conversion instruction).
-constexpr float kRoundMagic = 12582912.0f;
-constexpr int kRoundBits = 0x4B400000;
-__device__ __forceinline__ void red_fixed(uint32_t addr, float t) {
-  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(__float_as_int(t) - kRoundBits));
-}
+// FP32 fixed-point deposit with the scale folded into the 1D factors (one
+// FMA forms and rounds each contribution, see red_fixed).
 // Jx[l][q] = Px[q] Ay[l], Jy[q][l] = Py[l] Ax[q], Jz[l][q] = zA[q] Ay[l] +
 // zD[q] DSy[l], all already in units of the tile (scale folded into Px, Py,
 // zA, zD).  Entries are issued in groups, skipping those that are zero by

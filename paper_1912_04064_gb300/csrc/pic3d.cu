@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -537,39 +538,55 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
           // whole component when the particle did not move along it.
           const int st3[3] = {1, JW, JW * JH};
           const int base = (org[2] * JH + org[1]) * JW + org[0];
-          const R jsc = a.jscale;
           constexpr bool fixed = sizeof(R) == 4 && !JF;
+          // fixed point: the tile scale folded into the prefix factors, each
+          // contribution formed and rounded by one FMA (red_fixed)
+          const R jsc = fixed ? a.jscale : R(1);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
-            const R cw = a.cj[c] * w;
+            const R cw = a.cj[c] * w * jsc;
             const R P0 = cw * DS[c][0], P1 = cw * (DS[c][0] + DS[c][1]), P2 = -cw * DS[c][3];
             if (P0 == R(0) && P1 == R(0) && P2 == R(0)) continue;
             R *J = Jt + c * JT + base;
             const int sc = st3[c], s1 = st3[b1], s2 = st3[b2];
             const bool w1 = x4[b1], w2 = x4[b2], wc = x4[c];
-#pragma unroll
-            for (int m2 = 0; m2 < 4; ++m2) {
-              if (m2 == 3 && !w2) continue;
-#pragma unroll
-              for (int m1 = 0; m1 < 4; ++m1) {
-                if (m1 == 3 && !w1) continue;
+            // the (m1, m2) entries of the component, issued in groups: the
+            // window's node 3 along b1 (b2) only when w1 (w2), the third
+            // prefix entry only when wc
+            auto groups = [&](auto WC) {
+              constexpr bool kWC = decltype(WC)::value;
+              auto put = [&](int m1, int m2) {
                 const R A = S0[b1][m1] * (S0[b2][m2] + R(0.5) * DS[b2][m2]) +
                             DS[b1][m1] * (R(0.5) * S0[b2][m2] + R(1.0 / 3.0) * DS[b2][m2]);
                 R *row = J + m1 * s1 + m2 * s2;
-                if (fixed) {
-                  // 32-bit fixed point (native integer shared atomics)
-                  int *ir = reinterpret_cast<int *>(row);
-                  atomicAdd(ir, __float2int_rn(P0 * A * jsc));
-                  atomicAdd(ir + sc, __float2int_rn(P1 * A * jsc));
-                  if (wc) atomicAdd(ir + 2 * sc, __float2int_rn(P2 * A * jsc));
+                if constexpr (fixed) {
+                  const uint32_t ad = smem_u32(row);
+                  red_fixed(ad, fmaf(P0, A, kRoundMagic));
+                  red_fixed(ad + 4u * sc, fmaf(P1, A, kRoundMagic));
+                  if constexpr (kWC) red_fixed(ad + 8u * sc, fmaf(P2, A, kRoundMagic));
                 } else {
                   atomicAdd(row, P0 * A);
                   atomicAdd(row + sc, P1 * A);
-                  if (wc) atomicAdd(row + 2 * sc, P2 * A);
+                  if constexpr (kWC) atomicAdd(row + 2 * sc, P2 * A);
                 }
+              };
+#pragma unroll
+              for (int m2 = 0; m2 < 3; ++m2)
+#pragma unroll
+                for (int m1 = 0; m1 < 3; ++m1) put(m1, m2);
+              if (w1) {
+#pragma unroll
+                for (int m2 = 0; m2 < 3; ++m2) put(3, m2);
               }
-            }
+              if (w2) {
+#pragma unroll
+                for (int m1 = 0; m1 < 3; ++m1) put(m1, 3);
+                if (w1) put(3, 3);
+              }
+            };
+            if (wc) groups(std::true_type{});
+            else groups(std::false_type{});
           }
           // boundary conditions, destination patch
           int dd[3];
@@ -1538,11 +1555,12 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   // most at rate 1) and the transverse weight A <= (3/4)^2: below (3/4)^2
   // |q| w_max.  The scale 2^K / ((3/4)^3 |q| w_max) keeps it below (4/3)
   // 2^K and an item's sums below (4/3) 2^30 < 2^31 (K = 30 - ceil(log2 of
-  // the particles of an item)).
+  // the particles of an item)); K <= 20 keeps each contribution below
+  // 2^22, the range in which the kernel rounds it by adding 1.5 * 2^23.
   const int per_item = c->plan.chunk > 0 ? c->plan.chunk : 2048;
   int lg = 0;
   while ((1 << lg) < per_item) ++lg;
-  const double two_k = std::ldexp(1.0, 30 - lg);
+  const double two_k = std::ldexp(1.0, std::min(30 - lg, 20));
   const double cm = 0.421875 * std::fabs(g.q);
   const double wm = cm > 0 ? std::max(c->wmax, two_k / (cm * 1e30)) : 0.0;
   const double sc = cm > 0 ? two_k / (cm * wm) : 0.0;

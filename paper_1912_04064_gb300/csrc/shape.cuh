@@ -68,6 +68,17 @@ __device__ __forceinline__ int shape_primal(R xi, R S[3]) {
   return i;
 }
 
+// FP32 fixed-point current tiles: adding 1.5 * 2^23 to a value |v| < 2^22
+// leaves round(v) (to nearest even) in the low mantissa bits, so one FMA
+// both forms a contribution (already in the tile's unit) and rounds it, with
+// no conversion instruction; red_fixed adds the rounded value of t = v +
+// 1.5 * 2^23 into the 32-bit integer at shared address addr.
+constexpr float kRoundMagic = 12582912.0f;
+constexpr int kRoundBits = 0x4B400000;
+__device__ __forceinline__ void red_fixed(uint32_t addr, float t) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(__float_as_int(t) - kRoundBits));
+}
+
 // Place three shape weights in a 4-node window, shifted one node when sh.
 template <typename R>
 __device__ __forceinline__ void window4(const R S3[3], bool sh, R S[4]) {
