@@ -540,7 +540,9 @@ def run_precision(device, steps=2000, every=50):
     component; worst of the E, B and J components), with the particle count,
     both paths' FP64 continuity and Gauss residuals and their energies.
     Accumulated differences, not single-step errors: the FP32 run is never
-    reset to the FP64 state."""
+    reset to the FP64 state.  The FP32 path runs twice: with its default
+    fixed-point current tile and with float shared-atomic accumulation
+    (`float_current`), for comparison."""
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -549,62 +551,74 @@ def run_precision(device, steps=2000, every=50):
     run, parts = W.lwfa_2d()
     stream = torch.cuda.Stream(device=device)
     ctx = {}
-    for prec in ("fp64", "fp32"):
+    for name, prec, cf in (("fp64", "fp64", False), ("fp32", "fp32", False),
+                           ("fp32f", "fp32", True)):
         g = pic.Pic(pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
-                                        use_graph=True, capacity_factor=4.0))
+                                        use_graph=True, capacity_factor=4.0, current_float=cf))
         g.pic_load_particles(parts)
         g.pic_set_background("neutralising")
-        ctx[prec] = g
+        ctx[name] = g
     shape = ctx["fp64"].shape
     bufs = {p: torch.empty(shape, dtype=torch.float64, device=f"cuda:{device}") for p in ctx}
     groups = {"E": ("Ex", "Ey", "Ez"), "B": ("Bx", "By", "Bz"), "J": ("Jx", "Jy", "Jz")}
     marks = sorted({1, 10, *range(every, steps + 1, every)})
-    hist, done = [], 0
+    hist = {"fp32": [], "fp32f": []}
+    done = 0
     for m in marks:
         for g in ctx.values():
             g.pic_step(m - done)
         done = m
-        rec = {"step": m}
+        recs = {v: {"step": m} for v in hist}
         for grp, names in groups.items():
-            worst = 0.0
+            worst = {v: 0.0 for v in hist}
             for k in names:
                 for p, g in ctx.items():
                     g.pic_get_field(k, out=bufs[p])
                 torch.cuda.synchronize(device)
                 ref = bufs["fp64"].abs().max().item()
-                diff = (bufs["fp32"] - bufs["fp64"]).abs().max().item()
-                worst = max(worst, diff / ref if ref > 0 else diff)
-            rec[grp] = worst
-        d64, d32 = ctx["fp64"].pic_diag(), ctx["fp32"].pic_diag()
-        for k in ("U_E", "U_B", "U_K"):
-            rec[k] = abs(d32[k] - d64[k]) / max(abs(d64[k]), 1e-300)
-        rec["np"] = (d32["np"], d64["np"])
+                for v in hist:
+                    diff = (bufs[v] - bufs["fp64"]).abs().max().item()
+                    worst[v] = max(worst[v], diff / ref if ref > 0 else diff)
+            for v in hist:
+                recs[v][grp] = worst[v]
+        d64 = ctx["fp64"].pic_diag()
         # residuals not available at this step (e.g. right after a window
         # shift) are reported as null
-        fin = lambda v: v if math.isfinite(v) else None  # noqa: E731
-        rec["continuity"] = (fin(d32["continuity"]), fin(d64["continuity"]))
-        rec["gauss"] = (fin(d32["gauss"]), fin(d64["gauss"]))
-        hist.append(rec)
+        fin = lambda x: x if math.isfinite(x) else None  # noqa: E731
+        for v in hist:
+            d32 = ctx[v].pic_diag()
+            for k in ("U_E", "U_B", "U_K"):
+                recs[v][k] = abs(d32[k] - d64[k]) / max(abs(d64[k]), 1e-300)
+            recs[v]["np"] = (d32["np"], d64["np"])
+            recs[v]["continuity"] = (fin(d32["continuity"]), fin(d64["continuity"]))
+            recs[v]["gauss"] = (fin(d32["gauss"]), fin(d64["gauss"]))
+            hist[v].append(recs[v])
     for g in ctx.values():
         g.close()
-
-    def at(step):
-        r = next(h for h in hist if h["step"] == step)
-        return {k: r[k] for k in ("E", "B", "J", "U_E", "U_B", "U_K")}
-
     pick = [m for m in (1, 10, 100, 500, 1000, 2000) if m in marks]
-    last = hist[-1]
-    return {"workload": "the LWFA workload above, FP32 and FP64 from identical inputs at t = 0, "
-                        f"{steps} steps, recorded every {every}",
-            "metric": "||fp32 - fp64||_inf / ||fp64||_inf per field component (worst of each "
-                      "group); relative energy difference",
-            "at_step": {str(m): at(m) for m in pick},
-            "max_over_run": {k: max(h[k] for h in hist) for k in ("E", "B", "J", "U_E", "U_B", "U_K")},
-            "particles_at_end": {"fp32": last["np"][0], "fp64": last["np"][1]},
-            "continuity_at_end": {"fp32": last["continuity"][0], "fp64": last["continuity"][1]},
-            "gauss_at_end": {"fp32": last["gauss"][0], "fp64": last["gauss"][1]},
-            "gauss_max_over_run": {p: max((h["gauss"][i] for h in hist if h["gauss"][i] is not None),
-                                          default=None) for i, p in enumerate(("fp32", "fp64"))}}
+
+    def summary(h):
+        def at(step):
+            r = next(x for x in h if x["step"] == step)
+            return {k: r[k] for k in ("E", "B", "J", "U_E", "U_B", "U_K")}
+        last = h[-1]
+        return {"at_step": {str(m): at(m) for m in pick},
+                "max_over_run": {k: max(x[k] for x in h) for k in ("E", "B", "J", "U_E", "U_B", "U_K")},
+                "particles_at_end": {"fp32": last["np"][0], "fp64": last["np"][1]},
+                "continuity_at_end": {"fp32": last["continuity"][0], "fp64": last["continuity"][1]},
+                "gauss_at_end": {"fp32": last["gauss"][0], "fp64": last["gauss"][1]},
+                "gauss_max_over_run": {p: max((x["gauss"][i] for x in h if x["gauss"][i] is not None),
+                                              default=None) for i, p in enumerate(("fp32", "fp64"))}}
+
+    out = {"workload": "the LWFA workload above, FP32 and FP64 from identical inputs at t = 0, "
+                       f"{steps} steps, recorded every {every}",
+           "metric": "||fp32 - fp64||_inf / ||fp64||_inf per field component (worst of each "
+                     "group); relative energy difference"}
+    out.update(summary(hist["fp32"]))
+    out["float_current"] = summary(hist["fp32f"])
+    out["float_current"]["note"] = ("the same FP32 path with the current tile accumulated by float "
+                                    "shared atomics (pic_config.current_float = 1)")
+    return out
 
 
 def cpu_oracle(steps, threads=0):

@@ -40,6 +40,9 @@ struct pic_ctx {
   // counts of the previous state's particle sets (the inputs of the most
   // recent step), copied aside by the work plan that clears the arrays
   int *cnt_prev = nullptr, *bcnt_prev = nullptr;
+  // per-slot maxima of (w |u|)^2 and w for the FP32 tile scale
+  // (StepArgs::stat_in / stat_out), by step parity like calm
+  unsigned *stat[2] = {};
   int cap = 0;
   Buckets bk{};
   Plan plan{};
@@ -272,6 +275,13 @@ pic_status poll_device(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+// Particles per work item of the 2D particle step unless configured: a
+// whole 32 x 32-cell patch at 4 per cell in FP32 (the per-item fixed-point
+// scale keeps the current resolution), 2048 in FP64 (one block per SM; more
+// items balance better).
+template <typename R>
+constexpr int default_chunk() { return sizeof(R) == 4 ? 4096 : 2048; }
+
 template <typename R>
 pic_status alloc_particles(pic_ctx *ctx, int cap) {
   ctx->cap = cap;
@@ -287,6 +297,7 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
     CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
     CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
     CK(cmalloc(ctx, &ctx->calm[s], g.nslots));
+    CK(cmalloc(ctx, &ctx->stat[s], sizeof(unsigned) * 2 * g.nslots));
   }
   CK(cmalloc(ctx, &ctx->cnt_prev, sizeof(int) * g.nslots));
   CK(cmalloc(ctx, &ctx->bcnt_prev, sizeof(int) * g.nslots * 8));
@@ -298,7 +309,7 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
   const bool merge = ctx->cfg.merge > 0;
   Plan &pl = ctx->plan;
   pl.unit = merge ? (int)(16 / sizeof(R)) : 1;
-  const int chunk_particles = ctx->cfg.task_chunk > 0 ? ctx->cfg.task_chunk : 2048;
+  const int chunk_particles = ctx->cfg.task_chunk > 0 ? ctx->cfg.task_chunk : default_chunk<R>();
   pl.chunk = std::max(1, chunk_particles / pl.unit);
   const long long units_max = (long long)(cap + ctx->bk.stride) / pl.unit + 9;
   pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
@@ -393,6 +404,10 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.calm_out = ctx->calm[1 - p];
   a.cnt_prev = ctx->cnt_prev;
   a.bcnt_prev = ctx->bcnt_prev;
+  a.stat_in = ctx->stat[p];
+  a.stat_out = ctx->stat[1 - p];
+  a.jk = R(g.q != 0.0 ? 1.0 / (0.5625 * std::fabs(g.q)) : 0.0);
+  a.wglob = R(ctx->wmax);
   a.cap = ctx->cap;
   a.bk = ctx->bk;
   a.parity = p;
@@ -573,8 +588,10 @@ void free_particles(pic_ctx *c) {
     cfree(c, c->cnt[s]);
     cfree(c, c->bcnt[s]);
     cfree(c, c->calm[s]);
+    cfree(c, c->stat[s]);
     c->cnt[s] = c->bcnt[s] = nullptr;
     c->calm[s] = nullptr;
+    c->stat[s] = nullptr;
   }
   cfree(c, c->cnt_prev);
   cfree(c, c->bcnt_prev);
@@ -688,7 +705,12 @@ pic_status run_steps(pic_ctx *ctx, int nsteps);
 // they were written (load, restore, window shift, sort, regrow).
 pic_status ensure_calm(pic_ctx *ctx, cudaStream_t s) {
   if (ctx->calm_ok) return PIC_OK;
-  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(ctx->calm[k], 0, ctx->g.nslots, s));
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMemsetAsync(ctx->calm[k], 0, ctx->g.nslots, s));
+    // unknown maxima: huge (0x7f7f7f7f), so the FP32 tile bound falls back
+    // to the run's largest weight with |v| <= 1
+    CK(cudaMemsetAsync(ctx->stat[k], 0x7f, sizeof(unsigned) * 2 * ctx->g.nslots, s));
+  }
   ctx->calm_ok = true;
   return PIC_OK;
 }
@@ -1332,7 +1354,7 @@ pic_status batch_build(pic_batch *b) {
   slots.n = n;
   for (int k = 0; k < 4; ++k) fg[k].n = n;
   long long max_items = 0;
-  const int chunk = std::max(1, b->task_chunk > 0 ? b->task_chunk : 2048);
+  const int chunk = std::max(1, b->task_chunk > 0 ? b->task_chunk : default_chunk<R>());
   for (int r = 0; r < n; ++r) {
     pic_ctx *c = b->runs[r];
     const Geom &g = c->g;

@@ -245,6 +245,18 @@ struct StepArgs {
   // of the most recent step), kept for the continuity diagnostic: the work
   // plan clears the step's output counts, which may still hold them
   int *cnt_prev, *bcnt_prev;
+  // FP32 fixed-point tile scale per work item (single particles): per slot
+  // the largest (w |u|)^2 and w of the particles its items processed, as
+  // float bits ([2 s], [2 s + 1]); the step reads the previous step's
+  // (stat_in) and writes its own (stat_out, cleared by the plan).  An item
+  // bounds its particles' contributions by (3/4) |q| B with
+  //   B = min(max w |u| + 2 |eps| |E|_tile max w, max w, wglob)
+  // (the Boris rotation keeps |u|; each half kick adds at most |eps| |E|;
+  // |v| <= min(|u|, 1)), maxima over the item's nine source slots, and
+  // scales its tile by 2^K jk / B, jk = 1 / ((3/4)^2 |q|).
+  const unsigned *stat_in;
+  unsigned *stat_out;
+  R jk, wglob;
   int cap;
   Buckets bk;
   int parity;

@@ -277,7 +277,7 @@ __device__ __forceinline__ void flush(R *Jt, int JWr, int JHW, int o, const Win<
 // (FP32): the current tile accumulates with float atomics instead of 32-bit
 // fixed point.
 template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH, bool JF = false>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 4)) : 1))
     k_particle_step(const __grid_constant__ TmapSet<BATCH ? kBatchMax : 1> tm,
                     const StepArgs<R> a0, const BatchRef<R> br) {
   // MERGE: M = 16 / sizeof(R) consecutive particles per thread, one 128-bit
@@ -286,6 +286,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
   // lanes of a warp on 32 distinct, neighbouring cells for particles stored
   // in the interleaved cell order (conflict-free gathers and atomics).
   constexpr int M = MERGE ? 16 / sizeof(R) : 1;
+  // FP32 fixed point with the tile scale chosen per work item (single
+  // particles; the merge variant keeps the run-wide scale)
+  constexpr bool FIXA = sizeof(R) == 4 && !JF && !MERGE;
   constexpr int BXc = PT ? PT + 8 : 0, BYc = QT ? QT + 3 : 0;
   constexpr int JWc = PT ? PT + 5 : 0, JHc = QT ? QT + 5 : 0;
   using V = typename Vec<R>::T;
@@ -298,11 +301,18 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
   __shared__ int s_ok;
   __shared__ int s_calm;
   __shared__ unsigned s_cmask;  // staged components that hold a nonzero value
+  // FP32 fixed point (StepArgs::stat_in): the item's source slots' largest
+  // (w |u|)^2 and w, the tile's largest |E_x|, |E_y|, |E_z|, and the
+  // item's own largest (w |u|)^2 and w (float bits, non-negative)
+  __shared__ unsigned s_src[2], s_emax[3], s_stat[2];
+  __shared__ float s_isc;  // the item's fixed-point scale
   // BATCH: the current item's run arguments, copied from the device array
   __shared__ __align__(16) StepArgs<R> s_args[1];
 
   const int tid = threadIdx.x, nth = blockDim.x;
   const uint32_t pad = (128u - (smem_u32(dsm_raw) & 127u)) & 127u;
+  if (tid < 2) s_src[tid] = s_stat[tid] = 0u;
+  if (tid < 3) s_emax[tid] = 0u;
   const int lane = tid & 31;
   const Plan &plan = BATCH ? br.plan : a0.plan;
   const int n_items = *plan.n_items;
@@ -401,6 +411,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
     if (tid < 9) {
       int cnt = 0;
       long long base = 0;
+      int src = s;
       if (tid == 0) {
         cnt = min(a.cnt_in[s], a.cap);
         base = (long long)s * a.cap;
@@ -408,11 +419,15 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
       } else {
         int k = tid - 1, ddx, ddy;
         dir_delta(k, ddx, ddy);
-        const int src = neighbour_slot(g, col0, s, -ddx, -ddy);
+        src = neighbour_slot(g, col0, s, -ddx, -ddy);
         if (src >= 0) {
           cnt = min(a.bcnt_in[(long long)src * 8 + k], a.bk.cap[k]);
           base = (long long)src * a.bk.stride + a.bk.off[k];
         }
+      }
+      if (FIXA && src >= 0) {
+        atomicMax(&s_src[0], a.stat_in[2 * src]);
+        atomicMax(&s_src[1], a.stat_in[2 * src + 1]);
       }
       s_cnt[tid] = cnt;
       s_base[tid] = base;
@@ -451,15 +466,33 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
       unsigned cmask = 0;
       const uint4 *F4 = reinterpret_cast<const uint4 *>(Ft);
       const int wc = (int)(FT * sizeof(R) / 16);  // 16-byte words per component
-      const int n4 = 6 * wc;
-      for (int e = tid; e < n4; e += nth) {
-        const uint4 v = F4[e];
-        const unsigned nz = sizeof(R) == 4 ? ((v.x | v.y | v.z | v.w) & 0x7fffffffu)
-                                           : (v.x | v.z | ((v.y | v.w) & 0x7fffffffu));
-        if (nz) cmask |= 1u << (e / wc);
+      unsigned em[3] = {0u, 0u, 0u};  // FIXA: largest |E_c| bits seen
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        unsigned any = 0u, mx = 0u;
+        for (int e = tid; e < wc; e += nth) {
+          const uint4 v = F4[c * wc + e];
+          if (sizeof(R) == 4) {
+            const unsigned ax = v.x & 0x7fffffffu, ay = v.y & 0x7fffffffu,
+                           az = v.z & 0x7fffffffu, aw = v.w & 0x7fffffffu;
+            any |= ax | ay | az | aw;
+            if (FIXA && c < 3) mx = max(mx, max(max(ax, ay), max(az, aw)));
+          } else {
+            any |= v.x | v.z | ((v.y | v.w) & 0x7fffffffu);
+          }
+        }
+        if (any) cmask |= 1u << c;
+        if (c < 3) em[c] = mx;
       }
       cmask = __reduce_or_sync(0xffffffffu, cmask);
       if (lane == 0 && cmask) atomicOr(&s_cmask, cmask);
+      if (FIXA) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const unsigned m = __reduce_max_sync(0xffffffffu, em[c]);
+          if (lane == 0 && m) atomicMax(&s_emax[c], m);
+        }
+      }
     }
     __syncthreads();
     const unsigned cmask = s_cmask;
@@ -473,6 +506,25 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
     const bool skip = quiet && !arrivals && s_calm;
     if (skip && tid == 0 && ufirst == 0) a.cnt_out[s] = s_cnt[0];
     bool moving = false;  // a particle of this item had u != 0
+    float st_wu2 = 0.0f, st_w = 0.0f;  // this thread's largest (w |u|)^2, w
+    // FIXA: this item's tile scale, formed once by thread 0
+    if (FIXA && !skip) {
+      if (tid == 0) {
+        const float ex = __uint_as_float(s_emax[0]), ey = __uint_as_float(s_emax[1]),
+                    ez = __uint_as_float(s_emax[2]);
+        const float m1 = sqrtf(__uint_as_float(s_src[0])), m2 = __uint_as_float(s_src[1]);
+        const float emax = sqrtf(ex * ex + ey * ey + ez * ez);
+        // bound on w |v| after the push, with a margin for rounding
+        float B = fminf(fminf(fmaf(2.0f * fabsf((float)eps) * emax, m2, m1), m2), (float)a.wglob);
+        B = fmaxf(B * 1.001f, 1e-30f);
+        const int n = totalq - ufirst;
+        const int lg = n > 1 ? 32 - __clz(n - 1) : 0;
+        const int K = min(30 - lg, 20);
+        s_isc = __int_as_float((127 + K) << 23) * (float)a.jk / B;
+      }
+      __syncthreads();
+    }
+    const R isc = FIXA ? R(s_isc) : R(0);
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -523,6 +575,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
       int dir = -2;  // -1 stay, -2 gone / invalid, 0..7 bucket
       R x1 = R(0), y1 = R(0), nux = R(0), nuy = R(0), nuz = R(0);
       moving |= m < nval && (ux[m] != R(0) || uy[m] != R(0) || uz[m] != R(0));
+      if (FIXA && m < nval) st_w = fmaxf(st_w, (float)w[m]);
       if (m < nval && quiet && ux[m] == R(0) && uy[m] == R(0) && uz[m] == R(0)) {
         x1 = x[m];
         y1 = y[m];
@@ -554,7 +607,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
         nux = umx + f * (upy * tz - upz * ty) + eps * Ex;
         nuy = umy + f * (upz * tx - upx * tz) + eps * Ey;
         nuz = umz + f * (upx * ty - upy * tx) + eps * Ez;
-        const R inv = rsq(R(1) + nux * nux + nuy * nuy + nuz * nuz);
+        const R usq = nux * nux + nuy * nuy + nuz * nuz;
+        const R inv = rsq(R(1) + usq);
+        if (FIXA) st_wu2 = fmaxf(st_wu2, (float)(w[m] * w[m] * usq));
         x1 = x[m] + rdx * nux * inv;
         y1 = y[m] + rdy * nuy * inv;
         R S1x3[3], S1y3[3];
@@ -584,9 +639,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
           // FP32 fixed point (single particles): the tile scale folded into
           // the per-particle factors
           constexpr bool FIX = sizeof(R) == 4 && !JF && !MERGE;
-          const R wx = (FIX ? cjx * jsc[0] : cjx) * w[m];
-          const R wy = (FIX ? cjy * jsc[1] : cjy) * w[m];
-          const R wz = (FIX ? cjz * jsc[2] : cjz) * w[m] * nuz * inv;
+          const R wx = (FIX ? cjx * isc : cjx) * w[m];
+          const R wy = (FIX ? cjy * isc : cjy) * w[m];
+          const R wz = (FIX ? cjz * isc : cjz) * w[m] * nuz * inv;
           const R Px[3] = {wx * DSx[0], wx * (DSx[0] + DSx[1]), -wx * DSx[3]};
           const R Py[3] = {wy * DSy[0], wy * (DSy[0] + DSy[1]), -wy * DSy[3]};
           R zA[4], zD[4];
@@ -729,10 +784,26 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
     }
     nval = nnval;
   }
+    if (FIXA) {
+      const unsigned m1 = __reduce_max_sync(0xffffffffu, __float_as_uint(st_wu2));
+      const unsigned m2 = __reduce_max_sync(0xffffffffu, __float_as_uint(st_w));
+      if (lane == 0 && m1) atomicMax(&s_stat[0], m1);
+      if (lane == 0 && m2) atomicMax(&s_stat[1], m2);
+    }
     // the slot stays calm only if every item of it was calm (its output is
     // then a copy of its input)
     const bool moved = __syncthreads_or(moving) != 0;
     if (tid == 0 && !skip && (!quiet || arrivals || moved)) a.calm_out[s] = 0;
+    if (FIXA && tid == 0) {
+      // a skipped slot keeps its particles, hence its maxima
+      const unsigned m1 = skip ? a.stat_in[2 * s] : s_stat[0];
+      const unsigned m2 = skip ? a.stat_in[2 * s + 1] : s_stat[1];
+      if (m1) atomicMax(&a.stat_out[2 * s], m1);
+      if (m2) atomicMax(&a.stat_out[2 * s + 1], m2);
+      s_stat[0] = s_stat[1] = 0u;
+      s_src[0] = s_src[1] = 0u;
+      s_emax[0] = s_emax[1] = s_emax[2] = 0u;
+    }
     // the field tile is free: fetch the next item and start its tile load
     if (PF && tid == 0) {
       const int nxt = atomicAdd(plan.next, 1);
@@ -740,12 +811,13 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : 4) : 1))
       if (nxt < n_items) issue_tile(nxt);
     }
     // ---- SDMD step (i): patch current tile -> region current
+    const R iju = FIXA && !skip ? R(1) / isc : R(0);
     for (int e = skip ? 3 * JT : tid; e < 3 * JT; e += nth) {
       R v;
       if (sizeof(R) == 4 && !jfloat) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
         const int c = e / JT;
-        v = iv ? R(iv) * (c == 0 ? ju0 : (c == 1 ? ju1 : ju2)) : R(0);
+        v = iv ? R(iv) * (FIXA ? iju : (c == 0 ? ju0 : (c == 1 ? ju1 : ju2))) : R(0);
       } else {
         v = Jt[e];
       }
@@ -811,6 +883,7 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
       a.cnt_out[s] = 0;
       for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
       a.calm_out[s] = 1;
+      if (a.stat_out) a.stat_out[2 * s] = a.stat_out[2 * s + 1] = 0u;
     }
     const int items = (units + plan.chunk - 1) / plan.chunk;
     if (items) atomicAdd(&hist[plan_class(items, a.calm_in[s])], items);

@@ -142,7 +142,7 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
   const double ms_given = time_candidate(base, p, n, where, steps);
   TuneEntry best{{cfg->patch[0], cfg->patch[1], cfg->patch[2]},
                  base.block > 0 ? base.block : 256,
-                 base.task_chunk > 0 ? base.task_chunk : 2048,
+                 base.task_chunk,  // 0: the library's default
                  ms_given, ms_given, cfg->window_cells};
   int timed = 1;
   // the moving window's step (cells) is part of the run: patch widths that
@@ -221,7 +221,7 @@ pic_status pic_autotune_plasma(const pic_config *cfg, int steps, pic_config *tun
   const double ms_given = time_candidate_plasma(base, steps);
   TuneEntry best{{cfg->patch[0], cfg->patch[1], cfg->patch[2]},
                  base.block > 0 ? base.block : 256,
-                 base.task_chunk > 0 ? base.task_chunk : 2048,
+                 base.task_chunk,  // 0: the library's default
                  ms_given, ms_given, cfg->window_cells};
   int timed = 1;
   const int wstep = cfg->window_cells > 0 ? cfg->window_cells : cfg->patch[0];
