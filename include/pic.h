@@ -168,6 +168,16 @@ typedef struct pic_config {
                              - 31) of the largest possible one are lost).
                              FP64 always accumulates in float64; batched
                              steps and merge = 1 always in fixed point. */
+  long long staging_wait_polls; /* bound on the polls of each wait for a
+                             field tile staged by TMA before the wait is
+                             declared lost: the block then drains the
+                             in-flight copy (itself bounded), records
+                             PIC_ETIMEOUT in the context's sticky device
+                             word and returns (the call reports
+                             PIC_ETIMEOUT, later calls PIC_ESTATE until
+                             pic_restore).  0 = default 2^24 polls; a
+                             negative value makes every wait run out at
+                             once, without a poll (for tests of this path) */
 } pic_config;
 
 typedef struct pic_diag_t {

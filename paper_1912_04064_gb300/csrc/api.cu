@@ -407,6 +407,7 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.stat_in = ctx->stat[p];
   a.stat_out = ctx->stat[1 - p];
   a.jk = R(g.q != 0.0 ? 1.0 / (0.5625 * std::fabs(g.q)) : 0.0);
+  a.wait_polls = wait_polls_of(ctx->cfg.staging_wait_polls);
   a.wglob = R(ctx->wmax);
   a.cap = ctx->cap;
   a.bk = ctx->bk;

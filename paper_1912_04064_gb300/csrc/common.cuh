@@ -202,12 +202,16 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
-// Bound on mbarrier polls before a wait is declared lost (each try_wait
-// suspends for up to a hardware time slice, so this is far beyond any real
-// copy latency) and the second bound used to drain an in-flight copy before
-// the block returns.
+// Default bound on mbarrier polls before a staging wait is declared lost
+// (each try_wait suspends for up to a hardware time slice, so this is far
+// beyond any real copy latency; the run's bound is StepArgs::wait_polls,
+// pic_config.staging_wait_polls) and the bound used to drain an in-flight
+// copy before the block returns.
 constexpr long long WAIT_POLLS = 1ll << 24;
 constexpr long long DRAIN_POLLS = 1ll << 22;
+// The run's bound from pic_config.staging_wait_polls: 0 = WAIT_POLLS, a
+// negative value = no poll (every wait runs out at once).
+inline long long wait_polls_of(long long cfg) { return cfg == 0 ? WAIT_POLLS : (cfg < 0 ? 0 : cfg); }
 
 // ----------------------------------------------------------- launchers ---
 // Work plan of one particle step: items (patch slot, first work unit), a
@@ -257,6 +261,7 @@ struct StepArgs {
   const unsigned *stat_in;
   unsigned *stat_out;
   R jk, wglob;
+  long long wait_polls;  // bound on polls of a tile-staging wait
   int cap;
   Buckets bk;
   int parity;

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       int ok = 1;
       if (TMA) {
         ok = 0;
-        for (long long it = 0; it < WAIT_POLLS; ++it)
+        for (long long it = 0; it < a.wait_polls; ++it)
           if (mbar_try_wait(&mbar, phase)) { ok = 1; break; }
         if (!ok) {
           atomicOr(&a.st->err, ERR_TIMEOUT);

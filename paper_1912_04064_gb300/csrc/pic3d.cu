@@ -165,6 +165,7 @@ struct Step3 {
   int jfloat;  // FP32: accumulate the tile with float atomics instead
   Plan plan;
   const int *active;  // per physical patch: E or Bm nonzero on one of its cells
+  long long wait_polls;  // bound on polls of a tile-staging wait
 };
 
 template <typename R>
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
       int ok = 1;
       if (STAGED) {
         ok = 0;
-        for (long long it = 0; it < WAIT_POLLS; ++it)
+        for (long long it = 0; it < a.wait_polls; ++it)
           if (mbar_try_wait(&mbar, phase)) { ok = 1; break; }
         if (!ok) {
           atomicOr(&a.st->err, ERR_TIMEOUT);
@@ -1528,6 +1529,7 @@ Step3<R> step_args3(Ctx3 *c, int p) {
   const Geom3 &g = c->g;
   Step3<R> a;
   a.g = g;
+  a.wait_polls = wait_polls_of(c->cfg.staging_wait_polls);
   a.F = (const R *)c->F;
   a.Jdst = (R *)c->F + (C_JA + 3 * p) * g.cs;
   a.pin = soa7<R>(c->seg[p]);

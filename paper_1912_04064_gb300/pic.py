@@ -46,7 +46,7 @@ class pic_config(C.Structure):
         ("sort_every", C.c_int), ("task_chunk", C.c_int), ("filter_passes", C.c_int),
         ("inj_ymin", C.c_double), ("laser_z_center", C.c_double), ("window_cells", C.c_int),
         ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_user", C.c_void_p),
-        ("current_float", C.c_int),
+        ("current_float", C.c_int), ("staging_wait_polls", C.c_longlong),
     ]
 
 
@@ -230,7 +230,8 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     use_graph: bool = True, timing: bool = False, tma: bool = True,
                     capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0,
                     merge: int = -1, auto_grow: bool = True, sort_every: int = 0,
-                    task_chunk: int = 0, patch=None, current_float: bool = False) -> pic_config:
+                    task_chunk: int = 0, patch=None, current_float: bool = False,
+                    staging_wait_polls: int = 0) -> pic_config:
     """pic_config of a run dictionary (see ``workloads``); `patch` overrides
     the run's patch size (the window step stays the run's patch width
     unless the run names its own ``moving_window["cells"]``)."""
@@ -279,6 +280,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     c.merge = merge
     c.auto_grow = int(auto_grow)
     c.current_float = int(current_float)
+    c.staging_wait_polls = int(staging_wait_polls)
     c.sort_every = sort_every
     c.task_chunk = task_chunk
     c.filter_passes = int(run.get("filter_passes", 0))

@@ -47,7 +47,7 @@ def _case(kind, seed, prec="fp64", **kw):
     if kind == "window":
         run, parts = _window_run()
         o, g = pair(run, parts, prec=prec, background=("neutralising", 0.0), **kw)
-        return o, g, 1e-9
+        return o, g, 1e-12
     if kind == "periodic16":
         run = W.periodic_run((64, 48), (0.1, 0.1), (16, 16))
     elif kind == "periodic8":
@@ -112,7 +112,7 @@ def test_batch_moving_window_and_many_steps():
     b.pic_batch_step(nsteps)
     assert cases[0][1].pic_diag()["shifts"] >= 2
     for o, g, tol in cases:
-        _check(o, g, 1e-9)
+        _check(o, g, 1e-12)
     b.close()
 
 

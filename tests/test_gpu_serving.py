@@ -70,7 +70,7 @@ def test_plasma_fill_matches_host_generator_and_oracle(ppc):
     g.pic_step(nsteps)
     assert g.pic_diag()["shifts"] == o.diag()["shifts"] >= 1
     errs = field_errors(o, g, names=EB)
-    assert max(errs.values()) <= 1e-9, errs
+    assert max(errs.values()) <= 1e-12, errs
 
 
 def _mix(prec):

@@ -55,7 +55,9 @@ def test_struct_layout_matches_header(tmp_path):
         "printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pic_tune_t), offsetof(pic_tune_t, candidates),"
         " sizeof(pic_server_config), offsetof(pic_server_config, use_graph),"
         " sizeof(pic_request_info), offsetof(pic_request_info, t_done),"
-        " sizeof(pic_server_stats), offsetof(pic_server_stats, busy_s));return 0;}\n")
+        " sizeof(pic_server_stats), offsetof(pic_server_stats, busy_s));"
+        "printf(\"%zu %zu\\n\", offsetof(pic_config, current_float),"
+        " offsetof(pic_config, staging_wait_polls));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
@@ -68,7 +70,8 @@ def test_struct_layout_matches_header(tmp_path):
             C.sizeof(pic.pic_tune_t), pic.pic_tune_t.candidates.offset,
             C.sizeof(pic.pic_server_config), pic.pic_server_config.use_graph.offset,
             C.sizeof(pic.pic_request_info), pic.pic_request_info.t_done.offset,
-            C.sizeof(pic.pic_server_stats), pic.pic_server_stats.busy_s.offset]
+            C.sizeof(pic.pic_server_stats), pic.pic_server_stats.busy_s.offset,
+            pic.pic_config.current_float.offset, pic.pic_config.staging_wait_polls.offset]
     assert got == want
 
 
