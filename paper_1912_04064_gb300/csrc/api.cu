@@ -854,19 +854,27 @@ pic_status run_steps(pic_ctx *ctx, int nsteps) {
   return poll_device(ctx);
 }
 
+const void *pinned_view(const void *host);
+pic_status ensure_staging(pic_ctx *ctx, size_t n);
+
 template <typename R>
 pic_status do_load(pic_ctx *ctx, const double *x, const double *y, const double *ux,
                    const double *uy, const double *uz, const double *w, size_t n, int where) {
   const Geom &g = ctx->g;
   const double *src[6] = {x, y, ux, uy, uz, w};
   const double *d[6];
-  double *tmp = nullptr;
+  double *tmp = nullptr;  // a staging copy for pageable host arrays
   if (where == PIC_HOST) {
-    CK(cmalloc(ctx, &tmp, sizeof(double) * 6 * std::max<size_t>(n, 1)));
-    for (int a = 0; a < 6; ++a) {
-      CK(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
-                         ctx->stream));
-      d[a] = tmp + a * n;
+    bool pinned = true;
+    for (int a = 0; a < 6 && pinned; ++a) pinned = (d[a] = (const double *)pinned_view(src[a])) != nullptr;
+    if (!pinned) {
+      // (device memory of this call only: a load is not on the stepping path)
+      CK(cmalloc(ctx, &tmp, sizeof(double) * 6 * std::max<size_t>(n, 1)));
+      for (int a = 0; a < 6; ++a) {
+        CK(cudaMemcpyAsync(tmp + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
+                           ctx->stream));
+        d[a] = tmp + a * n;
+      }
     }
   } else {
     for (int a = 0; a < 6; ++a) d[a] = src[a];
@@ -1005,20 +1013,34 @@ pic_status do_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n, in
   CK(cudaMemcpyAsync(ctx->offsets, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
   double *dst = out;
-  double *tmp = nullptr;
+  bool copy_out = false;
   if (where == PIC_HOST) {
-    CK(cmalloc(ctx, &tmp, sizeof(double) * 6 * std::max<size_t>(cap, 1)));
-    dst = tmp;
+    dst = (double *)pinned_view(out);  // written in place when page-locked
+    if (!dst) {
+      const pic_status s = ensure_staging(ctx, 6 * std::max<size_t>(cap, 1));
+      if (s) return s;
+      dst = ctx->staging;
+      copy_out = true;
+    }
   }
   CK(launch_get_particles<R>(g, ctx->col0, view<R>(ctx, q, 1 - q), ctx->offsets, dst, cap,
                              ctx->stream));
   ctx->launches += 1;
-  if (tmp) {
-    CK(cudaMemcpyAsync(out, tmp, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    cfree(ctx, tmp);
-  }
+  if (copy_out)
+    CK(cudaMemcpyAsync(out, dst, sizeof(double) * 6 * cap, cudaMemcpyDeviceToHost, ctx->stream));
   return poll_device(ctx);
+}
+
+// Device address of a host buffer the GPU can reach directly (page-locked
+// memory of this process: on GB300 the kernels read and write it over the
+// coherent CPU-GPU link, with no staging copy), or null for pageable memory.
+const void *pinned_view(const void *host) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();  // pageable memory on older drivers reports an error
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 pic_status ensure_staging(pic_ctx *ctx, size_t n) {
@@ -1075,10 +1097,15 @@ pic_status do_get_field(pic_ctx *ctx, int which, double *dst, int where) {
   out_shape(g, nxo, nyo);
   const size_t n = (size_t)nxo * nyo;
   double *d = dst;
+  bool copy_out = false;
   if (where == PIC_HOST) {
-    pic_status s = ensure_staging(ctx, n);
-    if (s) return s;
-    d = ctx->staging;
+    d = (double *)pinned_view(dst);
+    if (!d) {
+      pic_status s = ensure_staging(ctx, n);
+      if (s) return s;
+      d = ctx->staging;
+      copy_out = true;
+    }
   }
   if (which == PIC_RHO || which == PIC_RHO_BG) {
     const double *src = ctx->rho_bg;
@@ -1111,7 +1138,7 @@ pic_status do_get_field(pic_ctx *ctx, int which, double *dst, int where) {
                          ctx->stream));
   }
   ctx->launches += 1;
-  if (where == PIC_HOST) {
+  if (copy_out) {
     CK(cudaMemcpyAsync(dst, d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
   }
   return poll_device(ctx);

@@ -396,15 +396,21 @@ class Pic:
         self._check(lib().pic_get_field(self.h, FIELDS.index(name), q, where))
         return out
 
-    def pic_get_particles(self) -> dict:
+    def pic_get_particles(self, out=None) -> dict:
+        """Particles as float64 arrays (global positions, u, w).  `out`: an
+        optional host array of shape (6, >= count) (7 rows in 3D) to fill,
+        e.g. page-locked memory, which the library writes in place; the
+        returned arrays are views of it."""
         n = C.c_size_t()
         self._check(lib().pic_get_particles(self.h, None, 0, C.byref(n), PIC_HOST))
-        cap = max(n.value, 1)
         keys = KEYS3 if self.cfg.dims == 3 else KEYS2
-        out = np.empty((len(keys), cap), dtype=np.float64)
+        if out is None or out.shape[0] != len(keys) or out.shape[1] < n.value or \
+                out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+            out = np.empty((len(keys), max(n.value, 1)), dtype=np.float64)
+        cap = out.shape[1]
         self._check(lib().pic_get_particles(self.h, out.ctypes.data, cap, C.byref(n), PIC_HOST))
         m = n.value
-        return {k: out[i, :m].copy() for i, k in enumerate(keys)}
+        return {k: out[i, :m] for i, k in enumerate(keys)}
 
     def pic_diag(self) -> dict:
         d = pic_diag_t()
