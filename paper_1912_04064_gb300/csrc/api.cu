@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pic.h"
@@ -43,6 +44,7 @@ struct pic_ctx {
   // per-slot maxima of (w |u|)^2 and w for the FP32 tile scale
   // (StepArgs::stat_in / stat_out), by step parity like calm
   unsigned *stat[2] = {};
+  void *parena = nullptr;  // the one allocation all particle arrays live in
   int cap = 0;
   Buckets bk{};
   Plan plan{};
@@ -287,38 +289,56 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
   ctx->cap = cap;
   ctx->bk = bucket_layout(cap);
   const Geom &g = ctx->g;
-  for (int s = 0; s < 2; ++s) {
-    for (int a = 0; a < 6; ++a) {
-      CK(cmalloc(ctx, &ctx->seg[s][a], sizeof(R) * (size_t)g.nslots * cap));
-      CK(cmalloc(ctx, &ctx->bkt[s][a], sizeof(R) * (size_t)g.nslots * ctx->bk.stride));
-    }
-    CK(cmalloc(ctx, &ctx->cnt[s], sizeof(int) * g.nslots));
-    CK(cmalloc(ctx, &ctx->bcnt[s], sizeof(int) * g.nslots * 8));
-    CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
-    CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
-    CK(cmalloc(ctx, &ctx->calm[s], g.nslots));
-    CK(cmalloc(ctx, &ctx->stat[s], sizeof(unsigned) * 2 * g.nslots));
-  }
-  CK(cmalloc(ctx, &ctx->cnt_prev, sizeof(int) * g.nslots));
-  CK(cmalloc(ctx, &ctx->bcnt_prev, sizeof(int) * g.nslots * 8));
-  CK(cudaMemsetAsync(ctx->cnt_prev, 0, sizeof(int) * g.nslots, ctx->stream));
-  CK(cudaMemsetAsync(ctx->bcnt_prev, 0, sizeof(int) * g.nslots * 8, ctx->stream));
-  ctx->calm_ok = false;
-  CK(cmalloc(ctx, &ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1)));
-  // work plan: a slot holds at most cap + bucket stride particles per step
   const bool merge = ctx->cfg.merge > 0;
   Plan &pl = ctx->plan;
   pl.unit = merge ? (int)(16 / sizeof(R)) : 1;
   const int chunk_particles = ctx->cfg.task_chunk > 0 ? ctx->cfg.task_chunk : default_chunk<R>();
   pl.chunk = std::max(1, chunk_particles / pl.unit);
+  // work plan: a slot holds at most cap + bucket stride particles per step
   const long long units_max = (long long)(cap + ctx->bk.stride) / pl.unit + 9;
   pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
                                           1ll << 30);
-  CK(cmalloc(ctx, &pl.item_slot, sizeof(int) * pl.max_items));
-  CK(cmalloc(ctx, &pl.item_first, sizeof(int) * pl.max_items));
-  CK(cmalloc(ctx, &pl.n_items, sizeof(int) * 2));
+  // every array of the particle storage carved from one allocation (one
+  // allocator call for the load), 256-byte aligned
+  char *base = nullptr;
+  size_t used = 0;
+  auto carve = [&](auto **p, size_t bytes) {
+    used = (used + 255) & ~(size_t)255;
+    *p = reinterpret_cast<std::remove_reference_t<decltype(*p)>>(base ? base + used : nullptr);
+    used += bytes;
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    used = 0;
+    for (int s = 0; s < 2; ++s) {
+      for (int a = 0; a < 6; ++a) {
+        carve(reinterpret_cast<R **>(&ctx->seg[s][a]), sizeof(R) * (size_t)g.nslots * cap);
+        carve(reinterpret_cast<R **>(&ctx->bkt[s][a]), sizeof(R) * (size_t)g.nslots * ctx->bk.stride);
+      }
+      carve(&ctx->cnt[s], sizeof(int) * g.nslots);
+      carve(&ctx->bcnt[s], sizeof(int) * g.nslots * 8);
+      carve(&ctx->calm[s], (size_t)g.nslots);
+      carve(&ctx->stat[s], sizeof(unsigned) * 2 * g.nslots);
+    }
+    carve(&ctx->cnt_prev, sizeof(int) * g.nslots);
+    carve(&ctx->bcnt_prev, sizeof(int) * g.nslots * 8);
+    carve(&ctx->offsets, sizeof(long long) * (g.nslots * 9 + 1));
+    carve(&pl.item_slot, sizeof(int) * pl.max_items);
+    carve(&pl.item_first, sizeof(int) * pl.max_items);
+    carve(&pl.n_items, sizeof(int) * 2);
+    carve(&pl.units, sizeof(int) * g.nslots);
+    if (pass == 0) {
+      CK(cmalloc(ctx, &ctx->parena, used));
+      base = static_cast<char *>(ctx->parena);
+    }
+  }
   pl.next = pl.n_items + 1;
-  CK(cmalloc(ctx, &pl.units, sizeof(int) * g.nslots));
+  for (int s = 0; s < 2; ++s) {
+    CK(cudaMemsetAsync(ctx->cnt[s], 0, sizeof(int) * g.nslots, ctx->stream));
+    CK(cudaMemsetAsync(ctx->bcnt[s], 0, sizeof(int) * g.nslots * 8, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->cnt_prev, 0, sizeof(int) * g.nslots, ctx->stream));
+  CK(cudaMemsetAsync(ctx->bcnt_prev, 0, sizeof(int) * g.nslots * 8, ctx->stream));
+  ctx->calm_ok = false;
   return PIC_OK;
 }
 
@@ -580,29 +600,16 @@ void free_backup(pic_ctx *c) {
 }
 
 void free_particles(pic_ctx *c) {
+  cfree(c, c->parena);  // every array of the particle storage (alloc_particles)
+  c->parena = nullptr;
   for (int s = 0; s < 2; ++s) {
-    for (int a = 0; a < 6; ++a) {
-      cfree(c, c->seg[s][a]);
-      cfree(c, c->bkt[s][a]);
-      c->seg[s][a] = c->bkt[s][a] = nullptr;
-    }
-    cfree(c, c->cnt[s]);
-    cfree(c, c->bcnt[s]);
-    cfree(c, c->calm[s]);
-    cfree(c, c->stat[s]);
+    for (int a = 0; a < 6; ++a) c->seg[s][a] = c->bkt[s][a] = nullptr;
     c->cnt[s] = c->bcnt[s] = nullptr;
     c->calm[s] = nullptr;
     c->stat[s] = nullptr;
   }
-  cfree(c, c->cnt_prev);
-  cfree(c, c->bcnt_prev);
   c->cnt_prev = c->bcnt_prev = nullptr;
-  cfree(c, c->offsets);
   c->offsets = nullptr;
-  cfree(c, c->plan.item_slot);
-  cfree(c, c->plan.item_first);
-  cfree(c, c->plan.n_items);
-  cfree(c, c->plan.units);
   c->plan = Plan{};
 }
 

@@ -36,11 +36,11 @@ __global__ void k_bin_count(const Geom g, int col0, const double *x, const doubl
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
     int slot, px, py;
-    if (!locate(g, col0, x[k], y[k], slot, px, py)) {
-      atomicOr(err, ERR_LOAD_RANGE);
-      continue;
-    }
-    atomicAdd(&counts[slot], 1);
+    const bool ok = locate(g, col0, x[k], y[k], slot, px, py);
+    if (!ok) atomicOr(err, ERR_LOAD_RANGE);
+    // neighbouring particles mostly share a slot: one atomic per slot and warp
+    const unsigned same = __match_any_sync(__activemask(), ok ? slot : -1);
+    if (ok && (unsigned)(__ffs(same) - 1) == (threadIdx.x & 31u)) atomicAdd(&counts[slot], __popc(same));
   }
 }
 
@@ -49,11 +49,19 @@ __global__ void k_bin_place(const Geom g, int col0, const double *x, const doubl
                             const double *ux, const double *uy, const double *uz,
                             const double *w, size_t n, SoA<R> seg, int *counts, int cap,
                             unsigned *err) {
+  const unsigned lane = threadIdx.x & 31u;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
     int slot, px, py;
-    if (!locate(g, col0, x[k], y[k], slot, px, py)) continue;
-    const int pos = atomicAdd(&counts[slot], 1);
+    const bool ok = locate(g, col0, x[k], y[k], slot, px, py);
+    // positions within a slot: one atomic per slot and warp, lanes in order
+    const unsigned same = __match_any_sync(__activemask(), ok ? slot : -1);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (ok && (int)lane == leader) base = atomicAdd(&counts[slot], __popc(same));
+    base = __shfl_sync(same, base, leader);
+    if (!ok) continue;
+    const int pos = base + __popc(same & ((1u << lane) - 1u));
     if (pos >= cap) {
       atomicOr(err, ERR_OVERFLOW_LOAD);
       continue;
