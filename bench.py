@@ -231,7 +231,7 @@ def algorithmic_bytes(npart, ncell, rsize):
 
 
 def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merge=-1, sort=0,
-            chunk=0, current_float=False):
+            chunk=0, current_float=False, deterministic=False):
     import torch
 
     from paper_1912_04064_gb300 import pic
@@ -245,7 +245,7 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     cfg = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                               use_graph=True, timing=False, capacity_factor=cf, merge=merge,
                               sort_every=sort, task_chunk=chunk,
-                              current_float=current_float)
+                              current_float=current_float, deterministic=deterministic)
     g = pic.Pic(cfg)
     g.pic_load_particles(parts)
     g.pic_set_background("neutralising")
@@ -275,7 +275,7 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
     cfg_t = pic.config_from_run(run, prec, stream=stream.cuda_stream, device=device,
                                 use_graph=False, timing=True, capacity_factor=cf, merge=merge,
                                 sort_every=sort, task_chunk=chunk,
-                              current_float=current_float)
+                                current_float=current_float, deterministic=deterministic)
     g.close()
     gt = pic.Pic(cfg_t)
     gt.pic_restore(blob)
@@ -750,6 +750,8 @@ def main():
                     help="steps of the FP32-vs-FP64 precision study (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=100,
                     help="steps of the batching comparison (0: skip)")
+    ap.add_argument("--det-steps", type=int, default=20,
+                    help="timed steps of the deterministic-mode legs, FP32 and FP64 (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -801,6 +803,11 @@ def main():
     if args.fp64_steps > 0:
         r64 = run_gpu("fp64", args.fp64_steps, max(3, args.warmup // 2), args.spinup, local, rank,
                       world, dist, args.capacity_factor, -1, args.sort_every, args.task_chunk)
+    dets = {}
+    if args.det_steps > 0:
+        for prec in ("fp32", "fp64"):
+            dets[prec] = run_gpu(prec, args.det_steps, 3, args.spinup, local, rank, world, dist,
+                                 args.capacity_factor, -1, 0, 0, deterministic=True)
     e2e = None if args.no_e2e else run_e2e("fp32", args.steps, local)
     serving = run_serving(local, args.serve_seconds) if args.serve_seconds > 0 else None
     r3 = (run_gpu3("fp32", args.steps3d, 3, max(0, 500 - args.steps3d - 3), local)
@@ -863,6 +870,17 @@ def main():
         line["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
         line["e2e"]["note"] = (f"C-ABI from pinned host buffers: H2D of the {r32['np0']} initial particles, "
                                f"{e2e['steps']} steps from t=0, D2H of E, B and all particles")
+    if dets:
+        line["deterministic"] = {
+            "note": "pic_config.deterministic = 1 (bitwise reproducible; fixed-order current "
+                    "reduction, one work item per patch, FP64 tiles in 64-bit fixed point), same "
+                    "workload and phase"}
+        for prec, r in dets.items():
+            base = r32 if prec == "fp32" else r64
+            line["deterministic"][prec] = {
+                "value": r["value"], "ms_per_step": r["ms_per_step"], "steps": args.det_steps,
+                "particle_step_ms": r["particle_step_ms"], "fields_ms": r["fields_ms"],
+                "ms_per_step_default_mode": None if base is None else base["ms_per_step"]}
     if serving:
         line["serving"] = serving
     if batching:

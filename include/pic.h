@@ -178,6 +178,19 @@ typedef struct pic_config {
                              pic_restore).  0 = default 2^24 polls; a
                              negative value makes every wait run out at
                              once, without a poll (for tests of this path) */
+  int deterministic;      /* 1: results bitwise reproducible from run to run
+                             and equal alone, batched and served (2D).  The
+                             SDMD patch -> region current reduction (Section
+                             2.2, step (i)) is made order-independent: a
+                             patch is one work item; its shared current tile
+                             accumulates in fixed point (FP32 32-bit as by
+                             default, FP64 64-bit integers at 2^-(62 -
+                             ceil(log2 n)) of the largest contribution);
+                             the tiles are stored whole and the region
+                             current summed from them in a fixed order.
+                             Slower (no heavy-patch splitting, 64-bit shared
+                             integer atomics in FP64); requires merge <= 0
+                             and current_float = 0 */
 } pic_config;
 
 typedef struct pic_diag_t {

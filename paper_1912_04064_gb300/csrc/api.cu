@@ -45,6 +45,9 @@ struct pic_ctx {
   // (StepArgs::stat_in / stat_out), by step parity like calm
   unsigned *stat[2] = {};
   void *parena = nullptr;  // the one allocation all particle arrays live in
+  // deterministic mode: the stored current tiles and their flags
+  void *jbuf = nullptr;
+  int *jflag = nullptr;
   int cap = 0;
   Buckets bk{};
   Plan plan{};
@@ -140,6 +143,10 @@ bool valid_config(const pic_config *c, std::string &why) {
   if (c->dims != 2 && c->dims != 3) { why = "dims must be 2 (2D3V) or 3 (3D3V)"; return false; }
   if (!c->dev_alloc != !c->dev_free) { why = "dev_alloc and dev_free are set together"; return false; }
   if (c->task_chunk < 0 || c->task_chunk > 4096) { why = "task_chunk must be in [0, 4096]"; return false; }
+  if (c->deterministic && (c->dims != 2 || c->merge > 0 || c->current_float)) {
+    why = "deterministic mode is 2D, without merge and float current accumulation";
+    return false;
+  }
   if (c->window_cells < 0 || (c->window_cells > 0 && c->window_cells % c->patch[0])) {
     why = "window_cells must be a multiple of patch[0]";
     return false;
@@ -296,6 +303,8 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
   pl.chunk = std::max(1, chunk_particles / pl.unit);
   // work plan: a slot holds at most cap + bucket stride particles per step
   const long long units_max = (long long)(cap + ctx->bk.stride) / pl.unit + 9;
+  const bool det = ctx->cfg.deterministic != 0;
+  if (det) pl.chunk = (int)units_max;  // one work item per patch
   pl.max_items = (int)std::min<long long>((long long)g.nslots * ((units_max + pl.chunk - 1) / pl.chunk),
                                           1ll << 30);
   // every array of the particle storage carved from one allocation (one
@@ -326,6 +335,10 @@ pic_status alloc_particles(pic_ctx *ctx, int cap) {
     carve(&pl.item_first, sizeof(int) * pl.max_items);
     carve(&pl.n_items, sizeof(int) * 2);
     carve(&pl.units, sizeof(int) * g.nslots);
+    if (det) {
+      carve(reinterpret_cast<R **>(&ctx->jbuf), sizeof(R) * (size_t)g.nslots * 3 * (g.P + 5) * (g.Q + 5));
+      carve(&ctx->jflag, sizeof(int) * g.nslots);
+    }
     if (pass == 0) {
       CK(cmalloc(ctx, &ctx->parena, used));
       base = static_cast<char *>(ctx->parena);
@@ -428,6 +441,9 @@ StepArgs<R> step_args(const pic_ctx *ctx, int p) {
   a.stat_out = ctx->stat[1 - p];
   a.jk = R(g.q != 0.0 ? 1.0 / (0.5625 * std::fabs(g.q)) : 0.0);
   a.wait_polls = wait_polls_of(ctx->cfg.staging_wait_polls);
+  a.det = ctx->cfg.deterministic != 0;
+  a.jbuf = (R *)ctx->jbuf;
+  a.jflag = ctx->jflag;
   a.wglob = R(ctx->wmax);
   a.cap = ctx->cap;
   a.bk = ctx->bk;
@@ -494,6 +510,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, bool with_plan, cudaEvent_t mi
   }
   CK(launch_particle_step<R>(a, &ctx->tmap, ctx->cfg.tma != 0, merge, block, ctx->ps_grid,
                              with_plan, ctx->stream));
+  if (a.det) CK(launch_gather_current<R>(a, ctx->stream));
   if (mid) CK(cudaEventRecord(mid, ctx->stream));
   CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
   CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
@@ -506,7 +523,7 @@ pic_status enqueue_step(pic_ctx *ctx, int parity, bool with_plan, cudaEvent_t mi
 
 int kernels_per_step(const pic_ctx *c) {
   return 4 + ((c->g.fbc_x == FBC_SM || c->g.fbc_y == FBC_SM) ? 1 : 0) +
-         (c->cfg.filter_passes > 0 ? 1 : 0);
+         (c->cfg.filter_passes > 0 ? 1 : 0) + (c->cfg.deterministic ? 1 : 0);
 }
 
 __global__ void k_window_state(DevState *st, int col0, int nshift) {
@@ -610,6 +627,8 @@ void free_particles(pic_ctx *c) {
   }
   c->cnt_prev = c->bcnt_prev = nullptr;
   c->offsets = nullptr;
+  c->jbuf = nullptr;
+  c->jflag = nullptr;
   c->plan = Plan{};
 }
 
@@ -1300,6 +1319,8 @@ struct pic_batch {
   int plan_items_alloc = 0, plan_slots_alloc = 0;
   BatchGrid slots{};
   BatchGrid fgrid[4]{};
+  bool det = false;   // runs in deterministic mode (all or none)
+  BatchGrid ggrid{};  // deterministic mode: blocks of the current gather per run
   TmapSet<kBatchMax> *tm = nullptr;  // host copy: the launch parameter
   int P = 0, Q = 0;                  // common patch shape, 0 when mixed
   bool tma = true;
@@ -1357,12 +1378,13 @@ pic_status batch_enqueue(pic_batch *b, int k) {
   br.plan = b->plan;
   BCK(launch_particle_step_batch<R>(br, b->tm, b->P, b->Q, b->tma, 256, b->grid, b->smem,
                                     b->stream));
+  if (b->det) BCK(launch_gather_current_batch<R>(br, b->ggrid, b->stream));
   BCK(launch_fields_batch<R>((const FieldArgs<R> *)b->fargs[k], b->fgrid, b->stream));
   return PIC_OK;
 }
 
 int batch_kernels_per_step(const pic_batch *b) {
-  int n = 4;  // plan, particle step, E, B
+  int n = 4 + (b->det ? 1 : 0);  // plan, particle step, (gather), E, B
   if (b->fgrid[0].off[b->fgrid[0].n] > 0) ++n;
   if (b->fgrid[3].off[b->fgrid[3].n] > 0) ++n;
   return n;
@@ -1389,7 +1411,21 @@ pic_status batch_build(pic_batch *b) {
   slots.n = n;
   for (int k = 0; k < 4; ++k) fg[k].n = n;
   long long max_items = 0;
-  const int chunk = std::max(1, b->task_chunk > 0 ? b->task_chunk : default_chunk<R>());
+  b->det = n > 0 && b->runs[0]->cfg.deterministic != 0;
+  int chunk = std::max(1, b->task_chunk > 0 ? b->task_chunk : default_chunk<R>());
+  if (b->det) {  // one work item per patch
+    chunk = 1;
+    for (int r = 0; r < n; ++r)
+      chunk = std::max(chunk, b->runs[r]->cap + b->runs[r]->bk.stride + 9);
+  }
+  b->ggrid = BatchGrid{};
+  b->ggrid.n = n;
+  for (int r = 0; r < n; ++r) {
+    const Geom &g = b->runs[r]->g;
+    const int ni = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
+    const int nj = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
+    b->ggrid.off[r + 1] = b->ggrid.off[r] + (b->det ? (ni * nj + 255) / 256 : 0);
+  }
   for (int r = 0; r < n; ++r) {
     pic_ctx *c = b->runs[r];
     const Geom &g = c->g;
@@ -1990,6 +2026,8 @@ pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n) {
     if (!c->cap) return bfail(b, PIC_ESTATE, "a run has no particles loaded");
     if (c->cfg.device != b->device) return bfail(b, PIC_EINVAL, "a run lives on another device");
     if (c->fp32 != runs[0]->fp32) return bfail(b, PIC_EINVAL, "runs of one batch share a precision");
+    if ((c->cfg.deterministic != 0) != (runs[0]->cfg.deterministic != 0))
+      return bfail(b, PIC_EINVAL, "runs of one batch share the deterministic setting");
   }
   b->runs.assign(runs, runs + n);
   b->fp32 = n ? runs[0]->fp32 : false;

@@ -262,6 +262,13 @@ struct StepArgs {
   unsigned *stat_out;
   R jk, wglob;
   long long wait_polls;  // bound on polls of a tile-staging wait
+  // deterministic mode: one work item per slot; FP64 tiles in 64-bit fixed
+  // point; each item stores its whole current tile (as reals) into jbuf at
+  // [slot][3 (P+5) (Q+5)] and sets jflag[slot]; the region current is then
+  // summed from the stored tiles in a fixed order (launch_gather_current)
+  int det;
+  R *jbuf;
+  int *jflag;
   int cap;
   Buckets bk;
   int parity;
@@ -296,6 +303,10 @@ cudaError_t launch_particle_step(const StepArgs<R> &a, const CUtensorMap *tmap, 
 // (its inputs are then the previous state kept aside).
 template <typename R>
 cudaError_t launch_plan(const StepArgs<R> &a, bool ahead, cudaStream_t s);
+// Deterministic mode: the region current of the step summed from the
+// stored tiles in a fixed order (after the particle step).
+template <typename R>
+cudaError_t launch_gather_current(const StepArgs<R> &a, cudaStream_t s);
 // Blocks of the particle step resident on the device at once.
 template <typename R>
 int particle_step_grid(int P, int Q, bool tma, bool merge, int block, bool jfloat = false);
@@ -330,6 +341,10 @@ struct BatchRef {
   BatchGrid slots;          // run r owns flattened slots [off[r], off[r + 1])
   Plan plan;                // the batch's plan (units indexed by flat slot)
 };
+// Deterministic mode, batched: the gather of every run, block b of the
+// launch working on run batch_run(bg, b) (blocks of 256 nodes per run).
+template <typename R>
+cudaError_t launch_gather_current_batch(const BatchRef<R> &b, const BatchGrid &bg, cudaStream_t s);
 // Batched plan + persistent particle step over every run of `b`.
 template <typename R>
 cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatchMax> *tm,

@@ -74,18 +74,29 @@ struct Win {
 __device__ __forceinline__ void red_f64(uint32_t addr, double v) {
   asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(addr), "d"(v));
 }
-template <int JWc>
+// FIX64 (deterministic mode): the tile holds 64-bit integers, a contribution
+// v adding round(v dsc) (integer sums do not depend on their order)
+template <bool FIX64>
+__device__ __forceinline__ void red_d(uint32_t addr, double v, double dsc) {
+  if constexpr (FIX64)
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(addr), "l"(__double2ll_rn(v * dsc)));
+  else
+    red_f64(addr, v);
+}
+template <int JWc, bool FIX64 = false>
 __device__ __forceinline__ void deposit_f64(const double *Jt, int JWr, int JHW, int o,
                                             const double Px[3], const double Py[3],
                                             const double Ax[4], const double Ay[4],
                                             const double zA[4], const double zD[4],
                                             const double DSy[4], bool x4, bool y4, bool jx,
-                                            bool jy, bool jz) {
+                                            bool jy, bool jz, double dsc = 0.0) {
   const int JW = JWc ? JWc : JWr;
   const uint32_t bx = smem_u32(Jt + o), by = bx + 8u * JHW, bz = by + 8u * JHW;
-  auto ax = [&](int l, int q) { red_f64(bx + 8u * (l * JW + q), Px[q] * Ay[l]); };
-  auto ay = [&](int q, int l) { red_f64(by + 8u * (l * JW + q), Py[l] * Ax[q]); };
-  auto az = [&](int l, int q) { red_f64(bz + 8u * (l * JW + q), zA[q] * Ay[l] + zD[q] * DSy[l]); };
+  auto ax = [&](int l, int q) { red_d<FIX64>(bx + 8u * (l * JW + q), Px[q] * Ay[l], dsc); };
+  auto ay = [&](int q, int l) { red_d<FIX64>(by + 8u * (l * JW + q), Py[l] * Ax[q], dsc); };
+  auto az = [&](int l, int q) {
+    red_d<FIX64>(bz + 8u * (l * JW + q), zA[q] * Ay[l] + zD[q] * DSy[l], dsc);
+  };
   if (jx) {
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -165,6 +176,10 @@ __device__ __forceinline__ void flush_fixed(float *Jt, int JWr, int JHW, int o, 
       if (v != 0) atomicAdd(&Jz[l * JW + q], v);
     }
 }
+
+// A float not below v (statistics bounding the fixed-point scales).
+__device__ __forceinline__ float to_float_up(float v) { return v; }
+__device__ __forceinline__ float to_float_up(double v) { return __double2float_ru(v); }
 
 // FP32 fixed-point deposit with the scale folded into the 1D factors (one
 // FMA forms and rounds each contribution, see red_fixed).
@@ -305,7 +320,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
   // (w |u|)^2 and w, the tile's largest |E_x|, |E_y|, |E_z|, and the
   // item's own largest (w |u|)^2 and w (float bits, non-negative)
   __shared__ unsigned s_src[2], s_emax[3], s_stat[2];
-  __shared__ float s_isc;  // the item's fixed-point scale
+  __shared__ float s_isc;   // the item's fixed-point scale (FP32)
+  __shared__ double s_dsc;  // the item's 64-bit fixed-point scale (FP64, deterministic)
   // BATCH: the current item's run arguments, copied from the device array
   __shared__ __align__(16) StepArgs<R> s_args[1];
 
@@ -364,6 +380,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       __syncthreads();
     }
     const StepArgs<R> &a = BATCH ? s_args[0] : a0;
+    // the item's fixed-point tile scale follows a bound on its contributions
+    // (FP32 by default; FP64 in deterministic mode)
+    const bool adapt = FIXA || (sizeof(R) == 8 && a.det != 0);
     const CUtensorMap *tmap = &tm.m[BATCH ? run : 0];
     const Geom &g = a.g;
     const int P = PT ? PT : g.P, Q = QT ? QT : g.Q;
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
           base = (long long)src * a.bk.stride + a.bk.off[k];
         }
       }
-      if (FIXA && src >= 0) {
+      if (adapt && src >= 0) {
         atomicMax(&s_src[0], a.stat_in[2 * src]);
         atomicMax(&s_src[1], a.stat_in[2 * src + 1]);
       }
@@ -479,6 +498,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
             if (FIXA && c < 3) mx = max(mx, max(max(ax, ay), max(az, aw)));
           } else {
             any |= v.x | v.z | ((v.y | v.w) & 0x7fffffffu);
+            // FP64: the high words (sign masked) of the two values; their
+            // largest + 1, shifted up, bounds the largest |value|
+            if (adapt && c < 3) mx = max(mx, max(v.y & 0x7fffffffu, v.w & 0x7fffffffu));
           }
         }
         if (any) cmask |= 1u << c;
@@ -486,7 +508,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       }
       cmask = __reduce_or_sync(0xffffffffu, cmask);
       if (lane == 0 && cmask) atomicOr(&s_cmask, cmask);
-      if (FIXA) {
+      if (adapt) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const unsigned m = __reduce_max_sync(0xffffffffu, em[c]);
@@ -507,11 +529,14 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
     if (skip && tid == 0 && ufirst == 0) a.cnt_out[s] = s_cnt[0];
     bool moving = false;  // a particle of this item had u != 0
     float st_wu2 = 0.0f, st_w = 0.0f;  // this thread's largest (w |u|)^2, w
-    // FIXA: this item's tile scale, formed once by thread 0
-    if (FIXA && !skip) {
+    // this item's tile scale, formed once by thread 0
+    if (adapt && !skip) {
       if (tid == 0) {
-        const float ex = __uint_as_float(s_emax[0]), ey = __uint_as_float(s_emax[1]),
-                    ez = __uint_as_float(s_emax[2]);
+        auto emax_of = [&](unsigned m) -> float {
+          if (sizeof(R) == 4) return __uint_as_float(m);
+          return m ? __double2float_ru(__longlong_as_double((long long)(m + 1u) << 32)) : 0.0f;
+        };
+        const float ex = emax_of(s_emax[0]), ey = emax_of(s_emax[1]), ez = emax_of(s_emax[2]);
         const float m1 = sqrtf(__uint_as_float(s_src[0])), m2 = __uint_as_float(s_src[1]);
         const float emax = sqrtf(ex * ex + ey * ey + ez * ez);
         // bound on w |v| after the push, with a margin for rounding
@@ -519,12 +544,20 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
         B = fmaxf(B * 1.001f, 1e-30f);
         const int n = totalq - ufirst;
         const int lg = n > 1 ? 32 - __clz(n - 1) : 0;
-        const int K = min(30 - lg, 20);
-        s_isc = __int_as_float((127 + K) << 23) * (float)a.jk / B;
+        if (sizeof(R) == 4) {
+          const int K = min(30 - lg, 20);
+          s_isc = __int_as_float((127 + K) << 23) * (float)a.jk / B;
+        } else {
+          // FP64 deterministic mode: 64-bit fixed point, K = 62 - ceil(log2
+          // n): every contribution below (4/3) 2^K, an item's sums below
+          // (4/3) 2^62
+          s_dsc = ldexp((double)a.jk, 62 - lg) / (double)B;
+        }
       }
       __syncthreads();
     }
     const R isc = FIXA ? R(s_isc) : R(0);
+    const R dsc = (sizeof(R) == 8 && a.det) ? R(s_dsc) : R(0);
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {
@@ -575,7 +608,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       int dir = -2;  // -1 stay, -2 gone / invalid, 0..7 bucket
       R x1 = R(0), y1 = R(0), nux = R(0), nuy = R(0), nuz = R(0);
       moving |= m < nval && (ux[m] != R(0) || uy[m] != R(0) || uz[m] != R(0));
-      if (FIXA && m < nval) st_w = fmaxf(st_w, (float)w[m]);
+      if (adapt && m < nval) st_w = fmaxf(st_w, to_float_up(w[m]));
       if (m < nval && quiet && ux[m] == R(0) && uy[m] == R(0) && uz[m] == R(0)) {
         x1 = x[m];
         y1 = y[m];
@@ -609,7 +642,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
         nuz = umz + f * (upx * ty - upy * tx) + eps * Ez;
         const R usq = nux * nux + nuy * nuy + nuz * nuz;
         const R inv = rsq(R(1) + usq);
-        if (FIXA) st_wu2 = fmaxf(st_wu2, (float)(w[m] * w[m] * usq));
+        if (adapt) st_wu2 = fmaxf(st_wu2, to_float_up(w[m] * w[m] * usq));
         x1 = x[m] + rdx * nux * inv;
         y1 = y[m] + rdy * nuy * inv;
         R S1x3[3], S1y3[3];
@@ -690,16 +723,23 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
             // the structural zeros by integer flags (an FP64 compare per
             // entry costs FP64-pipe slots, the path's bound); FP32 converts
             // each entry to fixed point and skips the zeros.
-            if constexpr (sizeof(R) == 8)
-              deposit_f64<JWc>(reinterpret_cast<const double *>(Jt), JW, JT, o,
-                               reinterpret_cast<const double *>(Px),
-                               reinterpret_cast<const double *>(Py),
-                               reinterpret_cast<const double *>(Ax),
-                               reinterpret_cast<const double *>(Ay),
-                               reinterpret_cast<const double *>(zA),
-                               reinterpret_cast<const double *>(zD),
-                               reinterpret_cast<const double *>(DSy), di != 0, dj != 0,
-                               wx != R(0) && x1 != x[m], wy != R(0) && y1 != y[m], wz != R(0));
+            if constexpr (sizeof(R) == 8) {
+              const double *dPx = reinterpret_cast<const double *>(Px);
+              const double *dPy = reinterpret_cast<const double *>(Py);
+              const double *dAx = reinterpret_cast<const double *>(Ax);
+              const double *dAy = reinterpret_cast<const double *>(Ay);
+              const double *dzA = reinterpret_cast<const double *>(zA);
+              const double *dzD = reinterpret_cast<const double *>(zD);
+              const double *dDSy = reinterpret_cast<const double *>(DSy);
+              const bool fx = wx != R(0) && x1 != x[m], fy = wy != R(0) && y1 != y[m];
+              if (a.det)
+                deposit_f64<JWc, true>(reinterpret_cast<const double *>(Jt), JW, JT, o, dPx, dPy,
+                                       dAx, dAy, dzA, dzD, dDSy, di != 0, dj != 0, fx, fy,
+                                       wz != R(0), (double)dsc);
+              else
+                deposit_f64<JWc>(reinterpret_cast<const double *>(Jt), JW, JT, o, dPx, dPy, dAx,
+                                 dAy, dzA, dzD, dDSy, di != 0, dj != 0, fx, fy, wz != R(0));
+            }
             else if constexpr (FIX)
               deposit_fixed<JWc>(reinterpret_cast<const float *>(Jt), JW, JT, o,
                                  reinterpret_cast<const float *>(Px),
@@ -784,7 +824,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
     }
     nval = nnval;
   }
-    if (FIXA) {
+    if (adapt) {
       const unsigned m1 = __reduce_max_sync(0xffffffffu, __float_as_uint(st_wu2));
       const unsigned m2 = __reduce_max_sync(0xffffffffu, __float_as_uint(st_w));
       if (lane == 0 && m1) atomicMax(&s_stat[0], m1);
@@ -794,7 +834,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
     // then a copy of its input)
     const bool moved = __syncthreads_or(moving) != 0;
     if (tid == 0 && !skip && (!quiet || arrivals || moved)) a.calm_out[s] = 0;
-    if (FIXA && tid == 0) {
+    if (adapt && tid == 0) {
       // a skipped slot keeps its particles, hence its maxima
       const unsigned m1 = skip ? a.stat_in[2 * s] : s_stat[0];
       const unsigned m2 = skip ? a.stat_in[2 * s + 1] : s_stat[1];
@@ -810,18 +850,26 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       s_item = nxt;
       if (nxt < n_items) issue_tile(nxt);
     }
-    // ---- SDMD step (i): patch current tile -> region current
+    // ---- SDMD step (i): patch current tile -> region current (deterministic
+    // mode: the whole tile stored for the fixed-order reduction)
     const R iju = FIXA && !skip ? R(1) / isc : R(0);
+    const bool det = a.det != 0;
+    if (det && !skip && tid == 0) a.jflag[s] = 1;
     for (int e = skip ? 3 * JT : tid; e < 3 * JT; e += nth) {
       R v;
       if (sizeof(R) == 4 && !jfloat) {
         const int iv = reinterpret_cast<const int *>(Jt)[e];
         const int c = e / JT;
         v = iv ? R(iv) * (FIXA ? iju : (c == 0 ? ju0 : (c == 1 ? ju1 : ju2))) : R(0);
+      } else if (sizeof(R) == 8 && det) {
+        const long long iv = reinterpret_cast<const long long *>(Jt)[e];
+        v = iv ? R((double)iv / (double)dsc) : R(0);
       } else {
         v = Jt[e];
       }
-      if (v != R(0)) {
+      if (det) {
+        a.jbuf[(long long)s * 3 * JT + e] = v;
+      } else if (v != R(0)) {
         const int c = e / JT, r = e - c * JT, l = r / JW, q = r - l * JW;
         int gi = X0 - 2 + q, gj = Y0 - 2 + l;
         if (g.fbc_x == FBC_PERIODIC) gi = gi < 0 ? gi + g.nx : (gi >= g.nx ? gi - g.nx : gi);
@@ -884,6 +932,7 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
       for (int d = 0; d < 8; ++d) a.bcnt_out[(long long)s * 8 + d] = 0;
       a.calm_out[s] = 1;
       if (a.stat_out) a.stat_out[2 * s] = a.stat_out[2 * s + 1] = 0u;
+      if (a.det) a.jflag[s] = 0;
     }
     const int items = (units + plan.chunk - 1) / plan.chunk;
     if (items) atomicAdd(&hist[plan_class(items, a.calm_in[s])], items);
@@ -912,6 +961,57 @@ __global__ void __launch_bounds__(1024) k_plan(const StepArgs<R> a0, const Batch
       if (BATCH) br.item_run[base + k] = run;
     }
   }
+}
+
+// Deterministic mode: the region current of every stored node (periodic
+// axes: [0, n); open axes: the ghost band included) is the sum, in a fixed
+// order (patch rows ascending, then columns), of the entries of the stored
+// tiles that cover it (a tile spans nodes -2 .. P+2 of its patch; periodic
+// images wrap).  BATCH: block b works on run batch_run(bg, b).
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <typename R, bool BATCH>
+__global__ void __launch_bounds__(256) k_gather_current(const StepArgs<R> a0, const BatchRef<R> br,
+                                                        const BatchGrid bg) {
+  const int run = BATCH ? batch_run(bg.off, bg.n, blockIdx.x) : 0;
+  const StepArgs<R> &a = BATCH ? br.args[run] : a0;
+  const Geom &g = a.g;
+  const int b = BATCH ? blockIdx.x - bg.off[run] : blockIdx.x;
+  const bool px_per = g.fbc_x == FBC_PERIODIC, py_per = g.fbc_y == FBC_PERIODIC;
+  const int i0 = px_per ? 0 : -GX, j0 = py_per ? 0 : -GY;
+  const int ni = px_per ? g.nx : g.nx + 2 * GX, nj = py_per ? g.ny : g.ny + 2 * GY;
+  const int e = b * blockDim.x + threadIdx.x;
+  if (e >= ni * nj) return;
+  const int i = i0 + e % ni, j = j0 + e / ni;
+  const int JW = g.P + 5, JH = g.Q + 5, JT = JW * JH;
+  const int col0 = a.st->col0;
+  R acc[3] = {R(0), R(0), R(0)};
+  for (int pyu = floor_div(j + 2 - JH + 1, g.Q); pyu <= floor_div(j + 2, g.Q); ++pyu) {
+    const int l = j + 2 - pyu * g.Q;
+    if (l < 0 || l >= JH) continue;
+    int py = pyu;
+    if (py < 0 || py >= g.npy) {
+      if (!py_per) continue;
+      py = ((py % g.npy) + g.npy) % g.npy;
+    }
+    for (int pxu = floor_div(i + 2 - JW + 1, g.P); pxu <= floor_div(i + 2, g.P); ++pxu) {
+      const int q = i + 2 - pxu * g.P;
+      if (q < 0 || q >= JW) continue;
+      int px = pxu;
+      if (px < 0 || px >= g.npx) {
+        if (!px_per) continue;
+        px = ((px % g.npx) + g.npx) % g.npx;
+      }
+      const int slot = py * g.npx + (px + col0) % g.npx;
+      if (!a.jflag[slot]) continue;
+      const R *t = a.jbuf + (long long)slot * 3 * JT + l * JW + q;
+      acc[0] += t[0];
+      acc[1] += t[JT];
+      acc[2] += t[2 * JT];
+    }
+  }
+  const long long o = fidx(g, i, j);
+  for (int c = 0; c < 3; ++c) a.Jdst[c * g.cs + o] = acc[c];
 }
 
 template <typename R, int PT, int QT, bool TMA, bool MERGE, bool BATCH, bool JF>
@@ -1032,6 +1132,25 @@ cudaError_t launch_particle_step_batch(const BatchRef<R> &b, const TmapSet<kBatc
   return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, s);
 }
 
+template <typename R>
+cudaError_t launch_gather_current(const StepArgs<R> &a, cudaStream_t s) {
+  const Geom &g = a.g;
+  const int ni = g.fbc_x == FBC_PERIODIC ? g.nx : g.nx + 2 * GX;
+  const int nj = g.fbc_y == FBC_PERIODIC ? g.ny : g.ny + 2 * GY;
+  BatchRef<R> none{};
+  BatchGrid bg{};
+  k_gather_current<R, false><<<(ni * nj + 255) / 256, 256, 0, s>>>(a, none, bg);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gather_current_batch(const BatchRef<R> &b, const BatchGrid &bg, cudaStream_t s) {
+  StepArgs<R> none{};
+  if (bg.off[bg.n] == 0) return cudaSuccess;
+  k_gather_current<R, true><<<bg.off[bg.n], 256, 0, s>>>(none, b, bg);
+  return cudaGetLastError();
+}
+
 template int particle_step_grid<float>(int, int, bool, bool, int, bool);
 template int particle_step_grid<double>(int, int, bool, bool, int, bool);
 template int particle_step_batch_grid<float>(int, int, bool, int, size_t);
@@ -1045,6 +1164,12 @@ template cudaError_t launch_particle_step<float>(const StepArgs<float> &, const 
 template cudaError_t launch_particle_step<double>(const StepArgs<double> &,
                                                   const CUtensorMap *, bool, bool, int, int, bool,
                                                   cudaStream_t);
+template cudaError_t launch_gather_current<float>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_gather_current<double>(const StepArgs<double> &, cudaStream_t);
+template cudaError_t launch_gather_current_batch<float>(const BatchRef<float> &, const BatchGrid &,
+                                                        cudaStream_t);
+template cudaError_t launch_gather_current_batch<double>(const BatchRef<double> &,
+                                                         const BatchGrid &, cudaStream_t);
 template cudaError_t launch_plan<float>(const StepArgs<float> &, bool, cudaStream_t);
 template cudaError_t launch_plan<double>(const StepArgs<double> &, bool, cudaStream_t);
 template cudaError_t launch_particle_step_batch<float>(const BatchRef<float> &,

@@ -309,7 +309,8 @@ struct pic_server {
   std::map<long long, Request> reqs;
   std::deque<long long> queue;
   std::vector<long long> running;
-  pic_batch *batch[2] = {nullptr, nullptr};  // [0] FP64 runs, [1] FP32 runs
+  // one batch per kind of run: [FP64, FP32] x [default, deterministic]
+  pic_batch *batch[4] = {nullptr, nullptr, nullptr, nullptr};
   long long next_id = 1;
   size_t in_use = 0;
   long long ticks = 0, batched_steps = 0, done = 0, failed = 0, submitted = 0, cancelled = 0;
@@ -320,15 +321,19 @@ namespace {
 
 double server_now(const pic_server *s) { return now_ms() * 1e-3 - s->t0; }
 
-// Point each batch at the current running runs of its precision.
+// The batch a run belongs to (runs of one batch share precision and the
+// deterministic setting).
+int batch_of(const pic_config &c) { return (c.prec == PIC_FP32 ? 1 : 0) + (c.deterministic ? 2 : 0); }
+
+// Point each batch at the current running runs of its kind.
 pic_status sync_batches(pic_server *s) {
-  for (int prec = 0; prec < 2; ++prec) {
+  for (int kind = 0; kind < 4; ++kind) {
     std::vector<pic_ctx *> runs;
     for (long long id : s->running) {
       const Request &r = s->reqs[id];
-      if (r.cfg.prec == (prec ? PIC_FP32 : PIC_FP64)) runs.push_back(r.ctx);
+      if (batch_of(r.cfg) == kind) runs.push_back(r.ctx);
     }
-    const pic_status st = pic_batch_set(s->batch[prec], runs.data(), (int)runs.size());
+    const pic_status st = pic_batch_set(s->batch[kind], runs.data(), (int)runs.size());
     if (st) return st;
   }
   return PIC_OK;
@@ -381,12 +386,12 @@ pic_status pic_server_create(const pic_server_config *cfg, pic_server **out) {
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return bail(PIC_ECUDA);
     s->cfg.hbm_budget = (size_t)(0.9 * (double)fr);
   }
-  for (int prec = 0; prec < 2; ++prec) {
+  for (int kind = 0; kind < 4; ++kind) {
     pic_batch_config bc{};
     bc.stream = s->stream;
     bc.device = cfg->device;
     bc.use_graph = cfg->use_graph;
-    const pic_status st = pic_batch_create(&bc, &s->batch[prec]);
+    const pic_status st = pic_batch_create(&bc, &s->batch[kind]);
     if (st) return bail(st);
   }
   *out = s;
@@ -458,13 +463,13 @@ pic_status pic_server_tick(pic_server *s, int *running) {
     long long k = s->cfg.steps_per_tick;
     for (long long id : s->running) k = std::min(k, s->reqs[id].nsteps - s->reqs[id].steps_done);
     std::vector<long long> bad;
-    for (int prec = 0; prec < 2; ++prec) {
-      if (pic_batch_size(s->batch[prec]) == 0) continue;
-      const pic_status st = pic_batch_step(s->batch[prec], (int)k);
+    for (int kind = 0; kind < 4; ++kind) {
+      if (pic_batch_size(s->batch[kind]) == 0) continue;
+      const pic_status st = pic_batch_step(s->batch[kind], (int)k);
       if (st == PIC_OK) continue;
       for (long long id : s->running) {
         Request &r = s->reqs[id];
-        if (r.cfg.prec == (prec ? PIC_FP32 : PIC_FP64) && pic_sync(r.ctx) != PIC_OK) {
+        if (batch_of(r.cfg) == kind && pic_sync(r.ctx) != PIC_OK) {
           r.status = st;
           bad.push_back(id);
         }
@@ -588,8 +593,8 @@ double pic_server_clock(const pic_server *s) { return s ? server_now(s) : 0.0; }
 
 void pic_server_destroy(pic_server *s) {
   if (!s) return;
-  for (int prec = 0; prec < 2; ++prec)
-    if (s->batch[prec]) pic_batch_destroy(s->batch[prec]);
+  for (int kind = 0; kind < 4; ++kind)
+    if (s->batch[kind]) pic_batch_destroy(s->batch[kind]);
   for (auto &kv : s->reqs)
     if (kv.second.ctx) pic_destroy(kv.second.ctx);
   if (s->own_stream) cudaStreamDestroy(s->stream);

@@ -47,6 +47,7 @@ class pic_config(C.Structure):
         ("inj_ymin", C.c_double), ("laser_z_center", C.c_double), ("window_cells", C.c_int),
         ("dev_alloc", C.c_void_p), ("dev_free", C.c_void_p), ("alloc_user", C.c_void_p),
         ("current_float", C.c_int), ("staging_wait_polls", C.c_longlong),
+        ("deterministic", C.c_int),
     ]
 
 
@@ -231,7 +232,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
                     capacity_factor: float = 0.0, capacity_min: int = 0, block: int = 0,
                     merge: int = -1, auto_grow: bool = True, sort_every: int = 0,
                     task_chunk: int = 0, patch=None, current_float: bool = False,
-                    staging_wait_polls: int = 0) -> pic_config:
+                    staging_wait_polls: int = 0, deterministic: bool = False) -> pic_config:
     """pic_config of a run dictionary (see ``workloads``); `patch` overrides
     the run's patch size (the window step stays the run's patch width
     unless the run names its own ``moving_window["cells"]``)."""
@@ -281,6 +282,7 @@ def config_from_run(run: dict, prec: str = "fp64", stream=None, device: int = 0,
     c.auto_grow = int(auto_grow)
     c.current_float = int(current_float)
     c.staging_wait_polls = int(staging_wait_polls)
+    c.deterministic = int(deterministic)
     c.sort_every = sort_every
     c.task_chunk = task_chunk
     c.filter_passes = int(run.get("filter_passes", 0))

@@ -63,7 +63,8 @@ def test_reference_arm_prints_on_rank_zero_only():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
-           "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--cpu-steps", "1"]
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "1", "--cpu-steps", "1",
+           "--spinup", "2"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
