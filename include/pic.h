@@ -38,7 +38,14 @@
  * 3D contexts (dims = 3) exchange (nz_e, ny_e, nx_e) arrays with the same
  * per-axis rule on the 3D Yee lattice: Ex (1/2,0,0), Ey (0,1/2,0),
  * Ez (0,0,1/2), Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0).  A 3D context
- * has no current filter, snapshot, auto-grow replay or batch membership.
+ * has no current filter, snapshot, auto-grow replay, batch membership or
+ * deterministic mode.
+ *
+ * Species and initial charge: pic_load_particles takes one species, the
+ * configuration's mobile one (pic_config.q, m); the immobile ions (a
+ * species with no motion, and the background charge of the initial field
+ * solve) are the charge background of pic_set_background.  pic_get_field
+ * reads one component per call.
  */
 #ifndef PIC_H
 #define PIC_H
@@ -88,7 +95,13 @@ typedef struct pic_config {
   int bc_field[3];       /* PIC_BC_* per axis */
   int bc_part[3][2];     /* PIC_PBC_* per face (lo, hi); periodic must pair
                             with a periodic field axis */
-  double q, m;           /* charge and mass of the mobile species */
+  double q, m;           /* charge and mass of the mobile species.  The
+                             runs have one mobile species (electrons) and
+                             immobile ions: the species, q, m and "mobile"
+                             arguments of a per-species load call are these
+                             two fields plus pic_set_background, which holds
+                             the immobile ions' charge (the bg_rho of an
+                             initial-field call). */
   /* Laser entering through x_min (requires an open x axis): Ey_inc(y, t) =
    * a0 exp(-((y-yc)/waist)^2) exp(-2 ln2 (tr/tau)^2) sin(tr),
    * tr = t - x_shift - t_peak, x_shift the moving window's displacement;
@@ -132,11 +145,11 @@ typedef struct pic_config {
   int task_chunk;         /* particles per work item of the particle step: a
                              patch holding more is split over several
                              blocks, each with its own current tile
-                             (0 = 2048; at most 4096: the FP32 tile
-                             accumulates in 32-bit fixed point whose
-                             resolution, 2^(ceil(log2 task_chunk) - 30)
-                             of the largest particle's contribution,
-                             follows from it) */
+                             (0 = 4096 in FP32, 2048 in FP64; at most 4096:
+                             the FP32 tile accumulates in 32-bit fixed point
+                             whose resolution, 2^(ceil(log2 n) - 30) of a
+                             bound on the contributions of the item's n
+                             particles, follows from it) */
   int filter_passes;      /* binomial current filter (Section 3.2): 0 off, 1 or
                              2 passes of (1,2,1)/4 along x then y applied to
                              J before the field update (2D only) */
@@ -162,12 +175,17 @@ typedef struct pic_config {
   void *alloc_user;
   int current_float;      /* FP32 path: 1 = the shared current tile
                              accumulates with float atomics; 0 (default) =
-                             32-bit fixed point scaled to the largest
-                             particle weight (native integer shared atomics;
-                             contributions below 2^(ceil(log2 task_chunk)
-                             - 31) of the largest possible one are lost).
-                             FP64 always accumulates in float64; batched
-                             steps and merge = 1 always in fixed point. */
+                             32-bit fixed point (native integer shared
+                             atomics) scaled per work item to a bound on its
+                             own contributions: (3/4) |q| times the largest
+                             w |v| its particles can reach, from the previous
+                             step's largest w |u| and w of its source
+                             patches and the staged tile's largest |E|;
+                             contributions below 2^(ceil(log2 n) - 31) of
+                             that bound round to zero.  FP64 accumulates in
+                             float64 (64-bit fixed point when
+                             deterministic); merge = 1 keeps a run-wide
+                             fixed-point scale. */
   long long staging_wait_polls; /* bound on the polls of each wait for a
                              field tile staged by TMA before the wait is
                              declared lost: the block then drains the
@@ -220,19 +238,24 @@ typedef struct pic_ctx pic_ctx;
 
 /* Create a context: validates the configuration and allocates the fields
  * (particles are allocated by the first pic_load_particles).  The context
- * owns all device memory it allocates. */
+ * owns all device memory it allocates.
+ * Paper: the single domain (region) and its patches, Section 2.2. */
 pic_status pic_create(const pic_config *cfg, pic_ctx **out);
 
 /* Append n particles (global positions x, y in c/w; momenta u; weights w =
  * local density / particles per cell), float64, PIC_HOST or PIC_DEVICE.
  * They are binned into patches on the device; positions outside the domain
  * give PIC_EINVAL.  The first call sizes the patch capacity.  2D contexts
- * only (PIC_EINVAL for dims = 3). */
+ * only (PIC_EINVAL for dims = 3).  Page-locked host arrays are read in
+ * place by the kernels (no staging copy).  The species is the
+ * configuration's mobile one (pic_config.q, m).
+ * Paper: macro-particles held by the patches, Section 2.2. */
 pic_status pic_load_particles(pic_ctx *ctx, const double *x, const double *y,
                               const double *ux, const double *uy,
                               const double *uz, const double *w, size_t n,
                               int where);
-/* The same with z positions, for 3D contexts (PIC_EINVAL for dims = 2). */
+/* The same with z positions, for 3D contexts (PIC_EINVAL for dims = 2).
+ * Paper: as pic_load_particles, in three dimensions. */
 pic_status pic_load_particles3(pic_ctx *ctx, const double *x, const double *y,
                                const double *z, const double *ux,
                                const double *uy, const double *uz,
@@ -245,59 +268,83 @@ pic_status pic_load_particles3(pic_ctx *ctx, const double *x, const double *y,
  * charge of the co-located immobile ions is added to the background.  Only
  * before any particles are loaded (PIC_ESTATE otherwise); sizes the patch
  * capacity like the first pic_load_particles (a full patch x
- * capacity_factor). */
+ * capacity_factor).
+ * Paper: macro-particles placed regularly in every cell, Section 3.2. */
 pic_status pic_load_plasma(pic_ctx *ctx);
 
 /* Overwrite one field component (PIC_EX..PIC_BMZ or PIC_RHO_BG) from an
- * array in the layout above.  B is taken at t + dt/2, Bm at t. */
+ * array in the layout above.  B is taken at t + dt/2, Bm at t.
+ * Paper: the region's fields on the Yee lattice, Sections 2.2 and 3.2. */
 pic_status pic_set_field(pic_ctx *ctx, int which, const double *src, int where);
 
 /* Background charge (immobile ions): none, uniform value, or neutralising
- * the particles currently loaded. */
+ * the particles currently loaded.  This is the immobile species and the
+ * bg_rho of the initial field solve (it enters Gauss's law and the Poisson
+ * start; the ions deposit no current).
+ * Paper: the immobile-ion background of the runs, Section 3.1. */
 pic_status pic_set_background(pic_ctx *ctx, int mode, double value);
 
 /* Initial fields.  PIC_INIT_ZERO: E, B and Bm zero.  PIC_INIT_POISSON (every
  * axis periodic): E from Gauss's law for the loaded particles and the
  * background, div_h E = rho - <rho>, E = -grad_h phi on the Yee lattice,
  * solved in FP64 with a spectral (FFT) Poisson solve; B = Bm = 0.  Other
- * boundaries give PIC_EINVAL. */
+ * boundaries give PIC_EINVAL.
+ * Paper: the Maxwell-Gauss system the Yee update preserves, Section 3.2. */
 enum { PIC_INIT_ZERO = 0, PIC_INIT_POISSON = 1 };
 pic_status pic_init_fields(pic_ctx *ctx, int mode);
 
 /* Advance nsteps steps.  Synchronises with the device at the end and reports
- * device-side faults. */
+ * device-side faults.
+ * Paper: one PIC iteration with the two SDMD synchronisations, Section 2.2
+ * steps (i) (patch currents reduced into the region) and (ii) (region
+ * fields sent to the patches); the operators of Section 3.2 (Yee FDTD,
+ * Esirkepov deposition of order 2 on a 5-point stencil, optional binomial
+ * filter) and the "Particles" phase of Section 3.3 (interpolation, push,
+ * deposition). */
 pic_status pic_step(pic_ctx *ctx, int nsteps);
 
 /* Read one field component (PIC_EX..PIC_RHO_BG) into dst (layout above).
  * PIC_JX..PIC_JZ give the current of the last step as the field update used
  * it (after the binomial filter when filter_passes > 0); PIC_RHO deposits
- * the particles' charge in float64. */
+ * the particles' charge in float64.  A page-locked host dst is written in
+ * place.
+ * Paper: the region fields of Section 2.2 on the Yee lattice of 3.2. */
 pic_status pic_get_field(pic_ctx *ctx, int which, double *dst, int where);
 
 /* Copy the particles out as 6 x n float64 rows (x, y, ux, uy, uz, w), global
  * positions, in patch order; 3D contexts give 7 rows (x, y, z, ux, uy, uz,
  * w).  cap is the row length of out; *n receives the count (PIC_EINVAL if
- * it exceeds cap). */
+ * it exceeds cap).  A page-locked host out is written in place.
+ * Paper: the patches' macro-particles, Section 2.2. */
 pic_status pic_get_particles(pic_ctx *ctx, double *out, size_t cap, size_t *n,
                              int where);
 
-/* Diagnostics (float64 reductions on the device). */
+/* Diagnostics (float64 reductions on the device).
+ * Paper: the energy and load measures of Section 3.3 (field and kinetic
+ * energy, particle counts per patch), with the discrete Gauss and
+ * continuity residuals the Yee / Esirkepov pair (Section 3.2) conserves. */
 pic_status pic_diag(pic_ctx *ctx, pic_diag_t *out);
 
-/* Wait for the context's stream and report sticky device faults. */
+/* Wait for the context's stream and report sticky device faults.
+ * (Library plumbing; the paper has no counterpart.) */
 pic_status pic_sync(pic_ctx *ctx);
 
 /* Checkpoint: with host == NULL, *bytes receives the size needed; otherwise
- * the whole state is written to host (size *bytes). */
+ * the whole state is written to host (size *bytes).
+ * (Fault recovery of this library; the paper has no counterpart.) */
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes);
 /* Restore a snapshot taken from a context with the same configuration; also
  * clears a sticky device fault. */
 pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes);
 
 /* Device bytes a context with this configuration and at most np_max
- * particles at the first load would allocate (used for admission). */
+ * particles at the first load would allocate (used for admission).
+ * (Serving admission; the paper has no counterpart.) */
 size_t pic_footprint(const pic_config *cfg, size_t np_max);
 
+/* Human-readable reason of the context's last failure; destroy a context
+ * (every allocation it made returned).  (Library plumbing; the paper has no
+ * counterpart.) */
 const char *pic_last_error(const pic_ctx *ctx);
 void pic_destroy(pic_ctx *ctx);
 
@@ -328,7 +375,8 @@ typedef struct pic_batch_config {
   void *stream;    /* cudaStream_t of the batch; NULL = library-owned */
   int device;      /* CUDA device ordinal (every run's) */
   int use_graph;   /* 1: each step replays a captured CUDA graph */
-  int task_chunk;  /* particles per work item (0 = 2048, at most 4096) */
+  int task_chunk;  /* particles per work item (0 = 4096 in FP32, 2048 in
+                      FP64; at most 4096) */
 } pic_batch_config;
 typedef struct pic_batch_diag_t {
   long long steps;     /* batched steps taken */
@@ -338,12 +386,17 @@ typedef struct pic_batch_diag_t {
   int grid;            /* blocks of the persistent particle step */
 } pic_batch_diag_t;
 
+/* Paper (all batch calls): the patch-level task decomposition of Section
+ * 2.2 applied across independent runs; batching itself has no counterpart
+ * in the paper. */
 pic_status pic_batch_create(const pic_batch_config *cfg, pic_batch **out);
 /* Replace the batch's runs (n = 0 empties it); PIC_EINVAL / PIC_ESTATE when
- * a run breaks a rule above, leaving the batch unchanged. */
+ * a run breaks a rule above (runs of one batch also share the deterministic
+ * setting), leaving the batch unchanged. */
 pic_status pic_batch_set(pic_batch *b, pic_ctx *const *runs, int n);
 /* Advance every run nsteps steps (moving-window shifts of each run applied
- * as they fall due).  Synchronises at the end. */
+ * as they fall due).  Synchronises at the end.  Each run's step is the one
+ * of pic_step (Section 2.2 steps (i) and (ii), Section 3.2 operators). */
 pic_status pic_batch_step(pic_batch *b, int nsteps);
 int pic_batch_size(const pic_batch *b);
 pic_status pic_batch_get_diag(const pic_batch *b, pic_batch_diag_t *out);
@@ -385,6 +438,9 @@ pic_status pic_autotune(const pic_config *cfg, const double *x, const double *y,
  * per process like pic_autotune, keyed by the full grid and the plasma. */
 pic_status pic_autotune_plasma(const pic_config *cfg, int steps, pic_config *tuned,
                                pic_tune_t *out);
+/* Forget every cached choice.  (Autotuning has no counterpart in the paper;
+ * its candidates are the patch sizes of Section 2.2, the paper's own
+ * performance knob, Section 3.3.) */
 void pic_autotune_clear_cache(void);
 
 /* ---- Serving ------------------------------------------------------------
@@ -403,9 +459,11 @@ void pic_autotune_clear_cache(void);
  *     recorded; the context destroyed, or kept for pic_server_take).
  * A request that arrives while others run joins at the next tick in which
  * a slot and memory are free.  Times are seconds on the server's clock
- * (pic_server_clock).  FP32 and FP64 requests may be mixed: the server
- * keeps one batch per precision and steps both in every tick.  Not
- * thread-safe: one host thread drives a server. */
+ * (pic_server_clock).  FP32 and FP64 requests, deterministic or not, may be
+ * mixed: the server keeps one batch per precision and mode and steps each
+ * in every tick.  Not thread-safe: one host thread drives a server.
+ * (Serving has no counterpart in the paper; each served run is the step of
+ * pic_step.) */
 typedef struct pic_server pic_server;
 typedef struct pic_server_config {
   void *stream;          /* cudaStream_t of the batches; NULL = library-owned */
@@ -461,7 +519,7 @@ pic_status pic_server_get_stats(const pic_server *s, pic_server_stats *out);
 double pic_server_clock(const pic_server *s);
 void pic_server_destroy(pic_server *s);
 
-/* Library version string. */
+/* Library version string.  (No counterpart in the paper.) */
 const char *pic_version(void);
 
 /* Allocation-free field energy (the paper has no counterpart: this is a
