@@ -278,6 +278,7 @@ pic_status poll_device(pic_ctx *ctx) {
     if (h.err & ERR_NONFINITE) m += " non-finite particle;";
     if (h.err & ERR_FAST) m += " particle moved more than one cell;";
     if (h.err & ERR_LOAD_RANGE) { s = PIC_EINVAL; m += " particle outside the domain;"; }
+    if (h.err & ERR_BOUNDS) { s = PIC_ECUDA; m += " index out of bounds (checked build);"; }
     ctx->sticky = s;
     return fail(ctx, s, m);
   }

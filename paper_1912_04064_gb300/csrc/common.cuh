@@ -41,8 +41,19 @@ enum : unsigned {
   ERR_FAST = 8u,
   ERR_TIMEOUT = 16u,
   ERR_LOAD_RANGE = 32u,
-  ERR_OVERFLOW_LOAD = 64u
+  ERR_OVERFLOW_LOAD = 64u,
+  ERR_BOUNDS = 128u  // checked build: an index out of its array (access skipped)
 };
+
+// Checked build (-DPIC_CHECKED): PIC_IN(err, cond) is cond, and records
+// ERR_BOUNDS in the unsigned err when it fails (the caller then skips the
+// access: no trap, no early return, so every block still reaches its
+// barriers); otherwise it is true and costs nothing.
+#ifdef PIC_CHECKED
+#define PIC_IN(err, cond) ((cond) ? true : ((err) |= ERR_BOUNDS, false))
+#else
+#define PIC_IN(err, cond) true
+#endif
 
 // Device-resident state; t and step are double-buffered by step parity so
 // that the kernels of one step read slot p while the last one writes 1 - p.

@@ -71,6 +71,14 @@ __device__ __forceinline__ void update_E(const FieldArgs<R> &a, int blk_x, int b
   const R *J = F + (C_JA + 3 * (a.filter_passes > 0 ? 1 - a.parity : a.parity)) * cs;
   const R dt = a.dt, idx = a.idx, idy = a.idy;
   const long long o = (long long)(j + GY) * sx + (i + GX);
+  {
+    // checked build: the cell and its lower neighbours inside the arrays
+    unsigned err = 0;
+    if (!PIC_IN(err, o >= sx && o < cs)) {
+      atomicOr(&a.st->err, err);
+      return;
+    }
+  }
   const R bz = Bz[o], bzl = Bz[o - 1], bzd = Bz[o - sx];
   const R by = By[o], byl = By[o - 1];
   const R bx = Bx[o], bxd = Bx[o - sx];
@@ -129,6 +137,15 @@ __device__ __forceinline__ void update_B(const FieldArgs<R> &a, int blk_x, int b
   const bool ux = in && i < rg.nxp && j < rg.nyd;
   const bool uy = in && i < rg.nxd && j < rg.nyp;
   const bool uz = in && i < rg.nxd && j < rg.nyd;
+  {
+    // checked build: the cell, and its upper neighbours where read, inside
+    // the arrays
+    unsigned err = 0;
+    if (!PIC_IN(err, o >= 0 && o < cs && (!(ux || uy || uz) || o + sx + 1 < cs))) {
+      atomicOr(&a.st->err, err);
+      return;
+    }
+  }
   const R bx0 = Bx[o], by0 = By[o], bz0 = Bz[o];
   R ez = R(0), ezu = R(0), ezr = R(0), ey = R(0), eyr = R(0), ex = R(0), exu = R(0);
   if (ux || uy) ez = Ez[o];
@@ -207,6 +224,13 @@ __device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, in
     const R ez = Ez[fidx(g, ib, j)], byi = By[fidx(g, in, j)];
     const R ey = hasz ? Ey[fidx(g, ib, j)] : R(0), bzi = hasz ? Bz[fidx(g, in, j)] : R(0);
     const long long og = fidx(g, gh, j);
+    {
+      unsigned err = 0;  // checked build: ghost and boundary nodes inside the arrays
+      if (!PIC_IN(err, og >= 0 && og < cs && fidx(g, ib, j) < cs && fidx(g, ib, j - 1) >= 0)) {
+        atomicOr(&a.st->err, err);
+        return;
+      }
+    }
     const R by_old = Bmy[og], bz_old = hasz ? Bmz[og] : R(0);
     R by, bz;
     if (!upper) {
@@ -240,6 +264,13 @@ __device__ __forceinline__ void silver_mueller(const FieldArgs<R> &a, int bx, in
     const R ez = Ez[fidx(g, i, jb)], bxi = Bx[fidx(g, i, jn)];
     const R ex = hasz ? Ex[fidx(g, i, jb)] : R(0), bzi = hasz ? Bz[fidx(g, i, jn)] : R(0);
     const long long og = fidx(g, i, gh);
+    {
+      unsigned err = 0;  // checked build: ghost and boundary nodes inside the arrays
+      if (!PIC_IN(err, og >= 0 && og < cs && fidx(g, i, jb) < cs && fidx(g, i - 1, jb) >= 0)) {
+        atomicOr(&a.st->err, err);
+        return;
+      }
+    }
     const R bx_old = Bmx[og], bz_old = hasz ? Bmz[og] : R(0);
     R bx, bz;
     if (!upper) {

@@ -569,6 +569,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       while (src < 8 && qi >= s_qoff[src + 1]) ++src;
       const int k0 = (qi - s_qoff[src]) * M;
       nval = min(M, s_cnt[src] - k0);
+      // checked build: the source's elements stay inside its segment or bucket
+      if (!PIC_IN(err, k0 >= 0 && k0 + nval <= (src == 0 ? a.cap : a.bk.cap[src - 1]))) return 0;
       const SoA<R> &A = src == 0 ? a.pin : a.bin;
       const long long b = s_base[src] + k0;
       if (M > 1 && nval == M) {
@@ -623,12 +625,18 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
         // stencil at n - 1); row node n -> n (tile starts at node -1)
         const int opp = jp * BX + ip + 3, opd = jd * BX + ip + 3;
         const int odp = jp * BX + id + 3, odd = jd * BX + id + 3;
-        const R Ex = (cmask & 1u) ? gather<R, BXc>(Ft, BX, odp, Sxd, Syp) : R(0);
-        const R Ey = (cmask & 2u) ? gather<R, BXc>(Ft + FT, BX, opd, Sxp, Syd) : R(0);
-        const R Ez = (cmask & 4u) ? gather<R, BXc>(Ft + 2 * FT, BX, opp, Sxp, Syp) : R(0);
-        const R Bx = (cmask & 8u) ? gather<R, BXc>(Ft + 3 * FT, BX, opd, Sxp, Syd) : R(0);
-        const R By = (cmask & 16u) ? gather<R, BXc>(Ft + 4 * FT, BX, odp, Sxd, Syp) : R(0);
-        const R Bz = (cmask & 32u) ? gather<R, BXc>(Ft + 5 * FT, BX, odd, Sxd, Syd) : R(0);
+        // checked build: every 3 x 3 stencil inside its component's tile
+        const unsigned gm =
+            PIC_IN(err, min(min(opp, opd), min(odp, odd)) >= 0 &&
+                            max(max(opp, opd), max(odp, odd)) + 2 * BX + 2 < FT)
+                ? cmask
+                : 0u;
+        const R Ex = (gm & 1u) ? gather<R, BXc>(Ft, BX, odp, Sxd, Syp) : R(0);
+        const R Ey = (gm & 2u) ? gather<R, BXc>(Ft + FT, BX, opd, Sxp, Syd) : R(0);
+        const R Ez = (gm & 4u) ? gather<R, BXc>(Ft + 2 * FT, BX, opp, Sxp, Syp) : R(0);
+        const R Bx = (gm & 8u) ? gather<R, BXc>(Ft + 3 * FT, BX, opd, Sxp, Syd) : R(0);
+        const R By = (gm & 16u) ? gather<R, BXc>(Ft + 4 * FT, BX, odp, Sxd, Syp) : R(0);
+        const R Bz = (gm & 32u) ? gather<R, BXc>(Ft + 5 * FT, BX, odd, Sxd, Syd) : R(0);
         // Boris push u^{n-1/2} -> u^{n+1/2}
         const R umx = ux[m] + eps * Ex, umy = uy[m] + eps * Ey, umz = uz[m] + eps * Ez;
         const R ig = eps * rsq(R(1) + umx * umx + umy * umy + umz * umz);
@@ -718,7 +726,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
               acc = cur;
               key = o;
             }
-          } else if (x1 != x[m] || y1 != y[m] || nuz != R(0)) {
+          } else if ((x1 != x[m] || y1 != y[m] || nuz != R(0)) &&
+                     PIC_IN(err, o >= 0 && o + 3 * JW + 3 < JT)) {  // window in the tile
             // (a particle that did not move deposits nothing).  FP64 skips
             // the structural zeros by integer flags (an FP64 compare per
             // entry costs FP64-pipe slots, the path's bound); FP32 converts
@@ -874,7 +883,9 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
         int gi = X0 - 2 + q, gj = Y0 - 2 + l;
         if (g.fbc_x == FBC_PERIODIC) gi = gi < 0 ? gi + g.nx : (gi >= g.nx ? gi - g.nx : gi);
         if (g.fbc_y == FBC_PERIODIC) gj = gj < 0 ? gj + g.ny : (gj >= g.ny ? gj - g.ny : gj);
-        atomicAdd(&a.Jdst[c * g.cs + fidx(g, gi, gj)], v);
+        // checked build: the node inside the stored region
+        if (PIC_IN(err, gi >= -GX && gi < g.nx + GX && gj >= -GY && gj < g.ny + GY))
+          atomicAdd(&a.Jdst[c * g.cs + fidx(g, gi, gj)], v);
       }
     }
     if (tid == 0) atomicMax(&a.st->maxcnt[a.parity], atomicAdd(&a.cnt_out[s], 0));

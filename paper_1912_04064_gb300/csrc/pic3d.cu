@@ -477,7 +477,18 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
         const int gp[3] = {X0 + ip[0] - 1, Y0 + ip[1] - 1, Z0 + ip[2] - 1};
         const int gd[3] = {X0 + id[0] - 1, Y0 + id[1] - 1, Z0 + id[2] - 1};
         R Ex, Ey, Ez, Bx, By, Bz;
-        if (STAGED) {
+        // checked build: every 3 x 3 x 3 stencil inside the staged tile, or
+        // inside the stored region when gathered from HBM
+        const bool gok = STAGED
+            ? PIC_IN(err, min(id[0] + 3, ip[0] + 3) >= 0 && max(id[0], ip[0]) + 3 + 2 < BX &&
+                              min(min(id[1], ip[1]), min(id[2], ip[2])) >= 0 &&
+                              max(id[1], ip[1]) + 2 < BY && max(id[2], ip[2]) + 2 < BZ)
+            : PIC_IN(err, min(gd[0], gp[0]) >= -G3 && max(gd[0], gp[0]) + 2 < g.n[0] + G3 &&
+                              min(gd[1], gp[1]) >= -G3 && max(gd[1], gp[1]) + 2 < g.n[1] + G3 &&
+                              min(gd[2], gp[2]) >= -G3 && max(gd[2], gp[2]) + 2 < g.n[2] + G3);
+        if (!gok) {
+          Ex = Ey = Ez = Bx = By = Bz = R(0);
+        } else if (STAGED) {
           // tile index of patch-relative node (x, y, z): x + 4, y + 1, z + 1
           const int tp[3] = {ip[0] + 3, ip[1], ip[2]}, td[3] = {id[0] + 3, id[1], id[2]};
           Ex = gather27t(Ft, BX, BY, td[0], tp[1], tp[2], Sd[0], Sp[1], Sp[2]);
@@ -539,6 +550,8 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
           // whole component when the particle did not move along it.
           const int st3[3] = {1, JW, JW * JH};
           const int base = (org[2] * JH + org[1]) * JW + org[0];
+          // checked build: the 4 x 4 x 4 window inside the current tile
+          const bool wok = PIC_IN(err, base >= 0 && base + 3 * (1 + JW + JW * JH) < JT);
           constexpr bool fixed = sizeof(R) == 4 && !JF;
           // fixed point: the tile scale folded into the prefix factors, each
           // contribution formed and rounded by one FMA (red_fixed)
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
             const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
             const R cw = a.cj[c] * w * jsc;
             const R P0 = cw * DS[c][0], P1 = cw * (DS[c][0] + DS[c][1]), P2 = -cw * DS[c][3];
-            if (P0 == R(0) && P1 == R(0) && P2 == R(0)) continue;
+            if (!wok || (P0 == R(0) && P1 == R(0) && P2 == R(0))) continue;
             R *J = Jt + c * JT + base;
             const int sc = st3[c], s1 = st3[b1], s2 = st3[b2];
             const bool w1 = x4[b1], w2 = x4[b2], wc = x4[c];
@@ -672,7 +685,10 @@ __global__ void __launch_bounds__(256, (k3_min_blocks<R, STAGED, PX, PY, PZ>()))
       if (g.fbc[0] == FBC_PERIODIC) gi = gi < 0 ? gi + g.n[0] : (gi >= g.n[0] ? gi - g.n[0] : gi);
       if (g.fbc[1] == FBC_PERIODIC) gj = gj < 0 ? gj + g.n[1] : (gj >= g.n[1] ? gj - g.n[1] : gj);
       if (g.fbc[2] == FBC_PERIODIC) gk = gk < 0 ? gk + g.n[2] : (gk >= g.n[2] ? gk - g.n[2] : gk);
-      atomicAdd(&a.Jdst[c * g.cs + fidx3(g, gi, gj, gk)], v);
+      // checked build: the node inside the stored region
+      if (PIC_IN(err, gi >= -G3 && gi < g.n[0] + G3 && gj >= -G3 && gj < g.n[1] + G3 &&
+                          gk >= -G3 && gk < g.n[2] + G3))
+        atomicAdd(&a.Jdst[c * g.cs + fidx3(g, gi, gj, gk)], v);
     }
     if (tid == 0) atomicMax(&a.st->maxcnt[a.parity], atomicAdd(&a.cnt_out[s], 0));
   }
@@ -1460,6 +1476,7 @@ pic_status poll3(Ctx3 *c) {
     if (h.err & ERR_NONFINITE) m += " non-finite particle;";
     if (h.err & ERR_FAST) m += " particle moved more than one cell;";
     if (h.err & ERR_LOAD_RANGE) { s = PIC_EINVAL; m += " particle outside the domain;"; }
+    if (h.err & ERR_BOUNDS) { s = PIC_ECUDA; m += " index out of bounds (checked build);"; }
     c->sticky = s;
     return fail3(c, s, m);
   }

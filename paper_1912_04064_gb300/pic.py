@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpic.so")
+# PIC_CHECKED=1: the bounds-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(HERE, "libpic_checked.so" if os.environ.get("PIC_CHECKED") == "1"
+                        else "libpic.so")
 
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_EOVERFLOW, PIC_ETIMEOUT, PIC_ENONFINITE, PIC_ESTATE = range(8)
 STATUS = ["PIC_OK", "PIC_EINVAL", "PIC_ENOMEM", "PIC_ECUDA", "PIC_EOVERFLOW", "PIC_ETIMEOUT",
