@@ -533,10 +533,15 @@ const char *pic_version(void);
  * It allocates nothing: its scratch is a fixed file-scope device array of
  * PIC_NOALLOC_MAX_ROWS x 2 doubles (1 MiB) that every GPU loading the library
  * holds until exit.  ny > PIC_NOALLOC_MAX_ROWS, nx or ny <= 0, or a null
- * pointer gives PIC_EINVAL.  The first call on a device looks up the
- * scratch array's device address (so make it before any stream capture on
- * that device).  Calls share the scratch array: calls that overlap on the
- * GPU race; a call rewrites every row it reads.  Runs asynchronously on
+ * pointer gives PIC_EINVAL.  Set-up, once per device and CUDA context: the
+ * first call on a device (or any pic_create on it) loads this code's module
+ * and kernels and looks up the scratch array's device address; until then
+ * the array is not yet resident, and that first set-up may allocate and
+ * synchronise like any module load, so make one call, or create a context,
+ * on each device before serving and before any stream capture on it.  After
+ * a device reset (cudaDeviceReset, a new primary context) the next call sets
+ * up again.  Calls share the scratch array: calls that overlap on the GPU
+ * race; a call rewrites every row it reads.  Runs asynchronously on
  * `stream` (a cudaStream_t; NULL = the default stream). */
 #define PIC_NOALLOC_MAX_ROWS 65536
 pic_status pic_field_energy_noalloc(const double *Ex, const double *Ey,

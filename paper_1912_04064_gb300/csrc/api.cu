@@ -14,6 +14,7 @@
 #include "../../include/pic.h"
 #include "alloc.h"
 #include "common.cuh"
+#include "noalloc.h"
 #include "pic3d.h"
 #include "poisson.h"
 
@@ -1627,6 +1628,9 @@ pic_status pic_create(const pic_config *cfg, pic_ctx **out) {
     return s;
   };
   if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(PIC_ECUDA);
+  // the allocation-free entry point made ready on this device, so that its
+  // calls never load code or allocate
+  if (noalloc_setup(cfg->device) != PIC_OK) return bail(PIC_ECUDA);
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {
