@@ -38,8 +38,8 @@
  * 3D contexts (dims = 3) exchange (nz_e, ny_e, nx_e) arrays with the same
  * per-axis rule on the 3D Yee lattice: Ex (1/2,0,0), Ey (0,1/2,0),
  * Ez (0,0,1/2), Bx (0,1/2,1/2), By (1/2,0,1/2), Bz (1/2,1/2,0).  A 3D context
- * has no current filter, snapshot, auto-grow replay, batch membership or
- * deterministic mode.
+ * has snapshots and the auto-grow replay, but no current filter, cell-order
+ * sort, batch membership or deterministic mode.
  *
  * Species and initial charge: pic_load_particles takes one species, the
  * configuration's mobile one (pic_config.q, m); the immobile ions (a
@@ -334,7 +334,9 @@ pic_status pic_sync(pic_ctx *ctx);
  * (Fault recovery of this library; the paper has no counterpart.) */
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes);
 /* Restore a snapshot taken from a context with the same configuration; also
- * clears a sticky device fault. */
+ * clears a sticky device fault.  A context with particle storage takes only
+ * a snapshot of its own capacity; one without (never loaded) allocates it.
+ * 2D and 3D snapshots are distinct formats (PIC_EINVAL across them). */
 pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes);
 
 /* Device bytes a context with this configuration and at most np_max

@@ -1876,8 +1876,11 @@ pic_status pic_sync(pic_ctx *ctx) {
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   pic_status s = check_usable(ctx);
   if (s) return s;
-  if (ctx->c3) return fail(ctx, PIC_EINVAL, "snapshots are a 2D feature");
   if (!bytes) return fail(ctx, PIC_EINVAL, "null size");
+  if (ctx->c3) {
+    CK(cudaSetDevice(ctx->cfg.device));
+    return c3_snapshot(ctx->c3, host, bytes);
+  }
   const size_t need = snapshot_bytes(ctx);
   if (!host) {
     *bytes = need;
@@ -1920,7 +1923,10 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
 
 pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (!ctx || !host) return PIC_EINVAL;
-  if (ctx->c3) return fail(ctx, PIC_EINVAL, "snapshots are a 2D feature");
+  if (ctx->c3) {
+    CK(cudaSetDevice(ctx->cfg.device));
+    return c3_restore(ctx->c3, host, bytes);
+  }
   SnapHeader h;
   if (bytes < sizeof h) return fail(ctx, PIC_EINVAL, "snapshot too small");
   memcpy(&h, host, sizeof h);

@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
       __syncthreads();
     }
     const R isc = FIXA ? R(s_isc) : R(0);
-    const R dsc = (sizeof(R) == 8 && a.det) ? R(s_dsc) : R(0);
+    const R dsc = (sizeof(R) == 8 && a.det) ? R(s_dsc) : R(1);  // read only in deterministic FP64
 
   // particles of work item qi (M consecutive of one source) -> registers
   auto load = [&](int qi, R(&x)[M], R(&y)[M], R(&ux)[M], R(&uy)[M], R(&uz)[M], R(&w)[M]) {

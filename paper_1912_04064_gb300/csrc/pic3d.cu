@@ -1325,6 +1325,32 @@ __global__ void k3_window_state(DevState *st, int col0, int nshift) {
   st->nshift = nshift;
 }
 
+// Copy one particle set (patch segments of capacity cap_src and the 26
+// direction buckets of layout bk_src) into storage of another capacity and
+// bucket layout; counts beyond a destination capacity are cut to it.
+template <typename R>
+__global__ void k3_repack(int nslots, SoA7<R> src, const int *cnt_src, int cap_src, SoA7<R> bsrc,
+                          const int *bcnt_src, Buckets26 bk_src, SoA7<R> dst, int *cnt_dst,
+                          int cap_dst, SoA7<R> bdst, int *bcnt_dst, Buckets26 bk_dst) {
+  auto copy = [](SoA7<R> &d, long long i, const SoA7<R> &s, long long j) {
+    d.x[i] = s.x[j]; d.y[i] = s.y[j]; d.z[i] = s.z[j];
+    d.ux[i] = s.ux[j]; d.uy[i] = s.uy[j]; d.uz[i] = s.uz[j]; d.w[i] = s.w[j];
+  };
+  for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+    const int n = min(min(cnt_src[slot], cap_src), cap_dst);
+    const long long so = (long long)slot * cap_src, dof = (long long)slot * cap_dst;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) copy(dst, dof + k, src, so + k);
+    for (int d = 0; d < NB3; ++d) {
+      const int nb = min(min(bcnt_src[(long long)slot * NB3 + d], bk_src.cap[d]), bk_dst.cap[d]);
+      const long long bs = (long long)slot * bk_src.stride + bk_src.off[d];
+      const long long bd = (long long)slot * bk_dst.stride + bk_dst.off[d];
+      for (int k = threadIdx.x; k < nb; k += blockDim.x) copy(bdst, bd + k, bsrc, bs + k);
+      if (threadIdx.x == 0) bcnt_dst[(long long)slot * NB3 + d] = nb;
+    }
+    if (threadIdx.x == 0) cnt_dst[slot] = n;
+  }
+}
+
 }  // namespace
 
 // ================================================================ host ====
@@ -1366,6 +1392,20 @@ struct Ctx3 {
   long long launches = 0, ps_launches = 0;
   int sticky = PIC_OK;
   std::string err;
+  // state at the entry of pic_step (auto_grow): replayed after an overflow
+  struct Backup {
+    void *F = nullptr;
+    double *rho_bg = nullptr;
+    void *seg[7] = {}, *bkt[7] = {};
+    int *cnt = nullptr, *bcnt = nullptr;
+    DevState *st = nullptr;
+    int cap = 0;
+    Buckets26 bk{};
+    long long step = 0;
+    double t = 0.0;
+    int nshift = 0, col0 = 0;
+  } bak;
+  int grows = 0;
 };
 
 // Device memory of a 3D context (the caller's allocator when configured).
@@ -2175,7 +2215,147 @@ pic_status diag3(Ctx3 *c, pic_diag_t *out) {
   c->launches += 5 + (cont ? 1 : 0);
   out->launches = c->launches;
   out->particle_step_launches = c->ps_launches;
+  out->grows = c->grows;
   return poll3(c);
+}
+
+// -------------------------------------- auto-grow replay and snapshots ----
+
+void free_backup3(Ctx3 *c) {
+  auto &b = c->bak;
+  cfree3(c, b.F);
+  cfree3(c, b.rho_bg);
+  for (int a = 0; a < 7; ++a) {
+    cfree3(c, b.seg[a]);
+    cfree3(c, b.bkt[a]);
+  }
+  cfree3(c, b.cnt);
+  cfree3(c, b.bcnt);
+  cfree3(c, b.st);
+  b = Ctx3::Backup{};
+}
+
+// Copy the live state (current particle set and its in-flight buckets, E,
+// B, Bm, background charge, device scalars) into the backup; particles are
+// copied patch by patch, only the slots each count covers.
+template <typename R>
+pic_status take_backup3(Ctx3 *c) {
+  auto &b = c->bak;
+  const Geom3 &g = c->g;
+  if (b.cap != c->cap) free_backup3(c);
+  if (!b.F) {
+    b.cap = c->cap;
+    b.bk = c->bk;
+    CK3(cmalloc3(c, &b.F, 9 * g.cs * sizeof(R)));
+    CK3(cmalloc3(c, &b.rho_bg, g.cs * sizeof(double)));
+    for (int a = 0; a < 7; ++a) {
+      CK3(cmalloc3(c, &b.seg[a], sizeof(R) * (size_t)g.nslots * b.cap));
+      CK3(cmalloc3(c, &b.bkt[a], sizeof(R) * (size_t)g.nslots * b.bk.stride));
+    }
+    CK3(cmalloc3(c, &b.cnt, sizeof(int) * g.nslots));
+    CK3(cmalloc3(c, &b.bcnt, sizeof(int) * (size_t)g.nslots * NB3));
+    CK3(cmalloc3(c, &b.st, sizeof(DevState)));
+  }
+  const int q = (int)(c->step & 1);
+  CK3(cudaMemcpyAsync(b.F, c->F, 9 * g.cs * sizeof(R), cudaMemcpyDeviceToDevice, c->stream));
+  CK3(cudaMemcpyAsync(b.rho_bg, c->rho_bg, g.cs * sizeof(double), cudaMemcpyDeviceToDevice,
+                      c->stream));
+  const int blocks = std::min(g.nslots, 65535);
+  k3_repack<R><<<blocks, 256, 0, c->stream>>>(g.nslots, soa7<R>(c->seg[q]), c->cnt[q], c->cap,
+                                              soa7<R>(c->bkt[1 - q]), c->bcnt[1 - q], c->bk,
+                                              soa7<R>(b.seg), b.cnt, b.cap, soa7<R>(b.bkt), b.bcnt,
+                                              b.bk);
+  CK3(cudaGetLastError());
+  CK3(cudaMemcpyAsync(b.st, c->st, sizeof(DevState), cudaMemcpyDeviceToDevice, c->stream));
+  b.step = c->step;
+  b.t = c->t;
+  b.nshift = c->nshift;
+  b.col0 = c->col0;
+  c->launches += 1;
+  return PIC_OK;
+}
+
+// Return to the backup with a patch capacity of new_cap (particle storage
+// reallocated, bucket layout recomputed, particles repacked); clears the
+// device fault.  The current sets restart at zero, as after a load.
+template <typename R>
+pic_status restore_backup3(Ctx3 *c, int new_cap) {
+  auto &b = c->bak;
+  const Geom3 &g = c->g;
+  CK3(cudaStreamSynchronize(c->stream));
+  if (new_cap != c->cap) {
+    free_graphs3(c);
+    free_particles3(c);
+    pic_status s = alloc3<R>(c, new_cap);
+    if (s) return s;
+  }
+  const int q = (int)(b.step & 1);
+  CK3(cudaMemcpyAsync(c->F, b.F, 9 * g.cs * sizeof(R), cudaMemcpyDeviceToDevice, c->stream));
+  CK3(cudaMemsetAsync((R *)c->F + C_JA * g.cs, 0, 6 * g.cs * sizeof(R), c->stream));
+  CK3(cudaMemcpyAsync(c->rho_bg, b.rho_bg, g.cs * sizeof(double), cudaMemcpyDeviceToDevice,
+                      c->stream));
+  CK3(cudaMemsetAsync(c->cnt[1 - q], 0, sizeof(int) * g.nslots, c->stream));
+  CK3(cudaMemsetAsync(c->bcnt[q], 0, sizeof(int) * (size_t)g.nslots * NB3, c->stream));
+  const int blocks = std::min(g.nslots, 65535);
+  k3_repack<R><<<blocks, 256, 0, c->stream>>>(g.nslots, soa7<R>(b.seg), b.cnt, b.cap,
+                                              soa7<R>(b.bkt), b.bcnt, b.bk, soa7<R>(c->seg[q]),
+                                              c->cnt[q], c->cap, soa7<R>(c->bkt[1 - q]),
+                                              c->bcnt[1 - q], c->bk);
+  CK3(cudaGetLastError());
+  DevState ds;
+  CK3(cudaMemcpyAsync(&ds, b.st, sizeof ds, cudaMemcpyDeviceToHost, c->stream));
+  CK3(cudaStreamSynchronize(c->stream));
+  ds.err = 0;
+  CK3(cudaMemcpy(c->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
+  c->step = b.step;
+  c->t = b.t;
+  c->nshift = b.nshift;
+  c->col0 = b.col0;
+  c->prev_valid = false;
+  c->active_valid = false;
+  c->sticky = PIC_OK;
+  c->launches += 1;
+  return PIC_OK;
+}
+
+// Advance nsteps; with auto_grow, an overflow of a patch or bucket capacity
+// grows the capacity and replays the steps from the state at entry.
+template <typename R>
+pic_status step3(Ctx3 *c, int nsteps) {
+  if (!c->cfg.auto_grow) return run3<R>(c, nsteps);
+  pic_status s = take_backup3<R>(c);
+  if (s) return s;
+  for (int attempt = 0;; ++attempt) {
+    s = run3<R>(c, nsteps);
+    if (s != PIC_EOVERFLOW || attempt >= 4) return s;
+    DevState h;
+    CK3(cudaMemcpy(&h, c->st, sizeof h, cudaMemcpyDeviceToHost));
+    const int seen = std::max(h.maxcnt[0], h.maxcnt[1]);
+    int cap = std::max((int)(1.5 * c->cap), (int)(1.25 * seen));
+    cap = (cap + 31) / 32 * 32;
+    s = restore_backup3<R>(c, cap);
+    if (s) return s;
+    c->grows += 1;
+    c->err.clear();
+  }
+}
+
+// Host snapshot: header, the 15 field components, the background charge,
+// both particle sets with their buckets and counts, the device scalars.
+struct Snap3Header {
+  char magic[8];
+  int n[3], p[3];
+  int fp32, cap, nshift, col0;
+  long long step;
+  double t;
+  int prev_valid, pad;
+  double wmax;
+};
+
+size_t snapshot_bytes3(const Ctx3 *c) {
+  const Geom3 &g = c->g;
+  return sizeof(Snap3Header) + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
+         sizeof(DevState) + (c->cap ? particle_bytes3(g, c->cap, c->rs) : 0);
 }
 
 }  // namespace
@@ -2284,6 +2464,7 @@ void c3_destroy(Ctx3 *c) {
   cfree3(c, c->plan_hist);
   cfree3(c, c->partials);
   cfree3(c, c->staging);
+  free_backup3(c);
   free_particles3(c);
   delete c;
 }
@@ -2392,7 +2573,7 @@ pic_status c3_step(Ctx3 *c, int nsteps) {
   pic_status s = usable3(c);
   if (s) return s;
   if (!c->cap) return fail3(c, PIC_ESTATE, "no particles loaded");
-  return c->fp32 ? run3<float>(c, nsteps) : run3<double>(c, nsteps);
+  return c->fp32 ? step3<float>(c, nsteps) : step3<double>(c, nsteps);
 }
 
 pic_status c3_get_particles(Ctx3 *c, double *out, size_t cap, size_t *n, int where) {
@@ -2412,6 +2593,102 @@ pic_status c3_sync(Ctx3 *c) {
   pic_status s = usable3(c);
   if (s) return s;
   return poll3(c);
+}
+
+pic_status c3_snapshot(Ctx3 *c, void *host, size_t *bytes) {
+  const size_t need = snapshot_bytes3(c);
+  if (!host) {
+    *bytes = need;
+    return PIC_OK;
+  }
+  if (*bytes < need) return fail3(c, PIC_EINVAL, "snapshot buffer too small");
+  CK3(cudaStreamSynchronize(c->stream));
+  const Geom3 &g = c->g;
+  char *p = (char *)host;
+  Snap3Header h{};
+  memcpy(h.magic, "PICSNAP3", 8);
+  for (int a = 0; a < 3; ++a) {
+    h.n[a] = g.n[a];
+    h.p[a] = g.p[a];
+  }
+  h.fp32 = c->fp32; h.cap = c->cap; h.nshift = c->nshift; h.col0 = c->col0;
+  h.step = c->step; h.t = c->t; h.prev_valid = c->prev_valid; h.wmax = c->wmax;
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  auto d2h = [&](const void *src, size_t n) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(p, src, n, cudaMemcpyDeviceToHost);
+    p += n;
+    return e;
+  };
+  CK3(d2h(c->F, (size_t)NCOMP * g.cs * c->rs));
+  CK3(d2h(c->rho_bg, sizeof(double) * g.cs));
+  if (c->cap) {
+    // both sets: the current one (segments q, buckets 1 - q) and the
+    // previous state's (segments 1 - q, buckets q), whose counts the next
+    // step's plan clears
+    for (int st = 0; st < 2; ++st) {
+      for (int a = 0; a < 7; ++a) CK3(d2h(c->seg[st][a], c->rs * (size_t)g.nslots * c->cap));
+      for (int a = 0; a < 7; ++a) CK3(d2h(c->bkt[st][a], c->rs * (size_t)g.nslots * c->bk.stride));
+      CK3(d2h(c->cnt[st], sizeof(int) * g.nslots));
+      CK3(d2h(c->bcnt[st], sizeof(int) * (size_t)g.nslots * NB3));
+    }
+  }
+  CK3(d2h(c->st, sizeof(DevState)));
+  *bytes = need;
+  return PIC_OK;
+}
+
+pic_status c3_restore(Ctx3 *c, const void *host, size_t bytes) {
+  Snap3Header h;
+  if (bytes < sizeof h) return fail3(c, PIC_EINVAL, "snapshot too small");
+  memcpy(&h, host, sizeof h);
+  const Geom3 &g = c->g;
+  bool same = !memcmp(h.magic, "PICSNAP3", 8) && h.fp32 == (int)c->fp32;
+  for (int a = 0; a < 3; ++a) same = same && h.n[a] == g.n[a] && h.p[a] == g.p[a];
+  if (!same) return fail3(c, PIC_EINVAL, "snapshot does not match this configuration");
+  if (h.cap < 0 || (h.cap % 32)) return fail3(c, PIC_EINVAL, "snapshot capacity is invalid");
+  CK3(cudaStreamSynchronize(c->stream));
+  if (h.cap != c->cap) {
+    if (c->cap) return fail3(c, PIC_EINVAL, "snapshot capacity differs from this context's");
+    free_graphs3(c);
+    if (h.cap) {
+      const pic_status s = c->fp32 ? alloc3<float>(c, h.cap) : alloc3<double>(c, h.cap);
+      if (s) return s;
+    }
+  }
+  const size_t need = snapshot_bytes3(c);
+  if (bytes < need) return fail3(c, PIC_EINVAL, "snapshot truncated");
+  if (h.wmax != c->wmax) free_graphs3(c);  // the current scale is baked into captured steps
+  c->wmax = h.wmax;
+  const char *p = (const char *)host + sizeof h;
+  auto h2d = [&](void *dst, size_t n) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);
+    p += n;
+    return e;
+  };
+  CK3(h2d(c->F, (size_t)NCOMP * g.cs * c->rs));
+  CK3(h2d(c->rho_bg, sizeof(double) * g.cs));
+  if (h.cap) {
+    for (int st = 0; st < 2; ++st) {
+      for (int a = 0; a < 7; ++a) CK3(h2d(c->seg[st][a], c->rs * (size_t)g.nslots * c->cap));
+      for (int a = 0; a < 7; ++a) CK3(h2d(c->bkt[st][a], c->rs * (size_t)g.nslots * c->bk.stride));
+      CK3(h2d(c->cnt[st], sizeof(int) * g.nslots));
+      CK3(h2d(c->bcnt[st], sizeof(int) * (size_t)g.nslots * NB3));
+    }
+  }
+  DevState ds;
+  memcpy(&ds, p, sizeof ds);
+  ds.err = 0;
+  CK3(cudaMemcpy(c->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
+  c->step = h.step;
+  c->t = h.t;
+  c->nshift = h.nshift;
+  c->col0 = h.col0;
+  c->prev_valid = h.prev_valid != 0;
+  c->active_valid = false;
+  c->sticky = PIC_OK;
+  c->err.clear();
+  return PIC_OK;
 }
 
 }  // namespace pic

@@ -29,6 +29,10 @@ pic_status c3_step(Ctx3 *c, int nsteps);
 pic_status c3_get_particles(Ctx3 *c, double *out, size_t cap, size_t *n, int where);
 pic_status c3_diag(Ctx3 *c, pic_diag_t *out);
 pic_status c3_sync(Ctx3 *c);
+// Host snapshot of the whole 3D state (host == nullptr: *bytes = size) and
+// its restore into a context of the same geometry and precision.
+pic_status c3_snapshot(Ctx3 *c, void *host, size_t *bytes);
+pic_status c3_restore(Ctx3 *c, const void *host, size_t bytes);
 const char *c3_error(const Ctx3 *c);
 
 }  // namespace pic

@@ -241,9 +241,13 @@ def test_error_paths_3d():
     two_d = W.small_random_particles3(run, 10, seed=2)
     rc = pic.lib().pic_load_particles(g.h, *[two_d[k].ctypes.data for k in pic.KEYS2], 10, pic.PIC_HOST)
     assert rc == pic.PIC_EINVAL
-    with pytest.raises(pic.PicError):
-        g.pic_snapshot()
+    with pytest.raises(pic.PicError) as e:
+        g.pic_restore(b"PICSNAP2" + bytes(256))  # a 2D snapshot's header
+    assert e.value.status == pic.PIC_EINVAL
     nan = W.small_random_particles3(run, 100, seed=3)
+    good = pic.Pic(pic.config_from_run(run, "fp64"))
+    good.pic_load_particles(nan)
+    blob = good.pic_snapshot()
     nan["uy"][5] = np.nan
     g.pic_load_particles(nan)
     with pytest.raises(pic.PicError) as e:
@@ -252,6 +256,13 @@ def test_error_paths_3d():
     with pytest.raises(pic.PicError) as e:
         g.pic_step(1)
     assert e.value.status == pic.PIC_ESTATE
+    # a restore clears the fault: the context steps again
+    g.pic_restore(blob)
+    g.pic_step(2)
+    assert g.pic_diag()["np"] == 100
+    with pytest.raises(pic.PicError) as e:
+        g.pic_restore(blob[:-8])
+    assert e.value.status == pic.PIC_EINVAL
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -318,3 +329,90 @@ def test_plasma_autotuner_3d_choice_is_valid_cached_and_exact():
     assert da["np"] == db["np"] and da["shifts"] == db["shifts"] >= 2
     for k in EB:
         assert rel(b.pic_get_field(k), a.pic_get_field(k)) <= 1e-9, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_snapshot_round_trip_is_bytewise_3d(prec):
+    """A snapshot restored into a fresh context (particle storage allocated
+    from the snapshot's capacity) and snapshotted again gives the same
+    bytes: fields, background charge, both particle sets, counts, scalars."""
+    run = _open3()
+    parts = W.small_random_particles3(run, 20000, seed=21, uth=0.4)
+    g = pic.Pic(pic.config_from_run(run, prec))
+    g.pic_load_particles(parts)
+    g.pic_step(3)
+    blob = g.pic_snapshot()
+    g2 = pic.Pic(pic.config_from_run(run, prec))
+    g2.pic_restore(blob)
+    assert g2.pic_snapshot() == blob
+    d, d2 = g.pic_diag(), g2.pic_diag()
+    for k in ("step", "np", "capacity", "U_E", "U_B", "U_K", "charge"):
+        assert d2[k] == d[k], k
+
+
+def test_snapshot_restore_resume_3d_moving_window():
+    """A 3D snapshot taken after window shifts and restored into a fresh
+    context resumes the run: the resumed state equals the oracle's
+    uninterrupted run; restoring into the original context, which has
+    stepped past the snapshot, rewinds it to the same result."""
+    run = W.lwfa_3d(n=(64, 32, 16), d=(0.125, 0.5, 0.5), patch=(16, 8, 8), ppc=(2, 1, 1),
+                    n0=0.01, ramp=3.0, a0=1.0, waist=4.0, tau=3.0, t_mw=0.5)
+    run["laser"]["t_peak"] = 4.0
+    o, g = pair3(run, fill=True)
+    n1 = math.ceil(16 * 0.125 / run["dt"]) + 5
+    n2 = math.ceil(16 * 0.125 / run["dt"]) + 3
+    for _ in range(n1):
+        o.step(1)
+        g.pic_step(1)
+    assert g.pic_diag()["shifts"] >= 1
+    blob = g.pic_snapshot()
+    g.pic_step(4)
+    g2 = pic.Pic(pic.config_from_run(run, "fp64"))
+    g2.pic_restore(blob)
+    assert g2.pic_diag()["step"] == n1
+    for _ in range(n2):
+        o.step(1)
+        g2.pic_step(1)
+    do, d2 = o.diag(), g2.pic_diag()
+    assert d2["shifts"] == do["shifts"] >= 2 and d2["np"] == do["np"]
+    _assert(field_errs(o, g2, EB), 1e-12)
+    _assert(particle_errs(o, g2), 1e-12)
+    g.pic_restore(blob)
+    g.pic_step(n2)
+    _assert(field_errs(o, g, EB), 1e-12)
+    _assert(particle_errs(o, g), 1e-12)
+
+
+def test_auto_grow_replays_overflowing_steps_3d():
+    """Converging flows pile particles into the central patches; with a
+    patch capacity sized exactly to the initial load, pic_step grows the
+    capacity (and the 26 direction buckets with it) and replays from the
+    state at entry: results equal a run that never overflowed."""
+    run = W.periodic_run3((32, 32, 32), (0.1, 0.1, 0.1), (8, 8, 8))
+    rng = np.random.default_rng(7)
+    n = 40000
+    pos = {k: rng.uniform(0, 3.2, n) for k in ("x", "y", "z")}
+    parts = {**pos, "ux": -2.0 * np.sign(pos["x"] - 1.6), "uy": -2.0 * np.sign(pos["y"] - 1.6),
+             "uz": -2.0 * np.sign(pos["z"] - 1.6), "w": np.full(n, 0.01)}
+    small = pic.Pic(pic.config_from_run(run, "fp64", capacity_factor=1.0, capacity_min=32))
+    big = pic.Pic(pic.config_from_run(run, "fp64", capacity_factor=8.0))
+    for g in (small, big):
+        g.pic_load_particles(parts)
+    cap0 = small.pic_diag()["capacity"]
+    small.pic_step(20)
+    big.pic_step(20)
+    d = small.pic_diag()
+    assert d["grows"] >= 1 and d["capacity"] > cap0
+    assert d["max_patch_count"] > cap0
+    for k in ("Ex", "Ey", "Ez", "Jx", "Jy", "Jz", "Bx"):
+        a, b = small.pic_get_field(k), big.pic_get_field(k)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), k
+    assert small.pic_diag()["np"] == big.pic_diag()["np"] == n
+    _assert(particle_errs_between(small, big), 1e-12)
+
+
+def particle_errs_between(g, h):
+    a, b = g.pic_get_particles(), h.pic_get_particles()
+    assert a["x"].size == b["x"].size
+    b = match_particles3(a, b)
+    return {k: rel(a[k], b[k]) for k in KEYS}
