@@ -170,6 +170,18 @@ def _summary_matches(text):
     return source_digest(re.findall(r"`([^`]+)`", m.group(2))).startswith(m.group(1))
 
 
+def moved_bytes(r, hbm):
+    """The roofline against the bytes the particle step had to move: the
+    algorithmic bytes less those of the particles in skipped calm slots
+    (11 s each: nothing read or written), over the same launch time."""
+    calm = r.get("calm_per_step", 0.0)
+    b = r["kernel_bytes"] - calm * 11 * r["rs"]
+    ach = b / (r["particle_step_ms"] * 1e-3) / 1e9
+    return {"bytes_per_launch": b, "calm_particles_per_launch": calm,
+            "calm_share": calm / r["np"] if r["np"] else 0.0,
+            "achieved": ach, "frac": ach / hbm}
+
+
 def profiled_traffic(name):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     from the committed ncu summary profiles/<name>, if the kernel sources
@@ -304,6 +316,9 @@ def run_gpu(prec, steps, warmup, spinup, device, rank, world, dist, cf=2.0, merg
         "capacity": d1["capacity"], "grows_in_timed_region": d1["grows"] - d0["grows"],
         "clocks": clk.summary(),
         "energy": {"U_E": d1["U_E"], "U_B": d1["U_B"], "U_K": d1["U_K"]},
+        # particle-steps of the timed steps that the calm-slot skip did no
+        # work for (particles at rest in zero fields whose copy was kept)
+        "calm_per_step": (d1["calm_particle_steps"] - d0["calm_particle_steps"]) / steps,
     }
 
 
@@ -858,6 +873,7 @@ def main():
                                        "(profiles/particle_step_fp32_lwfa2048.md); null when "
                                        "the kernel sources changed since",
                      "bytes_per_launch": r32["kernel_bytes"], "launch_ms": r32["particle_step_ms"],
+                     "moved": moved_bytes(r32, hbm),
                      "whole_step": {"achieved": step_gbs, "frac": step_gbs / hbm,
                                     "bytes_per_step": r32["step_bytes"]},
                      "issue": issue_roofline(r32["particle_step_ms"]),

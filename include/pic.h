@@ -232,6 +232,9 @@ typedef struct pic_diag_t {
   int grows;              /* capacity growths done by auto_grow */
   long long sorts;        /* cell-order sorts done */
   double ms_sort;         /* timer of the sorts (timing = 1) */
+  long long calm_particle_steps; /* particle-steps skipped so far: particles
+                             at rest in zero fields, in patches whose copy
+                             the step kept (2D; 0 in 3D) */
 } pic_diag_t;
 
 typedef struct pic_ctx pic_ctx;

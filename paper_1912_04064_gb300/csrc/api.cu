@@ -1256,6 +1256,7 @@ pic_status do_diag(pic_ctx *ctx, pic_diag_t *out) {
   out->max_patch_count = hs.maxcnt[(ctx->step + 1) & 1];
   out->capacity = ctx->cap;
   out->grows = ctx->grows;
+  out->calm_particle_steps = (long long)hs.calm_particles;
   out->sorts = ctx->sorts;
   out->ms_particles = ctx->ms_particles;
   out->ms_fields = ctx->ms_fields;

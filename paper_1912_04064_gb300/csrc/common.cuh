@@ -65,6 +65,9 @@ struct DevState {
   unsigned err;
   int maxcnt[2];  // fullest patch written by the particle step of parity p
   double laser_h; // laser temporal factor at t_{n+3/2}, set by the E update
+  // particles carried over in calm slots that a step skipped, summed over
+  // all steps (each such particle is one particle-step with no work)
+  unsigned long long calm_particles;
 };
 
 struct Geom {

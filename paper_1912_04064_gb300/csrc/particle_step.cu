@@ -526,7 +526,10 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? (MERGE ? 2 : (JF ? 3 : 
     const bool arrivals = (s_cnt[1] | s_cnt[2] | s_cnt[3] | s_cnt[4] | s_cnt[5] | s_cnt[6] |
                            s_cnt[7] | s_cnt[8]) != 0;
     const bool skip = quiet && !arrivals && s_calm;
-    if (skip && tid == 0 && ufirst == 0) a.cnt_out[s] = s_cnt[0];
+    if (skip && tid == 0 && ufirst == 0) {
+      a.cnt_out[s] = s_cnt[0];
+      atomicAdd(&a.st->calm_particles, (unsigned long long)s_cnt[0]);
+    }
     bool moving = false;  // a particle of this item had u != 0
     float st_wu2 = 0.0f, st_w = 0.0f;  // this thread's largest (w |u|)^2, w
     // this item's tile scale, formed once by thread 0

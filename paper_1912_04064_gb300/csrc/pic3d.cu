@@ -2216,6 +2216,7 @@ pic_status diag3(Ctx3 *c, pic_diag_t *out) {
   out->launches = c->launches;
   out->particle_step_launches = c->ps_launches;
   out->grows = c->grows;
+  out->calm_particle_steps = 0;  // the 3D step has no calm-slot skip
   return poll3(c);
 }
 

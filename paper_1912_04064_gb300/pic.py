@@ -85,6 +85,7 @@ class pic_diag_t(C.Structure):
         ("ms_particles", C.c_double), ("ms_fields", C.c_double), ("ms_window", C.c_double),
         ("launches", C.c_longlong), ("particle_step_launches", C.c_longlong),
         ("grows", C.c_int), ("sorts", C.c_longlong), ("ms_sort", C.c_double),
+        ("calm_particle_steps", C.c_longlong),
     ]
 
     def as_dict(self):
