@@ -259,11 +259,14 @@ __global__ void k_window_migrate(const Geom g, int col0, SoA<R> seg, int *cnt, S
 
 // Plasma at rest, regularly placed (ppcx x ppcy per cell), weight =
 // density / ppc at the particle's x in the laboratory frame, with the
-// co-located immobile ions added to the background charge.  Block (py, c)
-// fills physical patch column phys0 + c, held by slot column
-// (slot_col0 + c) mod npx.  Moving window, part 2: after the ring advanced,
-// the leaving slots (slot_col0 = old col0) hold the new column
-// (phys0 = npx - 1); loading a run's initial plasma fills every column.
+// co-located immobile ions added to the background charge.  Blocks (py, c,
+// *) fill physical patch column phys0 + c, held by slot column
+// (slot_col0 + c) mod npx; the z index splits a patch's particles among
+// gridDim.z blocks (each particle's slot index k is fixed by its cell and
+// sub-cell, whichever block writes it).  Moving window, part 2: after the
+// ring advanced, the leaving slots (slot_col0 = old col0) hold the new
+// column (phys0 = npx - 1); loading a run's initial plasma fills every
+// column.
 template <typename R>
 __global__ void k_window_inject(const Geom g, int slot_col0, int phys0, int nshift, SoA<R> seg,
                                 int *cnt, int cap, double n0, double x0, double ramp, int ppcx,
@@ -274,12 +277,12 @@ __global__ void k_window_inject(const Geom g, int slot_col0, int phys0, int nshi
   const int ppc = ppcx * ppcy;
   const int total = g.P * g.Q * ppc;
   if (total > cap) {
-    if (threadIdx.x == 0) atomicOr(err, ERR_OVERFLOW_SEG);
+    if (threadIdx.x == 0 && blockIdx.z == 0) atomicOr(err, ERR_OVERFLOW_SEG);
     return;
   }
   const int X0 = (phys0 + (int)blockIdx.y) * g.P, Y0 = py * g.Q;
   const double shift = __dmul_rn((double)nshift * g.P, g.dx);
-  for (int k = threadIdx.x; k < total; k += blockDim.x) {
+  for (int k = blockIdx.z * blockDim.x + threadIdx.x; k < total; k += gridDim.z * blockDim.x) {
     // order: cell row, cell column, sub-row, sub-column
     const int a = k % ppcx, b = (k / ppcx) % ppcy, cell = k / ppc;
     const int ci = cell % g.P, cj = cell / g.P;
@@ -304,7 +307,13 @@ __global__ void k_window_inject(const Geom g, int slot_col0, int phys0, int nshi
     seg.w[o] = R(w);
     if (rho_bg) deposit_node(g, rho_bg, X0, Y0, (double)ci + fx, (double)cj + fy, -g.q * (double)R(w));
   }
-  if (threadIdx.x == 0) cnt[slot] = total;
+  if (threadIdx.x == 0 && blockIdx.z == 0) cnt[slot] = total;
+}
+
+// Blocks per patch of the plasma fill: one per 256 particles, at most 16.
+inline unsigned inject_split(const Geom &g, int ppcx, int ppcy) {
+  const int blocks = (g.P * g.Q * ppcx * ppcy + 255) / 256;
+  return (unsigned)(blocks < 1 ? 1 : (blocks > 16 ? 16 : blocks));
 }
 
 template <typename R>
@@ -562,8 +571,8 @@ cudaError_t launch_window_particles(const Geom &g, int old_col0, int nshift, SoA
                                     double n0, double x0, double ramp, int ppcx, int ppcy,
                                     double *rho_bg, unsigned *err, cudaStream_t s) {
   k_window_migrate<R><<<g.npy, 256, 0, s>>>(g, old_col0, seg, cnt, bkt, bcnt, cap, bk, err);
-  k_window_inject<R><<<g.npy, 256, 0, s>>>(g, old_col0, g.npx - 1, nshift, seg, cnt, cap, n0,
-                                            x0, ramp, ppcx, ppcy, rho_bg, err);
+  k_window_inject<R><<<dim3(g.npy, 1, inject_split(g, ppcx, ppcy)), 256, 0, s>>>(
+      g, old_col0, g.npx - 1, nshift, seg, cnt, cap, n0, x0, ramp, ppcx, ppcy, rho_bg, err);
   return cudaGetLastError();
 }
 
@@ -571,8 +580,8 @@ template <typename R>
 cudaError_t launch_fill_plasma(const Geom &g, int col0, int nshift, SoA<R> seg, int *cnt, int cap,
                                double n0, double x0, double ramp, int ppcx, int ppcy,
                                double *rho_bg, unsigned *err, cudaStream_t s) {
-  k_window_inject<R><<<dim3(g.npy, g.npx), 256, 0, s>>>(g, col0, 0, nshift, seg, cnt, cap, n0,
-                                                         x0, ramp, ppcx, ppcy, rho_bg, err);
+  k_window_inject<R><<<dim3(g.npy, g.npx, inject_split(g, ppcx, ppcy)), 256, 0, s>>>(
+      g, col0, 0, nshift, seg, cnt, cap, n0, x0, ramp, ppcx, ppcy, rho_bg, err);
   return cudaGetLastError();
 }
 
