@@ -533,6 +533,22 @@ __global__ void k_window_state(DevState *st, int col0, int nshift) {
   st->nshift = nshift;
 }
 
+// After a window shift only two slot columns hold changed particles: c0
+// (refilled with the new plasma column) and c1 (which received the
+// in-flight particles of the dropped column).  Their calm flags and scale
+// statistics (both parities) are reset; every other slot keeps its
+// particles, and the fields moved with the frame, so its flags stay valid.
+__global__ void k_calm_columns(unsigned char *calm0, unsigned char *calm1, unsigned *stat0,
+                               unsigned *stat1, int npx, int npy, int c0, int c1) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * npy) return;
+  const int slot = (t >> 1) * npx + ((t & 1) ? c1 : c0);
+  calm0[slot] = 0;
+  calm1[slot] = 0;
+  stat0[2 * slot] = stat0[2 * slot + 1] = 0x7f7f7f7fu;  // unknown: see ensure_calm
+  stat1[2 * slot] = stat1[2 * slot + 1] = 0x7f7f7f7fu;
+}
+
 template <typename R>
 pic_status window_shift(pic_ctx *ctx) {
   const Geom &g = ctx->g;
@@ -552,11 +568,15 @@ pic_status window_shift(pic_ctx *ctx) {
                                 ctx->cfg.inj_ppc[0], ctx->cfg.inj_ppc[1], ctx->rho_bg,
                                 &ctx->st->err, ctx->stream));
   k_window_state<<<1, 1, 0, ctx->stream>>>(ctx->st, ctx->col0, ctx->nshift);
-  CK(cudaGetLastError());
   ctx->launches += 7;
+  if (ctx->calm_ok) {
+    k_calm_columns<<<(2 * g.npy + 255) / 256, 256, 0, ctx->stream>>>(
+        ctx->calm[0], ctx->calm[1], ctx->stat[0], ctx->stat[1], g.npx, g.npy, old_col0, ctx->col0);
+    ctx->launches += 1;
+  }
+  CK(cudaGetLastError());
   ctx->prev_valid = false;
   ctx->plan_ready = false;  // particle counts changed
-  ctx->calm_ok = false;
   return PIC_OK;
 }
 
