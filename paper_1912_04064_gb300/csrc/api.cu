@@ -1955,10 +1955,15 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (memcmp(h.magic, "PICSNAP2", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
       h.fp32 != (int)ctx->fp32)
     return fail(ctx, PIC_EINVAL, "snapshot does not match this configuration");
+  if (h.cap < 0 || (h.cap % 32)) return fail(ctx, PIC_EINVAL, "snapshot capacity is invalid");
+  if (h.cap != ctx->cap && ctx->cap)
+    return fail(ctx, PIC_EINVAL, "snapshot capacity differs from this context's");
+  const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
+                      (h.cap ? particle_bytes(g, h.cap, ctx->rs) : 0);
+  if (bytes < need) return fail(ctx, PIC_EINVAL, "snapshot truncated");
   CK(cudaSetDevice(ctx->cfg.device));
   CK(cudaStreamSynchronize(ctx->stream));
-  if (h.cap != ctx->cap) {
-    if (ctx->cap) return fail(ctx, PIC_EINVAL, "snapshot capacity differs from this context's");
+  if (h.cap != ctx->cap) {  // a context without particle storage takes the snapshot's
     free_graphs(ctx);
     if (h.cap) {
       const pic_status s = ctx->fp32 ? alloc_particles<float>(ctx, h.cap) : alloc_particles<double>(ctx, h.cap);
@@ -1969,9 +1974,6 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (h.wmax != ctx->wmax) free_graphs(ctx);  // the current scales are baked into the graphs
   ctx->wmax = h.wmax;
   ctx->bk = bucket_layout(h.cap);
-  const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
-                      (h.cap ? particle_bytes(g, h.cap, ctx->rs) : 0);
-  if (bytes < need) return fail(ctx, PIC_EINVAL, "snapshot truncated");
   const char *p = (const char *)host + sizeof h;
   auto h2d = [&](void *dst, size_t n) -> cudaError_t {
     cudaError_t e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);

@@ -2648,17 +2648,19 @@ pic_status c3_restore(Ctx3 *c, const void *host, size_t bytes) {
   for (int a = 0; a < 3; ++a) same = same && h.n[a] == g.n[a] && h.p[a] == g.p[a];
   if (!same) return fail3(c, PIC_EINVAL, "snapshot does not match this configuration");
   if (h.cap < 0 || (h.cap % 32)) return fail3(c, PIC_EINVAL, "snapshot capacity is invalid");
+  if (h.cap != c->cap && c->cap)
+    return fail3(c, PIC_EINVAL, "snapshot capacity differs from this context's");
+  const size_t need = sizeof(Snap3Header) + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
+                      sizeof(DevState) + (h.cap ? particle_bytes3(g, h.cap, c->rs) : 0);
+  if (bytes < need) return fail3(c, PIC_EINVAL, "snapshot truncated");
   CK3(cudaStreamSynchronize(c->stream));
-  if (h.cap != c->cap) {
-    if (c->cap) return fail3(c, PIC_EINVAL, "snapshot capacity differs from this context's");
+  if (h.cap != c->cap) {  // a context without particle storage takes the snapshot's
     free_graphs3(c);
     if (h.cap) {
       const pic_status s = c->fp32 ? alloc3<float>(c, h.cap) : alloc3<double>(c, h.cap);
       if (s) return s;
     }
   }
-  const size_t need = snapshot_bytes3(c);
-  if (bytes < need) return fail3(c, PIC_EINVAL, "snapshot truncated");
   if (h.wmax != c->wmax) free_graphs3(c);  // the current scale is baked into captured steps
   c->wmax = h.wmax;
   const char *p = (const char *)host + sizeof h;

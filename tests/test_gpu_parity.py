@@ -367,6 +367,10 @@ def test_snapshot_restore_resume():
     g.pic_step(5)
     ref = {k: g.pic_get_field(k) for k in ("Ex", "Ez", "Bz")}
     g2 = pic.Pic(pic.config_from_run(run, "fp64"))
+    # a truncated snapshot is refused before anything of the context changes
+    with pytest.raises(pic.PicError) as e:
+        g2.pic_restore(blob[:-8])
+    assert e.value.status == pic.PIC_EINVAL
     g2.pic_restore(blob)
     g2.pic_step(5)
     for k, v in ref.items():
