@@ -466,7 +466,9 @@ void pic_autotune_clear_cache(void);
  * a slot and memory are free.  Times are seconds on the server's clock
  * (pic_server_clock).  FP32 and FP64 requests, deterministic or not, may be
  * mixed: the server keeps one batch per precision and mode and steps each
- * in every tick.  Not thread-safe: one host thread drives a server.
+ * in every tick.  3D requests are admitted the same way and stepped one by
+ * one in every tick, after the batches (there are no batched 3D kernels).
+ * Not thread-safe: one host thread drives a server.
  * (Serving has no counterpart in the paper; each served run is the step of
  * pic_step.) */
 typedef struct pic_server pic_server;
@@ -502,7 +504,8 @@ typedef struct pic_server_stats {
 
 pic_status pic_server_create(const pic_server_config *cfg, pic_server **out);
 /* Queue a request (cfg is copied; plasma from cfg's inj_* fields, which
- * must give at least one particle per cell); *id receives its handle.
+ * must give at least one particle per cell; dims 2 or 3); *id receives its
+ * handle.
  * keep = 1: the finished context is kept for pic_server_take.  The
  * configuration is validated here (PIC_EINVAL). */
 pic_status pic_server_submit(pic_server *s, const pic_config *cfg, long long nsteps, int keep,

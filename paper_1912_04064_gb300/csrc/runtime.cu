@@ -323,7 +323,13 @@ double server_now(const pic_server *s) { return now_ms() * 1e-3 - s->t0; }
 
 // The batch a run belongs to (runs of one batch share precision and the
 // deterministic setting).
-int batch_of(const pic_config &c) { return (c.prec == PIC_FP32 ? 1 : 0) + (c.deterministic ? 2 : 0); }
+// The batch a request's run joins: one per precision and mode for 2D runs;
+// 3D runs (kSolo3) join none and are stepped one by one in each tick.
+constexpr int kSolo3 = 4;
+int batch_of(const pic_config &c) {
+  if (c.dims == 3) return kSolo3;
+  return (c.prec == PIC_FP32 ? 1 : 0) + (c.deterministic ? 2 : 0);
+}
 
 // Point each batch at the current running runs of its kind.
 pic_status sync_batches(pic_server *s) {
@@ -401,13 +407,15 @@ pic_status pic_server_create(const pic_server_config *cfg, pic_server **out) {
 pic_status pic_server_submit(pic_server *s, const pic_config *cfg, long long nsteps, int keep,
                              long long *id) {
   if (!s || !cfg || !id || nsteps <= 0) return PIC_EINVAL;
-  if (cfg->dims != 2) return PIC_EINVAL;  // batches hold 2D runs
-  if (cfg->inj_ppc[0] < 1 || cfg->inj_ppc[1] < 1) return PIC_EINVAL;
+  if (cfg->dims != 2 && cfg->dims != 3) return PIC_EINVAL;
+  for (int a = 0; a < cfg->dims; ++a)
+    if (cfg->inj_ppc[a] < 1) return PIC_EINVAL;
   Request r;
   r.cfg = *cfg;
-  r.cfg.stream = s->stream;  // one stream for every run and both batches
+  r.cfg.stream = s->stream;  // one stream for every run and every batch
   r.cfg.device = s->cfg.device;
-  const size_t np = (size_t)cfg->n[0] * cfg->n[1] * cfg->inj_ppc[0] * cfg->inj_ppc[1];
+  size_t np = (size_t)cfg->n[0] * cfg->n[1] * cfg->inj_ppc[0] * cfg->inj_ppc[1];
+  if (cfg->dims == 3) np *= (size_t)cfg->n[2] * cfg->inj_ppc[2];
   r.footprint = pic_footprint(&r.cfg, np);
   if (!r.footprint) return PIC_EINVAL;
   r.np0 = (long long)np;
@@ -442,6 +450,12 @@ pic_status pic_server_tick(pic_server *s, int *running) {
     s->queue.pop_front();
     pic_status st = pic_create(&r.cfg, &r.ctx);
     if (st == PIC_OK) st = pic_load_plasma(r.ctx);
+    if (st == PIC_OK && r.cfg.dims == 3) {
+      // the 3D fill may leave part of the box empty (upper-half plasma)
+      pic_diag_t d{};
+      st = pic_diag(r.ctx, &d);
+      r.np0 = d.np;
+    }
     if (st != PIC_OK) {
       if (r.ctx) pic_destroy(r.ctx);
       r.ctx = nullptr;
@@ -473,6 +487,16 @@ pic_status pic_server_tick(pic_server *s, int *running) {
           r.status = st;
           bad.push_back(id);
         }
+      }
+    }
+    // 3D runs: k steps each on the same stream (no batched 3D kernels)
+    for (long long id : s->running) {
+      Request &r = s->reqs[id];
+      if (batch_of(r.cfg) != kSolo3) continue;
+      const pic_status st = pic_step(r.ctx, (int)k);
+      if (st != PIC_OK) {
+        r.status = st;
+        bad.push_back(id);
       }
     }
     s->batched_steps += k;

@@ -274,3 +274,44 @@ def test_autotuner_choice_is_valid_cached_and_exact():
     wt, winfo = pic.pic_autotune(pic.config_from_run(wrun, "fp32"), wparts, steps=3)
     assert winfo["patch"][0] in (8, 16) and 16 % winfo["patch"][0] == 0
     assert wt.window_cells in (0, 16) and (wt.window_cells or wt.patch[0]) == 16
+
+
+def test_3d_request_served_beside_2d_runs():
+    """A 3D request shares a server with a 2D one.  There are no batched 3D
+    kernels: the server admits it by its footprint like any request and
+    steps it on its own in every tick, after the 2D batches.  Its result
+    (with a window shift inside the run) equals the same run stepped alone,
+    and its particle count is the device fill's (upper-half plasma)."""
+    run3 = W.lwfa_3d(n=(64, 32, 16), d=(0.125, 0.5, 0.5), patch=(16, 8, 8), ppc=(2, 1, 1),
+                     n0=0.01, ramp=3.0, a0=1.0, waist=4.0, tau=3.0, t_mw=0.5)
+    run3["laser"]["t_peak"] = 4.0
+    run2 = _lwfa()
+    srv = pic.Server(max_runs=3, steps_per_tick=8)
+    cfg3, cfg2 = pic.config_from_run(run3, "fp64"), pic.config_from_run(run2, "fp64")
+    i3 = srv.pic_server_submit(cfg3, 30, keep=True)
+    i2 = srv.pic_server_submit(cfg2, 20, keep=True)
+    for _ in range(100):
+        srv.pic_server_tick()
+        st = srv.pic_server_get_stats()
+        if st["done"] + st["failed"] == 2:
+            break
+    assert st["done"] == 2 and st["failed"] == 0, st
+    info3 = srv.pic_server_info(i3)
+    assert info3["state"] == pic.PIC_REQ_DONE and info3["steps_done"] == 30
+    assert info3["np0"] == 64 * 16 * 16 * 2
+    for rid, cfg, run, nsteps, names in ((i3, cfg3, run3, 30, EB), (i2, cfg2, run2, 20, EB)):
+        served = srv.pic_server_take(rid, cfg)
+        alone = pic.Pic(pic.config_from_run(run, "fp64"))
+        alone.pic_load_plasma()
+        alone.pic_step(nsteps)
+        ds, da = served.pic_diag(), alone.pic_diag()
+        assert ds["step"] == da["step"] == nsteps and ds["np"] == da["np"]
+        assert ds["shifts"] == da["shifts"]
+        for k in names:
+            a, b = served.pic_get_field(k), alone.pic_get_field(k)
+            rel = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+            assert rel <= 1e-12, (rid, k, rel)
+        served.close()
+        alone.close()
+    assert srv.pic_server_info(i3)["state"] == pic.PIC_REQ_DONE
+    srv.close()
