@@ -15,6 +15,7 @@
 #include "alloc.h"
 #include "common.cuh"
 #include "noalloc.h"
+#include "pack.h"
 #include "pic3d.h"
 #include "poisson.h"
 
@@ -1299,13 +1300,6 @@ struct SnapHeader {
   double wmax;
 };
 
-size_t snapshot_bytes(const pic_ctx *c) {
-  const Geom &g = c->g;
-  size_t b = sizeof(SnapHeader) + field_bytes(g, c->rs) + sizeof(double) * g.cs + sizeof(DevState);
-  if (c->cap) b += particle_bytes(g, c->cap, c->rs);
-  return b;
-}
-
 // ================================================================ batches
 //
 // A batch advances several independent contexts with one launch per kernel
@@ -1894,26 +1888,70 @@ pic_status pic_sync(pic_ctx *ctx) {
   return poll_device(ctx);
 }
 
+// Snapshot layout (2D): SnapHeader, the 15 field components, the
+// background charge, the device scalars, then for each particle set st = 0, 1
+// (segments seg[st] with buckets bkt[st]): its segment counts (nslots ints),
+// its bucket counts (8 nslots ints) and its live particles packed into six
+// arrays (pack.h), slot by slot, segment then buckets.  Capacity slack is
+// not stored.  Set q = step % 2 holds the current particles in its segments
+// and the previous state's arrivals in its buckets; set 1 - q the previous
+// state's particles and the current in-flight buckets; each is saved with
+// the counts that describe it (the previous state's were kept aside).
+
+// Offsets of one set's packed arrays from its counts; returns the total.
+long long pack_offsets(const Geom &g, int cap, const Buckets &bk, const int *cnt, const int *bcnt,
+                       std::vector<long long> &off) {
+  off.assign((size_t)g.nslots * 9 + 1, 0);
+  long long o = 0;
+  for (int s = 0; s < g.nslots; ++s) {
+    off[9 * (size_t)s] = o;
+    o += std::min(std::max(cnt[s], 0), cap);
+    for (int d = 0; d < 8; ++d) {
+      off[9 * (size_t)s + 1 + d] = o;
+      o += std::min(std::max(bcnt[(size_t)s * 8 + d], 0), bk.cap[d]);
+    }
+  }
+  off.back() = o;
+  return o;
+}
+
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   pic_status s = check_usable(ctx);
   if (s) return s;
   if (!bytes) return fail(ctx, PIC_EINVAL, "null size");
-  if (ctx->c3) {
-    CK(cudaSetDevice(ctx->cfg.device));
-    return c3_snapshot(ctx->c3, host, bytes);
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->c3) return c3_snapshot(ctx->c3, host, bytes);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const Geom &g = ctx->g;
+  const int q = (int)(ctx->step & 1);
+  // the counts that describe each set
+  std::vector<int> cnt[2], bcnt[2];
+  std::vector<long long> off[2];
+  long long total[2] = {0, 0};
+  if (ctx->cap) {
+    for (int st = 0; st < 2; ++st) {
+      cnt[st].resize(g.nslots);
+      bcnt[st].resize((size_t)g.nslots * 8);
+      CK(cudaMemcpy(cnt[st].data(), st == q ? ctx->cnt[st] : ctx->cnt_prev,
+                    sizeof(int) * g.nslots, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(bcnt[st].data(), st == q ? ctx->bcnt_prev : ctx->bcnt[st],
+                    sizeof(int) * g.nslots * 8, cudaMemcpyDeviceToHost));
+      total[st] = pack_offsets(g, ctx->cap, ctx->bk, cnt[st].data(), bcnt[st].data(), off[st]);
+    }
   }
-  const size_t need = snapshot_bytes(ctx);
+  size_t need = sizeof(SnapHeader) + field_bytes(g, ctx->rs) + sizeof(double) * g.cs +
+                sizeof(DevState);
+  if (ctx->cap)
+    for (int st = 0; st < 2; ++st)
+      need += sizeof(int) * (size_t)g.nslots * 9 + 6 * ctx->rs * (size_t)total[st];
   if (!host) {
     *bytes = need;
     return PIC_OK;
   }
   if (*bytes < need) return fail(ctx, PIC_EINVAL, "snapshot buffer too small");
-  CK(cudaSetDevice(ctx->cfg.device));
-  CK(cudaStreamSynchronize(ctx->stream));
-  const Geom &g = ctx->g;
   char *p = (char *)host;
   SnapHeader h{};
-  memcpy(h.magic, "PICSNAP2", 8);
+  memcpy(h.magic, "PICSNAP4", 8);
   h.nx = g.nx; h.ny = g.ny; h.P = g.P; h.Q = g.Q; h.fp32 = ctx->fp32;
   h.cap = ctx->cap; h.nshift = ctx->nshift; h.col0 = ctx->col0;
   h.step = ctx->step; h.t = ctx->t; h.prev_valid = ctx->prev_valid; h.wmax = ctx->wmax;
@@ -1926,18 +1964,42 @@ pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes) {
   };
   CK(d2h(ctx->F, field_bytes(g, ctx->rs)));
   CK(d2h(ctx->rho_bg, sizeof(double) * g.cs));
-  if (ctx->cap) {
-    // the previous state's sets (segments 1 - q, buckets q) are saved with
-    // the counts kept aside for them
-    const int q = (int)(ctx->step & 1);
-    for (int st = 0; st < 2; ++st) {
-      for (int a = 0; a < 6; ++a) CK(d2h(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
-      for (int a = 0; a < 6; ++a) CK(d2h(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * ctx->bk.stride));
-      CK(d2h(st == q ? ctx->cnt[st] : ctx->cnt_prev, sizeof(int) * g.nslots));
-      CK(d2h(st == q ? ctx->bcnt_prev : ctx->bcnt[st], sizeof(int) * g.nslots * 8));
-    }
-  }
   CK(d2h(ctx->st, sizeof(DevState)));
+  if (ctx->cap) {
+    void *flat = nullptr;
+    const long long most = std::max(total[0], total[1]);
+    if (most > 0) CK(cmalloc(ctx, &flat, 6 * ctx->rs * (size_t)most));
+    pic_status rs = PIC_OK;
+    for (int st = 0; st < 2 && rs == PIC_OK; ++st) {
+      memcpy(p, cnt[st].data(), sizeof(int) * g.nslots);
+      p += sizeof(int) * g.nslots;
+      memcpy(p, bcnt[st].data(), sizeof(int) * g.nslots * 8);
+      p += sizeof(int) * g.nslots * 8;
+      if (total[st] == 0) continue;
+      cudaError_t e = cudaMemcpyAsync(ctx->offsets, off[st].data(), sizeof(long long) * off[st].size(),
+                                      cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess)
+        e = ctx->fp32 ? launch_pack<float>(g, soa<float>(ctx->seg[st]),
+                                           st == q ? ctx->cnt[st] : ctx->cnt_prev, ctx->cap,
+                                           soa<float>(ctx->bkt[st]),
+                                           st == q ? ctx->bcnt_prev : ctx->bcnt[st], ctx->bk,
+                                           ctx->offsets, (float *)flat, total[st], ctx->stream)
+                      : launch_pack<double>(g, soa<double>(ctx->seg[st]),
+                                            st == q ? ctx->cnt[st] : ctx->cnt_prev, ctx->cap,
+                                            soa<double>(ctx->bkt[st]),
+                                            st == q ? ctx->bcnt_prev : ctx->bcnt[st], ctx->bk,
+                                            ctx->offsets, (double *)flat, total[st], ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e == cudaSuccess) e = d2h(flat, 6 * ctx->rs * (size_t)total[st]);
+      if (e != cudaSuccess) rs = fail(ctx, PIC_ECUDA, std::string("snapshot: ") + cudaGetErrorString(e));
+      ctx->launches += 1;
+    }
+    if (flat) {
+      cudaStreamSynchronize(ctx->stream);
+      cfree(ctx, flat);
+    }
+    if (rs) return rs;
+  }
   *bytes = need;
   return PIC_OK;
 }
@@ -1952,15 +2014,36 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   if (bytes < sizeof h) return fail(ctx, PIC_EINVAL, "snapshot too small");
   memcpy(&h, host, sizeof h);
   const Geom &g = ctx->g;
-  if (memcmp(h.magic, "PICSNAP2", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
+  if (memcmp(h.magic, "PICSNAP4", 8) || h.nx != g.nx || h.ny != g.ny || h.P != g.P || h.Q != g.Q ||
       h.fp32 != (int)ctx->fp32)
     return fail(ctx, PIC_EINVAL, "snapshot does not match this configuration");
   if (h.cap < 0 || (h.cap % 32)) return fail(ctx, PIC_EINVAL, "snapshot capacity is invalid");
   if (h.cap != ctx->cap && ctx->cap)
     return fail(ctx, PIC_EINVAL, "snapshot capacity differs from this context's");
-  const size_t need = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState) +
-                      (h.cap ? particle_bytes(g, h.cap, ctx->rs) : 0);
-  if (bytes < need) return fail(ctx, PIC_EINVAL, "snapshot truncated");
+  // walk the layout on the host first: sizes and counts are checked before
+  // anything of the context changes
+  const size_t head = sizeof h + field_bytes(g, ctx->rs) + sizeof(double) * g.cs + sizeof(DevState);
+  if (bytes < head) return fail(ctx, PIC_EINVAL, "snapshot truncated");
+  const Buckets bk = bucket_layout(h.cap);
+  const char *sets[2] = {nullptr, nullptr};
+  std::vector<long long> off[2];
+  long long total[2] = {0, 0};
+  size_t pos = head;
+  if (h.cap) {
+    for (int st = 0; st < 2; ++st) {
+      const size_t cb = sizeof(int) * (size_t)g.nslots * 9;
+      if (bytes < pos + cb) return fail(ctx, PIC_EINVAL, "snapshot truncated");
+      sets[st] = (const char *)host + pos;
+      const int *c = reinterpret_cast<const int *>(sets[st]);
+      for (size_t k = 0; k < (size_t)g.nslots * 9; ++k) {
+        const int lim = k < (size_t)g.nslots ? h.cap : bk.cap[(k - g.nslots) % 8];
+        if (c[k] < 0 || c[k] > lim) return fail(ctx, PIC_EINVAL, "snapshot counts are invalid");
+      }
+      total[st] = pack_offsets(g, h.cap, bk, c, c + g.nslots, off[st]);
+      pos += cb + 6 * ctx->rs * (size_t)total[st];
+      if (bytes < pos) return fail(ctx, PIC_EINVAL, "snapshot truncated");
+    }
+  }
   CK(cudaSetDevice(ctx->cfg.device));
   CK(cudaStreamSynchronize(ctx->stream));
   if (h.cap != ctx->cap) {  // a context without particle storage takes the snapshot's
@@ -1973,7 +2056,7 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   ctx->cap = h.cap;
   if (h.wmax != ctx->wmax) free_graphs(ctx);  // the current scales are baked into the graphs
   ctx->wmax = h.wmax;
-  ctx->bk = bucket_layout(h.cap);
+  ctx->bk = bk;
   const char *p = (const char *)host + sizeof h;
   auto h2d = [&](void *dst, size_t n) -> cudaError_t {
     cudaError_t e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);
@@ -1982,21 +2065,51 @@ pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes) {
   };
   CK(h2d(ctx->F, field_bytes(g, ctx->rs)));
   CK(h2d(ctx->rho_bg, sizeof(double) * g.cs));
+  DevState ds;
+  memcpy(&ds, p, sizeof ds);
+  p += sizeof ds;
+  ds.err = 0;
+  CK(cudaMemcpy(ctx->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
   if (h.cap) {
-    for (int st = 0; st < 2; ++st) {
-      for (int a = 0; a < 6; ++a) CK(h2d(ctx->seg[st][a], ctx->rs * (size_t)g.nslots * ctx->cap));
-      for (int a = 0; a < 6; ++a) CK(h2d(ctx->bkt[st][a], ctx->rs * (size_t)g.nslots * ctx->bk.stride));
-      CK(h2d(ctx->cnt[st], sizeof(int) * g.nslots));
-      CK(h2d(ctx->bcnt[st], sizeof(int) * g.nslots * 8));
+    void *flat = nullptr;
+    const long long most = std::max(total[0], total[1]);
+    if (most > 0) CK(cmalloc(ctx, &flat, 6 * ctx->rs * (size_t)most));
+    pic_status rs = PIC_OK;
+    for (int st = 0; st < 2 && rs == PIC_OK; ++st) {
+      const char *c = sets[st];
+      cudaError_t e = cudaMemcpy(ctx->cnt[st], c, sizeof(int) * g.nslots, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->bcnt[st], c + sizeof(int) * g.nslots, sizeof(int) * g.nslots * 8,
+                       cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && total[st] > 0) {
+        e = cudaMemcpy(flat, c + sizeof(int) * (size_t)g.nslots * 9,
+                       6 * ctx->rs * (size_t)total[st], cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = cudaMemcpy(ctx->offsets, off[st].data(), sizeof(long long) * off[st].size(),
+                         cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = ctx->fp32 ? launch_unpack<float>(g, (const float *)flat, total[st], ctx->offsets,
+                                               soa<float>(ctx->seg[st]), ctx->cnt[st], ctx->cap,
+                                               soa<float>(ctx->bkt[st]), ctx->bcnt[st], ctx->bk,
+                                               ctx->stream)
+                        : launch_unpack<double>(g, (const double *)flat, total[st], ctx->offsets,
+                                                soa<double>(ctx->seg[st]), ctx->cnt[st], ctx->cap,
+                                                soa<double>(ctx->bkt[st]), ctx->bcnt[st], ctx->bk,
+                                                ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        ctx->launches += 1;
+      }
+      if (e != cudaSuccess) rs = fail(ctx, PIC_ECUDA, std::string("restore: ") + cudaGetErrorString(e));
     }
+    if (flat) {
+      cudaStreamSynchronize(ctx->stream);
+      cfree(ctx, flat);
+    }
+    if (rs) return rs;
     const int q = (int)(h.step & 1);
     CK(cudaMemcpy(ctx->cnt_prev, ctx->cnt[1 - q], sizeof(int) * g.nslots, cudaMemcpyDeviceToDevice));
     CK(cudaMemcpy(ctx->bcnt_prev, ctx->bcnt[q], sizeof(int) * g.nslots * 8, cudaMemcpyDeviceToDevice));
   }
-  DevState ds;
-  memcpy(&ds, p, sizeof ds);
-  ds.err = 0;
-  CK(cudaMemcpy(ctx->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
   ctx->step = h.step;
   ctx->t = h.t;
   ctx->nshift = h.nshift;

@@ -4,6 +4,7 @@
 // (migration of in-flight particles, removal of the leaving column and
 // injection of plasma in the new one).
 #include "common.cuh"
+#include "pack.h"
 
 namespace pic {
 
@@ -584,6 +585,67 @@ cudaError_t launch_fill_plasma(const Geom &g, int col0, int nshift, SoA<R> seg, 
       g, col0, 0, nshift, seg, cnt, cap, n0, x0, ramp, ppcx, ppcy, rho_bg, err);
   return cudaGetLastError();
 }
+
+// Snapshot packing (pack.h): block per slot, grid-stride over the slots.
+template <typename R, bool PACK>
+__global__ void k_pack(const Geom g, SoA<R> seg, const int *cnt, int cap, SoA<R> bkt,
+                       const int *bcnt, Buckets bk, const long long *off, R *flat,
+                       long long total) {
+  R *fa[6] = {flat, flat + total, flat + 2 * total, flat + 3 * total, flat + 4 * total,
+              flat + 5 * total};
+  R *sa[6] = {seg.x, seg.y, seg.ux, seg.uy, seg.uz, seg.w};
+  R *ba[6] = {bkt.x, bkt.y, bkt.ux, bkt.uy, bkt.uz, bkt.w};
+  for (int slot = blockIdx.x; slot < g.nslots; slot += gridDim.x) {
+    const int n = min(cnt[slot], cap);
+    const long long so = (long long)slot * cap, fo = off[9LL * slot];
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        if (PACK) fa[a][fo + k] = sa[a][so + k];
+        else sa[a][so + k] = fa[a][fo + k];
+      }
+    for (int d = 0; d < 8; ++d) {
+      const int nb = min(bcnt[(long long)slot * 8 + d], bk.cap[d]);
+      const long long bo = (long long)slot * bk.stride + bk.off[d], fb = off[9LL * slot + 1 + d];
+      for (int k = threadIdx.x; k < nb; k += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          if (PACK) fa[a][fb + k] = ba[a][bo + k];
+          else ba[a][bo + k] = fa[a][fb + k];
+        }
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_pack(const Geom &g, SoA<R> seg, const int *cnt, int cap, SoA<R> bkt,
+                        const int *bcnt, Buckets bk, const long long *off, R *dst,
+                        long long total, cudaStream_t s) {
+  const int blocks = g.nslots < 65535 ? g.nslots : 65535;
+  k_pack<R, true><<<blocks, 256, 0, s>>>(g, seg, cnt, cap, bkt, bcnt, bk, off, dst, total);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t launch_unpack(const Geom &g, const R *src, long long total, const long long *off,
+                          SoA<R> seg, const int *cnt, int cap, SoA<R> bkt, const int *bcnt,
+                          Buckets bk, cudaStream_t s) {
+  const int blocks = g.nslots < 65535 ? g.nslots : 65535;
+  k_pack<R, false><<<blocks, 256, 0, s>>>(g, seg, cnt, cap, bkt, bcnt, bk, off,
+                                          const_cast<R *>(src), total);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pack<float>(const Geom &, SoA<float>, const int *, int, SoA<float>,
+                                        const int *, Buckets, const long long *, float *,
+                                        long long, cudaStream_t);
+template cudaError_t launch_pack<double>(const Geom &, SoA<double>, const int *, int, SoA<double>,
+                                         const int *, Buckets, const long long *, double *,
+                                         long long, cudaStream_t);
+template cudaError_t launch_unpack<float>(const Geom &, const float *, long long,
+                                          const long long *, SoA<float>, const int *, int,
+                                          SoA<float>, const int *, Buckets, cudaStream_t);
+template cudaError_t launch_unpack<double>(const Geom &, const double *, long long,
+                                           const long long *, SoA<double>, const int *, int,
+                                           SoA<double>, const int *, Buckets, cudaStream_t);
 
 #define PIC_INST(R)                                                                           \
   template cudaError_t launch_sort_cells<R>(const Geom &, int, SoA<R>, int *, SoA<R>, int *,   \
