@@ -333,13 +333,18 @@ pic_status pic_diag(pic_ctx *ctx, pic_diag_t *out);
 pic_status pic_sync(pic_ctx *ctx);
 
 /* Checkpoint: with host == NULL, *bytes receives the size needed; otherwise
- * the whole state is written to host (size *bytes).
+ * the whole state is written to host (size *bytes).  A 2D snapshot holds
+ * fields, background charge, device scalars and the live particles of both
+ * particle sets (packed, without the capacity slack), so its size follows
+ * the particle count; the size query synchronises the context's stream.
  * (Fault recovery of this library; the paper has no counterpart.) */
 pic_status pic_snapshot(pic_ctx *ctx, void *host, size_t *bytes);
 /* Restore a snapshot taken from a context with the same configuration; also
  * clears a sticky device fault.  A context with particle storage takes only
  * a snapshot of its own capacity; one without (never loaded) allocates it.
- * 2D and 3D snapshots are distinct formats (PIC_EINVAL across them). */
+ * The snapshot's size and counts are checked before the context changes
+ * (PIC_EINVAL).  2D and 3D snapshots are distinct formats (PIC_EINVAL
+ * across them). */
 pic_status pic_restore(pic_ctx *ctx, const void *host, size_t bytes);
 
 /* Device bytes a context with this configuration and at most np_max
