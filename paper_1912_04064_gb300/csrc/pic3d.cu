@@ -1351,6 +1351,40 @@ __global__ void k3_repack(int nslots, SoA7<R> src, const int *cnt_src, int cap_s
   }
 }
 
+// Snapshot packing of one particle set: the live particles of every slot's
+// segment and 26 buckets to or from seven contiguous arrays (x y z ux uy uz
+// w), each `total` long; off[27 s] is slot s's segment offset, off[27 s + 1
+// + d] its bucket d's (counts clamped to the capacities).
+template <typename R, bool PACK>
+__global__ void k3_pack(int nslots, SoA7<R> seg, const int *cnt, int cap, SoA7<R> bkt,
+                        const int *bcnt, Buckets26 bk, const long long *off, R *flat,
+                        long long total) {
+  R *fa[7], *sa[7] = {seg.x, seg.y, seg.z, seg.ux, seg.uy, seg.uz, seg.w};
+  R *ba[7] = {bkt.x, bkt.y, bkt.z, bkt.ux, bkt.uy, bkt.uz, bkt.w};
+#pragma unroll
+  for (int a = 0; a < 7; ++a) fa[a] = flat + a * total;
+  for (int slot = blockIdx.x; slot < nslots; slot += gridDim.x) {
+    const int n = min(cnt[slot], cap);
+    const long long so = (long long)slot * cap, fo = off[27LL * slot];
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+#pragma unroll
+      for (int a = 0; a < 7; ++a) {
+        if (PACK) fa[a][fo + k] = sa[a][so + k];
+        else sa[a][so + k] = fa[a][fo + k];
+      }
+    for (int d = 0; d < NB3; ++d) {
+      const int nb = min(bcnt[(long long)slot * NB3 + d], bk.cap[d]);
+      const long long bo = (long long)slot * bk.stride + bk.off[d], fb = off[27LL * slot + 1 + d];
+      for (int k = threadIdx.x; k < nb; k += blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) {
+          if (PACK) fa[a][fb + k] = ba[a][bo + k];
+          else ba[a][bo + k] = fa[a][fb + k];
+        }
+    }
+  }
+}
+
 }  // namespace
 
 // ================================================================ host ====
@@ -2353,10 +2387,36 @@ struct Snap3Header {
   double wmax;
 };
 
-size_t snapshot_bytes3(const Ctx3 *c) {
-  const Geom3 &g = c->g;
-  return sizeof(Snap3Header) + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
-         sizeof(DevState) + (c->cap ? particle_bytes3(g, c->cap, c->rs) : 0);
+// Offsets of one set's packed arrays from its counts (nslots segment counts
+// then 26 nslots bucket counts); returns the total.
+long long pack_offsets3(const Geom3 &g, int cap, const Buckets26 &bk, const int *cnt,
+                        const int *bcnt, std::vector<long long> &off) {
+  off.assign((size_t)g.nslots * 27 + 1, 0);
+  long long o = 0;
+  for (int s = 0; s < g.nslots; ++s) {
+    off[27 * (size_t)s] = o;
+    o += std::min(std::max(cnt[s], 0), cap);
+    for (int d = 0; d < NB3; ++d) {
+      off[27 * (size_t)s + 1 + d] = o;
+      o += std::min(std::max(bcnt[(size_t)s * NB3 + d], 0), bk.cap[d]);
+    }
+  }
+  off.back() = o;
+  return o;
+}
+
+template <typename R>
+cudaError_t launch_pack3(const Ctx3 *c, int st, bool pack, void *flat, long long total) {
+  const int blocks = std::min(c->g.nslots, 65535);
+  if (pack)
+    k3_pack<R, true><<<blocks, 256, 0, c->stream>>>(c->g.nslots, soa7<R>(c->seg[st]), c->cnt[st],
+                                                    c->cap, soa7<R>(c->bkt[st]), c->bcnt[st],
+                                                    c->bk, c->offsets, (R *)flat, total);
+  else
+    k3_pack<R, false><<<blocks, 256, 0, c->stream>>>(c->g.nslots, soa7<R>(c->seg[st]), c->cnt[st],
+                                                     c->cap, soa7<R>(c->bkt[st]), c->bcnt[st],
+                                                     c->bk, c->offsets, (R *)flat, total);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -2596,18 +2656,38 @@ pic_status c3_sync(Ctx3 *c) {
   return poll3(c);
 }
 
+// Snapshot layout (3D): Snap3Header, the 15 field components, the
+// background charge, the device scalars, then for each particle set st = 0,
+// 1 (segments seg[st] with buckets bkt[st], counts cnt[st], bcnt[st]): its
+// 27 nslots counts and its live particles packed into seven arrays, slot by
+// slot (capacity slack not stored).
 pic_status c3_snapshot(Ctx3 *c, void *host, size_t *bytes) {
-  const size_t need = snapshot_bytes3(c);
+  CK3(cudaStreamSynchronize(c->stream));
+  const Geom3 &g = c->g;
+  std::vector<int> counts[2];
+  std::vector<long long> off[2];
+  long long total[2] = {0, 0};
+  size_t need = sizeof(Snap3Header) + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
+                sizeof(DevState);
+  if (c->cap) {
+    for (int st = 0; st < 2; ++st) {
+      counts[st].resize((size_t)g.nslots * 27);
+      CK3(cudaMemcpy(counts[st].data(), c->cnt[st], sizeof(int) * g.nslots, cudaMemcpyDeviceToHost));
+      CK3(cudaMemcpy(counts[st].data() + g.nslots, c->bcnt[st], sizeof(int) * (size_t)g.nslots * NB3,
+                     cudaMemcpyDeviceToHost));
+      total[st] = pack_offsets3(g, c->cap, c->bk, counts[st].data(), counts[st].data() + g.nslots,
+                                off[st]);
+      need += sizeof(int) * (size_t)g.nslots * 27 + 7 * c->rs * (size_t)total[st];
+    }
+  }
   if (!host) {
     *bytes = need;
     return PIC_OK;
   }
   if (*bytes < need) return fail3(c, PIC_EINVAL, "snapshot buffer too small");
-  CK3(cudaStreamSynchronize(c->stream));
-  const Geom3 &g = c->g;
   char *p = (char *)host;
   Snap3Header h{};
-  memcpy(h.magic, "PICSNAP3", 8);
+  memcpy(h.magic, "PICSNAP5", 8);
   for (int a = 0; a < 3; ++a) {
     h.n[a] = g.n[a];
     h.p[a] = g.p[a];
@@ -2623,18 +2703,31 @@ pic_status c3_snapshot(Ctx3 *c, void *host, size_t *bytes) {
   };
   CK3(d2h(c->F, (size_t)NCOMP * g.cs * c->rs));
   CK3(d2h(c->rho_bg, sizeof(double) * g.cs));
-  if (c->cap) {
-    // both sets: the current one (segments q, buckets 1 - q) and the
-    // previous state's (segments 1 - q, buckets q), whose counts the next
-    // step's plan clears
-    for (int st = 0; st < 2; ++st) {
-      for (int a = 0; a < 7; ++a) CK3(d2h(c->seg[st][a], c->rs * (size_t)g.nslots * c->cap));
-      for (int a = 0; a < 7; ++a) CK3(d2h(c->bkt[st][a], c->rs * (size_t)g.nslots * c->bk.stride));
-      CK3(d2h(c->cnt[st], sizeof(int) * g.nslots));
-      CK3(d2h(c->bcnt[st], sizeof(int) * (size_t)g.nslots * NB3));
-    }
-  }
   CK3(d2h(c->st, sizeof(DevState)));
+  if (c->cap) {
+    void *flat = nullptr;
+    const long long most = std::max(total[0], total[1]);
+    if (most > 0) CK3(cmalloc3(c, &flat, 7 * c->rs * (size_t)most));
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 2 && e == cudaSuccess; ++st) {
+      memcpy(p, counts[st].data(), sizeof(int) * counts[st].size());
+      p += sizeof(int) * counts[st].size();
+      if (total[st] == 0) continue;
+      e = cudaMemcpy(c->offsets, off[st].data(), sizeof(long long) * off[st].size(),
+                     cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = c->fp32 ? launch_pack3<float>(c, st, true, flat, total[st])
+                    : launch_pack3<double>(c, st, true, flat, total[st]);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e == cudaSuccess) e = d2h(flat, 7 * c->rs * (size_t)total[st]);
+      c->launches += 1;
+    }
+    if (flat) {
+      cudaStreamSynchronize(c->stream);
+      cfree3(c, flat);
+    }
+    if (e != cudaSuccess) return fail3(c, PIC_ECUDA, std::string("snapshot: ") + cudaGetErrorString(e));
+  }
   *bytes = need;
   return PIC_OK;
 }
@@ -2644,15 +2737,37 @@ pic_status c3_restore(Ctx3 *c, const void *host, size_t bytes) {
   if (bytes < sizeof h) return fail3(c, PIC_EINVAL, "snapshot too small");
   memcpy(&h, host, sizeof h);
   const Geom3 &g = c->g;
-  bool same = !memcmp(h.magic, "PICSNAP3", 8) && h.fp32 == (int)c->fp32;
+  bool same = !memcmp(h.magic, "PICSNAP5", 8) && h.fp32 == (int)c->fp32;
   for (int a = 0; a < 3; ++a) same = same && h.n[a] == g.n[a] && h.p[a] == g.p[a];
   if (!same) return fail3(c, PIC_EINVAL, "snapshot does not match this configuration");
   if (h.cap < 0 || (h.cap % 32)) return fail3(c, PIC_EINVAL, "snapshot capacity is invalid");
   if (h.cap != c->cap && c->cap)
     return fail3(c, PIC_EINVAL, "snapshot capacity differs from this context's");
-  const size_t need = sizeof(Snap3Header) + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
-                      sizeof(DevState) + (h.cap ? particle_bytes3(g, h.cap, c->rs) : 0);
-  if (bytes < need) return fail3(c, PIC_EINVAL, "snapshot truncated");
+  // walk the layout on the host first: sizes and counts are checked before
+  // anything of the context changes
+  const size_t head = sizeof h + (size_t)NCOMP * g.cs * c->rs + sizeof(double) * g.cs +
+                      sizeof(DevState);
+  if (bytes < head) return fail3(c, PIC_EINVAL, "snapshot truncated");
+  const Buckets26 bk = layout26(h.cap);
+  const char *sets[2] = {nullptr, nullptr};
+  std::vector<long long> off[2];
+  long long total[2] = {0, 0};
+  size_t pos = head;
+  if (h.cap) {
+    for (int st = 0; st < 2; ++st) {
+      const size_t cb = sizeof(int) * (size_t)g.nslots * 27;
+      if (bytes < pos + cb) return fail3(c, PIC_EINVAL, "snapshot truncated");
+      sets[st] = (const char *)host + pos;
+      const int *cn = reinterpret_cast<const int *>(sets[st]);
+      for (size_t k = 0; k < (size_t)g.nslots * 27; ++k) {
+        const int lim = k < (size_t)g.nslots ? h.cap : bk.cap[(k - g.nslots) % NB3];
+        if (cn[k] < 0 || cn[k] > lim) return fail3(c, PIC_EINVAL, "snapshot counts are invalid");
+      }
+      total[st] = pack_offsets3(g, h.cap, bk, cn, cn + g.nslots, off[st]);
+      pos += cb + 7 * c->rs * (size_t)total[st];
+      if (bytes < pos) return fail3(c, PIC_EINVAL, "snapshot truncated");
+    }
+  }
   CK3(cudaStreamSynchronize(c->stream));
   if (h.cap != c->cap) {  // a context without particle storage takes the snapshot's
     free_graphs3(c);
@@ -2671,18 +2786,40 @@ pic_status c3_restore(Ctx3 *c, const void *host, size_t bytes) {
   };
   CK3(h2d(c->F, (size_t)NCOMP * g.cs * c->rs));
   CK3(h2d(c->rho_bg, sizeof(double) * g.cs));
-  if (h.cap) {
-    for (int st = 0; st < 2; ++st) {
-      for (int a = 0; a < 7; ++a) CK3(h2d(c->seg[st][a], c->rs * (size_t)g.nslots * c->cap));
-      for (int a = 0; a < 7; ++a) CK3(h2d(c->bkt[st][a], c->rs * (size_t)g.nslots * c->bk.stride));
-      CK3(h2d(c->cnt[st], sizeof(int) * g.nslots));
-      CK3(h2d(c->bcnt[st], sizeof(int) * (size_t)g.nslots * NB3));
-    }
-  }
   DevState ds;
   memcpy(&ds, p, sizeof ds);
   ds.err = 0;
   CK3(cudaMemcpy(c->st, &ds, sizeof ds, cudaMemcpyHostToDevice));
+  if (h.cap) {
+    void *flat = nullptr;
+    const long long most = std::max(total[0], total[1]);
+    if (most > 0) CK3(cmalloc3(c, &flat, 7 * c->rs * (size_t)most));
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 2 && e == cudaSuccess; ++st) {
+      const char *cn = sets[st];
+      e = cudaMemcpy(c->cnt[st], cn, sizeof(int) * g.nslots, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(c->bcnt[st], cn + sizeof(int) * g.nslots, sizeof(int) * (size_t)g.nslots * NB3,
+                       cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && total[st] > 0) {
+        e = cudaMemcpy(flat, cn + sizeof(int) * (size_t)g.nslots * 27, 7 * c->rs * (size_t)total[st],
+                       cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = cudaMemcpy(c->offsets, off[st].data(), sizeof(long long) * off[st].size(),
+                         cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+          e = c->fp32 ? launch_pack3<float>(c, st, false, flat, total[st])
+                      : launch_pack3<double>(c, st, false, flat, total[st]);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        c->launches += 1;
+      }
+    }
+    if (flat) {
+      cudaStreamSynchronize(c->stream);
+      cfree3(c, flat);
+    }
+    if (e != cudaSuccess) return fail3(c, PIC_ECUDA, std::string("restore: ") + cudaGetErrorString(e));
+  }
   c->step = h.step;
   c->t = h.t;
   c->nshift = h.nshift;
