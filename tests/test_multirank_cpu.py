@@ -102,3 +102,24 @@ def test_committed_summaries_name_existing_sources():
             continue
         for f in re.findall(r"`([^`]+)`", m.group(2)):
             assert os.path.exists(os.path.join(ROOT, f)), (p, f)
+
+
+def test_moved_bytes_roofline_excludes_calm_particles():
+    """roofline.moved: the particle step's algorithmic bytes less 11 words
+    for every particle in a skipped calm slot, over the same launch time;
+    with no calm particles it equals the algorithmic roofline."""
+    sys.path.insert(0, ROOT)
+    import bench
+    np_, nc, rs = 4_000_000, 1_000_000, 4
+    _, k_bytes = bench.algorithmic_bytes(np_, nc, rs)
+    assert k_bytes == np_ * 11 * rs + nc * 9 * rs
+    r = {"kernel_bytes": k_bytes, "rs": rs, "np": np_, "particle_step_ms": 0.05,
+         "calm_per_step": 1_000_000}
+    m = bench.moved_bytes(r, 5000.0)
+    assert m["bytes_per_launch"] == k_bytes - 1_000_000 * 11 * rs
+    assert abs(m["calm_share"] - 0.25) < 1e-12
+    assert abs(m["achieved"] - m["bytes_per_launch"] / 0.05e-3 / 1e9) < 1e-6
+    assert abs(m["frac"] - m["achieved"] / 5000.0) < 1e-12
+    r["calm_per_step"] = 0
+    full = bench.moved_bytes(r, 5000.0)
+    assert full["bytes_per_launch"] == k_bytes
